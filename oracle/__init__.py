@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for the demagnetising field and the LLG step.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this package:
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline/reference legs
+of ``bench.py`` may use it.  It shares no code with the CUDA library.
+
+Paper: "Boris Computational Spintronics" (arXiv 2008.02478).
+  * ``boris_oracle.c``  - Newell tensor (Table 1, Ref. [50]), far-field form,
+    direct-sum demag (Table 1) and convolution-theorem demag with 2x zero
+    padding (Section 7), with its own mixed-radix FFT.
+  * ``llg.py``          - effective field (Eq. 1 and Table 1), LLG right-hand
+    side, RK4 / RKF45 steps (Section 2), energies, and the discrete adjoint of
+    an RK4 step.
+  * ``multilayer.py``   - the multi-mesh convolution sum (Eq. 4).
+
+Parity unpinned: the cross-layer tensor for layers of unequal thickness beyond
+its equal-thickness reduction and reciprocity (see ``multilayer.py``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "boris_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+#: far-field switch radius, in units of the largest cell dimension
+RS_DEFAULT = 40.0
+
+
+def build(force: bool = False) -> str:
+    """Compile ``boris_oracle.c`` into ``liboracle.so`` beside it (gcc, -O2, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            d, i, vp = ctypes.c_double, ctypes.c_int, ctypes.c_void_p
+            L.orc_newell_f.restype = d
+            L.orc_newell_f.argtypes = [d, d, d]
+            L.orc_newell_g.restype = d
+            L.orc_newell_g.argtypes = [d, d, d]
+            L.orc_newell_exact.argtypes = [d, d, d, d, d, d, vp]
+            L.orc_newell_asymptotic.argtypes = [d, d, d, d, d, d, vp]
+            L.orc_tensor_table.argtypes = [i, i, i, d, d, d, d, vp]
+            L.orc_demag_direct.argtypes = [i, i, i, vp, vp, vp]
+            L.orc_demag_direct_at.argtypes = [i, i, i, vp, vp, i, vp, vp]
+            L.orc_fft1d.argtypes = [vp, i, i]
+            L.orc_fft3d.argtypes = [vp, i, i, i, i]
+            L.orc_demag_plan.restype = vp
+            L.orc_demag_plan.argtypes = [i, i, i, vp]
+            L.orc_demag_plan_free.argtypes = [vp]
+            L.orc_demag_plan_spectrum.argtypes = [vp, vp]
+            L.orc_demag_plan_dims.argtypes = [vp, vp]
+            L.orc_demag_fft.restype = i
+            L.orc_demag_fft.argtypes = [vp, vp, vp]
+            L.orc_num_threads.restype = i
+            _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+# --------------------------------------------------------------------------
+# Newell tensor
+# --------------------------------------------------------------------------
+def newell_f(x, y, z) -> float:
+    return lib().orc_newell_f(float(x), float(y), float(z))
+
+
+def newell_g(x, y, z) -> float:
+    return lib().orc_newell_g(float(x), float(y), float(z))
+
+
+def newell_exact(X, Y, Z, dx, dy, dz) -> np.ndarray:
+    """Exact cell-averaged tensor (xx, yy, zz, xy, xz, yz) at separation (X,Y,Z)."""
+    out = np.zeros(6)
+    lib().orc_newell_exact(float(X), float(Y), float(Z), float(dx), float(dy), float(dz), _p(out))
+    return out
+
+
+def newell_asymptotic(X, Y, Z, dx, dy, dz) -> np.ndarray:
+    out = np.zeros(6)
+    lib().orc_newell_asymptotic(float(X), float(Y), float(Z), float(dx), float(dy), float(dz), _p(out))
+    return out
+
+
+def tensor_table(nx, ny, nz, dx, dy, dz, rs: float = RS_DEFAULT) -> np.ndarray:
+    """Tensor on the displacement octant, shape [6][nz][ny][nx]."""
+    out = np.zeros((6, nz, ny, nx))
+    lib().orc_tensor_table(nx, ny, nz, float(dx), float(dy), float(dz), float(rs), _p(out))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Demag
+# --------------------------------------------------------------------------
+def demag_direct(M: np.ndarray, T: np.ndarray) -> np.ndarray:
+    """O(N^2) direct sum H = -sum N(r - r0) M(r); M is [3][nz][ny][nx] FP64."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    _, nz, ny, nx = M.shape
+    H = np.zeros_like(M)
+    lib().orc_demag_direct(nx, ny, nz, _p(np.ascontiguousarray(T)), _p(M), _p(H))
+    return H
+
+
+def demag_direct_at(M: np.ndarray, T: np.ndarray, cells) -> np.ndarray:
+    """Direct sum at the flat cell indices ``cells``; returns [len(cells)][3]."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    _, nz, ny, nx = M.shape
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    H = np.zeros((len(cells), 3))
+    lib().orc_demag_direct_at(nx, ny, nz, _p(np.ascontiguousarray(T)), _p(M), len(cells), _p(cells), _p(H))
+    return H
+
+
+class DemagPlan:
+    """Convolution-theorem demag with the padded-tensor spectrum precomputed."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, rs: float = RS_DEFAULT, table: np.ndarray | None = None):
+        self.shape = (nx, ny, nz)
+        self.cell = (dx, dy, dz)
+        self.table = tensor_table(nx, ny, nz, dx, dy, dz, rs) if table is None else np.ascontiguousarray(table)
+        self._h = lib().orc_demag_plan(nx, ny, nz, _p(self.table))
+        if not self._h:
+            raise MemoryError("oracle plan allocation failed")
+
+    def padded_dims(self):
+        d = np.zeros(3, dtype=np.int32)
+        lib().orc_demag_plan_dims(self._h, _p(d))
+        return tuple(int(v) for v in d)
+
+    def spectrum(self) -> np.ndarray:
+        """Complex kernel spectrum, shape [6][pz][py][px]."""
+        px, py, pz = self.padded_dims()
+        out = np.zeros((6, pz, py, px), dtype=np.complex128)
+        lib().orc_demag_plan_spectrum(self._h, _p(out))
+        return out
+
+    def apply(self, M: np.ndarray) -> np.ndarray:
+        M = np.ascontiguousarray(M, dtype=np.float64)
+        assert M.shape == (3, self.shape[2], self.shape[1], self.shape[0])
+        H = np.zeros_like(M)
+        if lib().orc_demag_fft(self._h, _p(M), _p(H)) != 0:
+            raise MemoryError("oracle demag allocation failed")
+        return H
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_demag_plan_free(h)
+            self._h = None
+
+
+def fft1d(a: np.ndarray, sign: int = -1) -> np.ndarray:
+    a = np.array(a, dtype=np.complex128)
+    lib().orc_fft1d(_p(a), a.size, int(sign))
+    return a
+
+
+def fft3d(a: np.ndarray, sign: int = -1) -> np.ndarray:
+    """In-place-style 3D transform of a [n2][n1][n0] complex array."""
+    a = np.array(a, dtype=np.complex128, order="C")
+    n2, n1, n0 = a.shape
+    lib().orc_fft3d(_p(a), n0, n1, n2, int(sign))
+    return a
