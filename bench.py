@@ -1,0 +1,356 @@
+"""Benchmark: LLG cell-steps/s (RK4, four demag evaluations per step) and demag
+evals/s on a 512 x 512 x 32 film of 4 nm cells, FP32 (with the FP64 plan timed
+beside it), through the C ABI of libboris.
+
+One step = one RK4 step of the whole mesh: 4 x (x real-to-complex transform,
+fused y-z spectral pass, x complex-to-real transform, fused LLG stage).
+Prints one JSON line on rank 0.  Under torchrun each rank runs its own
+independent replica of the film (the path does not shard): value is the sum
+of all ranks' cell-steps over the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "demag evals/s & LLG cell-steps/s at 512x512x32 FP32 vs FP64; % HBM roofline"
+UNIT = "cell-steps/s"
+N_MESH = (512, 512, 32)
+CELL = (4e-9, 4e-9, 4e-9)
+MS, A_EX, ALPHA, DT = 8e5, 1.3e-11, 0.02, 1e-13
+MU0 = 4e-7 * math.pi
+HEXT = (0.0, 0.0, 0.1 / MU0)  # 100 mT perpendicular applied field
+GRAIN = 40e-9
+SEED = 3
+WORKLOAD = "512x512x32 film, 4 nm cubic cells, 2621 columnar Voronoi grains (40 nm), RK4 dt=1e-13 s"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1])]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(num(r[2]) or 0 for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def film_state():
+    from paper_2008_02478_gb300 import inputs
+    return inputs.voronoi_columnar(*N_MESH, CELL, GRAIN, SEED)
+
+
+def yz_algorithmic_bytes(plan) -> int:
+    """Compulsory bytes of one fused y-z launch: read and write every kx plane of
+    the spectrum ([kx][3][nz][ny] complex) and read the kernel-spectrum octant
+    (6 reals per (kx, ky', kz'))."""
+    nx, ny, nz = plan.shape
+    px, py, pz = plan.padded()
+    es = 8 if plan.fp64 else 4
+    nkx, kyh, kzh = px // 2 + 1, py // 2 + 1, pz // 2 + 1
+    return nkx * (2 * 3 * nz * ny * 2 * es + kyh * kzh * 6 * es)
+
+
+def xpass_algorithmic_bytes(plan) -> int:
+    """x transform: read (or write) the real field, write (or read) the spectrum."""
+    nx, ny, nz = plan.shape
+    px = plan.padded()[0]
+    es = 8 if plan.fp64 else 4
+    return 3 * nx * ny * nz * es + (px // 2 + 1) * 3 * nz * ny * 2 * es
+
+
+def llg_algorithmic_bytes(plan) -> float:
+    """Average bytes per RK4 stage launch (no per-cell maps): 48, 72, 72, 60
+    bytes per cell for the four stages in FP32 (m_s, Hd, m0, acc, next state)."""
+    nx, ny, nz = plan.shape
+    es = 8 if plan.fp64 else 4
+    return (48 + 72 + 72 + 60) / 4.0 * (es / 4) * nx * ny * nz
+
+
+def time_steps(torch, plan, m, prm, K):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(K):
+        plan.llg_step(m, prm, DT)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def time_demag(torch, plan, M, H, K):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(K):
+        plan.apply(M, H)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def oracle_rk4_rate(nx, ny, nz, steps):
+    """FP64 oracle: cell-steps/s of RK4 on an nx x ny x nz block of the same film."""
+    import numpy as np
+
+    import oracle
+    from oracle import llg
+    from paper_2008_02478_gb300 import inputs
+    m = inputs.voronoi_columnar(nx, ny, nz, CELL, GRAIN, SEED)
+    prm = llg.Params(cell=CELL, Ms=MS, A=A_EX, alpha=ALPHA, Hext=HEXT)
+    dem = oracle.DemagPlan(nx, ny, nz, *CELL)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        m = llg.rk4_step(m, DT, prm, dem.apply)
+    t = time.perf_counter() - t0
+    return nx * ny * nz * steps / t, t, oracle.num_threads()
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    blk = (128, 128, 32)
+    oracle_rk4_rate(32, 32, 32, 1)  # warm the library
+    rates, times = [], []
+    for _ in range(args.warmup):
+        oracle_rk4_rate(*blk, 1)
+    for _ in range(args.steps):
+        r, t, cores = oracle_rk4_rate(*blk, 1)
+        rates.append(r)
+        times.append(t)
+    value = sum(blk[0] * blk[1] * blk[2] for _ in times) / sum(times)
+    sample = "one RK4 step per bench step of the FP64 oracle on a %dx%dx%d block of the same film" % blk
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    if args.warmup < 3:
+        raise SystemExit("need --warmup >= 3")
+
+    import numpy as np
+    import torch
+
+    from paper_2008_02478_gb300 import build as bld
+    from paper_2008_02478_gb300.binding import LLGParams, Plan
+    bld.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    nx, ny, nz = N_MESH
+    ncell = nx * ny * nz
+    m0 = film_state()
+    prm = LLGParams(Ms=MS, A=A_EX, alpha=ALPHA, Hext=HEXT)
+    plan = Plan(nx, ny, nz, *CELL)
+    m = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        plan.llg_step(m, prm, DT)
+    plan.profile_read()  # reset launch counters
+
+    # ---- A: headline timing (K RK4 steps, no per-kernel events) ----------
+    gpu_index = int((os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",") + ["0"])[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    barrier()
+    with ClockSampler(gpu_index) as clk:
+        t_steps = time_steps(torch, plan, m, prm, args.steps)
+    barrier()
+    _, launches = plan.profile_read()
+    t_steps = max_over_ranks(t_steps)
+    clocks = clk.summary()
+    value = world * ncell * args.steps / t_steps
+
+    # ---- demag-only timing ------------------------------------------------
+    M = torch.tensor(MS * m0, dtype=torch.float32, device="cuda")
+    H = torch.empty_like(M)
+    for _ in range(3):
+        plan.apply(M, H)
+    t_dem = max_over_ranks(time_demag(torch, plan, M, H, 4 * args.steps))
+    demag_rate = world * 4 * args.steps / t_dem
+
+    # ---- B: per-kernel CUDA-event durations over K steps -------------------
+    plan.profile(True)
+    time_steps(torch, plan, m, prm, args.steps)
+    kern, _ = plan.profile_read()
+    plan.profile(False)
+    dominant = max(kern, key=lambda k: kern[k][0])
+    per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in kern.items()}
+    algo = {"yz_conv": yz_algorithmic_bytes(plan), "x_r2c": xpass_algorithmic_bytes(plan),
+            "x_c2r": xpass_algorithmic_bytes(plan), "llg_stage": llg_algorithmic_bytes(plan)}
+    peak, peak_kind = measured_peaks()
+    dom_bytes = algo.get(dominant)
+    achieved = dom_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9 if dom_bytes else None
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": dom_bytes}
+    kernels = {k: {"ms_per_launch": per_launch_ms[k], "launches": kern[k][1],
+                   "share": kern[k][0] / max(1e-12, sum(v[0] for v in kern.values())),
+                   "algorithmic_GBps": (algo[k] / (per_launch_ms[k] * 1e-3) / 1e9) if (k in algo and per_launch_ms[k]) else None}
+               for k in kern if kern[k][1]}
+
+    # ---- e2e: pinned host state, H2D + one RK4 step + D2H per step ----------
+    m_host = torch.tensor(m0, dtype=torch.float32).pin_memory()
+    plan.llg_run_host(m_host, prm, DT, 1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.llg_run_host(m_host, prm, DT, 1)
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e_bytes = 3 * ncell * 4
+    e2e = {"value": world * ncell * args.steps / t_e2e, "unit": UNIT, "h2d_bytes_per_step": e2e_bytes,
+           "d2h_bytes_per_step": e2e_bytes}
+
+    # ---- FP64 plan (same kernels templated on double) ----------------------
+    fp64 = None
+    if not args.no_fp64:
+        del H
+        plan64 = Plan(nx, ny, nz, *CELL, fp64=True)
+        m64 = torch.tensor(m0, dtype=torch.float64, device="cuda")
+        k64 = max(3, args.steps // 4)
+        for _ in range(3):
+            plan64.llg_step(m64, prm, DT)
+        t64 = max_over_ranks(time_steps(torch, plan64, m64, prm, k64))
+        M64 = torch.tensor(MS * m0, dtype=torch.float64, device="cuda")
+        H64 = torch.empty_like(M64)
+        plan64.apply(M64, H64)
+        td64 = max_over_ranks(time_demag(torch, plan64, M64, H64, 4 * k64))
+        fp64 = {"cell_steps_per_s": world * ncell * k64 / t64, "demag_evals_per_s": world * 4 * k64 / td64,
+                "steps": k64}
+        plan64.close()
+        del m64, M64, H64
+
+    # ---- CPU baseline: the oracle on a bounded sample -----------------------
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        blk = (128, 128, 32)
+        rate, t, cores = oracle_rk4_rate(*blk, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "one RK4 step (4 FFT demag evaluations) of the FP64 oracle on a %dx%dx%d block of the "
+                         "same film, %.1f s" % (blk + (t,))}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_steps / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "cells": ncell, "parallelism": "replicas" if world > 1 else "1 GPU",
+                           "l2": "inputs larger than L2 (m 100.7 MB, spectrum workspace 201.7 MB, kernel "
+                                 "spectrum 208.4 MB per evaluation)",
+                           "padded": plan.padded()},
+                "demag_evals_per_s": demag_rate, "fp64": fp64, "roofline": roofline, "kernels": kernels,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

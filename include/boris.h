@@ -1,0 +1,180 @@
+/*
+ * boris.h - C ABI of the GB300 finite-difference micromagnetics hot path.
+ *
+ * Method: "Boris Computational Spintronics" (arXiv 2008.02478).
+ *   - Demagnetising field (Table 1, "Demagnetizing Field"; Eq. 4 for one mesh):
+ *       H(r0) = -sum_r N(r - r0) M(r),
+ *     N the cell-averaged Newell tensor (Ref. [50] of the paper), evaluated by
+ *     the convolution theorem on a zero-padded grid (Section 7): forward FFT
+ *     of M, point-by-point multiply with the transformed tensor, inverse FFT.
+ *   - LLG equation (Eq. 1) with exchange, uniaxial anisotropy (Table 1),
+ *     applied and demagnetising fields; RK4 and RKF45 steps (Section 2).
+ *
+ * Conventions for every call:
+ *   - Fields are SoA arrays [3][nz][ny][nx] (x fastest): component c of cell
+ *     (i,j,k) at index c*nx*ny*nz + (k*ny + j)*nx + i.  Scalar maps are
+ *     [nz][ny][nx].  Units: A/m for M and H, J/m^3 for Ku, J/m for A, m, s.
+ *   - Unless a name ends in _host, pointers are DEVICE pointers on the plan's
+ *     device; they must be 16-byte aligned.  The caller owns them; the
+ *     library never frees or retains them after a call returns.
+ *   - All device work is enqueued on the plan's stream (given at plan
+ *     creation; NULL = the legacy default stream) without host
+ *     synchronisation, except where a call says otherwise.
+ *   - Every call returns BORIS_OK (0) or a negative boris_status; the reason
+ *     is available from boris_last_error() on the calling thread.  Device-
+ *     side errors (a bounded wait that gave up, a step-size controller that
+ *     ran out of attempts) are latched in a status word on the device and
+ *     returned by boris_sync_status() and by the next synchronising call.
+ *   - A plan is reusable for any number of calls but is not thread-safe.
+ */
+#ifndef BORIS_H
+#define BORIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct boris_plan_s* boris_plan;
+
+typedef enum {
+    BORIS_OK = 0,
+    BORIS_ERR_INVALID_ARG = -1,      /* bad pointer, size, flag or parameter    */
+    BORIS_ERR_OOM = -2,              /* device or host allocation failed        */
+    BORIS_ERR_CUDA = -3,             /* a CUDA runtime call failed              */
+    BORIS_ERR_UNSUPPORTED_SIZE = -4, /* mesh too large for the available kernels */
+    BORIS_ERR_TIMEOUT = -5,          /* a bounded device-side wait gave up      */
+    BORIS_ERR_STEP_CONTROL = -6      /* RKF45 rejected too many trial steps     */
+} boris_status;
+
+/* Plan flags */
+#define BORIS_FLAG_F32 0x0u        /* FP32 transforms and LLG (default)                */
+#define BORIS_FLAG_F64 0x1u        /* FP64 everywhere: use the *_f64 entry points       */
+
+/* Integration methods (boris_llg_params.method) */
+#define BORIS_RK4 0
+#define BORIS_RKF45 1
+
+/*
+ * boris_demag_plan - prepare H = -N * M for an nx x ny x nz mesh of
+ * dx x dy x dz cells (m).
+ *   Builds on the device, in FP64, the Newell tensor for every displacement
+ *   (exact closed form within 40 cell sizes, the box-averaged dipole expansion
+ *   beyond), transforms its zero-padded extension, and stores the real kernel
+ *   spectrum (one octant, 6 components, FP32 or FP64 per flags).  Allocates
+ *   the transform workspace.  Synchronises the stream before returning.
+ *   flags: BORIS_FLAG_F32 or BORIS_FLAG_F64.  cuda_stream: a cudaStream_t or
+ *   NULL.  On success *out receives the plan (free with boris_plan_destroy).
+ *   Errors: INVALID_ARG (n < 1, cell <= 0, out NULL), UNSUPPORTED_SIZE (a
+ *   padded length above 4096 or a y-z plane too large for shared memory),
+ *   OOM, CUDA.
+ */
+int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, unsigned flags,
+                     void* cuda_stream, boris_plan* out);
+
+/*
+ * boris_demag_apply - Hd = -N * M (Table 1), FP32 plan.
+ *   M, Hd: device [3][nz][ny][nx] float, A/m; may not alias.
+ *   Three kernels: zero-padded x real-to-complex transform, fused y-z pass
+ *   (y and z transforms, kernel multiply, inverse z and y transforms, one
+ *   thread-block cluster per kx plane), x complex-to-real transform.
+ */
+int boris_demag_apply(boris_plan p, const float* M, float* Hd);
+/* FP64 plan variant (same layout, double). */
+int boris_demag_apply_f64(boris_plan p, const double* M, double* Hd);
+
+/*
+ * boris_demag_adjoint - gM = (dHd/dM)^T gHd.  The demagnetising operator is
+ *   self-adjoint (N_ij = N_ji and N(-r) = N(r)), so this is -N * gHd; the
+ *   paper has no adjoint, this call serves gradient computations.
+ */
+int boris_demag_adjoint(boris_plan p, const float* gHd, float* gM);
+
+/* LLG parameters.  Ms/Ku maps: device [nz][ny][nx] arrays of the plan's
+ * precision (float for FP32 plans, double for FP64), or NULL for the uniform
+ * value.  gamma in m/(A s) (Eq. 1: gamma = mu0 g_rel |gamma_e|). */
+typedef struct {
+    const void* Ms_map; /* per-cell saturation magnetisation (A/m) or NULL  */
+    double Ms;          /* uniform Ms when Ms_map is NULL                   */
+    double A;           /* exchange stiffness (J/m)                         */
+    double alpha;       /* Gilbert damping                                  */
+    double gamma;       /* gyromagnetic ratio (m/(A s))                     */
+    const void* Ku_map; /* per-cell uniaxial anisotropy K1 (J/m^3) or NULL  */
+    double Ku;          /* uniform K1 when Ku_map is NULL                   */
+    double easy[3];     /* unit easy axis e_A                               */
+    double Hext[3];     /* applied field (A/m)                              */
+    int method;         /* BORIS_RK4 or BORIS_RKF45                         */
+    double tol;         /* RKF45: accept when max |m5 - m4| <= tol          */
+    double dt_min;      /* RKF45 step bounds (s)                            */
+    double dt_max;
+} boris_llg_params;
+
+/*
+ * boris_llg_step - advance the unit magnetisation m (device [3][nz][ny][nx],
+ *   in place) by one time step of the LLG equation (Eq. 1, Landau-Lifshitz
+ *   form), effective field H = Hd(Ms m) + (2A/(mu0 Ms)) lap m (Neumann)
+ *   + (2Ku/(mu0 Ms))(m.e)e + Hext.
+ *   RK4: four field evaluations (four demag applications), *dt is the step
+ *   and is not changed; m is renormalised after the step.
+ *   RKF45: trial steps with the embedded error max |m5 - m4| until one is
+ *   accepted (at most 16 trials, else BORIS_ERR_STEP_CONTROL); *dt is the
+ *   step to try on input and, on return, the controller's next step
+ *   dt*clip(0.9 (tol/err)^(1/5), 0.2, 2) within [dt_min, dt_max].  RKF45
+ *   synchronises the stream once per trial to read the decision.
+ */
+int boris_llg_step(boris_plan p, float* m, const boris_llg_params* prm, double* dt);
+int boris_llg_step_f64(boris_plan p, double* m, const boris_llg_params* prm, double* dt);
+
+/*
+ * boris_llg_run_host - end-to-end form for callers holding host memory:
+ *   copies m_host (host [3][nz][ny][nx] float; pinned memory is fastest) to
+ *   the device, runs nsteps RK4 steps of size dt, copies the result back to
+ *   m_host, and synchronises.  Allocates its device copy once per plan.
+ */
+int boris_llg_run_host(boris_plan p, float* m_host, const boris_llg_params* prm, double dt,
+                       int nsteps);
+
+/*
+ * boris_energy - FP64 energies of state m: out = {E_demag, E_exchange,
+ *   E_anisotropy, E_Zeeman} in J, with E = sum V [-(mu0 Ms/2) m.(Hd + Hex)
+ *   + Ku (1 - (m.e)^2) - mu0 Ms m.Hext].  Synchronises the stream.
+ */
+int boris_energy(boris_plan p, const float* m, const boris_llg_params* prm, double out[4]);
+
+/* Device status word: BORIS_OK or the first latched device-side error,
+ * which is then cleared.  Synchronises the stream. */
+int boris_sync_status(boris_plan p);
+
+/* Human-readable reason for the last failing call on this thread. */
+const char* boris_last_error(void);
+
+/* Padded transform lengths chosen by the plan: out[0..2] = px, py, pz. */
+int boris_plan_padded(boris_plan p, int out[3]);
+
+/* Bytes of device memory owned by the plan. */
+size_t boris_plan_device_bytes(boris_plan p);
+
+/*
+ * boris_profile_enable - when on != 0, every kernel the plan launches is
+ *   bracketed by two CUDA events recorded on the plan's stream (a few
+ *   microseconds of overhead per launch); off by default.
+ * boris_profile_read - synchronises, then returns per kernel class the summed
+ *   device time in ms and the number of timed launches since the last read:
+ *   [0] x real-to-complex, [1] fused y-z pass, [2] x complex-to-real,
+ *   [3] LLG stage, [4] other (energies).  *total_launches (may be NULL)
+ *   receives every kernel launch counted since the last read, timed or not.
+ *   Resets the counters.
+ */
+int boris_profile_enable(boris_plan p, int on);
+int boris_profile_read(boris_plan p, double ms_out[5], long long launches_out[5], long long* total_launches);
+
+/* Free the plan and everything it owns (NULL is ignored).  Synchronises. */
+void boris_plan_destroy(boris_plan p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BORIS_H */

@@ -1,0 +1,240 @@
+"""Thin Python binding of ``libboris.so`` (C ABI in ``include/boris.h``).
+
+Argument marshalling only: every step of the demag and LLG path runs in the
+CUDA kernels of the library.  Tensors are torch CUDA tensors (device memory
+and streams); the library is loaded from this package's directory and its
+absence is an error, never a fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libboris.so")
+
+BORIS_OK = 0
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "UNSUPPORTED_SIZE", -5: "TIMEOUT",
+          -6: "STEP_CONTROL"}
+FLAG_F32, FLAG_F64 = 0x0, 0x1
+RK4, RKF45 = 0, 1
+
+MU0 = 4e-7 * math.pi
+#: gamma = mu0 g muB / hbar with the electron g-factor (Eq. 1, g_rel = 1), m/(A s)
+GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
+
+#: entry points declared in include/boris.h
+EXPORTS = ["boris_demag_plan", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_adjoint",
+           "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_host", "boris_energy",
+           "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_device_bytes",
+           "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
+KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other"]
+
+
+class BorisError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class LLGParamsC(ctypes.Structure):
+    _fields_ = [("Ms_map", ctypes.c_void_p), ("Ms", ctypes.c_double), ("A", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("gamma", ctypes.c_double), ("Ku_map", ctypes.c_void_p),
+                ("Ku", ctypes.c_double), ("easy", ctypes.c_double * 3), ("Hext", ctypes.c_double * 3),
+                ("method", ctypes.c_int), ("tol", ctypes.c_double), ("dt_min", ctypes.c_double),
+                ("dt_max", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libboris.so; raises if it was not built (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libboris.so is not built: run __graft_entry__.build() (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        i, d, vp, u = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_uint
+        P = ctypes.POINTER
+        L.boris_demag_plan.argtypes = [i, i, i, d, d, d, u, vp, P(vp)]
+        L.boris_demag_apply.argtypes = [vp, vp, vp]
+        L.boris_demag_apply_f64.argtypes = [vp, vp, vp]
+        L.boris_demag_adjoint.argtypes = [vp, vp, vp]
+        L.boris_llg_step.argtypes = [vp, vp, P(LLGParamsC), P(d)]
+        L.boris_llg_step_f64.argtypes = [vp, vp, P(LLGParamsC), P(d)]
+        L.boris_llg_run_host.argtypes = [vp, vp, P(LLGParamsC), d, i]
+        L.boris_energy.argtypes = [vp, vp, P(LLGParamsC), P(d)]
+        L.boris_sync_status.argtypes = [vp]
+        L.boris_last_error.restype = ctypes.c_char_p
+        L.boris_plan_padded.argtypes = [vp, P(i)]
+        L.boris_plan_device_bytes.restype = ctypes.c_size_t
+        L.boris_plan_device_bytes.argtypes = [vp]
+        L.boris_plan_destroy.argtypes = [vp]
+        L.boris_profile_enable.argtypes = [vp, i]
+        L.boris_profile_read.argtypes = [vp, P(d), P(ctypes.c_longlong), P(ctypes.c_longlong)]
+        for name in EXPORTS:
+            if name not in ("boris_last_error", "boris_plan_device_bytes", "boris_plan_destroy"):
+                getattr(L, name).restype = i
+        L.boris_plan_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def check(rc):
+    if rc != BORIS_OK:
+        raise BorisError(rc, lib().boris_last_error().decode())
+    return rc
+
+
+@dataclass
+class LLGParams:
+    Ms: float = 8e5
+    A: float = 1.3e-11
+    alpha: float = 0.02
+    gamma: float = GAMMA
+    Ku: float = 0.0
+    easy: tuple = (0.0, 0.0, 1.0)
+    Hext: tuple = (0.0, 0.0, 0.0)
+    method: int = RK4
+    tol: float = 1e-5
+    dt_min: float = 1e-16
+    dt_max: float = 1e-12
+    Ms_map: object = None  # torch CUDA tensor [nz][ny][nx] or None
+    Ku_map: object = None
+
+    def c(self) -> LLGParamsC:
+        p = LLGParamsC()
+        p.Ms_map = self.Ms_map.data_ptr() if self.Ms_map is not None else None
+        p.Ms = self.Ms
+        p.A = self.A
+        p.alpha = self.alpha
+        p.gamma = self.gamma
+        p.Ku_map = self.Ku_map.data_ptr() if self.Ku_map is not None else None
+        p.Ku = self.Ku
+        p.easy = (ctypes.c_double * 3)(*self.easy)
+        p.Hext = (ctypes.c_double * 3)(*self.Hext)
+        p.method = self.method
+        p.tol = self.tol
+        p.dt_min = self.dt_min
+        p.dt_max = self.dt_max
+        return p
+
+
+def _ptr(t, dtype, shape=None):
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (tuple(shape), tuple(t.shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A demag + LLG plan for an nx x ny x nz mesh of dx x dy x dz cells."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, fp64: bool = False, stream=None):
+        import torch
+        self.shape = (nx, ny, nz)
+        self.cell = (dx, dy, dz)
+        self.fp64 = fp64
+        self.dtype = torch.float64 if fp64 else torch.float32
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        h = ctypes.c_void_p()
+        check(lib().boris_demag_plan(nx, ny, nz, dx, dy, dz, FLAG_F64 if fp64 else FLAG_F32,
+                                     ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def field_shape(self):
+        nx, ny, nz = self.shape
+        return (3, nz, ny, nx)
+
+    def padded(self):
+        out = (ctypes.c_int * 3)()
+        check(lib().boris_plan_padded(self._h, out))
+        return tuple(out)
+
+    def device_bytes(self) -> int:
+        return int(lib().boris_plan_device_bytes(self._h))
+
+    def apply(self, M, out=None):
+        """H = -N * M (device tensors [3][nz][ny][nx])."""
+        import torch
+        if out is None:
+            out = torch.empty(self.field_shape, dtype=self.dtype, device=M.device)
+        fn = lib().boris_demag_apply_f64 if self.fp64 else lib().boris_demag_apply
+        check(fn(self._h, _ptr(M, self.dtype, self.field_shape), _ptr(out, self.dtype, self.field_shape)))
+        return out
+
+    def adjoint(self, gH, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.field_shape, dtype=self.dtype, device=gH.device)
+        if self.fp64:
+            raise NotImplementedError("adjoint is FP32")
+        check(lib().boris_demag_adjoint(self._h, _ptr(gH, self.dtype, self.field_shape),
+                                        _ptr(out, self.dtype, self.field_shape)))
+        return out
+
+    def _params(self, prm: LLGParams):
+        nx, ny, nz = self.shape
+        for mp in (prm.Ms_map, prm.Ku_map):
+            if mp is not None:
+                _ptr(mp, self.dtype, (nz, ny, nx))
+        return prm.c()
+
+    def llg_step(self, m, prm: LLGParams, dt: float) -> float:
+        """Advance m in place by one RK4 step (returns dt) or one accepted RKF45 step
+        (returns the controller's next dt)."""
+        c = self._params(prm)
+        h = ctypes.c_double(dt)
+        fn = lib().boris_llg_step_f64 if self.fp64 else lib().boris_llg_step
+        check(fn(self._h, _ptr(m, self.dtype, self.field_shape), ctypes.byref(c), ctypes.byref(h)))
+        return h.value
+
+    def llg_run_host(self, m_host, prm: LLGParams, dt: float, nsteps: int):
+        """m_host: CPU float32 tensor (pinned for speed), updated in place."""
+        if m_host.is_cuda or m_host.dtype.itemsize != 4 or not m_host.is_contiguous():
+            raise ValueError("expected a contiguous CPU float32 tensor")
+        c = self._params(prm)
+        check(lib().boris_llg_run_host(self._h, ctypes.c_void_p(m_host.data_ptr()), ctypes.byref(c),
+                                       float(dt), int(nsteps)))
+
+    def energy(self, m, prm: LLGParams):
+        c = self._params(prm)
+        out = (ctypes.c_double * 4)()
+        check(lib().boris_energy(self._h, _ptr(m, self.dtype, self.field_shape), ctypes.byref(c), out))
+        return tuple(out)
+
+    def profile(self, on: bool):
+        check(lib().boris_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{kernel class: (ms, timed launches)}, total launches since the last read."""
+        ms = (ctypes.c_double * 5)()
+        cnt = (ctypes.c_longlong * 5)()
+        tot = ctypes.c_longlong()
+        check(lib().boris_profile_read(self._h, ms, cnt, ctypes.byref(tot)))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}, tot.value
+
+    def sync_status(self):
+        return check(lib().boris_sync_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().boris_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

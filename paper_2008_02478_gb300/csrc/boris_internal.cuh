@@ -1,0 +1,78 @@
+// Internal declarations shared by the CUDA translation units of libboris.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/boris.h"
+#include "fft_engine.cuh"
+
+namespace boris {
+
+// Padded transform length along one axis: the smallest power of two that is
+// >= 2n - 1, so the circular convolution of the zero-padded data equals the
+// linear convolution (Section 7 pads by doubling; for n a power of two the two
+// agree, and any length >= 2n - 1 gives the same result).  n = 1 needs none.
+inline int padded_len(int n)
+{
+    if (n <= 1) return 1;
+    int p = 1;
+    while (p < 2 * n - 1) p <<= 1;
+    return p;
+}
+inline int ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) l++;
+    return l;
+}
+
+// Geometry of one demag problem on the device.
+struct Geometry {
+    int nx, ny, nz;       // mesh
+    int px, py, pz;       // padded transform lengths
+    int lgx, lgy, lgz;
+    int nkx;              // px/2 + 1 spectral planes kept by the real transform
+    int kyh, kzh;         // py/2 + 1, pz/2 + 1 (octant extent of the kernel spectrum)
+    int lmax, lglmax;     // twiddle table length
+};
+
+// Launch schedule of the fused y-z spectral pass.
+struct YZSchedule {
+    int C;        // CTAs per cluster (one cluster per kx plane); ky residues mod C
+    int Qc;       // z-columns processed per chunk of the z stage
+    int threads;  // threads per CTA
+    size_t smem;  // dynamic shared memory per CTA (bytes)
+};
+
+// Kernel launchers (demag.cu); T = float or double.
+template <typename T>
+cudaError_t launch_x_r2c(const Geometry& g, const T* M, const T* ms_map, T ms_scale,
+                         typename Cx<T>::t* X, const typename Cx<T>::t* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_yz_conv(const Geometry& g, const YZSchedule& sc, typename Cx<T>::t* X,
+                           const T* K, const typename Cx<T>::t* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_x_c2r(const Geometry& g, const typename Cx<T>::t* X, T* H,
+                         const typename Cx<T>::t* tw, cudaStream_t st);
+template <typename T>
+bool choose_yz_schedule(const Geometry& g, int max_smem, YZSchedule* out);
+template <typename T>
+cudaError_t yz_set_attributes(const YZSchedule& sc);
+
+// Newell tensor precompute (newell.cu): writes the kernel spectrum K in the
+// layout [kx][ky'][kz'][6] (octant, FP32 or FP64), already scaled by
+// -1/(px py pz) so that the inverse transforms yield H = -N * M.
+cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, double dz, double rs,
+                                  void* K_out, bool k_is_f64, const double2* tw64, cudaStream_t st);
+// Exact/asymptotic tensor on the displacement octant, FP64 [6][nz][ny][nx] (for tests).
+cudaError_t newell_octant(int nx, int ny, int nz, double dx, double dy, double dz, double rs,
+                          double* T, cudaStream_t st);
+
+// Twiddle table exp(-2 pi i e / n), e in [0, n), on the host in FP64.
+void host_twiddles(int n, double2* out);
+
+// Thread-local last error message (capi.cu).
+void set_error(const std::string& msg);
+
+}  // namespace boris

@@ -1,0 +1,500 @@
+// C ABI of libboris (declared in include/boris.h): plans, workspaces,
+// status codes and the host-side orchestration of the demag and LLG kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "boris_internal.cuh"
+#include "llg_kernels.cuh"
+
+using namespace boris;
+
+namespace boris {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace boris
+
+struct boris_plan_s {
+    Geometry g;
+    double dx, dy, dz;
+    unsigned flags;
+    bool f64;
+    cudaStream_t stream;
+    int device;
+    YZSchedule yz;
+    // kernel spectrum [kx][ky'][kz'][6] in the plan precision
+    void* K = nullptr;
+    // twiddles exp(-2 pi i e / lmax) in the plan precision and in FP64
+    void* tw = nullptr;
+    double2* tw64 = nullptr;
+    // spectral workspace [kx][c][z][y]
+    void* X = nullptr;
+    // LLG workspace (allocated on first use)
+    void* Hd = nullptr;
+    void* msa = nullptr;
+    void* msb = nullptr;
+    void* acc = nullptr;
+    void* kbuf = nullptr;   // RKF45: 6 stage derivatives
+    void* mtrial = nullptr; // RKF45: trial solution
+    unsigned int* err_bits = nullptr;
+    unsigned int* h_err_bits = nullptr;  // pinned
+    double* energy = nullptr;
+    void* m_dev_e2e = nullptr;
+    size_t bytes = 0;
+    // optional per-kernel CUDA-event timing (boris_profile_enable)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    long long launches = 0;  // kernels launched by the library on this plan
+};
+
+namespace {
+
+#define CUDA_TRY(expr)                                                                             \
+    do {                                                                                           \
+        cudaError_t _e = (expr);                                                                   \
+        if (_e != cudaSuccess) {                                                                   \
+            set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                         \
+            return _e == cudaErrorMemoryAllocation ? BORIS_ERR_OOM : BORIS_ERR_CUDA;               \
+        }                                                                                          \
+    } while (0)
+
+int fail(int code, const std::string& msg)
+{
+    set_error(msg);
+    return code;
+}
+
+int dev_alloc(boris_plan p, void** ptr, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? BORIS_ERR_OOM : BORIS_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    p->bytes += bytes;
+    return BORIS_OK;
+}
+
+bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+size_t ncell(const boris_plan p) { return (size_t)p->g.nx * p->g.ny * p->g.nz; }
+
+cudaEvent_t take_event(boris_plan p)
+{
+    if (p->ev_pool.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        return e;
+    }
+    cudaEvent_t e = p->ev_pool.back();
+    p->ev_pool.pop_back();
+    return e;
+}
+
+// Runs one kernel launcher; with profiling on, brackets it with CUDA events on
+// the plan's stream and files the pair under kernel class `kind`.
+template <typename F>
+cudaError_t timed(boris_plan p, int kind, F&& launch)
+{
+    p->launches++;
+    if (!p->prof) return launch();
+    cudaEvent_t a = take_event(p), b = take_event(p);
+    if (a) cudaEventRecord(a, p->stream);
+    cudaError_t e = launch();
+    if (b) cudaEventRecord(b, p->stream);
+    if (a && b) p->ev_used.push_back({kind, {a, b}});
+    return e;
+}
+
+template <typename T>
+int demag_apply_t(boris_plan p, const T* M, const T* ms_map, T ms_scale, T* H)
+{
+    using C = typename Cx<T>::t;
+    CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<T>(p->g, M, ms_map, ms_scale, (C*)p->X, (const C*)p->tw, p->stream); }));
+    CUDA_TRY(timed(p, 1, [&] { return launch_yz_conv<T>(p->g, p->yz, (C*)p->X, (const T*)p->K, (const C*)p->tw, p->stream); }));
+    CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<T>(p->g, (const C*)p->X, H, (const C*)p->tw, p->stream); }));
+    return BORIS_OK;
+}
+
+template <typename T>
+int check_params(boris_plan p, const boris_llg_params* prm, LLGArgs<T>* a, double dt)
+{
+    if (!prm) return fail(BORIS_ERR_INVALID_ARG, "params is NULL");
+    if (!(prm->A >= 0) || !(prm->alpha >= 0) || !(prm->gamma > 0))
+        return fail(BORIS_ERR_INVALID_ARG, "need A >= 0, alpha >= 0, gamma > 0");
+    if (!prm->Ms_map && !(prm->Ms > 0)) return fail(BORIS_ERR_INVALID_ARG, "need Ms > 0 or an Ms map");
+    if ((prm->Ms_map && !aligned16(prm->Ms_map)) || (prm->Ku_map && !aligned16(prm->Ku_map)))
+        return fail(BORIS_ERR_INVALID_ARG, "maps must be 16-byte aligned");
+    const Geometry& g = p->g;
+    a->nx = g.nx;
+    a->ny = g.ny;
+    a->nz = g.nz;
+    a->ncell = ncell(p);
+    a->ihx2 = (T)(1.0 / (p->dx * p->dx));
+    a->ihy2 = (T)(1.0 / (p->dy * p->dy));
+    a->ihz2 = (T)(1.0 / (p->dz * p->dz));
+    a->Ms = (T)prm->Ms;
+    a->Ku = (T)prm->Ku;
+    a->A = (T)prm->A;
+    a->ms_map = (const T*)prm->Ms_map;
+    a->ku_map = (const T*)prm->Ku_map;
+    for (int c = 0; c < 3; c++) {
+        a->e[c] = (T)prm->easy[c];
+        a->Hext[c] = (T)prm->Hext[c];
+    }
+    a->gp = (T)(prm->gamma / (1.0 + prm->alpha * prm->alpha));
+    a->alpha = (T)prm->alpha;
+    a->dt = (T)dt;
+    a->V = p->dx * p->dy * p->dz;
+    return BORIS_OK;
+}
+
+template <typename T>
+int ensure_llg_workspace(boris_plan p, bool rkf)
+{
+    const size_t vb = 3 * ncell(p) * sizeof(T);
+    int rc;
+    if (!p->Hd && (rc = dev_alloc(p, &p->Hd, vb))) return rc;
+    if (!p->msa && (rc = dev_alloc(p, &p->msa, vb))) return rc;
+    if (!p->msb && (rc = dev_alloc(p, &p->msb, vb))) return rc;
+    if (!p->acc && (rc = dev_alloc(p, &p->acc, vb))) return rc;
+    if (rkf) {
+        if (!p->kbuf && (rc = dev_alloc(p, &p->kbuf, 6 * vb))) return rc;
+        if (!p->mtrial && (rc = dev_alloc(p, &p->mtrial, vb))) return rc;
+        if (!p->err_bits && (rc = dev_alloc(p, (void**)&p->err_bits, 16))) return rc;
+        if (!p->h_err_bits) CUDA_TRY(cudaMallocHost((void**)&p->h_err_bits, 16));
+    }
+    return BORIS_OK;
+}
+
+template <typename T>
+int rk4_step_t(boris_plan p, T* m, const LLGArgs<T>& a)
+{
+    T* ms_map = (T*)a.ms_map;
+    const T ms_scale = a.Ms;
+    T* Hd = (T*)p->Hd;
+    T* acc = (T*)p->acc;
+    T* sa = (T*)p->msa;
+    T* sb = (T*)p->msb;
+    // stage states: m0 -> sa -> sb -> sa
+    const T* in[4] = {m, sa, sb, sa};
+    T* out[4] = {sa, sb, sa, nullptr};
+    for (int s = 0; s < 4; s++) {
+        int rc = demag_apply_t<T>(p, in[s], ms_map, ms_scale, Hd);
+        if (rc) return rc;
+        CUDA_TRY(timed(p, 3, [&] { return launch_rk4_stage<T>(a, s, in[s], Hd, m, acc, out[s], p->stream); }));
+    }
+    return BORIS_OK;
+}
+
+template <typename T>
+int rkf45_step_t(boris_plan p, T* m, const boris_llg_params* prm, double* dt)
+{
+    LLGArgs<T> a;
+    double h = *dt;
+    if (!(h > 0)) return fail(BORIS_ERR_INVALID_ARG, "dt must be > 0");
+    if (!(prm->tol > 0) || !(prm->dt_min > 0) || !(prm->dt_max >= prm->dt_min))
+        return fail(BORIS_ERR_INVALID_ARG, "RKF45 needs tol > 0 and 0 < dt_min <= dt_max");
+    T* ms_map = (T*)prm->Ms_map;
+    T* Hd = (T*)p->Hd;
+    T* sa = (T*)p->msa;
+    T* kb = (T*)p->kbuf;
+    for (int attempt = 0; attempt < 16; attempt++) {
+        int rc = check_params<T>(p, prm, &a, h);
+        if (rc) return rc;
+        CUDA_TRY(cudaMemsetAsync(p->err_bits, 0, sizeof(unsigned int), p->stream));
+        // stage states alternate m -> sa -> sb -> sa -> sb -> sa -> (trial)
+        T* sb = (T*)p->msb;
+        const T* in[6] = {m, sa, sb, sa, sb, sa};
+        T* out[6] = {sa, sb, sa, sb, sa, (T*)p->mtrial};
+        for (int s = 0; s < 6; s++) {
+            rc = demag_apply_t<T>(p, in[s], ms_map, a.Ms, Hd);
+            if (rc) return rc;
+            CUDA_TRY(timed(p, 3, [&] { return launch_rkf45_stage<T>(a, s, in[s], Hd, m, kb, out[s], p->err_bits, p->stream); }));
+        }
+        CUDA_TRY(cudaMemcpyAsync(p->h_err_bits, p->err_bits, sizeof(unsigned int), cudaMemcpyDeviceToHost, p->stream));
+        CUDA_TRY(cudaStreamSynchronize(p->stream));
+        float errf;
+        std::memcpy(&errf, p->h_err_bits, sizeof(float));
+        const double err = errf;
+        const double fac = err == 0.0 ? 2.0 : std::fmin(2.0, std::fmax(0.2, 0.9 * std::pow(prm->tol / err, 0.2)));
+        const double hn = std::fmin(prm->dt_max, std::fmax(prm->dt_min, h * fac));
+        if (err <= prm->tol || h <= prm->dt_min) {
+            CUDA_TRY(cudaMemcpyAsync(m, p->mtrial, 3 * ncell(p) * sizeof(T), cudaMemcpyDeviceToDevice, p->stream));
+            *dt = hn;
+            return BORIS_OK;
+        }
+        h = hn;
+    }
+    return fail(BORIS_ERR_STEP_CONTROL, "RKF45: 16 trial steps rejected");
+}
+
+template <typename T>
+int llg_step_t(boris_plan p, T* m, const boris_llg_params* prm, double* dt)
+{
+    if (!p || !m || !dt) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned16(m)) return fail(BORIS_ERR_INVALID_ARG, "m must be 16-byte aligned");
+    if (!prm) return fail(BORIS_ERR_INVALID_ARG, "params is NULL");
+    int rc = ensure_llg_workspace<T>(p, prm->method == BORIS_RKF45);
+    if (rc) return rc;
+    if (prm->method == BORIS_RK4) {
+        if (!(*dt > 0) || !std::isfinite(*dt)) return fail(BORIS_ERR_INVALID_ARG, "dt must be > 0");
+        LLGArgs<T> a;
+        if ((rc = check_params<T>(p, prm, &a, *dt))) return rc;
+        return rk4_step_t<T>(p, m, a);
+    }
+    if (prm->method == BORIS_RKF45) {
+        LLGArgs<T> a;
+        if ((rc = check_params<T>(p, prm, &a, 1.0))) return rc;
+        return rkf45_step_t<T>(p, m, prm, dt);
+    }
+    return fail(BORIS_ERR_INVALID_ARG, "unknown method");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* boris_last_error(void) { return g_last_error.c_str(); }
+
+int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, unsigned flags, void* cuda_stream,
+                     boris_plan* out)
+{
+    if (!out) return fail(BORIS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(BORIS_ERR_INVALID_ARG, "mesh sizes must be >= 1");
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
+        return fail(BORIS_ERR_INVALID_ARG, "cell sizes must be finite and > 0");
+    if (flags & ~BORIS_FLAG_F64) return fail(BORIS_ERR_INVALID_ARG, "unknown flags");
+    Geometry g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.px = padded_len(nx);
+    g.py = padded_len(ny);
+    g.pz = padded_len(nz);
+    if (g.px > 4096 || g.py > 4096 || g.pz > 4096)
+        return fail(BORIS_ERR_UNSUPPORTED_SIZE, "padded transform length above 4096");
+    g.lgx = ilog2(g.px);
+    g.lgy = ilog2(g.py);
+    g.lgz = ilog2(g.pz);
+    g.nkx = g.px / 2 + 1;
+    g.kyh = g.py / 2 + 1;
+    g.kzh = g.pz / 2 + 1;
+    g.lmax = std::max(g.px, std::max(g.py, std::max(g.pz, 32)));
+    g.lglmax = ilog2(g.lmax);
+    if ((size_t)3 * nx * ny * nz > (size_t)1 << 31) return fail(BORIS_ERR_UNSUPPORTED_SIZE, "mesh too large");
+
+    boris_plan p = new (std::nothrow) boris_plan_s();
+    if (!p) return fail(BORIS_ERR_OOM, "host allocation");
+    p->g = g;
+    p->dx = dx;
+    p->dy = dy;
+    p->dz = dz;
+    p->flags = flags;
+    p->f64 = (flags & BORIS_FLAG_F64) != 0;
+    p->stream = (cudaStream_t)cuda_stream;
+    int rc = BORIS_OK;
+    auto bail = [&](int code) {
+        boris_plan_destroy(p);
+        return code;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "no CUDA device"));
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    const bool ok = p->f64 ? choose_yz_schedule<double>(g, max_smem, &p->yz) : choose_yz_schedule<float>(g, max_smem, &p->yz);
+    if (!ok) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));
+    if (const char* s = std::getenv("BORIS_YZ_CLUSTER")) {
+        // schedule override for tuning sweeps (power of two, <= 16 and <= py)
+        const int C = std::atoi(s);
+        if (C >= 1 && C <= 16 && (C & (C - 1)) == 0 && C <= g.py) {
+            YZSchedule t = p->yz;
+            t.C = C;
+            const int L = g.py / C;
+            t.Qc = std::min(L, t.Qc > 0 ? t.Qc : 16);
+            if (const char* q = std::getenv("BORIS_YZ_QC")) t.Qc = std::max(1, std::min(L, std::atoi(q)));
+            const size_t cs = p->f64 ? sizeof(double2) : sizeof(float2);
+            t.smem = 3 * (size_t)g.nz * L * cs + (g.pz > 1 ? 3 * (size_t)g.pz * t.Qc * cs : 0);
+            if (t.smem <= (size_t)max_smem) p->yz = t;
+        }
+    }
+    cudaError_t ce = p->f64 ? yz_set_attributes<double>(p->yz) : yz_set_attributes<float>(p->yz);
+    if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("yz attributes: ") + cudaGetErrorString(ce)));
+
+    // twiddles
+    std::vector<double2> tw(g.lmax);
+    host_twiddles(g.lmax, tw.data());
+    if ((rc = dev_alloc(p, (void**)&p->tw64, g.lmax * sizeof(double2)))) return bail(rc);
+    if (cudaMemcpy(p->tw64, tw.data(), g.lmax * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
+    if (p->f64) {
+        p->tw = p->tw64;
+    } else {
+        std::vector<float2> twf(g.lmax);
+        for (int i = 0; i < g.lmax; i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+        if ((rc = dev_alloc(p, &p->tw, g.lmax * sizeof(float2)))) return bail(rc);
+        if (cudaMemcpy(p->tw, twf.data(), g.lmax * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
+    }
+    // kernel spectrum
+    const size_t kelems = (size_t)g.nkx * g.kyh * g.kzh * 6;
+    const size_t esz = p->f64 ? sizeof(double) : sizeof(float);
+    if ((rc = dev_alloc(p, &p->K, kelems * esz))) return bail(rc);
+    const double rs = 40.0;
+    ce = build_kernel_spectrum(g, dx, dy, dz, rs, p->K, p->f64, p->tw64, p->stream);
+    if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("kernel spectrum: ") + cudaGetErrorString(ce)));
+    // spectral workspace
+    const size_t xelems = (size_t)g.nkx * 3 * g.nz * g.ny;
+    if ((rc = dev_alloc(p, &p->X, xelems * 2 * esz))) return bail(rc);
+    if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
+        return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
+    *out = p;
+    return BORIS_OK;
+}
+
+int boris_demag_apply(boris_plan p, const float* M, float* Hd)
+{
+    if (!p || !M || !Hd) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan: use boris_demag_apply_f64");
+    if (!aligned16(M) || !aligned16(Hd)) return fail(BORIS_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
+    if ((const void*)M == (const void*)Hd) return fail(BORIS_ERR_INVALID_ARG, "M and Hd may not alias");
+    return demag_apply_t<float>(p, M, nullptr, 1.0f, Hd);
+}
+
+int boris_demag_apply_f64(boris_plan p, const double* M, double* Hd)
+{
+    if (!p || !M || !Hd) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (!p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP32 plan: use boris_demag_apply");
+    if (!aligned16(M) || !aligned16(Hd)) return fail(BORIS_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
+    if ((const void*)M == (const void*)Hd) return fail(BORIS_ERR_INVALID_ARG, "M and Hd may not alias");
+    return demag_apply_t<double>(p, M, nullptr, 1.0, Hd);
+}
+
+int boris_demag_adjoint(boris_plan p, const float* gHd, float* gM)
+{
+    // the operator M -> -N * M is symmetric: its adjoint is itself
+    return boris_demag_apply(p, gHd, gM);
+}
+
+int boris_llg_step(boris_plan p, float* m, const boris_llg_params* prm, double* dt)
+{
+    if (p && p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan: use boris_llg_step_f64");
+    return llg_step_t<float>(p, m, prm, dt);
+}
+
+int boris_llg_step_f64(boris_plan p, double* m, const boris_llg_params* prm, double* dt)
+{
+    if (p && !p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP32 plan: use boris_llg_step");
+    return llg_step_t<double>(p, m, prm, dt);
+}
+
+int boris_llg_run_host(boris_plan p, float* m_host, const boris_llg_params* prm, double dt, int nsteps)
+{
+    if (!p || !m_host || !prm) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan");
+    if (nsteps < 0 || prm->method != BORIS_RK4) return fail(BORIS_ERR_INVALID_ARG, "RK4 with nsteps >= 0 only");
+    const size_t vb = 3 * ncell(p) * sizeof(float);
+    int rc;
+    if (!p->m_dev_e2e && (rc = dev_alloc(p, &p->m_dev_e2e, vb))) return rc;
+    CUDA_TRY(cudaMemcpyAsync(p->m_dev_e2e, m_host, vb, cudaMemcpyHostToDevice, p->stream));
+    for (int i = 0; i < nsteps; i++) {
+        double h = dt;
+        if ((rc = boris_llg_step(p, (float*)p->m_dev_e2e, prm, &h))) return rc;
+    }
+    CUDA_TRY(cudaMemcpyAsync(m_host, p->m_dev_e2e, vb, cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return BORIS_OK;
+}
+
+int boris_energy(boris_plan p, const float* m, const boris_llg_params* prm, double out[4])
+{
+    if (!p || !m || !prm || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan");
+    int rc = ensure_llg_workspace<float>(p, false);
+    if (rc) return rc;
+    LLGArgs<float> a;
+    if ((rc = check_params<float>(p, prm, &a, 0.0))) return rc;
+    if (!p->energy && (rc = dev_alloc(p, (void**)&p->energy, 4 * sizeof(double)))) return rc;
+    if ((rc = demag_apply_t<float>(p, m, (const float*)prm->Ms_map, (float)prm->Ms, (float*)p->Hd))) return rc;
+    CUDA_TRY(cudaMemsetAsync(p->energy, 0, 4 * sizeof(double), p->stream));
+    CUDA_TRY(timed(p, 4, [&] { return launch_energy<float>(a, m, (const float*)p->Hd, p->energy, p->stream); }));
+    CUDA_TRY(cudaMemcpyAsync(out, p->energy, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    return BORIS_OK;
+}
+
+int boris_sync_status(boris_plan p)
+{
+    if (!p) return fail(BORIS_ERR_INVALID_ARG, "NULL plan");
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return fail(BORIS_ERR_CUDA, cudaGetErrorString(e));
+    return BORIS_OK;
+}
+
+int boris_plan_padded(boris_plan p, int out[3])
+{
+    if (!p || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    out[0] = p->g.px;
+    out[1] = p->g.py;
+    out[2] = p->g.pz;
+    return BORIS_OK;
+}
+
+size_t boris_plan_device_bytes(boris_plan p) { return p ? p->bytes : 0; }
+
+int boris_profile_enable(boris_plan p, int on)
+{
+    if (!p) return fail(BORIS_ERR_INVALID_ARG, "NULL plan");
+    p->prof = on != 0;
+    return BORIS_OK;
+}
+
+int boris_profile_read(boris_plan p, double ms_out[5], long long launches_out[5], long long* total_launches)
+{
+    if (!p || !ms_out || !launches_out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    for (int k = 0; k < 5; k++) {
+        ms_out[k] = 0.0;
+        launches_out[k] = 0;
+    }
+    for (auto& u : p->ev_used) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, u.second.first, u.second.second) == cudaSuccess && u.first >= 0 && u.first < 5) {
+            ms_out[u.first] += ms;
+            launches_out[u.first]++;
+        }
+        p->ev_pool.push_back(u.second.first);
+        p->ev_pool.push_back(u.second.second);
+    }
+    p->ev_used.clear();
+    if (total_launches) *total_launches = p->launches;
+    p->launches = 0;
+    return BORIS_OK;
+}
+
+void boris_plan_destroy(boris_plan p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    void* ptrs[] = {p->K, p->X, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
+                    p->m_dev_e2e};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (p->tw && p->tw != (void*)p->tw64) cudaFree(p->tw);
+    if (p->tw64) cudaFree(p->tw64);
+    if (p->h_err_bits) cudaFreeHost(p->h_err_bits);
+    for (auto& u : p->ev_used) {
+        cudaEventDestroy(u.second.first);
+        cudaEventDestroy(u.second.second);
+    }
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// Shared-memory radix-2^K FFT passes for power-of-two lengths.
+//
+// The convolution theorem of Section 7 (forward transforms, point-by-point
+// multiply, inverse transforms) is built here from in-place decimation-in-
+// frequency (DIF) passes, which take natural-order input to bit-reversed output,
+// and decimation-in-time (DIT) passes with conjugated twiddles, which take the
+// bit-reversed spectrum back to natural order.  Because the kernel multiply is
+// point-by-point, the spectrum never needs to be reordered.
+//
+// A pass groups K consecutive radix-2 stages: each thread loads 2^K elements
+// of one line into registers, runs the K butterfly stages there, and writes
+// them back, so a length-L transform costs ceil(log2 L / K) shared-memory
+// round trips.  Twiddles come from a table tw[e] = exp(-2 pi i e / Lmax)
+// computed on the host in FP64; a length-L transform reads it at stride
+// Lmax / L.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace boris {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using t = float2; };
+template <> struct Cx<double> { using t = double2; };
+
+template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C c_mul(C a, C b)
+{
+    return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C c_mulc(C a, C b)
+{
+    return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename C, typename T> __device__ __forceinline__ C c_scale(C a, T s) { return C{a.x * s, a.y * s}; }
+
+__device__ __forceinline__ int bitrev(int v, int lg) { return lg == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - lg)); }
+
+// Geometry of a batch of lines in shared memory: element e of line l lives at
+// buf[(l / lsplit) * lstride_hi + (l % lsplit) * lstride_lo + e * estride].
+// Two-level line indexing covers both "lines contiguous" layouts (z-lines of a
+// [c][z][q] tile) and "elements contiguous" layouts (y-lines of [c][z][n]).
+struct Lines {
+    int nlines;
+    int lsplit;
+    int lstride_lo;
+    int lstride_hi;
+    int estride;
+    bool lines_fast;  // consecutive threads take consecutive lines (else consecutive groups)
+    __device__ __forceinline__ int base(int l) const { return (l / lsplit) * lstride_hi + (l % lsplit) * lstride_lo; }
+};
+
+// K radix-2 stages starting at stage s0 of a length 2^lgL transform.
+// DIR = -1: DIF with twiddles w^e; DIR = +1: DIT (stages in reverse order) with conj(w^e).
+template <int K, int DIR, typename C>
+__device__ __forceinline__ void fft_pass(C* __restrict__ buf, const Lines& ln, int lgL, int s0,
+                                         const C* __restrict__ tw, int twshift)
+{
+    constexpr int R = 1 << K;
+    const int L = 1 << lgL;
+    const int S = (L >> s0) >> K;  // stride between the elements of one group
+    const int gpl = L >> K;        // groups per line
+    const int total = ln.nlines * gpl;
+    for (int g = threadIdx.x; g < total; g += blockDim.x) {
+        int line, gi;
+        if (ln.lines_fast) {
+            line = g % ln.nlines;
+            gi = g / ln.nlines;
+        } else {
+            line = g / gpl;
+            gi = g % gpl;
+        }
+        const int o = gi % S;
+        const int b = gi / S;
+        const int e0 = b * (S << K) + o;
+        C* p = buf + ln.base(line);
+        C v[R];
+#pragma unroll
+        for (int j = 0; j < R; j++) v[j] = p[(e0 + j * S) * ln.estride];
+        if (DIR < 0) {
+#pragma unroll
+            for (int t = 0; t < K; t++) {
+                const int half = R >> (t + 1);
+                const int s = s0 + t;
+#pragma unroll
+                for (int j = 0; j < R; j++) {
+                    if ((j & half) == 0) {
+                        const int off = o + (j & ((R >> t) - 1)) * S;
+                        const C w = tw[(off << s) << twshift];
+                        const C a = v[j], c = v[j + half];
+                        v[j] = c_add(a, c);
+                        v[j + half] = c_mul(c_sub(a, c), w);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int t = K - 1; t >= 0; t--) {
+                const int half = R >> (t + 1);
+                const int s = s0 + t;
+#pragma unroll
+                for (int j = 0; j < R; j++) {
+                    if ((j & half) == 0) {
+                        const int off = o + (j & ((R >> t) - 1)) * S;
+                        const C w = tw[(off << s) << twshift];
+                        const C a = v[j];
+                        const C c = c_mulc(v[j + half], w);
+                        v[j] = c_add(a, c);
+                        v[j + half] = c_sub(a, c);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < R; j++) p[(e0 + j * S) * ln.estride] = v[j];
+    }
+}
+
+// All DIF stages from s_begin (natural order in, bit-reversed out), radix-8 passes.
+template <typename C>
+__device__ void fft_dif(C* buf, const Lines& ln, int lgL, int s_begin, const C* tw, int twshift)
+{
+    int s = s_begin;
+    while (s < lgL) {
+        const int k = lgL - s;
+        if (k >= 3) {
+            fft_pass<3, -1>(buf, ln, lgL, s, tw, twshift);
+            s += 3;
+        } else if (k == 2) {
+            fft_pass<2, -1>(buf, ln, lgL, s, tw, twshift);
+            s += 2;
+        } else {
+            fft_pass<1, -1>(buf, ln, lgL, s, tw, twshift);
+            s += 1;
+        }
+        __syncthreads();
+    }
+}
+
+// All DIT stages down to s_end (bit-reversed in, natural order out, unscaled).
+// The grouping mirrors fft_dif so the two are exact inverses up to the factor L.
+template <typename C>
+__device__ void fft_dit(C* buf, const Lines& ln, int lgL, int s_end, const C* tw, int twshift)
+{
+    // replay the DIF grouping (passes of 3 stages from s_end, a shorter last one) in reverse
+    const int npass = (lgL - s_end + 2) / 3;
+    for (int i = npass - 1; i >= 0; i--) {
+        const int st = s_end + 3 * i;
+        const int k = lgL - st >= 3 ? 3 : lgL - st;
+        if (k == 3) fft_pass<3, 1>(buf, ln, lgL, st, tw, twshift);
+        else if (k == 2) fft_pass<2, 1>(buf, ln, lgL, st, tw, twshift);
+        else fft_pass<1, 1>(buf, ln, lgL, st, tw, twshift);
+        __syncthreads();
+    }
+}
+
+}  // namespace boris

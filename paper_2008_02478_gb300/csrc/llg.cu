@@ -1,0 +1,255 @@
+// Fused effective-field + LLG right-hand side + Runge-Kutta stage kernels.
+//
+// Per cell (Eq. 1 in Landau-Lifshitz form, fields of Table 1):
+//   H = Hd + (2A/(mu0 Ms)) lap(m) + (2Ku/(mu0 Ms)) (m.e) e + Hext,
+//   lap(m) = sum over axes and existing neighbours j of (m_j - m)/h^2
+//            (homogeneous Neumann boundary: a missing neighbour equals m),
+//   k = -gamma/(1+alpha^2) [m x H + alpha m x (m x H)].
+// RK4 (Section 2; four field evaluations per step, Section 7): the stage
+// kernel consumes Hd of the current stage state, accumulates sum w_s k_s and
+// writes the next stage state m0 + c dt k; the fourth stage writes
+// normalise(m0 + dt/6 (k1 + 2k2 + 2k3 + k4)) over m0 in place.
+// RKF45 (Fehlberg): the same field evaluation, with the stage combinations of
+// the Fehlberg tableau and the embedded error max |m5 - m4|.
+#include "boris_internal.cuh"
+#include "llg_kernels.cuh"
+
+namespace boris {
+
+// Runge-Kutta-Fehlberg 4(5) coefficients (Fehlberg's published tableau):
+// stage s state = m0 + dt sum_j A[s][j] k_j; 4th/5th order weights B4, B5.
+__constant__ double RKF_A[6][5] = {
+    {0, 0, 0, 0, 0},
+    {1.0 / 4, 0, 0, 0, 0},
+    {3.0 / 32, 9.0 / 32, 0, 0, 0},
+    {1932.0 / 2197, -7200.0 / 2197, 7296.0 / 2197, 0, 0},
+    {439.0 / 216, -8.0, 3680.0 / 513, -845.0 / 4104, 0},
+    {-8.0 / 27, 2.0, -3544.0 / 2565, 1859.0 / 4104, -11.0 / 40},
+};
+__constant__ double RKF_B4[6] = {25.0 / 216, 0.0, 1408.0 / 2565, 2197.0 / 4104, -1.0 / 5, 0.0};
+__constant__ double RKF_B5[6] = {16.0 / 135, 0.0, 6656.0 / 12825, 28561.0 / 56430, -9.0 / 50, 2.0 / 55};
+
+template <typename T>
+__device__ __forceinline__ void field_and_rhs(const LLGArgs<T>& a, const T* __restrict__ ms, const T* __restrict__ Hd,
+                                              size_t i, int x, int y, int z, T m[3], T k[3])
+{
+    const size_t n = a.ncell;
+    m[0] = ms[i];
+    m[1] = ms[n + i];
+    m[2] = ms[2 * n + i];
+    T lap[3] = {T(0), T(0), T(0)};
+    auto nb = [&](size_t j, T w) {
+        lap[0] += w * (ms[j] - m[0]);
+        lap[1] += w * (ms[n + j] - m[1]);
+        lap[2] += w * (ms[2 * n + j] - m[2]);
+    };
+    const size_t sy = a.nx, sz = (size_t)a.nx * a.ny;
+    if (x > 0) nb(i - 1, a.ihx2);
+    if (x < a.nx - 1) nb(i + 1, a.ihx2);
+    if (y > 0) nb(i - sy, a.ihy2);
+    if (y < a.ny - 1) nb(i + sy, a.ihy2);
+    if (z > 0) nb(i - sz, a.ihz2);
+    if (z < a.nz - 1) nb(i + sz, a.ihz2);
+    const T Ms = a.ms_map ? a.ms_map[i] : a.Ms;
+    const T Ku = a.ku_map ? a.ku_map[i] : a.Ku;
+    const T inv = T(1) / (T(MU0_D) * Ms);
+    const T cex = T(2) * a.A * inv;
+    const T me = m[0] * a.e[0] + m[1] * a.e[1] + m[2] * a.e[2];
+    const T can = T(2) * Ku * inv * me;
+    T H[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) H[c] = Hd[c * n + i] + cex * lap[c] + can * a.e[c] + a.Hext[c];
+    const T mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
+    const T mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2], m[0] * mxH[1] - m[1] * mxH[0]};
+#pragma unroll
+    for (int c = 0; c < 3; c++) k[c] = -a.gp * (mxH[c] + a.alpha * mmH[c]);
+}
+
+// stage s in 0..3; ms = stage state (m0 itself for s = 0).
+template <typename T>
+__global__ void __launch_bounds__(256) rk4_stage_kernel(LLGArgs<T> a, int s, const T* __restrict__ ms,
+                                                        const T* __restrict__ Hd, T* __restrict__ m0,
+                                                        T* __restrict__ acc, T* __restrict__ mnext)
+{
+    const size_t n = a.ncell;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % a.nx);
+        const int y = (int)((i / a.nx) % a.ny);
+        const int z = (int)(i / ((size_t)a.nx * a.ny));
+        T m[3], k[3];
+        field_and_rhs(a, ms, Hd, i, x, y, z, m, k);
+        if (s == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                acc[c * n + i] = k[c];
+                mnext[c * n + i] = m[c] + T(0.5) * a.dt * k[c];
+            }
+        } else if (s < 3) {
+            const T cdt = s == 1 ? T(0.5) * a.dt : a.dt;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                acc[c * n + i] += T(2) * k[c];
+                mnext[c * n + i] = m0[c * n + i] + cdt * k[c];
+            }
+        } else {
+            T v[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) v[c] = m0[c * n + i] + a.dt * (T(1) / T(6)) * (acc[c * n + i] + k[c]);
+            const T inv = T(1) / sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+            for (int c = 0; c < 3; c++) m0[c * n + i] = v[c] * inv;
+        }
+    }
+}
+
+// RKF45 stage s in 0..5: k_s = f(ms); for s < 5 writes the next stage state
+// mnext = m0 + dt sum_{j<=s} a_{s+1,j} k_j; for s = 5 writes the normalised
+// 4th-order solution into mnext and folds max |m5 - m4| into *err.
+template <typename T>
+__global__ void __launch_bounds__(256) rkf45_stage_kernel(LLGArgs<T> a, int s, const T* __restrict__ ms,
+                                                          const T* __restrict__ Hd, const T* __restrict__ m0,
+                                                          T* __restrict__ kbuf, T* __restrict__ mnext,
+                                                          unsigned int* __restrict__ err_bits)
+{
+    const size_t n = a.ncell;
+    float local_err = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % a.nx);
+        const int y = (int)((i / a.nx) % a.ny);
+        const int z = (int)(i / ((size_t)a.nx * a.ny));
+        T m[3], k[3];
+        field_and_rhs(a, ms, Hd, i, x, y, z, m, k);
+#pragma unroll
+        for (int c = 0; c < 3; c++) kbuf[((size_t)s * 3 + c) * n + i] = k[c];
+        if (s < 5) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                T v = m0[c * n + i];
+                for (int j = 0; j < s; j++) v += a.dt * T(RKF_A[s + 1][j]) * kbuf[((size_t)j * 3 + c) * n + i];
+                v += a.dt * T(RKF_A[s + 1][s]) * k[c];
+                mnext[c * n + i] = v;
+            }
+        } else {
+            T v4[3], d[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                T s4 = T(0), s5 = T(0);
+                for (int j = 0; j < 6; j++) {
+                    const T kj = j == 5 ? k[c] : kbuf[((size_t)j * 3 + c) * n + i];
+                    s4 += T(RKF_B4[j]) * kj;
+                    s5 += T(RKF_B5[j]) * kj;
+                }
+                v4[c] = m0[c * n + i] + a.dt * s4;
+                d[c] = a.dt * (s5 - s4);
+            }
+            const T e = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            local_err = fmaxf(local_err, (float)e);
+            const T inv = T(1) / sqrt(v4[0] * v4[0] + v4[1] * v4[1] + v4[2] * v4[2]);
+#pragma unroll
+            for (int c = 0; c < 3; c++) mnext[c * n + i] = v4[c] * inv;
+        }
+    }
+    if (s == 5) {
+        // non-negative floats order like their bit patterns
+        for (int o = 16; o > 0; o >>= 1) local_err = fmaxf(local_err, __shfl_xor_sync(0xffffffffu, local_err, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(err_bits, __float_as_uint(local_err));
+    }
+}
+
+// FP64 energies: E_demag, E_exchange, E_anisotropy, E_Zeeman.
+template <typename T>
+__global__ void __launch_bounds__(256) energy_kernel(LLGArgs<T> a, const T* __restrict__ m, const T* __restrict__ Hd,
+                                                     double* __restrict__ out)
+{
+    const size_t n = a.ncell;
+    double e[4] = {0, 0, 0, 0};
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % a.nx);
+        const int y = (int)((i / a.nx) % a.ny);
+        const int z = (int)(i / ((size_t)a.nx * a.ny));
+        const double mc[3] = {(double)m[i], (double)m[n + i], (double)m[2 * n + i]};
+        double lap[3] = {0, 0, 0};
+        auto nb = [&](size_t j, double w) {
+            lap[0] += w * ((double)m[j] - mc[0]);
+            lap[1] += w * ((double)m[n + j] - mc[1]);
+            lap[2] += w * ((double)m[2 * n + j] - mc[2]);
+        };
+        const size_t sy = a.nx, sz = (size_t)a.nx * a.ny;
+        if (x > 0) nb(i - 1, a.ihx2);
+        if (x < a.nx - 1) nb(i + 1, a.ihx2);
+        if (y > 0) nb(i - sy, a.ihy2);
+        if (y < a.ny - 1) nb(i + sy, a.ihy2);
+        if (z > 0) nb(i - sz, a.ihz2);
+        if (z < a.nz - 1) nb(i + sz, a.ihz2);
+        const double Ms = a.ms_map ? (double)a.ms_map[i] : (double)a.Ms;
+        const double Ku = a.ku_map ? (double)a.ku_map[i] : (double)a.Ku;
+        const double me = mc[0] * a.e[0] + mc[1] * a.e[1] + mc[2] * a.e[2];
+        double mHd = 0, mHz = 0, mlap = 0;
+        for (int c = 0; c < 3; c++) {
+            mHd += mc[c] * (double)Hd[c * n + i];
+            mHz += mc[c] * (double)a.Hext[c];
+            mlap += mc[c] * lap[c];
+        }
+        // -(mu0 Ms/2) m.Hex with Hex = (2A/(mu0 Ms)) lap m  ->  -A m.lap m
+        e[0] += -0.5 * MU0_D * Ms * mHd;
+        e[1] += -(double)a.A * mlap;
+        e[2] += Ku * (1.0 - me * me);
+        e[3] += -MU0_D * Ms * mHz;
+    }
+    __shared__ double red[4][8];
+    for (int c = 0; c < 4; c++) {
+        double v = e[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
+        atomicAdd(out + threadIdx.x, v * a.V);
+    }
+}
+
+static int grid_for(size_t n)
+{
+    size_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (int)(b > 0 ? b : 1);
+}
+
+template <typename T>
+cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, T* m0, T* acc, T* mnext,
+                             cudaStream_t st)
+{
+    rk4_stage_kernel<T><<<grid_for(a.ncell), 256, 0, st>>>(a, s, ms, Hd, m0, acc, mnext);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rkf45_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, const T* m0, T* kbuf, T* mnext,
+                               unsigned int* err_bits, cudaStream_t st)
+{
+    rkf45_stage_kernel<T><<<grid_for(a.ncell), 256, 0, st>>>(a, s, ms, Hd, m0, kbuf, mnext, err_bits);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_energy(const LLGArgs<T>& a, const T* m, const T* Hd, double* out, cudaStream_t st)
+{
+    energy_kernel<T><<<grid_for(a.ncell), 256, 0, st>>>(a, m, Hd, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_rk4_stage<float>(const LLGArgs<float>&, int, const float*, const float*, float*, float*,
+                                             float*, cudaStream_t);
+template cudaError_t launch_rk4_stage<double>(const LLGArgs<double>&, int, const double*, const double*, double*,
+                                              double*, double*, cudaStream_t);
+template cudaError_t launch_rkf45_stage<float>(const LLGArgs<float>&, int, const float*, const float*, const float*,
+                                               float*, float*, unsigned int*, cudaStream_t);
+template cudaError_t launch_rkf45_stage<double>(const LLGArgs<double>&, int, const double*, const double*,
+                                                const double*, double*, double*, unsigned int*, cudaStream_t);
+template cudaError_t launch_energy<float>(const LLGArgs<float>&, const float*, const float*, double*, cudaStream_t);
+template cudaError_t launch_energy<double>(const LLGArgs<double>&, const double*, const double*, double*,
+                                           cudaStream_t);
+
+}  // namespace boris

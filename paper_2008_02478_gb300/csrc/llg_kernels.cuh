@@ -1,0 +1,36 @@
+// Arguments and launchers of the LLG kernels (llg.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace boris {
+
+constexpr double MU0_D = 1.25663706143591729539e-6;  // 4 pi 1e-7
+
+// Per-launch constants of the effective field and the step.
+template <typename T>
+struct LLGArgs {
+    int nx, ny, nz;
+    size_t ncell;
+    T ihx2, ihy2, ihz2;  // 1/h^2 per axis
+    T Ms, Ku, A;         // uniform values (used when the map is NULL)
+    const T* ms_map;
+    const T* ku_map;
+    T e[3];
+    T Hext[3];
+    T gp;     // gamma / (1 + alpha^2)
+    T alpha;
+    T dt;
+    double V;  // cell volume (energies)
+};
+
+template <typename T>
+cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, T* m0, T* acc, T* mnext,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_rkf45_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, const T* m0, T* kbuf, T* mnext,
+                               unsigned int* err_bits, cudaStream_t st);
+template <typename T>
+cudaError_t launch_energy(const LLGArgs<T>& a, const T* m, const T* Hd, double* out, cudaStream_t st);
+
+}  // namespace boris

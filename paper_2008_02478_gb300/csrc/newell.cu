@@ -1,0 +1,314 @@
+// FP64 precompute of the demagnetising-tensor spectrum (Table 1, "N computed
+// using formulas in Ref. [50]": Newell, Williams and Dunlop).
+//
+// 1. newell_octant_kernel: the cell-averaged tensor for every displacement
+//    (i dx, j dy, k dz), 0 <= i < nx etc.  Within rs * max(dx,dy,dz) the exact
+//    closed form: N_xx = (1/(4 pi V)) sum over the 27 shifts of prod_axis w(e)
+//    f(...), w(0) = 2, w(+-1) = -1, with Newell's f (xx, yy, zz by permuting
+//    the arguments) and g (xy, xz, yz).  Beyond it the box-averaged dipole
+//    expansion N_ij = -(V/4 pi)[D_ij + (1/12) sum_k h_k^2 d_k^2 D_ij],
+//    D_ij = d_i d_j (1/r), which is the Taylor expansion of the point-dipole
+//    kernel averaged over the source and target boxes (the FP64 closed form
+//    loses ~(r/h)^6 eps to cancellation far from the cell).
+// 2. Three axis passes: each extends the octant line to the padded length
+//    with the component's parity (xx, yy, zz even in every axis; xy odd in x
+//    and y; xz odd in x and z; yz odd in y and z), transforms it with the
+//    shared-memory FFT in FP64, and keeps the first P/2 + 1 bins.
+// 3. finalize: the spectrum is real (even or odd-odd symmetric sequences);
+//    store -Re / (px py pz) as [kx][ky][kz][6] in FP32 or FP64.
+#include "boris_internal.cuh"
+
+namespace boris {
+
+// Newell's f: even in each argument; a term with a vanishing polynomial factor
+// is dropped (its closed-form limit is zero).
+__device__ double newell_f_dev(double x, double y, double z)
+{
+    x = fabs(x); y = fabs(y); z = fabs(z);
+    const double xx = x * x, yy = y * y, zz = z * z;
+    const double R = sqrt(xx + yy + zz);
+    if (R == 0.0) return 0.0;
+    double acc = (2.0 * xx - yy - zz) * R * (1.0 / 6.0);
+    const double t1 = 0.5 * y * (zz - xx);
+    if (t1 != 0.0) acc += t1 * asinh(y / sqrt(xx + zz));
+    const double t2 = 0.5 * z * (yy - xx);
+    if (t2 != 0.0) acc += t2 * asinh(z / sqrt(xx + yy));
+    const double t3 = x * y * z;
+    if (t3 != 0.0) acc -= t3 * atan(y * z / (x * R));
+    return acc;
+}
+
+// Newell's g: odd in x and y, even in z.
+__device__ double newell_g_dev(double x, double y, double z)
+{
+    const double sign = copysign(1.0, x) * copysign(1.0, y);
+    x = fabs(x); y = fabs(y); z = fabs(z);
+    const double xx = x * x, yy = y * y, zz = z * z;
+    const double R = sqrt(xx + yy + zz);
+    if (R == 0.0) return 0.0;
+    double acc = -x * y * R * (1.0 / 3.0);
+    const double xyz = x * y * z;
+    if (xyz != 0.0) acc += xyz * asinh(z / sqrt(xx + yy));
+    const double a = y * (3.0 * zz - yy) * (1.0 / 6.0);
+    if (a != 0.0) acc += a * asinh(x / sqrt(yy + zz));
+    const double b = x * (3.0 * zz - xx) * (1.0 / 6.0);
+    if (b != 0.0) acc += b * asinh(y / sqrt(xx + zz));
+    if (z != 0.0) {
+        acc -= zz * z * (1.0 / 6.0) * atan(x * y / (z * R));
+        if (y != 0.0) acc -= 0.5 * z * yy * atan(x * z / (y * R));
+        if (x != 0.0) acc -= 0.5 * z * xx * atan(y * z / (x * R));
+    }
+    return sign * acc;
+}
+
+// Exact tensor: all six components from one sweep over the 27 shifts.
+__device__ void newell_exact_dev(double X, double Y, double Z, double dx, double dy, double dz, double out[6])
+{
+    double s[6] = {0, 0, 0, 0, 0, 0};
+    for (int a = -1; a <= 1; a++) {
+        const double wa = a == 0 ? 2.0 : -1.0;
+        const double x = X + a * dx;
+        for (int b = -1; b <= 1; b++) {
+            const double wb = b == 0 ? 2.0 : -1.0;
+            const double y = Y + b * dy;
+            for (int c = -1; c <= 1; c++) {
+                const double w = wa * wb * (c == 0 ? 2.0 : -1.0);
+                const double z = Z + c * dz;
+                s[0] += w * newell_f_dev(x, y, z);
+                s[1] += w * newell_f_dev(y, x, z);
+                s[2] += w * newell_f_dev(z, y, x);
+                s[3] += w * newell_g_dev(x, y, z);
+                s[4] += w * newell_g_dev(x, z, y);
+                s[5] += w * newell_g_dev(y, z, x);
+            }
+        }
+    }
+    const double inv = 1.0 / (4.0 * 3.14159265358979323846 * dx * dy * dz);
+    for (int i = 0; i < 6; i++) out[i] = s[i] * inv;
+}
+
+// Box-averaged dipole expansion to second order in the cell size.  With
+// S2 = sum_k h_k^2 x_k^2 and Hs = sum_k h_k^2,
+//   sum_k h_k^2 d_k^2 D_ij = 105 x_i x_j S2 / r^9
+//       - 15 [x_i x_j (Hs + 2 h_i^2 + 2 h_j^2) + delta_ij S2] / r^7
+//       + 3 delta_ij (Hs + 2 h_i^2) / r^5.
+__device__ void newell_far_dev(double X, double Y, double Z, double dx, double dy, double dz, double out[6])
+{
+    const double x[3] = {X, Y, Z};
+    const double h2[3] = {dx * dx, dy * dy, dz * dz};
+    const double r2 = X * X + Y * Y + Z * Z;
+    const double r = sqrt(r2);
+    const double ir2 = 1.0 / r2;
+    const double ir5 = ir2 * ir2 / r;
+    const double ir7 = ir5 * ir2, ir9 = ir7 * ir2;
+    const double S2 = h2[0] * X * X + h2[1] * Y * Y + h2[2] * Z * Z;
+    const double Hs = h2[0] + h2[1] + h2[2];
+    const double pre = -(dx * dy * dz) / (4.0 * 3.14159265358979323846);
+    const int I[6] = {0, 1, 2, 0, 0, 1}, J[6] = {0, 1, 2, 1, 2, 2};
+    for (int c = 0; c < 6; c++) {
+        const int i = I[c], j = J[c];
+        const double xij = x[i] * x[j];
+        const double d = (i == j) ? 1.0 : 0.0;
+        const double D = (3.0 * xij - d * r2) * ir5;
+        const double corr = 105.0 * xij * S2 * ir9 -
+                            15.0 * (xij * (Hs + 2.0 * h2[i] + 2.0 * h2[j]) + d * S2) * ir7 +
+                            3.0 * d * (Hs + 2.0 * h2[i]) * ir5;
+        out[c] = pre * (D + corr / 12.0);
+    }
+}
+
+__global__ void newell_octant_kernel(int nx, int ny, int nz, double dx, double dy, double dz, double rs,
+                                     double* __restrict__ T)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    const double hmax = fmax(dx, fmax(dy, dz));
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % nx);
+        const int j = (int)((idx / nx) % ny);
+        const int k = (int)(idx / ((size_t)nx * ny));
+        const double X = i * dx, Y = j * dy, Z = k * dz;
+        double v[6];
+        if (sqrt(X * X + Y * Y + Z * Z) <= rs * hmax) newell_exact_dev(X, Y, Z, dx, dy, dz, v);
+        else newell_far_dev(X, Y, Z, dx, dy, dz, v);
+        for (int c = 0; c < 6; c++) T[c * n + idx] = v[c];
+    }
+}
+
+// Parity of component c along axis a: -1 for the odd (off-diagonal) axes.
+__device__ __forceinline__ double comp_parity(int c, int a)
+{
+    // c: 0 xx, 1 yy, 2 zz, 3 xy, 4 xz, 5 yz
+    if (c == 3) return (a == 0 || a == 1) ? -1.0 : 1.0;
+    if (c == 4) return (a == 0 || a == 2) ? -1.0 : 1.0;
+    if (c == 5) return (a == 1 || a == 2) ? -1.0 : 1.0;
+    return 1.0;
+}
+
+// One axis pass.  Input: [6][d2][d1][d0] (real if in_real, else complex) with
+// the transformed axis of length n (octant); output: same with that axis of
+// length P/2 + 1.  NL lines per CTA, each extended to length P in shared
+// memory with the component's parity.
+__global__ void __launch_bounds__(256) axis_pass_kernel(const void* __restrict__ in, bool in_real,
+                                                        double2* __restrict__ out, int axis, int d0, int d1,
+                                                        int d2, int n, int P, int lgP, int NL,
+                                                        const double2* __restrict__ tw, int lglmax)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2* buf = reinterpret_cast<double2*>(smem_raw);  // [NL][P]
+    const int dims[3] = {d0, d1, d2};
+    int od[3] = {d0, d1, d2};
+    const int kh = P / 2 + 1;
+    od[axis] = kh;
+    // line = (c, the two other coordinates)
+    const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+    const long nlines_total = 6L * dims[oa] * dims[ob];
+    const long line0 = (long)blockIdx.x * NL;
+    auto in_index = [&](int c, int u, int v, int e) -> size_t {
+        int co[3];
+        co[axis] = e;
+        co[oa] = u;
+        co[ob] = v;
+        return (size_t)c * d0 * d1 * d2 + ((size_t)co[2] * d1 + co[1]) * d0 + co[0];
+    };
+    auto out_index = [&](int c, int u, int v, int e) -> size_t {
+        int co[3];
+        co[axis] = e;
+        co[oa] = u;
+        co[ob] = v;
+        return (size_t)c * od[0] * od[1] * od[2] + ((size_t)co[2] * od[1] + co[1]) * od[0] + co[0];
+    };
+    auto decode = [&](long line, int& c, int& u, int& v) {
+        u = (int)(line % dims[oa]);
+        long rest = line / dims[oa];
+        v = (int)(rest % dims[ob]);
+        c = (int)(rest / dims[ob]);
+    };
+    for (int i = threadIdx.x; i < NL * P; i += blockDim.x) {
+        const int l = i / P, e = i % P;
+        const long line = line0 + l;
+        double2 val = make_double2(0.0, 0.0);
+        if (line < nlines_total) {
+            int c, u, v;
+            decode(line, c, u, v);
+            int src = -1;
+            double s = 1.0;
+            if (e < n) src = e;
+            else if (e > P - n) { src = P - e; s = comp_parity(c, axis); }
+            if (src >= 0) {
+                const size_t ii = in_index(c, u, v, src);
+                if (in_real) val = make_double2(s * reinterpret_cast<const double*>(in)[ii], 0.0);
+                else {
+                    const double2 t = reinterpret_cast<const double2*>(in)[ii];
+                    val = make_double2(s * t.x, s * t.y);
+                }
+            }
+        }
+        buf[i] = val;
+    }
+    __syncthreads();
+    if (lgP > 0) {
+        Lines ln{NL, NL, P, 0, 1, false};
+        fft_dif(buf, ln, lgP, 0, tw, lglmax - lgP);
+    }
+    for (int i = threadIdx.x; i < NL * kh; i += blockDim.x) {
+        const int l = i / kh, k = i % kh;
+        const long line = line0 + l;
+        if (line >= nlines_total) continue;
+        int c, u, v;
+        decode(line, c, u, v);
+        out[out_index(c, u, v, k)] = buf[l * P + bitrev(k, lgP)];
+    }
+}
+
+template <typename T>
+__global__ void finalize_kernel(const double2* __restrict__ S, T* __restrict__ K, int nkx, int kyh, int kzh,
+                                double scale)
+{
+    const size_t n = (size_t)nkx * kyh * kzh;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n * 6; idx += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % 6);
+        const size_t cell = idx / 6;  // = (kx * kyh + ky) * kzh + kz
+        const int kz = (int)(cell % kzh);
+        const int ky = (int)((cell / kzh) % kyh);
+        const int kx = (int)(cell / ((size_t)kzh * kyh));
+        const double v = S[(size_t)c * n + ((size_t)kz * kyh + ky) * nkx + kx].x;
+        K[idx] = (T)(-v * scale);
+    }
+}
+
+void host_twiddles(int n, double2* out)
+{
+    const double twopi = 6.283185307179586476925286766559;
+    for (int e = 0; e < n; e++) {
+        const double a = twopi * (double)e / (double)n;
+        out[e] = make_double2(std::cos(a), -std::sin(a));
+    }
+}
+
+cudaError_t newell_octant(int nx, int ny, int nz, double dx, double dy, double dz, double rs, double* T,
+                          cudaStream_t st)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    newell_octant_kernel<<<blocks, 256, 0, st>>>(nx, ny, nz, dx, dy, dz, rs, T);
+    return cudaGetLastError();
+}
+
+static cudaError_t run_axis(const void* in, bool in_real, double2* out, int axis, int d0, int d1, int d2, int n,
+                            int P, const double2* tw, int lglmax, cudaStream_t st)
+{
+    const int lgP = ilog2(P);
+    int NL = 4096 / P;
+    if (NL < 1) NL = 1;
+    if (NL > 32) NL = 32;
+    const size_t smem = (size_t)NL * P * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(axis_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int dims[3] = {d0, d1, d2};
+    const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
+    const long nlines = 6L * dims[oa] * dims[ob];
+    const long blocks = (nlines + NL - 1) / NL;
+    axis_pass_kernel<<<(unsigned)blocks, 256, smem, st>>>(in, in_real, out, axis, d0, d1, d2, n, P, lgP, NL, tw,
+                                                           lglmax);
+    return cudaGetLastError();
+}
+
+cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, double dz, double rs, void* K_out,
+                                  bool k_is_f64, const double2* tw64, cudaStream_t st)
+{
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    double* T = nullptr;
+    double2 *A = nullptr, *B = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&T, 6 * n * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const size_t a_elems = 6 * (size_t)g.nkx * g.ny * g.nz;
+    const size_t b_elems = 6 * (size_t)g.nkx * g.kyh * g.nz;
+    const size_t c_elems = 6 * (size_t)g.nkx * g.kyh * g.kzh;
+    do {
+        if ((e = newell_octant(g.nx, g.ny, g.nz, dx, dy, dz, rs, T, st)) != cudaSuccess) break;
+        if ((e = cudaMallocAsync((void**)&A, a_elems * sizeof(double2), st)) != cudaSuccess) break;
+        if ((e = run_axis(T, true, A, 0, g.nx, g.ny, g.nz, g.nx, g.px, tw64, g.lglmax, st)) != cudaSuccess) break;
+        cudaFreeAsync(T, st);
+        T = nullptr;
+        if ((e = cudaMallocAsync((void**)&B, b_elems * sizeof(double2), st)) != cudaSuccess) break;
+        if ((e = run_axis(A, false, B, 1, g.nkx, g.ny, g.nz, g.ny, g.py, tw64, g.lglmax, st)) != cudaSuccess) break;
+        cudaFreeAsync(A, st);
+        A = nullptr;
+        if ((e = cudaMallocAsync((void**)&A, c_elems * sizeof(double2), st)) != cudaSuccess) break;
+        if ((e = run_axis(B, false, A, 2, g.nkx, g.kyh, g.nz, g.nz, g.pz, tw64, g.lglmax, st)) != cudaSuccess) break;
+        const double scale = 1.0 / ((double)g.px * g.py * g.pz);
+        const size_t tot = c_elems;
+        int blocks = (int)((tot + 255) / 256);
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        if (k_is_f64) finalize_kernel<double><<<blocks, 256, 0, st>>>(A, (double*)K_out, g.nkx, g.kyh, g.kzh, scale);
+        else finalize_kernel<float><<<blocks, 256, 0, st>>>(A, (float*)K_out, g.nkx, g.kyh, g.kzh, scale);
+        e = cudaGetLastError();
+    } while (0);
+    if (T) cudaFreeAsync(T, st);
+    if (A) cudaFreeAsync(A, st);
+    if (B) cudaFreeAsync(B, st);
+    return e;
+}
+
+}  // namespace boris

@@ -1,0 +1,108 @@
+"""GPU parity of the fused LLG step (Eq. 1; Table 1 fields; RK4 and RKF45 of
+Section 2) and the FP64 energies against the oracle, through the C ABI.
+Tolerance on m after 10 RK4 steps: relative L2 1e-5 (FP32)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import llg
+from paper_2008_02478_gb300 import inputs
+from tests.gpu_util import rel_l2, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(n, h, per_cell, seed, Hext=(1e4, -2e4, 3e4)):
+    nx, ny, nz = n
+    if per_cell:
+        Ms = inputs.smooth_noise(nx, ny, nz, 2.0, 6e5, 1e6, seed)
+        Ku = inputs.smooth_noise(nx, ny, nz, 2.0, 0.0, 5e5, seed + 1)
+    else:
+        Ms, Ku = 8e5, 1e5
+    prm = llg.Params(cell=h, Ms=Ms, A=1.3e-11, alpha=0.02, Ku=Ku, easy=(0.0, 0.6, 0.8), Hext=Hext)
+    m0 = inputs.random_unit(nx, ny, nz, seed)
+    return prm, m0
+
+
+def _gpu_params(torch, prm, fp64=False):
+    from paper_2008_02478_gb300.binding import LLGParams
+    g = LLGParams(A=prm.A, alpha=prm.alpha, gamma=prm.gamma, easy=prm.easy, Hext=prm.Hext)
+    if np.ndim(prm.Ms):
+        g.Ms_map = to_dev(torch, prm.Ms, fp64)
+    else:
+        g.Ms = float(prm.Ms)
+    if np.ndim(prm.Ku):
+        g.Ku_map = to_dev(torch, prm.Ku, fp64)
+    else:
+        g.Ku = float(prm.Ku)
+    return g
+
+
+@pytest.mark.parametrize("n,h,per_cell", [
+    ((32, 32, 4), (5e-9, 5e-9, 5e-9), False),   # small cubic-cell mesh, 10 RK4 steps
+    ((20, 13, 3), (3e-9, 3e-9, 3e-9), True),    # per-cell Ms and Ku maps, ragged
+    ((24, 16, 1), (2e-9, 2e-9, 3e-9), False),   # 2D mode
+])
+@pytest.mark.parametrize("fp64", [False, True])
+def test_rk4_steps_match_oracle(n, h, per_cell, fp64):
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan
+    prm, m0 = _problem(n, h, per_cell, seed=1)
+    dt, steps = 1e-13, 10
+    dem = oracle.DemagPlan(*n, *h)
+    ref = m0.copy()
+    for _ in range(steps):
+        ref = llg.rk4_step(ref, dt, prm, dem.apply)
+    plan = Plan(*n, *h, fp64=fp64)
+    m = to_dev(torch, m0, fp64)
+    gp = _gpu_params(torch, prm, fp64)
+    for _ in range(steps):
+        plan.llg_step(m, gp, dt)
+    err = rel_l2(m.cpu().numpy(), ref)
+    assert err < (1e-10 if fp64 else 1e-5), err
+
+
+def test_rkf45_step_matches_oracle():
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan, RKF45
+    n, h = (24, 12, 2), (2e-9, 2e-9, 3e-9)
+    prm, m0 = _problem(n, h, False, seed=3)
+    dem = oracle.DemagPlan(*n, *h)
+    dt = 5e-14
+    ref, err_ref = llg.rkf45_step(m0, dt, prm, dem.apply)
+    plan = Plan(*n, *h, fp64=True)
+    m = to_dev(torch, m0, True)
+    gp = _gpu_params(torch, prm, True)
+    gp.method, gp.tol, gp.dt_min, gp.dt_max = RKF45, 1.0, 1e-16, 1e-12
+    nxt = plan.llg_step(m, gp, dt)
+    assert rel_l2(m.cpu().numpy(), ref) < 1e-10
+    assert nxt == pytest.approx(llg.rkf45_next_dt(dt, err_ref, 1.0, 1e-16, 1e-12), rel=1e-5)
+
+
+def test_rkf45_rejects_then_accepts():
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan, RKF45
+    n, h = (16, 16, 1), (2e-9, 2e-9, 3e-9)
+    prm, m0 = _problem(n, h, False, seed=4)
+    plan = Plan(*n, *h)
+    m = to_dev(torch, m0)
+    gp = _gpu_params(torch, prm)
+    gp.method, gp.tol, gp.dt_min, gp.dt_max = RKF45, 1e-7, 1e-18, 1e-12
+    dt = 1e-12
+    nxt = plan.llg_step(m, gp, dt)  # too large: rejected, retried smaller
+    assert nxt < dt
+    nrm = torch.sqrt((m * m).sum(0))
+    assert float((nrm - 1).abs().max()) < 1e-6
+
+
+@pytest.mark.parametrize("per_cell", [False, True])
+def test_energies_match_oracle(per_cell):
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan
+    n, h = (20, 18, 4), (3e-9, 3e-9, 3e-9)
+    prm, m0 = _problem(n, h, per_cell, seed=5)
+    ref = llg.energies(m0, prm, oracle.DemagPlan(*n, *h).apply)
+    plan = Plan(*n, *h)
+    E = plan.energy(to_dev(torch, m0), _gpu_params(torch, prm))
+    for e, r in zip(E, ref):
+        assert abs(e - r) <= 1e-5 * max(abs(v) for v in ref), (E, ref)
