@@ -128,6 +128,24 @@ int boris_llg_step(boris_plan p, float* m, const boris_llg_params* prm, double* 
 int boris_llg_step_f64(boris_plan p, double* m, const boris_llg_params* prm, double* dt);
 
 /*
+ * boris_llg_step_backward - discrete adjoint of one RK4 step (the paper has
+ *   no adjoint; this serves gradient-based fitting of material maps).
+ *   Given the step's input state m_in (device [3][nz][ny][nx], unchanged) and
+ *   g_m_out = dL/dm_out, writes g_m_in = dL/dm_in (may not alias g_m_out)
+ *   and ADDS dL/dMs and dL/dKu into g_Ms and g_Ku (device [nz][ny][nx]; either
+ *   may be NULL to skip).  The step is recomputed (four demag applications)
+ *   and back-propagated through the renormalisation, the four stages, the
+ *   Landau-Lifshitz right-hand side, exchange (the Neumann Laplacian is
+ *   symmetric), anisotropy and the demagnetising operator, which is
+ *   self-adjoint so each transpose is one more demag application.
+ *   prm->method must be BORIS_RK4.  Workspace: 18 fields, allocated once.
+ */
+int boris_llg_step_backward(boris_plan p, const float* m_in, const boris_llg_params* prm, double dt,
+                            const float* g_m_out, float* g_m_in, float* g_Ms, float* g_Ku);
+int boris_llg_step_backward_f64(boris_plan p, const double* m_in, const boris_llg_params* prm, double dt,
+                                const double* g_m_out, double* g_m_in, double* g_Ms, double* g_Ku);
+
+/*
  * boris_llg_run_host - end-to-end form for callers holding host memory:
  *   copies m_host (host [3][nz][ny][nx] float; pinned memory is fastest) to
  *   the device, runs nsteps RK4 steps of size dt, copies the result back to

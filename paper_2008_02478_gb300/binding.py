@@ -27,7 +27,7 @@ GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
 
 #: entry points declared in include/boris.h
 EXPORTS = ["boris_demag_plan", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_adjoint",
-           "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_host", "boris_energy",
+           "boris_llg_step", "boris_llg_step_f64", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
 KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other"]
@@ -65,6 +65,8 @@ def lib():
         L.boris_demag_adjoint.argtypes = [vp, vp, vp]
         L.boris_llg_step.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_llg_step_f64.argtypes = [vp, vp, P(LLGParamsC), P(d)]
+        L.boris_llg_step_backward.argtypes = [vp, vp, P(LLGParamsC), d, vp, vp, vp, vp]
+        L.boris_llg_step_backward_f64.argtypes = [vp, vp, P(LLGParamsC), d, vp, vp, vp, vp]
         L.boris_llg_run_host.argtypes = [vp, vp, P(LLGParamsC), d, i]
         L.boris_energy.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_sync_status.argtypes = [vp]
@@ -199,6 +201,21 @@ class Plan:
         fn = lib().boris_llg_step_f64 if self.fp64 else lib().boris_llg_step
         check(fn(self._h, _ptr(m, self.dtype, self.field_shape), ctypes.byref(c), ctypes.byref(h)))
         return h.value
+
+    def llg_step_backward(self, m_in, prm: LLGParams, dt: float, g_out, g_in=None, g_Ms=None, g_Ku=None):
+        """g_in = dL/dm_in of one RK4 step from g_out = dL/dm_out; ADDS dL/dMs and
+        dL/dKu into g_Ms / g_Ku when given (tensors [nz][ny][nx])."""
+        import torch
+        if g_in is None:
+            g_in = torch.empty_like(g_out)
+        nx, ny, nz = self.shape
+        c = self._params(prm)
+        gms = _ptr(g_Ms, self.dtype, (nz, ny, nx)) if g_Ms is not None else None
+        gku = _ptr(g_Ku, self.dtype, (nz, ny, nx)) if g_Ku is not None else None
+        fn = lib().boris_llg_step_backward_f64 if self.fp64 else lib().boris_llg_step_backward
+        check(fn(self._h, _ptr(m_in, self.dtype, self.field_shape), ctypes.byref(c), float(dt),
+                 _ptr(g_out, self.dtype, self.field_shape), _ptr(g_in, self.dtype, self.field_shape), gms, gku))
+        return g_in
 
     def llg_run_host(self, m_host, prm: LLGParams, dt: float, nsteps: int):
         """m_host: CPU float32 tensor (pinned for speed), updated in place."""

@@ -43,6 +43,9 @@ struct boris_plan_s {
     unsigned int* h_err_bits = nullptr;  // pinned
     double* energy = nullptr;
     void* m_dev_e2e = nullptr;
+    // adjoint workspace: stage states m2..m4, stage fields, stage derivatives,
+    // stage cotangents, and three scratch fields
+    void* bw = nullptr;
     size_t bytes = 0;
     // optional per-kernel CUDA-event timing (boris_profile_enable)
     bool prof = false;
@@ -257,6 +260,54 @@ int llg_step_t(boris_plan p, T* m, const boris_llg_params* prm, double* dt)
     return fail(BORIS_ERR_INVALID_ARG, "unknown method");
 }
 
+template <typename T>
+int llg_backward_t(boris_plan p, const T* m_in, const boris_llg_params* prm, double dt, const T* g_out, T* g_in,
+                   T* g_Ms, T* g_Ku)
+{
+    if (!p || !m_in || !prm || !g_out || !g_in) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned16(m_in) || !aligned16(g_out) || !aligned16(g_in) || (g_Ms && !aligned16(g_Ms)) ||
+        (g_Ku && !aligned16(g_Ku)))
+        return fail(BORIS_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
+    if (prm->method != BORIS_RK4) return fail(BORIS_ERR_INVALID_ARG, "the adjoint is of the RK4 step");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(BORIS_ERR_INVALID_ARG, "dt must be > 0");
+    int rc = ensure_llg_workspace<T>(p, false);
+    if (rc) return rc;
+    LLGArgs<T> a;
+    if ((rc = check_params<T>(p, prm, &a, dt))) return rc;
+    const size_t n3 = 3 * ncell(p);
+    if (!p->bw && (rc = dev_alloc(p, &p->bw, 18 * n3 * sizeof(T)))) return rc;
+    T* w = (T*)p->bw;
+    T* mst[4] = {(T*)m_in, w, w + n3, w + 2 * n3};
+    T* Hs = w + 3 * n3;   // 4 x n3
+    T* ks = w + 7 * n3;   // 4 x n3
+    T* gk = w + 11 * n3;  // 4 x n3
+    T* gH = w + 15 * n3;
+    T* DgH = w + 16 * n3;
+    T* gml = w + 17 * n3;
+    T* Hd = (T*)p->Hd;
+    const T* ms_map = (const T*)prm->Ms_map;
+    for (int s = 0; s < 4; s++) {
+        if ((rc = demag_apply_t<T>(p, mst[s], ms_map, a.Ms, Hd))) return rc;
+        CUDA_TRY(timed(p, 3, [&] {
+            return launch_fwd_stage<T>(a, s, mst[s], Hd, m_in, Hs + s * n3, ks + s * n3, s < 3 ? mst[s + 1] : nullptr,
+                                       p->stream);
+        }));
+    }
+    CUDA_TRY(timed(p, 3, [&] {
+        return launch_bwd_start<T>(a, m_in, ks, ks + n3, ks + 2 * n3, ks + 3 * n3, g_out, g_in, gk, p->stream);
+    }));
+    const T back[4] = {T(0), T(0.5 * dt), T(0.5 * dt), T(dt)};
+    for (int s = 3; s >= 0; s--) {
+        CUDA_TRY(timed(p, 3, [&] { return launch_bwd_local<T>(a, mst[s], Hs + s * n3, gk + s * n3, gH, gml, p->stream); }));
+        if ((rc = demag_apply_t<T>(p, gH, nullptr, T(1), DgH))) return rc;
+        CUDA_TRY(timed(p, 3, [&] {
+            return launch_bwd_field<T>(a, mst[s], gH, DgH, gml, g_in, s > 0 ? gk + (s - 1) * n3 : nullptr, back[s],
+                                       g_Ms, g_Ku, p->stream);
+        }));
+    }
+    return BORIS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -394,6 +445,20 @@ int boris_llg_step_f64(boris_plan p, double* m, const boris_llg_params* prm, dou
     return llg_step_t<double>(p, m, prm, dt);
 }
 
+int boris_llg_step_backward(boris_plan p, const float* m_in, const boris_llg_params* prm, double dt,
+                            const float* g_m_out, float* g_m_in, float* g_Ms, float* g_Ku)
+{
+    if (p && p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan: use boris_llg_step_backward_f64");
+    return llg_backward_t<float>(p, m_in, prm, dt, g_m_out, g_m_in, g_Ms, g_Ku);
+}
+
+int boris_llg_step_backward_f64(boris_plan p, const double* m_in, const boris_llg_params* prm, double dt,
+                                const double* g_m_out, double* g_m_in, double* g_Ms, double* g_Ku)
+{
+    if (p && !p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP32 plan: use boris_llg_step_backward");
+    return llg_backward_t<double>(p, m_in, prm, dt, g_m_out, g_m_in, g_Ms, g_Ku);
+}
+
 int boris_llg_run_host(boris_plan p, float* m_host, const boris_llg_params* prm, double dt, int nsteps)
 {
     if (!p || !m_host || !prm) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
@@ -483,7 +548,7 @@ void boris_plan_destroy(boris_plan p)
     if (!p) return;
     cudaStreamSynchronize(p->stream);
     void* ptrs[] = {p->K, p->X, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
-                    p->m_dev_e2e};
+                    p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->tw && p->tw != (void*)p->tw64) cudaFree(p->tw);

@@ -31,6 +31,18 @@ template <typename T>
 cudaError_t launch_rkf45_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, const T* m0, T* kbuf, T* mnext,
                                unsigned int* err_bits, cudaStream_t st);
 template <typename T>
+cudaError_t launch_fwd_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, const T* m0, T* Hs, T* ks,
+                             T* mnext, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bwd_start(const LLGArgs<T>& a, const T* m0, const T* k1, const T* k2, const T* k3, const T* k4,
+                             const T* gout, T* gm, T* gk, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bwd_local(const LLGArgs<T>& a, const T* ms, const T* Hs, const T* gk, T* gH, T* gml,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_bwd_field(const LLGArgs<T>& a, const T* ms, const T* gH, const T* DgH, const T* gml, T* gm,
+                             T* gk_prev, T coef, T* gMs, T* gKu, cudaStream_t st);
+template <typename T>
 cudaError_t launch_energy(const LLGArgs<T>& a, const T* m, const T* Hd, double* out, cudaStream_t st);
 
 }  // namespace boris
