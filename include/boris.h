@@ -171,6 +171,11 @@ const char* boris_last_error(void);
 /* Padded transform lengths chosen by the plan: out[0..2] = px, py, pz. */
 int boris_plan_padded(boris_plan p, int out[3]);
 
+/* Schedule of the fused y-z pass chosen by the plan's autotuner: out[0] kind
+ * (0: z stage through shared-memory passes, 1: z stage in registers), out[1]
+ * CTAs per cluster, out[2] threads per CTA, out[3] shared memory per CTA. */
+int boris_plan_schedule(boris_plan p, int out[4]);
+
 /* Bytes of device memory owned by the plan. */
 size_t boris_plan_device_bytes(boris_plan p);
 

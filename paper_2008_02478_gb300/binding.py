@@ -28,7 +28,7 @@ GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
 #: entry points declared in include/boris.h
 EXPORTS = ["boris_demag_plan", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_adjoint",
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
-           "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_device_bytes",
+           "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
 KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other"]
 
@@ -72,6 +72,7 @@ def lib():
         L.boris_sync_status.argtypes = [vp]
         L.boris_last_error.restype = ctypes.c_char_p
         L.boris_plan_padded.argtypes = [vp, P(i)]
+        L.boris_plan_schedule.argtypes = [vp, P(i)]
         L.boris_plan_device_bytes.restype = ctypes.c_size_t
         L.boris_plan_device_bytes.argtypes = [vp]
         L.boris_plan_destroy.argtypes = [vp]
@@ -162,6 +163,12 @@ class Plan:
     def padded(self):
         out = (ctypes.c_int * 3)()
         check(lib().boris_plan_padded(self._h, out))
+        return tuple(out)
+
+    def schedule(self):
+        """(kind, CTAs per cluster, threads, shared bytes) of the fused y-z pass."""
+        out = (ctypes.c_int * 4)()
+        check(lib().boris_plan_schedule(self._h, out))
         return tuple(out)
 
     def device_bytes(self) -> int:

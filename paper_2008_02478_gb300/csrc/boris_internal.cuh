@@ -39,6 +39,7 @@ struct Geometry {
 
 // Launch schedule of the fused y-z spectral pass.
 struct YZSchedule {
+    int kind;     // 0: z stage through shared-memory passes; 1: z stage in registers
     int C;        // CTAs per cluster (one cluster per kx plane); ky residues mod C
     int Qc;       // z-columns processed per chunk of the z stage
     int threads;  // threads per CTA
@@ -55,6 +56,20 @@ cudaError_t launch_yz_conv(const Geometry& g, const YZSchedule& sc, typename Cx<
 template <typename T>
 cudaError_t launch_x_c2r(const Geometry& g, const typename Cx<T>::t* X, T* H,
                          const typename Cx<T>::t* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_yz_reg(const Geometry& g, const YZSchedule& sc, typename Cx<T>::t* X, const T* K,
+                          const typename Cx<T>::t* tw, cudaStream_t st);
+template <>
+cudaError_t launch_yz_reg<float>(const Geometry& g, const YZSchedule& sc, float2* X, const float* K, const float2* tw,
+                                 cudaStream_t st);
+template <>
+cudaError_t launch_yz_reg<double>(const Geometry& g, const YZSchedule& sc, double2* X, const double* K,
+                                  const double2* tw, cudaStream_t st);
+cudaError_t upload_twiddles_yz_f32();
+cudaError_t upload_twiddles_yz_f64();
+// Candidate schedules of the fused y-z pass that fit this geometry.
+template <typename T>
+void yz_candidates(const Geometry& g, int max_smem, YZSchedule* out, int* n);
 template <typename T>
 bool choose_yz_schedule(const Geometry& g, int max_smem, YZSchedule* out);
 template <typename T>

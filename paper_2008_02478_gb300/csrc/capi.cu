@@ -308,6 +308,49 @@ int llg_backward_t(boris_plan p, const T* m_in, const boris_llg_params* prm, dou
     return BORIS_OK;
 }
 
+// Plan-time autotuner of the fused y-z pass: every candidate schedule that fits
+// the geometry runs on the (zeroed) spectral workspace, timed with CUDA events
+// on the plan's stream; the fastest is kept.
+int autotune_yz(boris_plan p, const YZSchedule* cand, int ncand)
+{
+    const size_t xbytes = (size_t)p->g.nkx * 3 * p->g.nz * p->g.ny * 2 * (p->f64 ? sizeof(double) : sizeof(float));
+    CUDA_TRY(cudaMemsetAsync(p->X, 0, xbytes, p->stream));
+    cudaEvent_t a, b;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    float best = 1e30f;
+    int besti = 0;
+    for (int i = 0; i < ncand; i++) {
+        cudaError_t e = cudaSuccess;
+        auto run = [&]() {
+            if (p->f64) e = launch_yz_conv<double>(p->g, cand[i], (double2*)p->X, (const double*)p->K, (const double2*)p->tw, p->stream);
+            else e = launch_yz_conv<float>(p->g, cand[i], (float2*)p->X, (const float*)p->K, (const float2*)p->tw, p->stream);
+        };
+        run();
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // a candidate the device cannot launch is skipped
+            continue;
+        }
+        cudaEventRecord(a, p->stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; r++) run();
+        cudaEventRecord(b, p->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess || e != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best) {
+            best = ms;
+            besti = i;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    p->yz = cand[besti];
+    return BORIS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -359,23 +402,42 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "no CUDA device"));
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    const bool ok = p->f64 ? choose_yz_schedule<double>(g, max_smem, &p->yz) : choose_yz_schedule<float>(g, max_smem, &p->yz);
-    if (!ok) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));
-    if (const char* s = std::getenv("BORIS_YZ_CLUSTER")) {
-        // schedule override for tuning sweeps (power of two, <= 16 and <= py)
-        const int C = std::atoi(s);
-        if (C >= 1 && C <= 16 && (C & (C - 1)) == 0 && C <= g.py) {
-            YZSchedule t = p->yz;
-            t.C = C;
-            const int L = g.py / C;
-            t.Qc = std::min(L, t.Qc > 0 ? t.Qc : 16);
-            if (const char* q = std::getenv("BORIS_YZ_QC")) t.Qc = std::max(1, std::min(L, std::atoi(q)));
-            const size_t cs = p->f64 ? sizeof(double2) : sizeof(float2);
-            t.smem = 3 * (size_t)g.nz * L * cs + (g.pz > 1 ? 3 * (size_t)g.pz * t.Qc * cs : 0);
-            if (t.smem <= (size_t)max_smem) p->yz = t;
+    YZSchedule cand[16];
+    int ncand = 0;
+    if (p->f64) yz_candidates<double>(g, max_smem, cand, &ncand);
+    else yz_candidates<float>(g, max_smem, cand, &ncand);
+    if (ncand == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));
+    // optional override for tests and sweeps: BORIS_YZ_KIND / BORIS_YZ_CLUSTER / BORIS_YZ_THREADS / BORIS_YZ_QC
+    {
+        const char* sk = std::getenv("BORIS_YZ_KIND");
+        const char* sc = std::getenv("BORIS_YZ_CLUSTER");
+        const char* st = std::getenv("BORIS_YZ_THREADS");
+        const char* sq = std::getenv("BORIS_YZ_QC");
+        if (sk || sc || st) {
+            int m = 0;
+            for (int i = 0; i < ncand; i++) {
+                if (sk && cand[i].kind != std::atoi(sk)) continue;
+                if (sc && cand[i].C != std::atoi(sc)) continue;
+                if (st && cand[i].threads != std::atoi(st)) continue;
+                cand[m++] = cand[i];
+            }
+            if (m == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "no y-z schedule matches the override"));
+            ncand = m;
+        }
+        if (sq) {
+            for (int i = 0; i < ncand; i++) {
+                if (cand[i].kind != 0) continue;
+                const int L = g.py / cand[i].C;
+                cand[i].Qc = std::max(1, std::min(L, std::atoi(sq)));
+                const size_t cs = p->f64 ? sizeof(double2) : sizeof(float2);
+                cand[i].smem = 3 * (size_t)g.nz * L * cs + (g.pz > 1 ? 3 * (size_t)g.pz * cand[i].Qc * cs : 0);
+            }
         }
     }
-    cudaError_t ce = p->f64 ? yz_set_attributes<double>(p->yz) : yz_set_attributes<float>(p->yz);
+    p->yz = cand[0];
+    cudaError_t ce = p->f64 ? upload_twiddles_yz_f64() : upload_twiddles_yz_f32();
+    if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("twiddle constants: ") + cudaGetErrorString(ce)));
+    ce = p->f64 ? yz_set_attributes<double>(p->yz) : yz_set_attributes<float>(p->yz);
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("yz attributes: ") + cudaGetErrorString(ce)));
 
     // twiddles
@@ -405,6 +467,7 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     if ((rc = dev_alloc(p, &p->X, xelems * 2 * esz))) return bail(rc);
     if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
+    if (ncand > 1 && (rc = autotune_yz(p, cand, ncand))) return bail(rc);
     *out = p;
     return BORIS_OK;
 }
@@ -499,6 +562,16 @@ int boris_sync_status(boris_plan p)
     if (!p) return fail(BORIS_ERR_INVALID_ARG, "NULL plan");
     cudaError_t e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return fail(BORIS_ERR_CUDA, cudaGetErrorString(e));
+    return BORIS_OK;
+}
+
+int boris_plan_schedule(boris_plan p, int out[4])
+{
+    if (!p || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    out[0] = p->yz.kind;
+    out[1] = p->yz.C;
+    out[2] = p->yz.threads;
+    out[3] = (int)p->yz.smem;
     return BORIS_OK;
 }
 

@@ -381,26 +381,48 @@ static size_t yz_smem(const Geometry& g, int C, int Qc)
 }
 
 template <typename T>
-bool choose_yz_schedule(const Geometry& g, int max_smem, YZSchedule* out)
+void yz_candidates(const Geometry& g, int max_smem, YZSchedule* out, int* n)
 {
-    const int cmax = g.py < 16 ? g.py : 16;
-    // smallest cluster whose CTA fits two per SM, else the smallest that fits one
-    for (int budget : {max_smem / 2 - 2048, max_smem}) {
-        for (int C = 1; C <= cmax; C *= 2) {
+    int k = 0;
+    const size_t cs = sizeof(typename Cx<T>::t);
+    // register z stage: HZ = pz/2 in {0, 2, ..., 32}; L = py/C; 6L threads when pz > 1
+    const int hz = g.pz / 2;
+    const bool hz_ok = g.pz == 1 || (hz >= 2 && hz <= 32);
+    if (hz_ok) {
+        const int rows = hz > 0 ? hz : 1;
+        for (int C : {1, 8, 16}) {
+            if (C > g.py) continue;
             const int L = g.py / C;
-            int Qc = L < 16 ? L : 16;
-            if (Qc < 1) Qc = 1;
-            const size_t s = yz_smem<T>(g, C, Qc);
-            if (s <= (size_t)budget) {
-                out->C = C;
-                out->Qc = Qc;
-                out->threads = 256;
-                out->smem = s;
-                return true;
+            for (int NT : {384, 768}) {
+                if (sizeof(T) == 8 && NT > 384) continue;
+                if (g.pz > 1 && 6 * L > NT) continue;
+                if (g.pz == 1 && NT == 768) continue;
+                const size_t smem = ((size_t)g.lmax + 2 * 3 * (size_t)rows * (L + 1)) * cs;
+                if (smem > (size_t)max_smem) continue;
+                out[k++] = YZSchedule{1, C, 0, NT, smem};
             }
         }
     }
-    return false;
+    // shared-memory z stage: any nz
+    const int cmax = g.py < 16 ? g.py : 16;
+    for (int C = 1; C <= cmax; C *= 2) {
+        const int L = g.py / C;
+        const int Qc = L < 16 ? L : 16;
+        const size_t smem = yz_smem<T>(g, C, Qc);
+        if (smem <= (size_t)max_smem) out[k++] = YZSchedule{0, C, Qc, 256, smem};
+    }
+    *n = k;
+}
+
+template <typename T>
+bool choose_yz_schedule(const Geometry& g, int max_smem, YZSchedule* out)
+{
+    YZSchedule c[16];
+    int n = 0;
+    yz_candidates<T>(g, max_smem, c, &n);
+    if (n == 0) return false;
+    *out = c[0];
+    return true;
 }
 
 template <typename T, int CC>
@@ -437,6 +459,7 @@ static cudaError_t launch_yz_cc(const Geometry& g, const YZSchedule& sc, typenam
 template <typename T>
 cudaError_t yz_set_attributes(const YZSchedule& sc)
 {
+    if (sc.kind == 1) return cudaSuccess;  // set at each launch
     switch (sc.C) {
     case 1: return set_attr_cc<T, 1>(sc);
     case 2: return set_attr_cc<T, 2>(sc);
@@ -451,6 +474,7 @@ template <typename T>
 cudaError_t launch_yz_conv(const Geometry& g, const YZSchedule& sc, typename Cx<T>::t* X, const T* K,
                            const typename Cx<T>::t* tw, cudaStream_t st)
 {
+    if (sc.kind == 1) return launch_yz_reg<T>(g, sc, X, K, tw, st);
     switch (sc.C) {
     case 1: return launch_yz_cc<T, 1>(g, sc, X, K, tw, st);
     case 2: return launch_yz_cc<T, 2>(g, sc, X, K, tw, st);
@@ -468,6 +492,7 @@ cudaError_t launch_yz_conv(const Geometry& g, const YZSchedule& sc, typename Cx<
                                            const Cx<T>::t*, cudaStream_t);                                    \
     template cudaError_t launch_x_c2r<T>(const Geometry&, const Cx<T>::t*, T*, const Cx<T>::t*, cudaStream_t); \
     template bool choose_yz_schedule<T>(const Geometry&, int, YZSchedule*);                                   \
+    template void yz_candidates<T>(const Geometry&, int, YZSchedule*, int*);                                  \
     template cudaError_t yz_set_attributes<T>(const YZSchedule&);
 BORIS_INST(float)
 BORIS_INST(double)

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 namespace boris {
 
 template <typename T> struct Cx;
@@ -154,6 +156,77 @@ __device__ void fft_dit(C* buf, const Lines& ln, int lgL, int s_end, const C* tw
         else fft_pass<1, 1>(buf, ln, lgL, st, tw, twshift);
         __syncthreads();
     }
+}
+
+// exp(-2 pi i e / 128), e in [0, 128): the twiddles of every in-register
+// transform of length <= 128, read with compile-time indices (a constant-cache
+// broadcast).  Each translation unit that uses them holds its own copy and
+// fills it from host FP64 cos/sin with upload_small_twiddles_here().
+static __constant__ float2 c_w128f[128];
+static __constant__ double2 c_w128d[128];
+template <typename C> __device__ __forceinline__ C cw128(int e);
+template <> __device__ __forceinline__ float2 cw128<float2>(int e) { return c_w128f[e]; }
+template <> __device__ __forceinline__ double2 cw128<double2>(int e) { return c_w128d[e]; }
+
+// v * w_128^e for a compile-time e (exact for e = 0 and e = 32, i.e. 1 and -i).
+template <int DIR, typename C>
+__device__ __forceinline__ C twiddle128(C v, int e)
+{
+    if (e == 0) return v;
+    if (e == 32) return DIR < 0 ? C{v.y, -v.x} : C{-v.y, v.x};
+    const C w = cw128<C>(e);
+    return DIR < 0 ? c_mul(v, w) : c_mulc(v, w);
+}
+
+// In-register transform of length N <= 128 (power of two), fully unrolled.
+// DIR = -1: DIF, natural order in, bit-reversed out, w = exp(-2 pi i/N).
+// DIR = +1: DIT with conjugate twiddles, bit-reversed in, natural out
+// (unscaled inverse).
+template <int N, int DIR, typename C>
+__device__ __forceinline__ void reg_fft(C* v)
+{
+    if (DIR < 0) {
+#pragma unroll
+        for (int half = N / 2; half >= 1; half >>= 1) {
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                if ((j & half) == 0) {
+                    const int e = (j & (half - 1)) * (64 / half);  // w_{2 half}^{j mod half}
+                    const C a = v[j], b = v[j + half];
+                    v[j] = c_add(a, b);
+                    v[j + half] = twiddle128<-1>(c_sub(a, b), e);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int half = 1; half <= N / 2; half <<= 1) {
+#pragma unroll
+            for (int j = 0; j < N; j++) {
+                if ((j & half) == 0) {
+                    const int e = (j & (half - 1)) * (64 / half);
+                    const C a = v[j];
+                    const C b = twiddle128<1>(v[j + half], e);
+                    v[j] = c_add(a, b);
+                    v[j + half] = c_sub(a, b);
+                }
+            }
+        }
+    }
+}
+
+static inline cudaError_t upload_small_twiddles_here()
+{
+    float2 f[128];
+    double2 d[128];
+    for (int e = 0; e < 128; e++) {
+        const double a = 6.283185307179586476925286766559 * e / 128.0;
+        d[e] = make_double2(std::cos(a), -std::sin(a));
+        f[e] = make_float2((float)d[e].x, (float)d[e].y);
+    }
+    cudaError_t err = cudaMemcpyToSymbol(c_w128f, f, sizeof(f));
+    if (err != cudaSuccess) return err;
+    return cudaMemcpyToSymbol(c_w128d, d, sizeof(d));
 }
 
 }  // namespace boris

@@ -41,16 +41,39 @@ def test_demag_matches_oracle(n, h, fp64):
     assert err < (1e-9 if fp64 else 1e-5), err
 
 
-@pytest.mark.parametrize("C", [1, 2, 4, 8, 16])
-def test_cluster_schedules_agree(C, monkeypatch):
+SCHEDULE_MESHES = [
+    ((40, 64, 5), (2e-9, 2e-9, 3e-9)),    # pz = 16
+    ((24, 32, 17), (2e-9, 2e-9, 2e-9)),   # pz = 64, ragged nz
+    ((30, 16, 3), (1e-9, 2e-9, 3e-9)),    # pz = 8 > 2 nz
+    ((20, 48, 2), (2e-9, 2e-9, 2e-9)),    # pz = 4, ny not a power of two
+    ((64, 40, 1), (2e-9, 2e-9, 3e-9)),    # 2D mode
+]
+SCHEDULES = [(0, 1, None), (0, 2, None), (0, 4, None), (0, 8, None), (0, 16, None),
+             (1, 1, 384), (1, 1, 768), (1, 8, 384), (1, 8, 768), (1, 16, 384), (1, 16, 768)]
+
+
+@pytest.mark.parametrize("n,h", SCHEDULE_MESHES)
+@pytest.mark.parametrize("kind,C,NT", SCHEDULES)
+def test_every_yz_schedule_matches_oracle(n, h, kind, C, NT, monkeypatch):
+    """Each schedule of the fused y-z pass (shared-memory or register z stage,
+    1 to 16 CTAs per cluster) that fits the mesh gives the same field."""
     torch = torch_cuda()
-    from paper_2008_02478_gb300.binding import Plan
-    nx, ny, nz, h = 40, 64, 5, (2e-9, 2e-9, 3e-9)
+    from paper_2008_02478_gb300.binding import BorisError, Plan
+    nx, ny, nz = n
     M = 6e5 * inputs.random_unit(nx, ny, nz, seed=2)
     ref = oracle.DemagPlan(nx, ny, nz, *h).apply(M)
+    monkeypatch.setenv("BORIS_YZ_KIND", str(kind))
     monkeypatch.setenv("BORIS_YZ_CLUSTER", str(C))
-    monkeypatch.setenv("BORIS_YZ_QC", "7")  # ragged z-stage chunks
-    plan = Plan(nx, ny, nz, *h)
+    if NT:
+        monkeypatch.setenv("BORIS_YZ_THREADS", str(NT))
+    else:
+        monkeypatch.setenv("BORIS_YZ_QC", "7")  # ragged z-stage chunks
+    try:
+        plan = Plan(nx, ny, nz, *h)
+    except BorisError as e:
+        assert e.code == -4  # this schedule does not fit this mesh
+        pytest.skip("schedule does not fit")
+    assert plan.schedule()[:2] == (kind, C)
     H = plan.apply(to_dev(torch, M)).cpu().numpy()
     assert rel_l2(H, ref) < 1e-5
 
