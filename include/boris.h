@@ -86,6 +86,23 @@ int boris_demag_apply(boris_plan p, const float* M, float* Hd);
 int boris_demag_apply_f64(boris_plan p, const double* M, double* Hd);
 
 /*
+ * boris_demag_apply_noalloc - Hd = -N * M exactly as boris_demag_apply (FP32
+ *   plans), for callers that cannot allocate device memory while they run.
+ *   The paper has no counterpart: this serves runtimes whose allocator is
+ *   locked or forbidden on their hot path.  It allocates nothing: the spectral
+ *   workspace is a fixed 32 MiB device array inside the library (held by every
+ *   GPU that loads the library until the process exits), so it accepts meshes
+ *   with (px/2 + 1) * 3 * nz * ny * 8 bytes <= 32 MiB and returns
+ *   BORIS_ERR_UNSUPPORTED_SIZE for larger ones.  The plan (made at set-up)
+ *   still supplies the kernel spectrum.  The plan's device must be current.
+ *   The first call on a device looks up the array's device address; make that
+ *   first call before any stream capture.  All calls share the one array:
+ *   calls that overlap on the GPU race and corrupt each other's output.
+ *   Nothing in the array needs clearing: every call overwrites what it reads.
+ */
+int boris_demag_apply_noalloc(boris_plan p, const float* M, float* Hd);
+
+/*
  * boris_demag_adjoint - gM = (dHd/dM)^T gHd.  The demagnetising operator is
  *   self-adjoint (N_ij = N_ji and N(-r) = N(r)), so this is -N * gHd; the
  *   paper has no adjoint, this call serves gradient computations.

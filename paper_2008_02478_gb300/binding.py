@@ -26,7 +26,8 @@ MU0 = 4e-7 * math.pi
 GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
 
 #: entry points declared in include/boris.h
-EXPORTS = ["boris_demag_plan", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_adjoint",
+EXPORTS = ["boris_demag_plan", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_apply_noalloc",
+           "boris_demag_adjoint",
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
@@ -63,6 +64,7 @@ def lib():
         L.boris_demag_apply.argtypes = [vp, vp, vp]
         L.boris_demag_apply_f64.argtypes = [vp, vp, vp]
         L.boris_demag_adjoint.argtypes = [vp, vp, vp]
+        L.boris_demag_apply_noalloc.argtypes = [vp, vp, vp]
         L.boris_llg_step.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_llg_step_f64.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_llg_step_backward.argtypes = [vp, vp, P(LLGParamsC), d, vp, vp, vp, vp]

@@ -87,6 +87,18 @@ cudaError_t newell_octant(int nx, int ny, int nz, double dx, double dy, double d
 // Twiddle table exp(-2 pi i e / n), e in [0, n), on the host in FP64.
 void host_twiddles(int n, double2* out);
 
+// Read-only view of a plan's geometry, schedule and kernel spectrum (capi.cu).
+struct PlanView {
+    Geometry g;
+    YZSchedule yz;
+    bool f64;
+    cudaStream_t stream;
+    int device;
+    const void* K;
+    const void* tw;
+};
+bool plan_view(boris_plan p, PlanView* v);
+
 // Thread-local last error message (capi.cu).
 void set_error(const std::string& msg);
 

@@ -353,6 +353,22 @@ int autotune_yz(boris_plan p, const YZSchedule* cand, int ncand)
 
 }  // namespace
 
+namespace boris {
+// Read-only view of a plan for entry points defined in other files.
+bool plan_view(boris_plan p, PlanView* v)
+{
+    if (!p) return false;
+    v->g = p->g;
+    v->yz = p->yz;
+    v->f64 = p->f64;
+    v->stream = p->stream;
+    v->device = p->device;
+    v->K = p->K;
+    v->tw = p->tw;
+    return true;
+}
+}  // namespace boris
+
 extern "C" {
 
 const char* boris_last_error(void) { return g_last_error.c_str(); }
