@@ -126,6 +126,20 @@ def xpass_algorithmic_bytes(plan) -> int:
     return 3 * nx * ny * nz * es + (px // 2 + 1) * 3 * nz * ny * 2 * es
 
 
+def split_algorithmic_bytes(plan):
+    """y forward: read X, write the column-major padded spectrum Y; z
+    convolution: read and write Y and read the kernel octant; y inverse: read
+    Y, write X."""
+    nx, ny, nz = plan.shape
+    px, py, pz = plan.padded()
+    es = 8 if plan.fp64 else 4
+    nkx, kyh, kzh = px // 2 + 1, py // 2 + 1, pz // 2 + 1
+    xb = nkx * 3 * nz * ny * 2 * es
+    yb = nkx * py * 3 * nz * 2 * es
+    kb = nkx * kyh * kzh * 6 * es
+    return {"y_fwd": xb + yb, "z_conv": 2 * yb + kb, "y_inv": yb + xb}
+
+
 def llg_algorithmic_bytes(plan) -> float:
     """Average bytes per RK4 stage launch (no per-cell maps): 48, 72, 72, 60
     bytes per cell for the four stages in FP32 (m_s, Hd, m0, acc, next state)."""
@@ -281,6 +295,7 @@ def main():
     per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in kern.items()}
     algo = {"yz_conv": yz_algorithmic_bytes(plan), "x_r2c": xpass_algorithmic_bytes(plan),
             "x_c2r": xpass_algorithmic_bytes(plan), "llg_stage": llg_algorithmic_bytes(plan)}
+    algo.update(split_algorithmic_bytes(plan))
     peak, peak_kind = measured_peaks()
     dom_bytes = algo.get(dominant)
     achieved = dom_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9 if dom_bytes else None
@@ -341,7 +356,7 @@ def main():
                 "config": {"workload": WORKLOAD, "cells": ncell, "parallelism": "replicas" if world > 1 else "1 GPU",
                            "l2": "inputs larger than L2 (m 100.7 MB, spectrum workspace 201.7 MB, kernel "
                                  "spectrum 208.4 MB per evaluation)",
-                           "padded": plan.padded()},
+                           "padded": plan.padded(), "yz_schedule": plan.schedule()},
                 "demag_evals_per_s": demag_rate, "fp64": fp64, "roofline": roofline, "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)

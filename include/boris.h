@@ -92,8 +92,10 @@ int boris_demag_apply_f64(boris_plan p, const double* M, double* Hd);
  *   locked or forbidden on their hot path.  It allocates nothing: the spectral
  *   workspace is a fixed 32 MiB device array inside the library (held by every
  *   GPU that loads the library until the process exits), so it accepts meshes
- *   with (px/2 + 1) * 3 * nz * ny * 8 bytes <= 32 MiB and returns
- *   BORIS_ERR_UNSUPPORTED_SIZE for larger ones.  The plan (made at set-up)
+ *   whose spectral workspace - (px/2 + 1) * 3 * nz * ny * 8 bytes, plus
+ *   (px/2 + 1) * py * 3 * nz * 8 bytes when the plan chose the split y-z
+ *   schedule - fits in 32 MiB, and returns BORIS_ERR_UNSUPPORTED_SIZE for
+ *   larger ones.  The plan (made at set-up)
  *   still supplies the kernel spectrum.  The plan's device must be current.
  *   The first call on a device looks up the array's device address; make that
  *   first call before any stream capture.  All calls share the one array:
@@ -188,9 +190,11 @@ const char* boris_last_error(void);
 /* Padded transform lengths chosen by the plan: out[0..2] = px, py, pz. */
 int boris_plan_padded(boris_plan p, int out[3]);
 
-/* Schedule of the fused y-z pass chosen by the plan's autotuner: out[0] kind
- * (0: z stage through shared-memory passes, 1: z stage in registers), out[1]
- * CTAs per cluster, out[2] threads per CTA, out[3] shared memory per CTA. */
+/* Schedule of the y-z pass chosen by the plan's autotuner: out[0] kind
+ * (0: fused, z stage through shared-memory passes, 1: fused, z stage in registers,
+ * 2: split), out[1]
+ * CTAs per cluster, out[2] threads per CTA, out[3] shared memory per CTA;
+ * kind 2: split y-forward / z-convolution / y-inverse kernels). */
 int boris_plan_schedule(boris_plan p, int out[4]);
 
 /* Bytes of device memory owned by the plan. */
@@ -203,12 +207,13 @@ size_t boris_plan_device_bytes(boris_plan p);
  * boris_profile_read - synchronises, then returns per kernel class the summed
  *   device time in ms and the number of timed launches since the last read:
  *   [0] x real-to-complex, [1] fused y-z pass, [2] x complex-to-real,
- *   [3] LLG stage, [4] other (energies).  *total_launches (may be NULL)
+ *   [3] LLG stage, [4] other (energies), [5] y forward, [6] z convolution,
+ *   [7] y inverse (the last three: split y-z schedule).  *total_launches (may be NULL)
  *   receives every kernel launch counted since the last read, timed or not.
  *   Resets the counters.
  */
 int boris_profile_enable(boris_plan p, int on);
-int boris_profile_read(boris_plan p, double ms_out[5], long long launches_out[5], long long* total_launches);
+int boris_profile_read(boris_plan p, double ms_out[8], long long launches_out[8], long long* total_launches);
 
 /* Free the plan and everything it owns (NULL is ignored).  Synchronises. */
 void boris_plan_destroy(boris_plan p);

@@ -39,7 +39,8 @@ struct Geometry {
 
 // Launch schedule of the fused y-z spectral pass.
 struct YZSchedule {
-    int kind;     // 0: z stage through shared-memory passes; 1: z stage in registers
+    int kind;     // 0: fused, z stage through shared-memory passes; 1: fused, z stage in
+                  // registers; 2: split into y-forward, z-convolution and y-inverse kernels
     int C;        // CTAs per cluster (one cluster per kx plane); ky residues mod C
     int Qc;       // z-columns processed per chunk of the z stage
     int threads;  // threads per CTA
@@ -65,6 +66,14 @@ cudaError_t launch_yz_reg<float>(const Geometry& g, const YZSchedule& sc, float2
 template <>
 cudaError_t launch_yz_reg<double>(const Geometry& g, const YZSchedule& sc, double2* X, const double* K,
                                   const double2* tw, cudaStream_t st);
+// Split schedule (demag_split.cu): part 0 = y forward X -> Y, part 1 = z
+// transform + multiply + inverse z on Y, part 2 = y inverse Y -> X.
+template <typename T>
+bool split_supported(const Geometry& g, int max_smem);
+template <typename T>
+cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const T* K,
+                         const typename Cx<T>::t* tw, cudaStream_t st, int part);
+cudaError_t upload_twiddles_split();
 cudaError_t upload_twiddles_yz_f32();
 cudaError_t upload_twiddles_yz_f64();
 // Candidate schedules of the fused y-z pass that fit this geometry.
@@ -97,6 +106,8 @@ struct PlanView {
     const void* K;
     const void* tw;
 };
+// Number of kernel classes timed by the plan's profiler.
+constexpr int NPROF = 8;
 bool plan_view(boris_plan p, PlanView* v);
 
 // Thread-local last error message (capi.cu).

@@ -32,6 +32,8 @@ struct boris_plan_s {
     double2* tw64 = nullptr;
     // spectral workspace [kx][c][z][y]
     void* X = nullptr;
+    // column-major padded spectrum [kx][ky][c][z] of the split schedule
+    void* Y = nullptr;
     // LLG workspace (allocated on first use)
     void* Hd = nullptr;
     void* msa = nullptr;
@@ -116,11 +118,26 @@ cudaError_t timed(boris_plan p, int kind, F&& launch)
 }
 
 template <typename T>
+cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
+{
+    using C = typename Cx<T>::t;
+    if (sc.kind == 2) {
+        cudaError_t e = cudaSuccess;
+        for (int part = 0; part < 3 && e == cudaSuccess; part++)
+            e = timed(p, 5 + part, [&] {
+                return launch_split<T>(p->g, (C*)p->X, (C*)p->Y, (const T*)p->K, (const C*)p->tw, p->stream, part);
+            });
+        return e;
+    }
+    return timed(p, 1, [&] { return launch_yz_conv<T>(p->g, sc, (C*)p->X, (const T*)p->K, (const C*)p->tw, p->stream); });
+}
+
+template <typename T>
 int demag_apply_t(boris_plan p, const T* M, const T* ms_map, T ms_scale, T* H)
 {
     using C = typename Cx<T>::t;
     CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<T>(p->g, M, ms_map, ms_scale, (C*)p->X, (const C*)p->tw, p->stream); }));
-    CUDA_TRY(timed(p, 1, [&] { return launch_yz_conv<T>(p->g, p->yz, (C*)p->X, (const T*)p->K, (const C*)p->tw, p->stream); }));
+    CUDA_TRY(yz_stage<T>(p, p->yz));
     CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<T>(p->g, (const C*)p->X, H, (const C*)p->tw, p->stream); }));
     return BORIS_OK;
 }
@@ -322,10 +339,7 @@ int autotune_yz(boris_plan p, const YZSchedule* cand, int ncand)
     int besti = 0;
     for (int i = 0; i < ncand; i++) {
         cudaError_t e = cudaSuccess;
-        auto run = [&]() {
-            if (p->f64) e = launch_yz_conv<double>(p->g, cand[i], (double2*)p->X, (const double*)p->K, (const double2*)p->tw, p->stream);
-            else e = launch_yz_conv<float>(p->g, cand[i], (float2*)p->X, (const float*)p->K, (const float2*)p->tw, p->stream);
-        };
+        auto run = [&]() { e = p->f64 ? yz_stage<double>(p, cand[i]) : yz_stage<float>(p, cand[i]); };
         run();
         if (e != cudaSuccess) {
             cudaGetLastError();  // a candidate the device cannot launch is skipped
@@ -422,6 +436,8 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     int ncand = 0;
     if (p->f64) yz_candidates<double>(g, max_smem, cand, &ncand);
     else yz_candidates<float>(g, max_smem, cand, &ncand);
+    const bool split_ok = p->f64 ? split_supported<double>(g, max_smem) : split_supported<float>(g, max_smem);
+    if (split_ok && ncand < 16) cand[ncand++] = YZSchedule{2, 0, 0, 0, 0};
     if (ncand == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));
     // optional override for tests and sweeps: BORIS_YZ_KIND / BORIS_YZ_CLUSTER / BORIS_YZ_THREADS / BORIS_YZ_QC
     {
@@ -452,6 +468,7 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     }
     p->yz = cand[0];
     cudaError_t ce = p->f64 ? upload_twiddles_yz_f64() : upload_twiddles_yz_f32();
+    if (ce == cudaSuccess) ce = upload_twiddles_split();
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("twiddle constants: ") + cudaGetErrorString(ce)));
     ce = p->f64 ? yz_set_attributes<double>(p->yz) : yz_set_attributes<float>(p->yz);
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("yz attributes: ") + cudaGetErrorString(ce)));
@@ -481,6 +498,21 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     // spectral workspace
     const size_t xelems = (size_t)g.nkx * 3 * g.nz * g.ny;
     if ((rc = dev_alloc(p, &p->X, xelems * 2 * esz))) return bail(rc);
+    bool want_y = false;
+    for (int i = 0; i < ncand; i++) want_y |= cand[i].kind == 2;
+    if (want_y) {
+        const size_t yelems = (size_t)g.nkx * g.py * 3 * g.nz;
+        if (dev_alloc(p, &p->Y, yelems * 2 * esz) != BORIS_OK) {
+            // no room for the split schedule: drop it
+            cudaGetLastError();
+            int m = 0;
+            for (int i = 0; i < ncand; i++)
+                if (cand[i].kind != 2) cand[m++] = cand[i];
+            ncand = m;
+            if (ncand == 0) return bail(fail(BORIS_ERR_OOM, "no memory for the y-z workspace"));
+            p->yz = cand[0];
+        }
+    }
     if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
     if (ncand > 1 && (rc = autotune_yz(p, cand, ncand))) return bail(rc);
@@ -609,17 +641,18 @@ int boris_profile_enable(boris_plan p, int on)
     return BORIS_OK;
 }
 
-int boris_profile_read(boris_plan p, double ms_out[5], long long launches_out[5], long long* total_launches)
+int boris_profile_read(boris_plan p, double ms_out[8], long long launches_out[8], long long* total_launches)
 {
     if (!p || !ms_out || !launches_out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
     CUDA_TRY(cudaStreamSynchronize(p->stream));
-    for (int k = 0; k < 5; k++) {
+    for (int k = 0; k < NPROF; k++) {
         ms_out[k] = 0.0;
         launches_out[k] = 0;
     }
     for (auto& u : p->ev_used) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, u.second.first, u.second.second) == cudaSuccess && u.first >= 0 && u.first < 5) {
+        if (cudaEventElapsedTime(&ms, u.second.first, u.second.second) == cudaSuccess && u.first >= 0 &&
+            u.first < NPROF) {
             ms_out[u.first] += ms;
             launches_out[u.first]++;
         }
@@ -636,7 +669,7 @@ void boris_plan_destroy(boris_plan p)
 {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
-    void* ptrs[] = {p->K, p->X, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
+    void* ptrs[] = {p->K, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
                     p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);

@@ -73,7 +73,11 @@ extern "C" int boris_demag_apply_noalloc(boris_plan p, const float* M, float* Hd
         set_error("M and Hd must be 16-byte aligned and distinct");
         return BORIS_ERR_INVALID_ARG;
     }
-    const size_t need = (size_t)v.g.nkx * 3 * v.g.nz * v.g.ny * sizeof(float2);
+    const size_t xbytes = (size_t)v.g.nkx * 3 * v.g.nz * v.g.ny * sizeof(float2);
+    // the split y-z schedule also needs the column-major padded spectrum
+    const size_t ybytes = v.yz.kind == 2 ? (size_t)v.g.nkx * v.g.py * 3 * v.g.nz * sizeof(float2) : 0;
+    const size_t xoff = (xbytes + 255) & ~(size_t)255;
+    const size_t need = xoff + ybytes;
     if (need > NOALLOC_SCRATCH_BYTES) {
         set_error("mesh spectrum needs " + std::to_string(need) + " bytes; the allocation-free workspace holds " +
                   std::to_string(NOALLOC_SCRATCH_BYTES) + " bytes (use boris_demag_apply)");
@@ -87,12 +91,20 @@ extern "C" int boris_demag_apply_noalloc(boris_plan p, const float* M, float* Hd
     }
     float2* X = (float2*)scratch_address(dev);
     if (!X) return BORIS_ERR_CUDA;
-    // every element of the workspace is written by the forward x transform
-    // before it is read, so nothing needs clearing between calls
+    // every element of the workspace is written before it is read (X by the
+    // forward x transform, Y by the y-forward kernel), so nothing needs
+    // clearing between calls
     const float2* tw = (const float2*)v.tw;
-    if ((e = launch_x_r2c<float>(v.g, M, nullptr, 1.0f, X, tw, v.stream)) == cudaSuccess &&
-        (e = launch_yz_conv<float>(v.g, v.yz, X, (const float*)v.K, tw, v.stream)) == cudaSuccess)
-        e = launch_x_c2r<float>(v.g, X, Hd, tw, v.stream);
+    float2* Y = (float2*)((unsigned char*)X + xoff);
+    if ((e = launch_x_r2c<float>(v.g, M, nullptr, 1.0f, X, tw, v.stream)) == cudaSuccess) {
+        if (v.yz.kind == 2) {
+            for (int part = 0; part < 3 && e == cudaSuccess; part++)
+                e = launch_split<float>(v.g, X, Y, (const float*)v.K, tw, v.stream, part);
+        } else {
+            e = launch_yz_conv<float>(v.g, v.yz, X, (const float*)v.K, tw, v.stream);
+        }
+    }
+    if (e == cudaSuccess) e = launch_x_c2r<float>(v.g, X, Hd, tw, v.stream);
     if (e != cudaSuccess) {
         set_error(std::string("demag kernels: ") + cudaGetErrorString(e));
         return BORIS_ERR_CUDA;
