@@ -34,6 +34,8 @@ struct Geometry {
     int lgx, lgy, lgz;
     int nkx;              // px/2 + 1 spectral planes kept by the real transform
     int kyh, kzh;         // py/2 + 1, pz/2 + 1 (octant extent of the kernel spectrum)
+    int krow;             // floats per (kx, ky') row of the kernel spectrum: kzh * 6 rounded
+                          // up to a multiple of 4 (16-byte rows; the pad is zero)
     int lmax, lglmax;     // twiddle table length
 };
 
@@ -85,7 +87,8 @@ template <typename T>
 cudaError_t yz_set_attributes(const YZSchedule& sc);
 
 // Newell tensor precompute (newell.cu): writes the kernel spectrum K in the
-// layout [kx][ky'][kz'][6] (octant, FP32 or FP64), already scaled by
+// layout [kx][ky'][krow] with (kz', component) at kz' * 6 + component (octant,
+// FP32 or FP64), already scaled by
 // -1/(px py pz) so that the inverse transforms yield H = -N * M.
 cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, double dz, double rs,
                                   void* K_out, bool k_is_f64, const double2* tw64, cudaStream_t st);

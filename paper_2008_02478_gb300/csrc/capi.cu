@@ -411,6 +411,7 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     g.nkx = g.px / 2 + 1;
     g.kyh = g.py / 2 + 1;
     g.kzh = g.pz / 2 + 1;
+    g.krow = (g.kzh * 6 + 3) / 4 * 4;
     g.lmax = std::max(g.px, std::max(g.py, std::max(g.pz, 32)));
     g.lglmax = ilog2(g.lmax);
     if ((size_t)3 * nx * ny * nz > (size_t)1 << 31) return fail(BORIS_ERR_UNSUPPORTED_SIZE, "mesh too large");
@@ -489,7 +490,7 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
             return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
     }
     // kernel spectrum
-    const size_t kelems = (size_t)g.nkx * g.kyh * g.kzh * 6;
+    const size_t kelems = (size_t)g.nkx * g.kyh * g.krow;
     const size_t esz = p->f64 ? sizeof(double) : sizeof(float);
     if ((rc = dev_alloc(p, &p->K, kelems * esz))) return bail(rc);
     const double rs = 40.0;

@@ -53,14 +53,26 @@ __global__ void __launch_bounds__(256) x_r2c_kernel(Geometry g, const T* __restr
     if (px == 1) {
         for (int t = threadIdx.x; t < HL; t += blockDim.x) buf[t] = C{val(t, 0), val(t + HL, 0)};
     } else {
-        // pruned first DIF stage: the upper half of every padded line is zero
+        // pruned first DIF stage: the upper half of every padded line is zero;
+        // row t of the tile goes to the real part of line t % HL (t < HL) or
+        // its imaginary part (t >= HL)
         const int half = px >> 1;
         const int sh = g.lglmax - g.lgx;
+        const int nrow = min(TY, ny - y0);
+        for (int i = threadIdx.x; i < HL * half; i += blockDim.x) buf[(i / half) * px + i % half] = C{T(0), T(0)};
+        __syncthreads();
+        const T* base = Mc + ((size_t)z * ny + y0) * nx;  // nrow contiguous rows
+        const T* mbase = ms_map ? ms_map + ((size_t)z * ny + y0) * nx : nullptr;
+        staged_loop<256, T>(nrow * nx, [&](int i) { return mbase ? base[i] * mbase[i] : base[i] * ms_scale; },
+                            [&](int i, T v) {
+                                const int row = i / nx, x = i % nx;
+                                T* slot = reinterpret_cast<T*>(&buf[(row % HL) * px + x]) + (row >= HL ? 1 : 0);
+                                *slot = v;
+                            });
+        __syncthreads();
         for (int i = threadIdx.x; i < HL * half; i += blockDim.x) {
             const int t = i / half, o = i % half;
-            const C a = C{val(t, o), val(t + HL, o)};
-            buf[t * px + o] = a;
-            buf[t * px + o + half] = c_mul(a, tw[o << sh]);
+            buf[t * px + o + half] = c_mul(buf[t * px + o], tw[o << sh]);
         }
     }
     __syncthreads();
@@ -99,12 +111,20 @@ __global__ void __launch_bounds__(256) x_c2r_kernel(Geometry g, const typename C
     const int y0 = blockIdx.x * TY, z = blockIdx.y, c = blockIdx.z;
     const int px = g.px, nx = g.nx, ny = g.ny, nz = g.nz;
     const int nkx = g.nkx;
-    for (int i = threadIdx.x; i < nkx * HL; i += blockDim.x) {
+    struct AB {
+        C a, b;
+    };
+    staged_loop<256, AB>(nkx * HL, [&](int i) {
         const int t = i % HL, kx = i / HL;
         const int ya = y0 + t, yb = y0 + t + HL;
         const size_t rowbase = ((size_t)kx * 3 + c) * nz + z;
-        C A = ya < ny ? X[rowbase * ny + ya] : C{T(0), T(0)};
-        C B = yb < ny ? X[rowbase * ny + yb] : C{T(0), T(0)};
+        AB r;
+        r.a = ya < ny ? X[rowbase * ny + ya] : C{T(0), T(0)};
+        r.b = yb < ny ? X[rowbase * ny + yb] : C{T(0), T(0)};
+        return r;
+    }, [&](int i, AB r) {
+        const int t = i % HL, kx = i / HL;
+        const C A = r.a, B = r.b;
         const int km = (px - kx) & (px - 1);
         if (kx == 0 || kx == km) {
             // DC and Nyquist bins of a real signal are real
@@ -113,7 +133,7 @@ __global__ void __launch_bounds__(256) x_c2r_kernel(Geometry g, const typename C
             buf[t * px + bitrev(kx, g.lgx)] = C{A.x - B.y, A.y + B.x};
             buf[t * px + bitrev(km, g.lgx)] = C{A.x + B.y, B.x - A.y};
         }
-    }
+    });
     __syncthreads();
     if (px > 1) {
         Lines ln{HL, HL, px, 0, 1, false};
@@ -213,11 +233,11 @@ __global__ void __launch_bounds__(256) yz_conv_kernel(Geometry g, int Qc, typena
 
     // ---- 3: z stage and kernel multiply, Qc columns at a time ---------------
     const int kyh = g.kyh, kzh = g.kzh;
-    const T* Kx = K + (size_t)kx * kyh * kzh * 6;
+    const T* Kx = K + (size_t)kx * kyh * g.krow;
     auto kernel_at = [&](int ky, int kz, T k[6]) {
         const bool fy = ky > py / 2, fz = kz > pz / 2;
         const int kyf = fy ? py - ky : ky, kzf = fz ? pz - kz : kz;
-        const T* kp = Kx + ((size_t)kyf * kzh + kzf) * 6;
+        const T* kp = Kx + (size_t)kyf * g.krow + kzf * 6;
 #pragma unroll
         for (int i = 0; i < 6; i++) k[i] = kp[i];
         if (fy) { k[3] = -k[3]; k[5] = -k[5]; }
@@ -459,7 +479,7 @@ static cudaError_t launch_yz_cc(const Geometry& g, const YZSchedule& sc, typenam
 template <typename T>
 cudaError_t yz_set_attributes(const YZSchedule& sc)
 {
-    if (sc.kind == 1) return cudaSuccess;  // set at each launch
+    if (sc.kind != 0) return cudaSuccess;  // set at each launch
     switch (sc.C) {
     case 1: return set_attr_cc<T, 1>(sc);
     case 2: return set_attr_cc<T, 2>(sc);

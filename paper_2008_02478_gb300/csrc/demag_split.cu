@@ -19,7 +19,6 @@
 namespace boris {
 
 constexpr int YG = 8;  // lines per CTA in the y kernels
-
 template <typename T>
 __global__ void __launch_bounds__(256) y_fwd_kernel(Geometry g, const typename Cx<T>::t* __restrict__ X,
                                                     typename Cx<T>::t* __restrict__ Y,
@@ -42,12 +41,17 @@ __global__ void __launch_bounds__(256) y_fwd_kernel(Geometry g, const typename C
         // pruned first DIF stage: entries y >= ny (>= py/2) are zero
         const int half = py >> 1;
         __syncthreads();
-        for (int i = threadIdx.x; i < nl * half; i += blockDim.x) {
-            const int l = i / half, o = i % half;
-            const C a = o < ny ? src[(size_t)l * ny + o] : C{T(0), T(0)};
+        for (int i = threadIdx.x; i < nl * (half - ny); i += blockDim.x) {
+            const int l = i / (half - ny), o = ny + i % (half - ny);
+            buf[l * LP + o] = C{T(0), T(0)};
+            buf[l * LP + o + half] = C{T(0), T(0)};
+        }
+        // the nl source lines are contiguous: nl * ny complex values
+        staged_loop<256, C>(nl * ny, [&](int i) { return src[i]; }, [&](int i, C a) {
+            const int l = i / ny, o = i % ny;
             buf[l * LP + o] = a;
             buf[l * LP + o + half] = c_mul(a, tw[o]);
-        }
+        });
     }
     __syncthreads();
     if (py > 1) {
@@ -78,10 +82,9 @@ __global__ void __launch_bounds__(256) y_inv_kernel(Geometry g, const typename C
     const int shy = g.lglmax - g.lgy;
     for (int i = threadIdx.x; i < py; i += blockDim.x) tw[i] = tw_g[i << shy];
     const C* src = Y + (size_t)kx * py * lines + l0;
-    for (int i = threadIdx.x; i < py * nl; i += blockDim.x) {
-        const int l = i % nl, ky = i / nl;
-        buf[l * LP + bitrev(ky, g.lgy)] = src[(size_t)ky * lines + l];
-    }
+    staged_loop<256, C>(py * nl, [&](int i) { return src[(size_t)(i / nl) * lines + i % nl]; }, [&](int i, C a) {
+        buf[(i % nl) * LP + bitrev(i / nl, g.lgy)] = a;
+    });
     __syncthreads();
     if (py > 1) {
         Lines ln{nl, nl, LP, 0, 1, true};
@@ -203,26 +206,36 @@ __global__ void __launch_bounds__(QC * 6) z_conv_kernel(Geometry g, typename Cx<
     const int kx = blockIdx.y, ky0 = blockIdx.x * QC;
     const int ncol = min(QC, py - ky0);
     const int CS = 3 * HZ + 1;  // column stride (odd: bank spread)
-    const int KS = g.kzh * 6 + 1;
+    const int KS = g.krow + 1;
     C* tile = reinterpret_cast<C*>(smem_raw);     // [QC][CS]
     C* odd = tile + QC * CS;                      // [QC][CS]
     T* Ks = reinterpret_cast<T*>(odd + QC * CS);  // [QC][KS]
     C* col0 = Y + ((size_t)kx * py + ky0) * lines;
     // stage the columns (contiguous in Y) and their kernel rows; the columns
     // of a ragged last tile are zero and never written back
-    for (int i = threadIdx.x; i < QC * lines; i += blockDim.x) {
+    auto tpos = [&](int i) {
         const int col = i / lines, r = i % lines;
-        const int c = r / nz, z = r % nz;
-        tile[col * CS + c * HZ + z] = col < ncol ? col0[i] : C{T(0), T(0)};
-    }
-    const T* Kx = K + (size_t)kx * g.kyh * g.kzh * 6;
-    const int rowlen = g.kzh * 6;
-    for (int i = threadIdx.x; i < QC * rowlen; i += blockDim.x) {
-        const int col = i / rowlen, o = i % rowlen;
+        return col * CS + (r / nz) * HZ + r % nz;
+    };
+    staged_loop<QC * 6, C>(ncol * lines, [&](int i) { return col0[i]; }, [&](int i, C a) { tile[tpos(i)] = a; });
+    for (int i = ncol * lines + threadIdx.x; i < QC * lines; i += blockDim.x) tile[tpos(i)] = C{T(0), T(0)};
+    // kernel rows: krow floats (a multiple of 4: 16-byte vectors)
+    const T* Kx = K + (size_t)kx * g.kyh * g.krow;
+    const int vrow = g.krow * (int)sizeof(T) / 16;  // 16-byte vectors per row
+    staged_loop<QC * 6, float4>(ncol * vrow, [&](int i) {
+        const int col = i / vrow, o = i % vrow;
         const int ky = ky0 + col;
         const int kyf = ky > py / 2 ? py - ky : ky;
-        Ks[col * KS + o] = col < ncol ? Kx[(size_t)kyf * rowlen + o] : T(0);
-    }
+        return reinterpret_cast<const float4*>(Kx + (size_t)kyf * g.krow)[o];
+    }, [&](int i, float4 v4) {
+        const int col = i / vrow, o = i % vrow;
+        const T* e = reinterpret_cast<const T*>(&v4);
+        constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+        for (int k = 0; k < PER; k++) Ks[col * KS + o * PER + k] = e[k];
+    });
+    for (int i = ncol * g.krow + threadIdx.x; i < QC * g.krow; i += blockDim.x)
+        Ks[(i / g.krow) * KS + i % g.krow] = T(0);
     __syncthreads();
     const int warp = threadIdx.x >> 5, col = threadIdx.x & 31;
     C v[HZ];
@@ -264,7 +277,7 @@ __global__ void __launch_bounds__(256) z_mult_kernel(Geometry g, typename Cx<T>:
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < ncol; i += (size_t)gridDim.x * blockDim.x) {
         const int kx = (int)(i / py), ky = (int)(i % py);
         const bool fy = ky > py / 2;
-        const T* k = K + ((size_t)kx * g.kyh + (fy ? py - ky : ky)) * 6;
+        const T* k = K + ((size_t)kx * g.kyh + (fy ? py - ky : ky)) * g.krow;
         const T kxx = k[0], kyy = k[1], kzz = k[2];
         const T kxy = fy ? -k[3] : k[3], kxz = k[4], kyz = fy ? -k[5] : k[5];
         C* col = Y + i * 3;
@@ -285,7 +298,7 @@ template <typename T>
 size_t split_z_smem(const Geometry& g)
 {
     const int hz = g.pz / 2;
-    return (2 * (size_t)QC * (3 * hz + 1)) * sizeof(typename Cx<T>::t) + (size_t)QC * (g.kzh * 6 + 1) * sizeof(T);
+    return (2 * (size_t)QC * (3 * hz + 1)) * sizeof(typename Cx<T>::t) + (size_t)QC * (g.krow + 1) * sizeof(T);
 }
 
 template <typename T>

@@ -158,6 +158,29 @@ __device__ void fft_dit(C* buf, const Lines& ln, int lgL, int s_end, const C* tw
     }
 }
 
+constexpr int UNR = 8;  // independent global loads in flight per thread in staging loops
+
+// Staging loops: every thread issues UNR independent loads before it uses any
+// of them, so enough bytes are in flight per SM to cover HBM latency.
+// f(i) loads element i; g(i, v) consumes it.
+template <int NT, typename V, typename Load, typename Use>
+__device__ __forceinline__ void staged_loop(int n, Load f, Use g)
+{
+    for (int b = threadIdx.x; b < n; b += NT * UNR) {
+        V r[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const int i = b + u * NT;
+            if (i < n) r[u] = f(i);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; u++) {
+            const int i = b + u * NT;
+            if (i < n) g(i, r[u]);
+        }
+    }
+}
+
 // exp(-2 pi i e / 128), e in [0, 128): the twiddles of every in-register
 // transform of length <= 128, read with compile-time indices (a constant-cache
 // broadcast).  Each translation unit that uses them holds its own copy and

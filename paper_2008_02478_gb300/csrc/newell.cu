@@ -15,7 +15,8 @@
 //    and y; xz odd in x and z; yz odd in y and z), transforms it with the
 //    shared-memory FFT in FP64, and keeps the first P/2 + 1 bins.
 // 3. finalize: the spectrum is real (even or odd-odd symmetric sequences);
-//    store -Re / (px py pz) as [kx][ky][kz][6] in FP32 or FP64.
+//    store -Re / (px py pz) as rows [kx][ky] of kz * 6 + component (row
+//    length padded to a multiple of 4 with zeros) in FP32 or FP64.
 #include "boris_internal.cuh"
 
 namespace boris {
@@ -221,18 +222,23 @@ __global__ void __launch_bounds__(256) axis_pass_kernel(const void* __restrict__
 }
 
 template <typename T>
-__global__ void finalize_kernel(const double2* __restrict__ S, T* __restrict__ K, int nkx, int kyh, int kzh,
+__global__ void finalize_kernel(const double2* __restrict__ S, T* __restrict__ K, int nkx, int kyh, int kzh, int krow,
                                 double scale)
 {
     const size_t n = (size_t)nkx * kyh * kzh;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n * 6; idx += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(idx % 6);
-        const size_t cell = idx / 6;  // = (kx * kyh + ky) * kzh + kz
-        const int kz = (int)(cell % kzh);
-        const int ky = (int)((cell / kzh) % kyh);
-        const int kx = (int)(cell / ((size_t)kzh * kyh));
-        const double v = S[(size_t)c * n + ((size_t)kz * kyh + ky) * nkx + kx].x;
-        K[idx] = (T)(-v * scale);
+    const size_t total = (size_t)nkx * kyh * krow;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int o = (int)(idx % krow);
+        const size_t row = idx / krow;  // = kx * kyh + ky
+        const int ky = (int)(row % kyh);
+        const int kx = (int)(row / kyh);
+        T val = T(0);  // row padding
+        if (o < kzh * 6) {
+            const int kz = o / 6, c = o % 6;
+            const double v = S[(size_t)c * n + ((size_t)kz * kyh + ky) * nkx + kx].x;
+            val = (T)(-v * scale);
+        }
+        K[idx] = val;
     }
 }
 
@@ -298,11 +304,11 @@ cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, doubl
         if ((e = cudaMallocAsync((void**)&A, c_elems * sizeof(double2), st)) != cudaSuccess) break;
         if ((e = run_axis(B, false, A, 2, g.nkx, g.kyh, g.nz, g.nz, g.pz, tw64, g.lglmax, st)) != cudaSuccess) break;
         const double scale = 1.0 / ((double)g.px * g.py * g.pz);
-        const size_t tot = c_elems;
+        const size_t tot = (size_t)g.nkx * g.kyh * g.krow;
         int blocks = (int)((tot + 255) / 256);
         if (blocks > 152 * 64) blocks = 152 * 64;
-        if (k_is_f64) finalize_kernel<double><<<blocks, 256, 0, st>>>(A, (double*)K_out, g.nkx, g.kyh, g.kzh, scale);
-        else finalize_kernel<float><<<blocks, 256, 0, st>>>(A, (float*)K_out, g.nkx, g.kyh, g.kzh, scale);
+        if (k_is_f64) finalize_kernel<double><<<blocks, 256, 0, st>>>(A, (double*)K_out, g.nkx, g.kyh, g.kzh, g.krow, scale);
+        else finalize_kernel<float><<<blocks, 256, 0, st>>>(A, (float*)K_out, g.nkx, g.kyh, g.kzh, g.krow, scale);
         e = cudaGetLastError();
     } while (0);
     if (T) cudaFreeAsync(T, st);

@@ -79,13 +79,13 @@ __global__ void __launch_bounds__(NT) yz_conv_reg_kernel(Geometry g, typename Cx
 
     // ---- 3: z stage in registers and kernel multiply ------------------------
     const int kyh = g.kyh, kzh = g.kzh;
-    const T* Kx = K + (size_t)kx * kyh * kzh * 6;
+    const T* Kx = K + (size_t)kx * kyh * g.krow;
     if constexpr (HZ == 0) {
         // 2D mode: one row per component, multiply only
         for (int q = tid; q < L; q += NT) {
             const int ky = r + CC * bitrev(q, lgL);
             const bool fy = ky > py / 2;
-            const C* kp = reinterpret_cast<const C*>(Kx + (size_t)(fy ? py - ky : ky) * kzh * 6);
+            const C* kp = reinterpret_cast<const C*>(Kx + (size_t)(fy ? py - ky : ky) * g.krow);
             const C k01 = kp[0], k23 = kp[1], k45 = kp[2];  // (xx,yy) (zz,xy) (xz,yz)
             const T kxx = k01.x, kyy = k01.y, kzz = k23.x;
             const T kxy = fy ? -k23.y : k23.y, kxz = k45.x, kyz = fy ? -k45.y : k45.y;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(NT) yz_conv_reg_kernel(Geometry g, typename Cx
         if (active) {
             const int ky = r + CC * bitrev(q, lgL);
             const bool fy = ky > py / 2;
-            const T* Kr = Kx + (size_t)(fy ? py - ky : ky) * kzh * 6;
+            const T* Kr = Kx + (size_t)(fy ? py - ky : ky) * g.krow;
             // row c of the symmetric kernel: (xx xy xz) (xy yy yz) (xz yz zz)
             const int i0c = c == 0 ? 0 : c == 1 ? 3 : 4;
             const int i1c = c == 0 ? 3 : c == 1 ? 1 : 5;
