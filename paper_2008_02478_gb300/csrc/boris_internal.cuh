@@ -69,13 +69,29 @@ template <>
 cudaError_t launch_yz_reg<double>(const Geometry& g, const YZSchedule& sc, double2* X, const double* K,
                                   const double2* tw, cudaStream_t st);
 // Split schedule (demag_split.cu): part 0 = y forward X -> Y, part 1 = z
-// transform + multiply + inverse z on Y, part 2 = y inverse Y -> X.
+// transform + multiply + inverse z on Y, part 2 = y inverse Y -> X, with the
+// padded spectrum Y laid out [kx][c][z][ky] (ky fastest).
 template <typename T>
 bool split_supported(const Geometry& g, int max_smem);
 template <typename T>
 cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const T* K,
                          const typename Cx<T>::t* tw, cudaStream_t st, int part);
 cudaError_t upload_twiddles_split();
+// Warp-per-line kernels for transform length 1024 (demag_fast.cu).
+template <typename T>
+bool x1024_ok(const Geometry& g, int max_smem);
+template <typename T>
+bool y1024_ok(const Geometry& g, int max_smem);
+template <typename T>
+cudaError_t launch_x_r2c_1024(const Geometry& g, const T* M, const T* ms_map, T ms_scale, typename Cx<T>::t* X,
+                              const typename Cx<T>::t* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_x_c2r_1024(const Geometry& g, const typename Cx<T>::t* X, T* H, const typename Cx<T>::t* tw,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
+                          cudaStream_t st, bool forward);
+cudaError_t upload_twiddles_fast();
 cudaError_t upload_twiddles_yz_f32();
 cudaError_t upload_twiddles_yz_f64();
 // Candidate schedules of the fused y-z pass that fit this geometry.

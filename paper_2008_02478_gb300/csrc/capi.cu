@@ -470,6 +470,7 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     p->yz = cand[0];
     cudaError_t ce = p->f64 ? upload_twiddles_yz_f64() : upload_twiddles_yz_f32();
     if (ce == cudaSuccess) ce = upload_twiddles_split();
+    if (ce == cudaSuccess) ce = upload_twiddles_fast();
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("twiddle constants: ") + cudaGetErrorString(ce)));
     ce = p->f64 ? yz_set_attributes<double>(p->yz) : yz_set_attributes<float>(p->yz);
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("yz attributes: ") + cudaGetErrorString(ce)));

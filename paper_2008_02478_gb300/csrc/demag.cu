@@ -360,6 +360,7 @@ template <typename T>
 cudaError_t launch_x_r2c(const Geometry& g, const T* M, const T* ms_map, T ms_scale,
                          typename Cx<T>::t* X, const typename Cx<T>::t* tw, cudaStream_t st)
 {
+    if (x1024_ok<T>(g, 227 * 1024)) return launch_x_r2c_1024<T>(g, M, ms_map, ms_scale, X, tw, st);
     switch (xrow_tile<T>(g)) {
     case 16: return launch_r2c_ty<T, 16>(g, M, ms_map, ms_scale, X, tw, st);
     case 8: return launch_r2c_ty<T, 8>(g, M, ms_map, ms_scale, X, tw, st);
@@ -383,6 +384,7 @@ template <typename T>
 cudaError_t launch_x_c2r(const Geometry& g, const typename Cx<T>::t* X, T* H,
                          const typename Cx<T>::t* tw, cudaStream_t st)
 {
+    if (x1024_ok<T>(g, 227 * 1024)) return launch_x_c2r_1024<T>(g, X, H, tw, st);
     switch (xrow_tile<T>(g)) {
     case 16: return launch_c2r_ty<T, 16>(g, X, H, tw, st);
     case 8: return launch_c2r_ty<T, 8>(g, X, H, tw, st);

@@ -3,13 +3,13 @@
 //
 //   y_fwd  : per (kx, group of G lines (c, z)): zero-padded length-py y
 //            transform of each line (natural in, DIF, bit-reversed in shared
-//            memory), written column-major to Y[kx][ky][c][z] so every
-//            (kx, ky) column of 3 nz values is contiguous.
+//            memory), written to Y[kx][c][z][ky] (ky fastest).
 //   z_conv : the pipelined convolution of Section 7 (z transform, point-by-
 //            point kernel multiply, inverse z transform in one launch for all
 //            three components), one thread per (column, component, z-parity)
-//            with the half-length z transform in registers; columns of one
-//            kx plane are processed QC at a time.
+//            with the half-length z transform in registers; QC consecutive
+//            ky columns of one kx plane per CTA (32 consecutive ky per line
+//            load and store).
 //   y_inv  : inverse y transform of each line (DIT from bit-reversed order),
 //            cropped to ny, written back to X[kx][c][z][y].
 // Compared with the fused pass this moves the padded spectrum (2x the
@@ -58,11 +58,11 @@ __global__ void __launch_bounds__(256) y_fwd_kernel(Geometry g, const typename C
         Lines ln{nl, nl, LP, 0, 1, true};
         fft_dif(buf, ln, g.lgy, 1, tw, 0);
     }
-    // Y[kx][ky][line]: consecutive threads take consecutive lines of one ky
-    C* dst = Y + (size_t)kx * py * lines + l0;
+    // Y[kx][line][ky]
+    C* dst = Y + ((size_t)kx * lines + l0) * py;
     for (int i = threadIdx.x; i < py * nl; i += blockDim.x) {
-        const int l = i % nl, ky = i / nl;
-        dst[(size_t)ky * lines + l] = buf[l * LP + bitrev(ky, g.lgy)];
+        const int l = i / py, ky = i % py;
+        dst[(size_t)l * py + ky] = buf[l * LP + bitrev(ky, g.lgy)];
     }
 }
 
@@ -81,9 +81,9 @@ __global__ void __launch_bounds__(256) y_inv_kernel(Geometry g, const typename C
     const int nl = min(YG, lines - l0);
     const int shy = g.lglmax - g.lgy;
     for (int i = threadIdx.x; i < py; i += blockDim.x) tw[i] = tw_g[i << shy];
-    const C* src = Y + (size_t)kx * py * lines + l0;
-    staged_loop<256, C>(py * nl, [&](int i) { return src[(size_t)(i / nl) * lines + i % nl]; }, [&](int i, C a) {
-        buf[(i % nl) * LP + bitrev(i / nl, g.lgy)] = a;
+    const C* src = Y + ((size_t)kx * lines + l0) * py;
+    staged_loop<256, C>(py * nl, [&](int i) { return src[i]; }, [&](int i, C a) {
+        buf[(i / py) * LP + bitrev(i % py, g.lgy)] = a;
     });
     __syncthreads();
     if (py > 1) {
@@ -104,15 +104,27 @@ __global__ void __launch_bounds__(256) y_inv_kernel(Geometry g, const typename C
 // ---------------------------------------------------------------------------
 constexpr int QC = 32;
 
-// Phases of the per-warp work; (CP, HP) = (component, z parity) of the warp.
-// The kernel runs each phase through a warp-uniform switch and places the
-// block barriers between phases, outside the per-warp code.
-template <typename T, int HZ, int CP, int HP>
-__device__ __forceinline__ void zc_forward(const Geometry& g, int col, typename Cx<T>::t* tile, int CS,
+// Per-thread work of z_conv.  The component c is a runtime value (its kernel
+// row, the rows of the other two components and the sign pattern are
+// precomputed per thread); only the z parity HP is a template parameter, so
+// the kernel has two code paths.  The phases are separated by block
+// barriers placed in the kernel itself.
+template <typename T>
+struct ZcThread {
+    int col, c, o1, o2;  // column, component, row offsets of the other two components
+    const T* k0;         // kernel row entries of (c, c), (c, other1), (c, other2)
+    const T* k1;
+    const T* k2;
+    T a0, a1, a2;        // sign of each entry under ky -> -ky (xy, yz odd in ky)
+    T b0, b1, b2;        // sign of each entry under kz -> -kz (xz, yz odd in kz)
+};
+
+template <typename T, int HZ, int HP>
+__device__ __forceinline__ void zc_forward(const Geometry& g, const ZcThread<T>& t, typename Cx<T>::t* tile, int CS,
                                            typename Cx<T>::t (&v)[HZ])
 {
     using C = typename Cx<T>::t;
-    const C* mine = tile + col * CS + CP * HZ;
+    const C* mine = tile + t.col * CS + t.c * HZ;
 #pragma unroll
     for (int z = 0; z < HZ; z++) {
         C x = z < g.nz ? mine[z] : C{T(0), T(0)};
@@ -122,79 +134,28 @@ __device__ __forceinline__ void zc_forward(const Geometry& g, int col, typename 
     reg_fft<HZ, -1>(v);
 }
 
-template <typename T, int HZ, int CP, int HP>
-__device__ __forceinline__ void zc_store_spec(int col, typename Cx<T>::t* tile, typename Cx<T>::t* odd, int CS,
-                                              typename Cx<T>::t (&v)[HZ])
-{
-    typename Cx<T>::t* spec = HP ? odd : tile;  // spectrum of this parity: [col][c][pos]
-#pragma unroll
-    for (int pos = 0; pos < HZ; pos++) spec[col * CS + CP * HZ + pos] = v[pos];
-}
-
-template <typename T, int HZ, int CP, int HP>
-__device__ __forceinline__ void zc_multiply_inverse(const Geometry& g, int col, int ky0, const typename Cx<T>::t* tile,
-                                                    const typename Cx<T>::t* odd, const T* Ks, int CS, int KS,
+template <typename T, int HZ, int HP>
+__device__ __forceinline__ void zc_multiply_inverse(const ZcThread<T>& t, const typename Cx<T>::t* spec, int CS,
                                                     typename Cx<T>::t (&v)[HZ])
 {
     using C = typename Cx<T>::t;
-    const C* spec = HP ? odd : tile;
-    const int pz = 2 * HZ;
-    const int ky = ky0 + col;
-    const bool fy = ky > g.py / 2;
-    const T sy = fy ? T(-1) : T(1);
-    const T* kr = Ks + col * KS;
-    constexpr int i0 = CP == 0 ? 0 : CP == 1 ? 3 : 4;  // row c: (xx xy xz) (xy yy yz) (xz yz zz)
-    constexpr int i1 = CP == 0 ? 3 : CP == 1 ? 1 : 5;
-    constexpr int i2 = CP == 0 ? 4 : CP == 1 ? 5 : 2;
+    constexpr int PZ = 2 * HZ;
     constexpr int LGH = HZ == 2 ? 1 : HZ == 4 ? 2 : HZ == 8 ? 3 : HZ == 16 ? 4 : 5;
+    const C* s = spec + t.col * CS;
 #pragma unroll
     for (int pos = 0; pos < HZ; pos++) {
-        const int kz = 2 * (int)((__brev((unsigned)pos) >> (32 - LGH))) + HP;
-        const bool fz = kz > pz / 2;
-        const int kzf = fz ? pz - kz : kz;
-        const T sz = fz ? T(-1) : T(1);
-        // component signs: xy odd in ky; xz odd in kz; yz odd in both
-        auto sgn = [&](int idx) -> T { return idx == 3 ? sy : idx == 4 ? sz : idx == 5 ? sy * sz : T(1); };
-        const T k0 = kr[kzf * 6 + i0] * sgn(i0);
-        const T k1 = kr[kzf * 6 + i1] * sgn(i1);
-        const T k2 = kr[kzf * 6 + i2] * sgn(i2);
-        const C* s = spec + col * CS + pos;
-        const C m0 = CP == 0 ? v[pos] : s[0];
-        const C m1 = CP == 1 ? v[pos] : s[HZ];
-        const C m2 = CP == 2 ? v[pos] : s[2 * HZ];
-        v[pos] = C{k0 * m0.x + k1 * m1.x + k2 * m2.x, k0 * m0.y + k1 * m1.y + k2 * m2.y};
+        const int kz = 2 * (int)((__brev((unsigned)pos) >> (32 - LGH))) + HP;  // compile-time
+        const bool fz = kz > PZ / 2;
+        const int kzf = fz ? PZ - kz : kz;
+        const T w0 = t.k0[kzf * 6] * t.a0 * (fz ? t.b0 : T(1));
+        const T w1 = t.k1[kzf * 6] * t.a1 * (fz ? t.b1 : T(1));
+        const T w2 = t.k2[kzf * 6] * t.a2 * (fz ? t.b2 : T(1));
+        const C m1 = s[t.o1 + pos], m2 = s[t.o2 + pos];
+        const C own = v[pos];
+        v[pos] = C{w0 * own.x + w1 * m1.x + w2 * m2.x, w0 * own.y + w1 * m1.y + w2 * m2.y};
     }
     reg_fft<HZ, 1>(v);
 }
-
-template <typename T, int HZ, int CP, int HP>
-__device__ __forceinline__ void zc_odd_store(int col, typename Cx<T>::t* odd, int CS, typename Cx<T>::t (&v)[HZ])
-{
-    if (HP) {
-#pragma unroll
-        for (int z = 0; z < HZ; z++) odd[col * CS + CP * HZ + z] = c_mulc(v[z], cw128<typename Cx<T>::t>(z * (64 / HZ)));
-    }
-}
-
-template <typename T, int HZ, int CP, int HP>
-__device__ __forceinline__ void zc_combine(int col, typename Cx<T>::t* tile, const typename Cx<T>::t* odd, int CS,
-                                           typename Cx<T>::t (&v)[HZ])
-{
-    if (!HP) {
-#pragma unroll
-        for (int z = 0; z < HZ; z++) tile[col * CS + CP * HZ + z] = c_add(v[z], odd[col * CS + CP * HZ + z]);
-    }
-}
-
-#define ZC_DISPATCH(CALL)                    \
-    switch (warp) {                          \
-    case 0: CALL(0, 0); break;               \
-    case 1: CALL(1, 0); break;               \
-    case 2: CALL(2, 0); break;               \
-    case 3: CALL(0, 1); break;               \
-    case 4: CALL(1, 1); break;               \
-    default: CALL(2, 1); break;              \
-    }
 
 template <typename T, int HZ>
 __global__ void __launch_bounds__(QC * 6) z_conv_kernel(Geometry g, typename Cx<T>::t* __restrict__ Y,
@@ -210,18 +171,18 @@ __global__ void __launch_bounds__(QC * 6) z_conv_kernel(Geometry g, typename Cx<
     C* tile = reinterpret_cast<C*>(smem_raw);     // [QC][CS]
     C* odd = tile + QC * CS;                      // [QC][CS]
     T* Ks = reinterpret_cast<T*>(odd + QC * CS);  // [QC][KS]
-    C* col0 = Y + ((size_t)kx * py + ky0) * lines;
-    // stage the columns (contiguous in Y) and their kernel rows; the columns
-    // of a ragged last tile are zero and never written back
-    auto tpos = [&](int i) {
-        const int col = i / lines, r = i % lines;
-        return col * CS + (r / nz) * HZ + r % nz;
-    };
-    staged_loop<QC * 6, C>(ncol * lines, [&](int i) { return col0[i]; }, [&](int i, C a) { tile[tpos(i)] = a; });
-    for (int i = ncol * lines + threadIdx.x; i < QC * lines; i += blockDim.x) tile[tpos(i)] = C{T(0), T(0)};
+    // stage the QC columns: Y[kx][line][ky0 + col] (32 consecutive ky per line)
+    const C* ysrc = Y + (size_t)kx * lines * py + ky0;
+    staged_loop<QC * 6, C>(lines * QC, [&](int i) {
+        const int line = i / QC, col = i % QC;
+        return col < ncol ? ysrc[(size_t)line * py + col] : C{T(0), T(0)};
+    }, [&](int i, C a) {
+        const int line = i / QC, col = i % QC;
+        tile[col * CS + (line / nz) * HZ + line % nz] = a;
+    });
     // kernel rows: krow floats (a multiple of 4: 16-byte vectors)
     const T* Kx = K + (size_t)kx * g.kyh * g.krow;
-    const int vrow = g.krow * (int)sizeof(T) / 16;  // 16-byte vectors per row
+    const int vrow = g.krow * (int)sizeof(T) / 16;
     staged_loop<QC * 6, float4>(ncol * vrow, [&](int i) {
         const int col = i / vrow, o = i % vrow;
         const int ky = ky0 + col;
@@ -237,32 +198,52 @@ __global__ void __launch_bounds__(QC * 6) z_conv_kernel(Geometry g, typename Cx<
     for (int i = ncol * g.krow + threadIdx.x; i < QC * g.krow; i += blockDim.x)
         Ks[(i / g.krow) * KS + i % g.krow] = T(0);
     __syncthreads();
-    const int warp = threadIdx.x >> 5, col = threadIdx.x & 31;
+    // thread = (col, c, h): warp w takes component w % 3 and z parity w / 3
+    const int warp = threadIdx.x >> 5;
+    ZcThread<T> t;
+    t.col = threadIdx.x & 31;
+    t.c = warp % 3;
+    const int h = warp / 3;
+    const int c1 = t.c == 0 ? 1 : 0, c2 = t.c == 2 ? 1 : 2;
+    t.o1 = c1 * HZ;
+    t.o2 = c2 * HZ;
+    // entry (i, j) of the symmetric kernel in the (xx yy zz xy xz yz) order
+    auto comp = [](int i, int j) { return i == j ? i : (i + j == 1 ? 3 : (i + j == 2 ? 4 : 5)); };
+    const int e0 = comp(t.c, t.c), e1 = comp(t.c, c1), e2 = comp(t.c, c2);
+    const T* kr = Ks + t.col * KS;
+    t.k0 = kr + e0;
+    t.k1 = kr + e1;
+    t.k2 = kr + e2;
+    const bool fy = ky0 + t.col > py / 2;
+    auto sgn_y = [&](int e) { return (fy && (e == 3 || e == 5)) ? T(-1) : T(1); };
+    auto sgn_z = [](int e) { return (e == 4 || e == 5) ? T(-1) : T(1); };
+    t.a0 = sgn_y(e0); t.a1 = sgn_y(e1); t.a2 = sgn_y(e2);
+    t.b0 = sgn_z(e0); t.b1 = sgn_z(e1); t.b2 = sgn_z(e2);
     C v[HZ];
-#define ZC1(CP, HP) zc_forward<T, HZ, CP, HP>(g, col, tile, CS, v)
-    ZC_DISPATCH(ZC1)
+    if (h) zc_forward<T, HZ, 1>(g, t, tile, CS, v);
+    else zc_forward<T, HZ, 0>(g, t, tile, CS, v);
     __syncthreads();
-#define ZC2(CP, HP) zc_store_spec<T, HZ, CP, HP>(col, tile, odd, CS, v)
-    ZC_DISPATCH(ZC2)
+    C* spec = h ? odd : tile;  // spectrum of this parity: [col][c][pos]
+#pragma unroll
+    for (int pos = 0; pos < HZ; pos++) spec[t.col * CS + t.c * HZ + pos] = v[pos];
     __syncthreads();
-#define ZC3(CP, HP) zc_multiply_inverse<T, HZ, CP, HP>(g, col, ky0, tile, odd, Ks, CS, KS, v)
-    ZC_DISPATCH(ZC3)
+    if (h) zc_multiply_inverse<T, HZ, 1>(t, spec, CS, v);
+    else zc_multiply_inverse<T, HZ, 0>(t, spec, CS, v);
     __syncthreads();
-#define ZC4(CP, HP) zc_odd_store<T, HZ, CP, HP>(col, odd, CS, v)
-    ZC_DISPATCH(ZC4)
+    if (h) {
+#pragma unroll
+        for (int z = 0; z < HZ; z++) odd[t.col * CS + t.c * HZ + z] = c_mulc(v[z], cw128<C>(z * (64 / HZ)));
+    }
     __syncthreads();
-#define ZC5(CP, HP) zc_combine<T, HZ, CP, HP>(col, tile, odd, CS, v)
-    ZC_DISPATCH(ZC5)
+    if (!h) {
+#pragma unroll
+        for (int z = 0; z < HZ; z++) tile[t.col * CS + t.c * HZ + z] = c_add(v[z], odd[t.col * CS + t.c * HZ + z]);
+    }
     __syncthreads();
-#undef ZC1
-#undef ZC2
-#undef ZC3
-#undef ZC4
-#undef ZC5
-    for (int i = threadIdx.x; i < ncol * lines; i += blockDim.x) {
-        const int col = i / lines, r = i % lines;
-        const int c = r / nz, z = r % nz;
-        col0[i] = tile[col * CS + c * HZ + z];
+    C* ydst = Y + (size_t)kx * lines * py + ky0;
+    for (int i = threadIdx.x; i < lines * QC; i += blockDim.x) {
+        const int line = i / QC, col = i % QC;
+        if (col < ncol) ydst[(size_t)line * py + col] = tile[col * CS + (line / nz) * HZ + line % nz];
     }
 }
 
@@ -280,11 +261,12 @@ __global__ void __launch_bounds__(256) z_mult_kernel(Geometry g, typename Cx<T>:
         const T* k = K + ((size_t)kx * g.kyh + (fy ? py - ky : ky)) * g.krow;
         const T kxx = k[0], kyy = k[1], kzz = k[2];
         const T kxy = fy ? -k[3] : k[3], kxz = k[4], kyz = fy ? -k[5] : k[5];
-        C* col = Y + i * 3;
-        const C a = col[0], b = col[1], c = col[2];
+        // Y[kx][c][ky] (nz = 1)
+        C* col = Y + (size_t)kx * 3 * py + ky;
+        const C a = col[0], b = col[py], c = col[2 * py];
         col[0] = C{kxx * a.x + kxy * b.x + kxz * c.x, kxx * a.y + kxy * b.y + kxz * c.y};
-        col[1] = C{kxy * a.x + kyy * b.x + kyz * c.x, kxy * a.y + kyy * b.y + kyz * c.y};
-        col[2] = C{kxz * a.x + kyz * b.x + kzz * c.x, kxz * a.y + kyz * b.y + kzz * c.y};
+        col[py] = C{kxy * a.x + kyy * b.x + kyz * c.x, kxy * a.y + kyy * b.y + kyz * c.y};
+        col[2 * py] = C{kxz * a.x + kyz * b.x + kzz * c.x, kxz * a.y + kyz * b.y + kzz * c.y};
     }
 }
 
@@ -330,6 +312,7 @@ cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>
     const int lines = 3 * g.nz;
     dim3 ygrid((lines + YG - 1) / YG, g.nkx);
     cudaError_t e = cudaSuccess;
+    if (part != 1 && y1024_ok<T>(g, 227 * 1024)) return launch_y_1024<T>(g, X, Y, tw, st, part == 0);
     if (part == 0) {
         e = cudaFuncSetAttribute(y_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys);
         if (e != cudaSuccess) return e;

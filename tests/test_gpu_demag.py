@@ -24,6 +24,8 @@ CASES = [
     ((50, 37, 6), (3e-9, 3e-9, 2e-9)),      # several tiles + ragged tails
     ((64, 48, 16), (4e-9, 4e-9, 4e-9)),
     ((256, 64, 1), (1.953125e-9, 1.953125e-9, 3e-9)),  # SP4-shaped film
+    ((300, 280, 3), (3e-9, 3e-9, 3e-9)),    # length-1024 x and y transforms, ragged rows
+    ((512, 300, 2), (4e-9, 4e-9, 4e-9)),    # full 512-cell rows
 ]
 
 
