@@ -34,16 +34,30 @@ __global__ void __launch_bounds__(256) x_r2c_1024_kernel(Geometry g, const T* __
     const T* ma = ms_map ? ms_map + ((size_t)z * ny + ya) * nx : nullptr;
     const T* mb = ms_map ? ms_map + ((size_t)z * ny + yb) * nx : nullptr;
     C v[32];
+    const bool oka = ya < ny, okb = yb < ny;
 #pragma unroll
-    for (int a = 0; a < 32; a++) {
+    for (int a = 0; a < 16; a++) {
         const int x = 32 * a + lane;
-        T va = T(0), vb = T(0);
-        if (a < 16 && x < nx) {
-            if (ya < ny) va = ms_map ? ra[x] * ma[x] : ra[x] * ms_scale;
-            if (yb < ny) vb = ms_map ? rb[x] * mb[x] : rb[x] * ms_scale;
-        }
-        v[a] = C{va, vb};
+        const bool in = x < nx;
+        v[a] = C{(in && oka) ? ra[x] : T(0), (in && okb) ? rb[x] : T(0)};
     }
+    if (ms_map) {
+#pragma unroll
+        for (int a = 0; a < 16; a++) {
+            const int x = 32 * a + lane;
+            const bool in = x < nx;
+            v[a].x *= (in && oka) ? ma[x] : T(0);
+            v[a].y *= (in && okb) ? mb[x] : T(0);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 16; a++) {
+            v[a].x *= ms_scale;
+            v[a].y *= ms_scale;
+        }
+    }
+#pragma unroll
+    for (int a = 16; a < 32; a++) v[a] = C{T(0), T(0)};
     C* mine = reg + warp * REG1025;
     warp_fft1024_fwd(v, mine, tws);
 #pragma unroll
@@ -80,15 +94,21 @@ __global__ void __launch_bounds__(256) x_c2r_1024_kernel(Geometry g, const typen
     load_tw1024(tws, tw_g, g.lglmax - 10);
     __syncthreads();
     const int ya = y0 + warp, yb = y0 + warp + 8;
+    // stage the 513 x 16 half-spectrum block ([kx][17]: odd stride, no bank
+    // conflicts when lanes walk kx) with coalesced 128-byte rows
+    C* S = reg;
+    staged_loop<256, C>(513 * 16, [&](int i) {
+        const int kx = i >> 4, t = i & 15;
+        return y0 + t < ny ? X[(((size_t)kx * 3 + c) * nz + z) * ny + y0 + t] : C{T(0), T(0)};
+    }, [&](int i, C a) { S[(i >> 4) * 17 + (i & 15)] = a; });
+    __syncthreads();
     C v[32];
 #pragma unroll
     for (int d = 0; d < 32; d++) {
         const int k = lane + 32 * d;
         const bool upper = k > 512;
         const int kx = upper ? 1024 - k : k;
-        const size_t rowbase = ((size_t)kx * 3 + c) * nz + z;
-        C A = ya < ny ? X[rowbase * ny + ya] : C{T(0), T(0)};
-        C B = yb < ny ? X[rowbase * ny + yb] : C{T(0), T(0)};
+        C A = S[kx * 17 + warp], B = S[kx * 17 + warp + 8];
         if (kx == 0 || kx == 512) {
             A.y = T(0);  // DC and Nyquist bins of a real signal are real
             B.y = T(0);
@@ -99,6 +119,7 @@ __global__ void __launch_bounds__(256) x_c2r_1024_kernel(Geometry g, const typen
         }
         v[brev5(d)] = C{A.x - B.y, A.y + B.x};
     }
+    __syncthreads();  // the staging area becomes the warps' transpose tiles
     warp_fft1024_inv(v, reg + warp * REG1025, tws);
     const size_t ncell = (size_t)nx * ny * nz;
     T* ha = H + c * ncell + ((size_t)z * ny + ya) * nx;
@@ -174,7 +195,9 @@ __global__ void __launch_bounds__(256) y_inv_1024_kernel(Geometry g, const typen
 template <typename T>
 static size_t smem_1024()
 {
-    return ((size_t)TW1024_SLOTS + 8 * (size_t)REG1025) * sizeof(typename Cx<T>::t);
+    // per-warp regions, also used as the 513 x 17 staging block of x_c2r
+    const size_t regions = 8 * (size_t)REG1025 > 513 * 17 ? 8 * (size_t)REG1025 : 513 * 17;
+    return ((size_t)TW1024_SLOTS + regions) * sizeof(typename Cx<T>::t);
 }
 
 template <typename T>

@@ -158,8 +158,9 @@ __device__ __forceinline__ void zc_multiply_inverse(const ZcThread<T>& t, const 
 }
 
 template <typename T, int HZ>
-__global__ void __launch_bounds__(QC * 6) z_conv_kernel(Geometry g, typename Cx<T>::t* __restrict__ Y,
-                                                        const T* __restrict__ K)
+__global__ void __launch_bounds__(QC * 6, sizeof(T) == 4 ? 3 : 1) z_conv_kernel(Geometry g,
+                                                                                 typename Cx<T>::t* __restrict__ Y,
+                                                                                 const T* __restrict__ K)
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -173,12 +174,15 @@ __global__ void __launch_bounds__(QC * 6) z_conv_kernel(Geometry g, typename Cx<
     T* Ks = reinterpret_cast<T*>(odd + QC * CS);  // [QC][KS]
     // stage the QC columns: Y[kx][line][ky0 + col] (32 consecutive ky per line)
     const C* ysrc = Y + (size_t)kx * lines * py + ky0;
+    // line = c * nz + z sits at row c * HZ + z of a column
+    const bool full = nz == HZ;  // then the row is the line index itself
+    auto row_of = [&](int line) { return full ? line : (line / nz) * HZ + line % nz; };
     staged_loop<QC * 6, C>(lines * QC, [&](int i) {
         const int line = i / QC, col = i % QC;
         return col < ncol ? ysrc[(size_t)line * py + col] : C{T(0), T(0)};
     }, [&](int i, C a) {
         const int line = i / QC, col = i % QC;
-        tile[col * CS + (line / nz) * HZ + line % nz] = a;
+        tile[col * CS + row_of(line)] = a;
     });
     // kernel rows: krow floats (a multiple of 4: 16-byte vectors)
     const T* Kx = K + (size_t)kx * g.kyh * g.krow;
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(QC * 6) z_conv_kernel(Geometry g, typename Cx<
     C* ydst = Y + (size_t)kx * lines * py + ky0;
     for (int i = threadIdx.x; i < lines * QC; i += blockDim.x) {
         const int line = i / QC, col = i % QC;
-        if (col < ncol) ydst[(size_t)line * py + col] = tile[col * CS + (line / nz) * HZ + line % nz];
+        if (col < ncol) ydst[(size_t)line * py + col] = tile[col * CS + row_of(line)];
     }
 }
 
