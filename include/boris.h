@@ -52,6 +52,14 @@ typedef enum {
 /* Plan flags */
 #define BORIS_FLAG_F32 0x0u        /* FP32 transforms and LLG (default)                */
 #define BORIS_FLAG_F64 0x1u        /* FP64 everywhere: use the *_f64 entry points       */
+/* Mixed-precision z stage (FP32 plans, pz = 64, i.e. 17 <= nz <= 32): the
+ * zero-padded z transform and its inverse run as dense matrix products on the
+ * tensor cores with FP16 (or BF16) operands, one FP32 scale per (kx, ky,
+ * component) column, FP32 accumulation; everything else stays FP32.  The
+ * paper has FP32/FP64 only; expected relative L2 error of H_d ~1e-3 (FP16)
+ * to ~5e-3 (BF16). */
+#define BORIS_FLAG_FP16_TC 0x2u
+#define BORIS_FLAG_BF16_TC 0x4u
 
 /* Integration methods (boris_llg_params.method) */
 #define BORIS_RK4 0

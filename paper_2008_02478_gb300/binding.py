@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libboris.so")
 BORIS_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "UNSUPPORTED_SIZE", -5: "TIMEOUT",
           -6: "STEP_CONTROL"}
-FLAG_F32, FLAG_F64 = 0x0, 0x1
+FLAG_F32, FLAG_F64, FLAG_FP16_TC, FLAG_BF16_TC = 0x0, 0x1, 0x2, 0x4
 RK4, RKF45 = 0, 1
 
 MU0 = 4e-7 * math.pi
@@ -144,7 +144,7 @@ def _ptr(t, dtype, shape=None):
 class Plan:
     """A demag + LLG plan for an nx x ny x nz mesh of dx x dy x dz cells."""
 
-    def __init__(self, nx, ny, nz, dx, dy, dz, fp64: bool = False, stream=None):
+    def __init__(self, nx, ny, nz, dx, dy, dz, fp64: bool = False, stream=None, tc: str | None = None):
         import torch
         self.shape = (nx, ny, nz)
         self.cell = (dx, dy, dz)
@@ -153,8 +153,12 @@ class Plan:
         st = stream if stream is not None else torch.cuda.current_stream()
         self.stream = st
         h = ctypes.c_void_p()
-        check(lib().boris_demag_plan(nx, ny, nz, dx, dy, dz, FLAG_F64 if fp64 else FLAG_F32,
-                                     ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)))
+        flags = FLAG_F64 if fp64 else FLAG_F32
+        if tc is not None:
+            flags |= {"fp16": FLAG_FP16_TC, "bf16": FLAG_BF16_TC}[tc]
+        self.tc = tc
+        check(lib().boris_demag_plan(nx, ny, nz, dx, dy, dz, flags, ctypes.c_void_p(st.cuda_stream),
+                                     ctypes.byref(h)))
         self._h = h
 
     @property

@@ -92,6 +92,9 @@ template <typename T>
 cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
                           cudaStream_t st, bool forward);
 cudaError_t upload_twiddles_fast();
+// Tensor-core (FP16 / BF16) z stage of the split schedule (zconv_tc.cu), pz = 64.
+bool zconv_tc_supported(const Geometry& g);
+cudaError_t launch_zconv_tc(const Geometry& g, float2* Y, const float* K, const float2* tw, bool bf16, cudaStream_t st);
 cudaError_t upload_twiddles_yz_f32();
 cudaError_t upload_twiddles_yz_f64();
 // Candidate schedules of the fused y-z pass that fit this geometry.

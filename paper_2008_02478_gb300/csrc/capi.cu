@@ -22,6 +22,7 @@ struct boris_plan_s {
     double dx, dy, dz;
     unsigned flags;
     bool f64;
+    int tc = 0;  // 0: FP32 z stage; 1: FP16 tensor cores; 2: BF16 tensor cores
     cudaStream_t stream;
     int device;
     YZSchedule yz;
@@ -125,6 +126,9 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
         cudaError_t e = cudaSuccess;
         for (int part = 0; part < 3 && e == cudaSuccess; part++)
             e = timed(p, 5 + part, [&] {
+                if (part == 1 && p->tc)
+                    return launch_zconv_tc(p->g, (float2*)p->Y, (const float*)p->K, (const float2*)p->tw, p->tc == 2,
+                                           p->stream);
                 return launch_split<T>(p->g, (C*)p->X, (C*)p->Y, (const T*)p->K, (const C*)p->tw, p->stream, part);
             });
         return e;
@@ -395,7 +399,11 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     if (nx < 1 || ny < 1 || nz < 1) return fail(BORIS_ERR_INVALID_ARG, "mesh sizes must be >= 1");
     if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
         return fail(BORIS_ERR_INVALID_ARG, "cell sizes must be finite and > 0");
-    if (flags & ~BORIS_FLAG_F64) return fail(BORIS_ERR_INVALID_ARG, "unknown flags");
+    if (flags & ~(BORIS_FLAG_F64 | BORIS_FLAG_FP16_TC | BORIS_FLAG_BF16_TC)) return fail(BORIS_ERR_INVALID_ARG, "unknown flags");
+    const int tc = (flags & BORIS_FLAG_FP16_TC) ? 1 : (flags & BORIS_FLAG_BF16_TC) ? 2 : 0;
+    if (tc && (flags & BORIS_FLAG_F64)) return fail(BORIS_ERR_INVALID_ARG, "tensor-core z stage is an FP32-plan option");
+    if ((flags & BORIS_FLAG_FP16_TC) && (flags & BORIS_FLAG_BF16_TC))
+        return fail(BORIS_ERR_INVALID_ARG, "choose FP16 or BF16 tensor cores, not both");
     Geometry g;
     g.nx = nx;
     g.ny = ny;
@@ -424,6 +432,7 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     p->dz = dz;
     p->flags = flags;
     p->f64 = (flags & BORIS_FLAG_F64) != 0;
+    p->tc = tc;
     p->stream = (cudaStream_t)cuda_stream;
     int rc = BORIS_OK;
     auto bail = [&](int code) {
@@ -439,6 +448,13 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     else yz_candidates<float>(g, max_smem, cand, &ncand);
     const bool split_ok = p->f64 ? split_supported<double>(g, max_smem) : split_supported<float>(g, max_smem);
     if (split_ok && ncand < 16) cand[ncand++] = YZSchedule{2, 0, 0, 0, 0};
+    if (tc) {
+        // the tensor-core z stage runs inside the split schedule only
+        if (!split_ok || !zconv_tc_supported(g))
+            return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "tensor-core z stage needs pz = 64 (17 <= nz <= 32)"));
+        cand[0] = YZSchedule{2, 0, 0, 0, 0};
+        ncand = 1;
+    }
     if (ncand == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));
     // optional override for tests and sweeps: BORIS_YZ_KIND / BORIS_YZ_CLUSTER / BORIS_YZ_THREADS / BORIS_YZ_QC
     {
