@@ -342,8 +342,8 @@ def main():
 
     # ---- FP64 plan (same kernels templated on double) ----------------------
     fp64 = None
+    mixed = None
     if not args.no_fp64:
-        del H
         plan64 = Plan(nx, ny, nz, *CELL, fp64=True)
         m64 = torch.tensor(m0, dtype=torch.float64, device="cuda")
         k64 = max(3, args.steps // 4)
@@ -357,7 +357,36 @@ def main():
         fp64 = {"cell_steps_per_s": world * ncell * k64 / t64, "demag_evals_per_s": world * 4 * k64 / td64,
                 "steps": k64}
         plan64.close()
-        del m64, M64, H64
+        del m64, M64
+
+        # H_d of the film from the FP64 plan (within 1e-9 of the FP64 oracle in
+        # the parity tests) is the reference for the FP32 and mixed-precision errors
+        def rel_err(Hx):
+            d = (Hx.double() - H64).norm() / H64.norm()
+            return float(d)
+        plan.apply(M, H)
+        fp64["h_rel_l2_fp32_vs_fp64"] = rel_err(H)
+        mixed = {}
+        for tc in ("fp16", "bf16"):
+            pt = Plan(nx, ny, nz, *CELL, tc=tc)
+            pt.apply(M, H)
+            err = rel_err(H)
+            for _ in range(3):
+                pt.apply(M, H)
+            td = max_over_ranks(time_demag(torch, pt, M, H, 4 * args.steps))
+            mt = torch.tensor(m0, dtype=torch.float32, device="cuda")
+            for _ in range(2):
+                pt.llg_step(mt, prm, DT)
+            pt.profile(True)
+            ts = max_over_ranks(time_steps(torch, pt, mt, prm, args.steps))
+            kk, _ = pt.profile_read()
+            mixed[tc] = {"demag_evals_per_s": world * 4 * args.steps / td,
+                         "cell_steps_per_s": world * ncell * args.steps / ts,
+                         "h_rel_l2_vs_fp64": err,
+                         "z_stage_ms_per_launch": kk["z_conv"][0] / max(1, kk["z_conv"][1])}
+            pt.close()
+            del mt
+        del H64
 
     # ---- CPU baseline: the oracle on a bounded sample -----------------------
     cpu = None
@@ -378,7 +407,8 @@ def main():
                            "l2": "inputs larger than L2 (m 100.7 MB, spectrum workspace 201.7 MB, kernel "
                                  "spectrum 208.4 MB per evaluation)",
                            "padded": plan.padded(), "yz_schedule": plan.schedule()},
-                "demag_evals_per_s": demag_rate, "fp64": fp64, "roofline": roofline, "kernels": kernels,
+                "demag_evals_per_s": demag_rate, "fp64": fp64, "mixed_precision": mixed, "roofline": roofline,
+                "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()
