@@ -43,7 +43,8 @@ struct Geometry {
 struct YZSchedule {
     int kind;     // 0: fused, z stage through shared-memory passes; 1: fused, z stage in
                   // registers; 2: split into y-forward, z-convolution and y-inverse kernels
-    int C;        // CTAs per cluster (one cluster per kx plane); ky residues mod C
+    int C;        // kinds 0/1: CTAs per cluster (one cluster per kx plane; ky residues mod C);
+                  // kind 2: CTAs per SM targeted by the z-convolution's register budget
     int Qc;       // z-columns processed per chunk of the z stage
     int threads;  // threads per CTA
     size_t smem;  // dynamic shared memory per CTA (bytes)
@@ -73,9 +74,10 @@ cudaError_t launch_yz_reg<double>(const Geometry& g, const YZSchedule& sc, doubl
 // padded spectrum Y laid out [kx][c][z][ky] (ky fastest).
 template <typename T>
 bool split_supported(const Geometry& g, int max_smem);
+// occ: CTAs per SM that the z-convolution's register budget targets (2 or 3).
 template <typename T>
 cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const T* K,
-                         const typename Cx<T>::t* tw, cudaStream_t st, int part);
+                         const typename Cx<T>::t* tw, cudaStream_t st, int part, int occ);
 cudaError_t upload_twiddles_split();
 // Warp-per-line kernels for transform length 1024 (demag_fast.cu).
 template <typename T>

@@ -129,7 +129,8 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
                 if (part == 1 && p->tc)
                     return launch_zconv_tc(p->g, (float2*)p->Y, (const float*)p->K, (const float2*)p->tw, p->tc == 2,
                                            p->stream);
-                return launch_split<T>(p->g, (C*)p->X, (C*)p->Y, (const T*)p->K, (const C*)p->tw, p->stream, part);
+                return launch_split<T>(p->g, (C*)p->X, (C*)p->Y, (const T*)p->K, (const C*)p->tw, p->stream, part,
+                                       sc.C);
             });
         return e;
     }
@@ -447,12 +448,15 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     if (p->f64) yz_candidates<double>(g, max_smem, cand, &ncand);
     else yz_candidates<float>(g, max_smem, cand, &ncand);
     const bool split_ok = p->f64 ? split_supported<double>(g, max_smem) : split_supported<float>(g, max_smem);
-    if (split_ok && ncand < 16) cand[ncand++] = YZSchedule{2, 0, 0, 0, 0};
+    if (split_ok && ncand < 15) {
+        cand[ncand++] = YZSchedule{2, 2, 0, 0, 0};
+        if (!p->f64) cand[ncand++] = YZSchedule{2, 3, 0, 0, 0};
+    }
     if (tc) {
         // the tensor-core z stage runs inside the split schedule only
         if (!split_ok || !zconv_tc_supported(g))
             return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "tensor-core z stage needs pz = 64 (17 <= nz <= 32)"));
-        cand[0] = YZSchedule{2, 0, 0, 0, 0};
+        cand[0] = YZSchedule{2, 2, 0, 0, 0};
         ncand = 1;
     }
     if (ncand == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));

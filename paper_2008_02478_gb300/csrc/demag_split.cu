@@ -157,18 +157,18 @@ __device__ __forceinline__ void zc_multiply_inverse(const ZcThread<T>& t, const 
     reg_fft<HZ, 1>(v);
 }
 
-template <typename T, int HZ>
-__global__ void __launch_bounds__(QC * 6, sizeof(T) == 4 ? 3 : 1) z_conv_kernel(Geometry g,
-                                                                                 typename Cx<T>::t* __restrict__ Y,
-                                                                                 const T* __restrict__ K)
+template <typename T, int HZ, int MINB>
+__global__ void __launch_bounds__(QC * 6, MINB) z_conv_kernel(Geometry g, typename Cx<T>::t* __restrict__ Y,
+                                                              const T* __restrict__ K)
 {
+    constexpr int KROW = ((HZ + 1) * 6 + 3) / 4 * 4;  // kernel row length (g.krow for pz = 2 HZ)
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nz = g.nz, lines = 3 * nz, py = g.py;
     const int kx = blockIdx.y, ky0 = blockIdx.x * QC;
     const int ncol = min(QC, py - ky0);
     const int CS = 3 * HZ + 1;  // column stride (odd: bank spread)
-    const int KS = g.krow + 1;
+    constexpr int KS = KROW + 1;
     C* tile = reinterpret_cast<C*>(smem_raw);     // [QC][CS]
     C* odd = tile + QC * CS;                      // [QC][CS]
     T* Ks = reinterpret_cast<T*>(odd + QC * CS);  // [QC][KS]
@@ -184,14 +184,14 @@ __global__ void __launch_bounds__(QC * 6, sizeof(T) == 4 ? 3 : 1) z_conv_kernel(
         const int line = i / QC, col = i % QC;
         tile[col * CS + row_of(line)] = a;
     });
-    // kernel rows: krow floats (a multiple of 4: 16-byte vectors)
-    const T* Kx = K + (size_t)kx * g.kyh * g.krow;
-    const int vrow = g.krow * (int)sizeof(T) / 16;
+    // kernel rows: KROW values (a multiple of 4: 16-byte vectors)
+    const T* Kx = K + (size_t)kx * g.kyh * KROW;
+    constexpr int vrow = KROW * (int)sizeof(T) / 16;
     staged_loop<QC * 6, float4>(ncol * vrow, [&](int i) {
         const int col = i / vrow, o = i % vrow;
         const int ky = ky0 + col;
         const int kyf = ky > py / 2 ? py - ky : ky;
-        return reinterpret_cast<const float4*>(Kx + (size_t)kyf * g.krow)[o];
+        return reinterpret_cast<const float4*>(Kx + (size_t)kyf * KROW)[o];
     }, [&](int i, float4 v4) {
         const int col = i / vrow, o = i % vrow;
         const T* e = reinterpret_cast<const T*>(&v4);
@@ -199,8 +199,7 @@ __global__ void __launch_bounds__(QC * 6, sizeof(T) == 4 ? 3 : 1) z_conv_kernel(
 #pragma unroll
         for (int k = 0; k < PER; k++) Ks[col * KS + o * PER + k] = e[k];
     });
-    for (int i = ncol * g.krow + threadIdx.x; i < QC * g.krow; i += blockDim.x)
-        Ks[(i / g.krow) * KS + i % g.krow] = T(0);
+    for (int i = ncol * KROW + threadIdx.x; i < QC * KROW; i += blockDim.x) Ks[(i / KROW) * KS + i % KROW] = T(0);
     __syncthreads();
     // thread = (col, c, h): warp w takes component w % 3 and z parity w / 3
     const int warp = threadIdx.x >> 5;
@@ -297,20 +296,30 @@ bool split_supported(const Geometry& g, int max_smem)
     return true;
 }
 
-template <typename T, int HZ>
+template <typename T, int HZ, int MINB>
 static cudaError_t launch_zconv_hz(const Geometry& g, typename Cx<T>::t* Y, const T* K, cudaStream_t st)
 {
     const size_t smem = split_z_smem<T>(g);
-    cudaError_t e = cudaFuncSetAttribute(z_conv_kernel<T, HZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(z_conv_kernel<T, HZ, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.py + QC - 1) / QC, g.nkx);
-    z_conv_kernel<T, HZ><<<grid, QC * 6, smem, st>>>(g, Y, K);
+    z_conv_kernel<T, HZ, MINB><<<grid, QC * 6, smem, st>>>(g, Y, K);
     return cudaGetLastError();
+}
+
+template <typename T, int HZ>
+static cudaError_t launch_zconv_occ(const Geometry& g, typename Cx<T>::t* Y, const T* K, cudaStream_t st, int occ)
+{
+    // occ: CTAs per SM the register budget is fitted to (FP64 always 1)
+    if (sizeof(T) == 8) return launch_zconv_hz<T, HZ, 1>(g, Y, K, st);
+    if (occ == 3) return launch_zconv_hz<T, HZ, 3>(g, Y, K, st);
+    return launch_zconv_hz<T, HZ, 2>(g, Y, K, st);
 }
 
 template <typename T>
 cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const T* K,
-                         const typename Cx<T>::t* tw, cudaStream_t st, int part)
+                         const typename Cx<T>::t* tw, cudaStream_t st, int part, int occ)
 {
     const size_t ys = split_y_smem<T>(g);
     const int lines = 3 * g.nz;
@@ -331,11 +340,11 @@ cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>
             return cudaGetLastError();
         }
         switch (g.pz / 2) {
-        case 2: return launch_zconv_hz<T, 2>(g, Y, K, st);
-        case 4: return launch_zconv_hz<T, 4>(g, Y, K, st);
-        case 8: return launch_zconv_hz<T, 8>(g, Y, K, st);
-        case 16: return launch_zconv_hz<T, 16>(g, Y, K, st);
-        case 32: return launch_zconv_hz<T, 32>(g, Y, K, st);
+        case 2: return launch_zconv_occ<T, 2>(g, Y, K, st, occ);
+        case 4: return launch_zconv_occ<T, 4>(g, Y, K, st, occ);
+        case 8: return launch_zconv_occ<T, 8>(g, Y, K, st, occ);
+        case 16: return launch_zconv_occ<T, 16>(g, Y, K, st, occ);
+        case 32: return launch_zconv_occ<T, 32>(g, Y, K, st, occ);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -350,8 +359,8 @@ cudaError_t upload_twiddles_split() { return upload_small_twiddles_here(); }
 template bool split_supported<float>(const Geometry&, int);
 template bool split_supported<double>(const Geometry&, int);
 template cudaError_t launch_split<float>(const Geometry&, float2*, float2*, const float*, const float2*, cudaStream_t,
-                                         int);
+                                         int, int);
 template cudaError_t launch_split<double>(const Geometry&, double2*, double2*, const double*, const double2*,
-                                          cudaStream_t, int);
+                                          cudaStream_t, int, int);
 
 }  // namespace boris

@@ -99,7 +99,7 @@ extern "C" int boris_demag_apply_noalloc(boris_plan p, const float* M, float* Hd
     if ((e = launch_x_r2c<float>(v.g, M, nullptr, 1.0f, X, tw, v.stream)) == cudaSuccess) {
         if (v.yz.kind == 2) {
             for (int part = 0; part < 3 && e == cudaSuccess; part++)
-                e = launch_split<float>(v.g, X, Y, (const float*)v.K, tw, v.stream, part);
+                e = launch_split<float>(v.g, X, Y, (const float*)v.K, tw, v.stream, part, v.yz.C);
         } else {
             e = launch_yz_conv<float>(v.g, v.yz, X, (const float*)v.K, tw, v.stream);
         }

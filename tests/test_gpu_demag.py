@@ -51,7 +51,7 @@ SCHEDULE_MESHES = [
     ((64, 40, 1), (2e-9, 2e-9, 3e-9)),    # 2D mode
 ]
 SCHEDULES = [(0, 1, None), (0, 2, None), (0, 4, None), (0, 8, None), (0, 16, None),
-             (1, 1, 384), (1, 1, 768), (1, 8, 384), (1, 8, 768), (1, 16, 384), (1, 16, 768), (2, 0, None)]
+             (1, 1, 384), (1, 1, 768), (1, 8, 384), (1, 8, 768), (1, 16, 384), (1, 16, 768), (2, 2, None), (2, 3, None)]
 
 
 @pytest.mark.parametrize("n,h", SCHEDULE_MESHES)
@@ -65,8 +65,7 @@ def test_every_yz_schedule_matches_oracle(n, h, kind, C, NT, monkeypatch):
     M = 6e5 * inputs.random_unit(nx, ny, nz, seed=2)
     ref = oracle.DemagPlan(nx, ny, nz, *h).apply(M)
     monkeypatch.setenv("BORIS_YZ_KIND", str(kind))
-    if kind != 2:
-        monkeypatch.setenv("BORIS_YZ_CLUSTER", str(C))
+    monkeypatch.setenv("BORIS_YZ_CLUSTER", str(C))
     if NT:
         monkeypatch.setenv("BORIS_YZ_THREADS", str(NT))
     elif kind == 0:
@@ -76,7 +75,7 @@ def test_every_yz_schedule_matches_oracle(n, h, kind, C, NT, monkeypatch):
     except BorisError as e:
         assert e.code == -4  # this schedule does not fit this mesh
         pytest.skip("schedule does not fit")
-    assert plan.schedule()[0] == kind and (kind == 2 or plan.schedule()[1] == C)
+    assert plan.schedule()[:2] == (kind, C)
     H = plan.apply(to_dev(torch, M)).cpu().numpy()
     assert rel_l2(H, ref) < 1e-5
 
