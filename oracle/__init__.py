@@ -13,8 +13,9 @@ Paper: "Boris Computational Spintronics" (arXiv 2008.02478).
     an RK4 step.
   * ``multilayer.py``   - the multi-mesh convolution sum (Eq. 4).
 
-Parity unpinned: the cross-layer tensor for layers of unequal thickness beyond
-its equal-thickness reduction and reciprocity (see ``multilayer.py``).
+The cross-layer tensor for cells of unequal thickness (``multilayer.py``) is
+pinned by its equal-thickness reduction, reciprocity, source splitting and
+Gauss-Legendre quadrature of the dipole kernel over the two boxes.
 """
 from __future__ import annotations
 
@@ -71,6 +72,10 @@ def lib():
             L.orc_demag_fft.restype = i
             L.orc_demag_fft.argtypes = [vp, vp, vp]
             L.orc_num_threads.restype = i
+            L.orc_newell_pair_exact.argtypes = [d, d, d, d, d, d, d, vp]
+            L.orc_newell_pair_asymptotic.argtypes = [d, d, d, d, d, d, d, vp]
+            L.orc_newell_pair.argtypes = [d, d, d, d, d, d, d, d, vp]
+            L.orc_multilayer_direct_at.argtypes = [i, vp, vp, vp, vp, vp, d, d, d, vp, i, vp, vp]
             _lib = L
     return _lib
 

@@ -445,3 +445,140 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* Multi-mesh (Eq. 4): cells of different z thickness                        */
+/* ------------------------------------------------------------------------ */
+/* Generalised stencil for a target box of z size a and a source box of z size
+ * b (equal in-plane sizes hx, hy).  Per axis the double integral over the two
+ * boxes of a function whose second antiderivative is F is
+ *   F(z + s) - F(z + d) - F(z - d) + F(z - s),  s = (a + b)/2, d = (a - b)/2,
+ * which is F(z+h) - 2F(z) + F(z-h) for a = b: the Newell weights (2, -1, -1)
+ * are minus this.  The tensor is normalised by 1/(4 pi hx hy a) (target
+ * volume). */
+typedef struct {
+    int n;
+    double off[4], w[4];
+} orc_axis_stencil;
+
+static orc_axis_stencil stencil_equal(double h)
+{
+    orc_axis_stencil s = {3, {-h, 0.0, h, 0}, {-1.0, 2.0, -1.0, 0}};
+    return s;
+}
+
+static orc_axis_stencil stencil_pair(double a, double b)
+{
+    double s = 0.5 * (a + b), d = 0.5 * (a - b);
+    orc_axis_stencil st = {4, {-s, -d, d, s}, {1.0, -1.0, -1.0, 1.0}};
+    /* minus the double integral: -[F(z+s) - F(z+d) - F(z-d) + F(z-s)] */
+    for (int i = 0; i < 4; i++) st.w[i] = -st.w[i];
+    return st;
+}
+
+static double stencil3(double (*F)(double, double, double), double X, double Y, double Z,
+                       const orc_axis_stencil* s1, const orc_axis_stencil* s2, const orc_axis_stencil* s3)
+{
+    double acc = 0.0;
+    for (int i = 0; i < s1->n; i++)
+        for (int j = 0; j < s2->n; j++)
+            for (int k = 0; k < s3->n; k++)
+                acc += s1->w[i] * s2->w[j] * s3->w[k] * F(X + s1->off[i], Y + s2->off[j], Z + s3->off[k]);
+    return acc;
+}
+
+/* Exact pair tensor at centre separation (X,Y,Z), target z size a, source z
+ * size b.  out = {xx, yy, zz, xy, xz, yz}. */
+void orc_newell_pair_exact(double X, double Y, double Z, double hx, double hy, double a, double b, double* out)
+{
+    orc_axis_stencil sx = stencil_equal(hx), sy = stencil_equal(hy), sz = stencil_pair(a, b);
+    double norm = 1.0 / (4.0 * ORC_PI * hx * hy * a);
+    out[0] = norm * stencil3(orc_newell_f, X, Y, Z, &sx, &sy, &sz);
+    out[1] = norm * stencil3(orc_newell_f, Y, X, Z, &sy, &sx, &sz);
+    out[2] = norm * stencil3(orc_newell_f, Z, Y, X, &sz, &sy, &sx);
+    out[3] = norm * stencil3(orc_newell_g, X, Y, Z, &sx, &sy, &sz);
+    out[4] = norm * stencil3(orc_newell_g, X, Z, Y, &sx, &sz, &sy);
+    out[5] = norm * stencil3(orc_newell_g, Y, Z, X, &sy, &sz, &sx);
+}
+
+/* Far field of the pair tensor: box-averaged dipole expansion with the
+ * variance of the difference of two uniform points per axis, hx^2/6, hy^2/6
+ * and (a^2 + b^2)/12, and the source volume hx hy b. */
+void orc_newell_pair_asymptotic(double X, double Y, double Z, double hx, double hy, double a, double b, double* out)
+{
+    double x[3] = {X, Y, Z};
+    double var[3] = {hx * hx / 6.0, hy * hy / 6.0, (a * a + b * b) / 12.0};
+    double r = sqrt(X * X + Y * Y + Z * Z);
+    double r2 = r * r, r5 = r2 * r2 * r;
+    double Vs = hx * hy * b;
+    static const int ci[6] = {0, 1, 2, 0, 0, 1};
+    static const int cj[6] = {0, 1, 2, 1, 2, 2};
+    for (int c = 0; c < 6; c++) {
+        int i = ci[c], j = cj[c];
+        double D = (3.0 * x[i] * x[j] - (i == j ? r2 : 0.0)) / r5;
+        double corr = 0.0;
+        for (int k = 0; k < 3; k++) corr += 0.5 * var[k] * d4inv(x, r, i, j, k, k);
+        out[c] = -Vs / (4.0 * ORC_PI) * (D + corr);
+    }
+}
+
+/* Pair tensor with the far-field switch at rs times the largest cell size. */
+void orc_newell_pair(double X, double Y, double Z, double hx, double hy, double a, double b, double rs, double* out)
+{
+    double hmax = fmax(fmax(hx, hy), fmax(a, b));
+    if (sqrt(X * X + Y * Y + Z * Z) <= rs * hmax) orc_newell_pair_exact(X, Y, Z, hx, hy, a, b, out);
+    else orc_newell_pair_asymptotic(X, Y, Z, hx, hy, a, b, out);
+}
+
+/* Direct sum of Eq. 4 over a stack of layers sharing the in-plane cell
+ * (hx, hy).  Layer l: nxyz[3l..3l+2] cells, z size hz[l], in-plane offset
+ * (ox[l], oy[l]) in cells, bottom face at zb[l]; fields of all layers are
+ * concatenated, each SoA [3][nz][ny][nx].  H at the cells listed in `cells`
+ * (global cell index into the concatenation) -> H[3 * s + c]. */
+void orc_multilayer_direct_at(int nl, const int* nxyz, const double* hz, const int* ox, const int* oy,
+                              const double* zb, double hx, double hy, double rs, const double* M, int ns,
+                              const int64_t* cells, double* H)
+{
+    long off[64];
+    long tot = 0;
+    for (int l = 0; l < nl; l++) {
+        off[l] = tot;
+        tot += 3L * nxyz[3 * l] * nxyz[3 * l + 1] * nxyz[3 * l + 2];
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int s = 0; s < ns; s++) {
+        /* locate the target cell */
+        long g = cells[s], base = 0;
+        int tl = 0;
+        for (int l = 0; l < nl; l++) {
+            long n = (long)nxyz[3 * l] * nxyz[3 * l + 1] * nxyz[3 * l + 2];
+            if (g < base + n) { tl = l; break; }
+            base += n;
+        }
+        long loc = g - base;
+        int tnx = nxyz[3 * tl], tny = nxyz[3 * tl + 1];
+        int ti = (int)(loc % tnx), tj = (int)((loc / tnx) % tny), tk = (int)(loc / ((long)tnx * tny));
+        double tx = (ox[tl] + ti + 0.5) * hx, ty = (oy[tl] + tj + 0.5) * hy, tz = zb[tl] + (tk + 0.5) * hz[tl];
+        double h3[3] = {0, 0, 0};
+        for (int l = 0; l < nl; l++) {
+            int nx = nxyz[3 * l], ny = nxyz[3 * l + 1], nz = nxyz[3 * l + 2];
+            long n = (long)nx * ny * nz;
+            const double* Ml = M + off[l];
+            for (int k = 0; k < nz; k++)
+                for (int j = 0; j < ny; j++)
+                    for (int i = 0; i < nx; i++) {
+                        double sx = (ox[l] + i + 0.5) * hx, sy = (oy[l] + j + 0.5) * hy, sz = zb[l] + (k + 0.5) * hz[l];
+                        double v[6];
+                        orc_newell_pair(tx - sx, ty - sy, tz - sz, hx, hy, hz[tl], hz[l], rs, v);
+                        long c = ((long)k * ny + j) * nx + i;
+                        double mx = Ml[c], my = Ml[n + c], mz = Ml[2 * n + c];
+                        h3[0] -= v[0] * mx + v[3] * my + v[4] * mz;
+                        h3[1] -= v[3] * mx + v[1] * my + v[5] * mz;
+                        h3[2] -= v[4] * mx + v[5] * my + v[2] * mz;
+                    }
+        }
+        H[3 * s] = h3[0];
+        H[3 * s + 1] = h3[1];
+        H[3 * s + 2] = h3[2];
+    }
+}
