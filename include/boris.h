@@ -83,6 +83,32 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
                      void* cuda_stream, boris_plan* out);
 
 /*
+ * boris_multimesh_plan - prepare the multi-mesh demagnetising field of Eq. 4
+ *   for a stack of n_layers (1..16) rectangular meshes:
+ *     H(r'_kl) = -sum_i sum_{r_ij in V_i} N(r'_kl - r_ij, h_k, h_i) M(r_ij).
+ *   Layer l has nxyz[3l..3l+2] cells of size hxyz[3l..3l+2] (m) with its
+ *   lower corner at origin[3l..3l+2] (m).  All layers share the in-plane cell
+ *   size, and their in-plane origins differ by whole cells; their z sizes,
+ *   z positions and gaps are arbitrary (at most 256 z planes in total).  The
+ *   inter-mesh tensor between cells of z size a (target) and b (source) is
+ *   Newell's construction with the two-box z stencil, normalised by the
+ *   target volume (a far-field dipole expansion beyond 40 cell sizes), built
+ *   in FP64 on the device for every distinct (a, b, |dz|) and stored as its
+ *   2D in-plane spectrum.  flags: BORIS_FLAG_F32 only.  The plan works with
+ *   boris_demag_apply on the layers' fields concatenated in layer order, each
+ *   SoA [3][nz][ny][nx], and with boris_llg_step (per-cell maps concatenated
+ *   the same way).  Synchronises the stream.
+ *   Errors: INVALID_ARG, UNSUPPORTED_SIZE (frame transform above 4096 or
+ *   more than 256 planes), OOM, CUDA.
+ */
+int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, const double* origin, unsigned flags,
+                         void* cuda_stream, boris_plan* out);
+
+/* Multi-mesh plan facts: out[0] z planes, out[1] distinct inter-plane spectra,
+ * out[2..3] in-plane frame size (cells). */
+int boris_plan_multimesh_info(boris_plan p, int out[4]);
+
+/*
  * boris_demag_apply - Hd = -N * M (Table 1), FP32 plan.
  *   M, Hd: device [3][nz][ny][nx] float, A/m; may not alias.
  *   Three kernels: zero-padded x real-to-complex transform, fused y-z pass

@@ -26,7 +26,7 @@ MU0 = 4e-7 * math.pi
 GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
 
 #: entry points declared in include/boris.h
-EXPORTS = ["boris_demag_plan", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_apply_noalloc",
+EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_info", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_apply_noalloc",
            "boris_demag_adjoint",
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
@@ -62,6 +62,8 @@ def lib():
         P = ctypes.POINTER
         L.boris_demag_plan.argtypes = [i, i, i, d, d, d, u, vp, P(vp)]
         L.boris_demag_apply.argtypes = [vp, vp, vp]
+        L.boris_multimesh_plan.argtypes = [i, vp, vp, vp, u, vp, P(vp)]
+        L.boris_plan_multimesh_info.argtypes = [vp, P(i)]
         L.boris_demag_apply_f64.argtypes = [vp, vp, vp]
         L.boris_demag_adjoint.argtypes = [vp, vp, vp]
         L.boris_demag_apply_noalloc.argtypes = [vp, vp, vp]
@@ -166,6 +168,11 @@ class Plan:
         nx, ny, nz = self.shape
         return (3, nz, ny, nx)
 
+    @property
+    def map_shape(self):
+        nx, ny, nz = self.shape
+        return (nz, ny, nx)
+
     def padded(self):
         out = (ctypes.c_int * 3)()
         check(lib().boris_plan_padded(self._h, out))
@@ -200,10 +207,9 @@ class Plan:
         return out
 
     def _params(self, prm: LLGParams):
-        nx, ny, nz = self.shape
         for mp in (prm.Ms_map, prm.Ku_map):
             if mp is not None:
-                _ptr(mp, self.dtype, (nz, ny, nx))
+                _ptr(mp, self.dtype, self.map_shape)
         return prm.c()
 
     def llg_step(self, m, prm: LLGParams, dt: float) -> float:
@@ -221,10 +227,9 @@ class Plan:
         import torch
         if g_in is None:
             g_in = torch.empty_like(g_out)
-        nx, ny, nz = self.shape
         c = self._params(prm)
-        gms = _ptr(g_Ms, self.dtype, (nz, ny, nx)) if g_Ms is not None else None
-        gku = _ptr(g_Ku, self.dtype, (nz, ny, nx)) if g_Ku is not None else None
+        gms = _ptr(g_Ms, self.dtype, self.map_shape) if g_Ms is not None else None
+        gku = _ptr(g_Ku, self.dtype, self.map_shape) if g_Ku is not None else None
         fn = lib().boris_llg_step_backward_f64 if self.fp64 else lib().boris_llg_step_backward
         check(fn(self._h, _ptr(m_in, self.dtype, self.field_shape), ctypes.byref(c), float(dt),
                  _ptr(g_out, self.dtype, self.field_shape), _ptr(g_in, self.dtype, self.field_shape), gms, gku))
@@ -268,3 +273,44 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class MultiPlan(Plan):
+    """Multi-mesh plan (Eq. 4): layers[i] = (nx, ny, nz) cells of size
+    cells[i] = (hx, hy, hz) with lower corner origins[i] = (x, y, z), m.
+    Fields are the layers' SoA [3][nz][ny][nx] arrays concatenated in layer
+    order (flat tensors of 3 * total cells); maps likewise (total cells)."""
+
+    def __init__(self, layers, cells, origins, stream=None):
+        import numpy as np
+        import torch
+        self.layers = [tuple(int(v) for v in l) for l in layers]
+        self.fp64 = False
+        self.tc = None
+        self.dtype = torch.float32
+        self.total = sum(nx * ny * nz for nx, ny, nz in self.layers)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = st
+        nxyz = np.ascontiguousarray(np.array(self.layers, dtype=np.int32).reshape(-1))
+        hxyz = np.ascontiguousarray(np.array(cells, dtype=np.float64).reshape(-1))
+        org = np.ascontiguousarray(np.array(origins, dtype=np.float64).reshape(-1))
+        h = ctypes.c_void_p()
+        check(lib().boris_multimesh_plan(len(self.layers), nxyz.ctypes.data_as(ctypes.c_void_p),
+                                         hxyz.ctypes.data_as(ctypes.c_void_p), org.ctypes.data_as(ctypes.c_void_p),
+                                         FLAG_F32, ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        self.shape = None
+
+    @property
+    def field_shape(self):
+        return (3 * self.total,)
+
+    @property
+    def map_shape(self):
+        return (self.total,)
+
+    def info(self):
+        """(z planes, distinct inter-plane spectra, frame nx, frame ny)."""
+        out = (ctypes.c_int * 4)()
+        check(lib().boris_plan_multimesh_info(self._h, out))
+        return tuple(out)

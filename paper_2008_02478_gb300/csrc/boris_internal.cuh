@@ -129,6 +129,7 @@ struct PlanView {
     int device;
     const void* K;
     const void* tw;
+    bool ml;  // multi-mesh plan
 };
 // Number of kernel classes timed by the plan's profiler.
 constexpr int NPROF = 8;

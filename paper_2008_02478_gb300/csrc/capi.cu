@@ -7,8 +7,14 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <tuple>
+
 #include "boris_internal.cuh"
 #include "llg_kernels.cuh"
+#include "multilayer.cuh"
 
 using namespace boris;
 
@@ -46,6 +52,14 @@ struct boris_plan_s {
     unsigned int* h_err_bits = nullptr;  // pinned
     double* energy = nullptr;
     void* m_dev_e2e = nullptr;
+    // multi-mesh plans (boris_multimesh_plan)
+    bool ml = false;
+    MLTable mlt;
+    void* Kml = nullptr;    // unique inter-plane spectra [u][kx][ky'][6]
+    int* d_pairs = nullptr; // [Z * Z]
+    float* Mf = nullptr;    // frame fields [3][Z][NY][NX]
+    float* Hf = nullptr;
+    int ml_unique = 0;
     // adjoint workspace: stage states m2..m4, stage fields, stage derivatives,
     // stage cotangents, and three scratch fields
     void* bw = nullptr;
@@ -89,7 +103,11 @@ int dev_alloc(boris_plan p, void** ptr, size_t bytes)
 
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
-size_t ncell(const boris_plan p) { return (size_t)p->g.nx * p->g.ny * p->g.nz; }
+size_t ncell(const boris_plan p)
+{
+    if (p->ml) return p->mlt.total3 / 3;
+    return (size_t)p->g.nx * p->g.ny * p->g.nz;
+}
 
 cudaEvent_t take_event(boris_plan p)
 {
@@ -137,10 +155,28 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
     return timed(p, 1, [&] { return launch_yz_conv<T>(p->g, sc, (C*)p->X, (const T*)p->K, (const C*)p->tw, p->stream); });
 }
 
+int ml_demag_apply(boris_plan p, const float* M, const float* ms_map, float ms_scale, float* H)
+{
+    float2* X = (float2*)p->X;
+    float2* Yb = (float2*)p->Y;
+    const float2* tw = (const float2*)p->tw;
+    CUDA_TRY(timed(p, 4, [&] { return ml_embed(p->mlt, M, ms_map, ms_scale, p->Mf, p->stream); }));
+    CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<float>(p->g, p->Mf, nullptr, 1.0f, X, tw, p->stream); }));
+    CUDA_TRY(timed(p, 5, [&] { return launch_split<float>(p->g, X, Yb, nullptr, tw, p->stream, 0, 2); }));
+    CUDA_TRY(timed(p, 6, [&] { return ml_mix(p->g, p->mlt.Z, Yb, (const float*)p->Kml, p->d_pairs, p->stream); }));
+    CUDA_TRY(timed(p, 7, [&] { return launch_split<float>(p->g, X, Yb, nullptr, tw, p->stream, 2, 2); }));
+    CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<float>(p->g, X, p->Hf, tw, p->stream); }));
+    CUDA_TRY(timed(p, 4, [&] { return ml_extract(p->mlt, p->Hf, H, p->stream); }));
+    return BORIS_OK;
+}
+
 template <typename T>
 int demag_apply_t(boris_plan p, const T* M, const T* ms_map, T ms_scale, T* H)
 {
     using C = typename Cx<T>::t;
+    if constexpr (sizeof(T) == 4) {
+        if (p->ml) return ml_demag_apply(p, M, ms_map, ms_scale, H);
+    }
     CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<T>(p->g, M, ms_map, ms_scale, (C*)p->X, (const C*)p->tw, p->stream); }));
     CUDA_TRY(yz_stage<T>(p, p->yz));
     CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<T>(p->g, (const C*)p->X, H, (const C*)p->tw, p->stream); }));
@@ -213,6 +249,14 @@ int rk4_step_t(boris_plan p, T* m, const LLGArgs<T>& a)
     for (int s = 0; s < 4; s++) {
         int rc = demag_apply_t<T>(p, in[s], ms_map, ms_scale, Hd);
         if (rc) return rc;
+        if constexpr (sizeof(T) == 4) {
+            if (p->ml) {
+                CUDA_TRY(timed(p, 3, [&] {
+                    return launch_rk4_stage_ml(a, p->mlt, s, in[s], Hd, m, acc, out[s], p->stream);
+                }));
+                continue;
+            }
+        }
         CUDA_TRY(timed(p, 3, [&] { return launch_rk4_stage<T>(a, s, in[s], Hd, m, acc, out[s], p->stream); }));
     }
     return BORIS_OK;
@@ -275,6 +319,7 @@ int llg_step_t(boris_plan p, T* m, const boris_llg_params* prm, double* dt)
         return rk4_step_t<T>(p, m, a);
     }
     if (prm->method == BORIS_RKF45) {
+        if (p->ml) return fail(BORIS_ERR_INVALID_ARG, "multi-mesh plans step with RK4");
         LLGArgs<T> a;
         if ((rc = check_params<T>(p, prm, &a, 1.0))) return rc;
         return rkf45_step_t<T>(p, m, prm, dt);
@@ -291,6 +336,7 @@ int llg_backward_t(boris_plan p, const T* m_in, const boris_llg_params* prm, dou
         (g_Ku && !aligned16(g_Ku)))
         return fail(BORIS_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
     if (prm->method != BORIS_RK4) return fail(BORIS_ERR_INVALID_ARG, "the adjoint is of the RK4 step");
+    if (p->ml) return fail(BORIS_ERR_INVALID_ARG, "the adjoint serves single-mesh plans");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(BORIS_ERR_INVALID_ARG, "dt must be > 0");
     int rc = ensure_llg_workspace<T>(p, false);
     if (rc) return rc;
@@ -384,6 +430,7 @@ bool plan_view(boris_plan p, PlanView* v)
     v->device = p->device;
     v->K = p->K;
     v->tw = p->tw;
+    v->ml = p->ml;
     return true;
 }
 }  // namespace boris
@@ -542,6 +589,161 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     return BORIS_OK;
 }
 
+int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, const double* origin, unsigned flags,
+                         void* cuda_stream, boris_plan* out)
+{
+    if (!out) return fail(BORIS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_layers < 1 || n_layers > ML_MAX_LAYERS || !nxyz || !hxyz || !origin)
+        return fail(BORIS_ERR_INVALID_ARG, "need 1..16 layers and their sizes, cells and origins");
+    if (flags != BORIS_FLAG_F32) return fail(BORIS_ERR_INVALID_ARG, "multi-mesh plans are FP32");
+    const double hx = hxyz[0], hy = hxyz[1];
+    double x0 = origin[0], y0 = origin[1];
+    int Z = 0;
+    for (int l = 0; l < n_layers; l++) {
+        if (nxyz[3 * l] < 1 || nxyz[3 * l + 1] < 1 || nxyz[3 * l + 2] < 1)
+            return fail(BORIS_ERR_INVALID_ARG, "layer sizes must be >= 1");
+        if (!(hxyz[3 * l + 2] > 0) || std::fabs(hxyz[3 * l] - hx) > 1e-9 * hx || std::fabs(hxyz[3 * l + 1] - hy) > 1e-9 * hy)
+            return fail(BORIS_ERR_INVALID_ARG, "all layers must share the in-plane cell size (hx, hy)");
+        x0 = std::min(x0, origin[3 * l]);
+        y0 = std::min(y0, origin[3 * l + 1]);
+        Z += nxyz[3 * l + 2];
+    }
+    if (!(hx > 0) || !(hy > 0)) return fail(BORIS_ERR_INVALID_ARG, "cell sizes must be > 0");
+    if (Z > ML_MAX_PLANES) return fail(BORIS_ERR_UNSUPPORTED_SIZE, "more than 256 z planes in the stack");
+    MLTable t = {};
+    t.nl = n_layers;
+    t.Z = Z;
+    std::vector<double> zc(Z), hzp(Z);
+    size_t off = 0;
+    int p0 = 0;
+    for (int l = 0; l < n_layers; l++) {
+        const double fx = (origin[3 * l] - x0) / hx, fy = (origin[3 * l + 1] - y0) / hy;
+        const int ox = (int)std::lround(fx), oy = (int)std::lround(fy);
+        if (std::fabs(fx - ox) > 1e-6 || std::fabs(fy - oy) > 1e-6)
+            return fail(BORIS_ERR_INVALID_ARG, "in-plane layer offsets must be whole cells");
+        t.nx[l] = nxyz[3 * l];
+        t.ny[l] = nxyz[3 * l + 1];
+        t.nz[l] = nxyz[3 * l + 2];
+        t.ox[l] = ox;
+        t.oy[l] = oy;
+        t.hz[l] = (float)hxyz[3 * l + 2];
+        t.plane0[l] = p0;
+        t.off[l] = off;
+        off += 3 * (size_t)t.nx[l] * t.ny[l] * t.nz[l];
+        t.NX = std::max(t.NX, ox + t.nx[l]);
+        t.NY = std::max(t.NY, oy + t.ny[l]);
+        for (int q = 0; q < t.nz[l]; q++) {
+            zc[p0 + q] = origin[3 * l + 2] + (q + 0.5) * hxyz[3 * l + 2];
+            hzp[p0 + q] = hxyz[3 * l + 2];
+            t.plane_layer[p0 + q] = (unsigned char)l;
+        }
+        p0 += t.nz[l];
+    }
+    t.off[n_layers] = off;
+    t.total3 = off;
+    // unique inter-plane spectra keyed by (target size, source size, |dz|)
+    MLHost h;
+    h.hx = hx;
+    h.hy = hy;
+    h.pairs.resize((size_t)Z * Z);
+    std::map<std::tuple<long long, long long, long long>, int> uniq;
+    const double qz = 1e-6 * *std::min_element(hzp.begin(), hzp.end());
+    for (int pp = 0; pp < Z; pp++)
+        for (int q = 0; q < Z; q++) {
+            const double dz = zc[pp] - zc[q];
+            auto key = std::make_tuple(std::llround(hzp[pp] / qz), std::llround(hzp[q] / qz), std::llround(std::fabs(dz) / qz));
+            auto it = uniq.find(key);
+            int u;
+            if (it == uniq.end()) {
+                u = (int)h.ua.size();
+                uniq[key] = u;
+                h.ua.push_back(hzp[pp]);
+                h.ub.push_back(hzp[q]);
+                h.udz.push_back(std::fabs(dz));
+            } else {
+                u = it->second;
+            }
+            h.pairs[(size_t)pp * Z + q] = u | (dz < 0 ? (1 << 30) : 0);
+        }
+    Geometry g;
+    g.nx = t.NX;
+    g.ny = t.NY;
+    g.nz = Z;
+    g.px = padded_len(t.NX);
+    g.py = padded_len(t.NY);
+    g.pz = 1;
+    if (g.px > 4096 || g.py > 4096) return fail(BORIS_ERR_UNSUPPORTED_SIZE, "padded transform length above 4096");
+    g.lgx = ilog2(g.px);
+    g.lgy = ilog2(g.py);
+    g.lgz = 0;
+    g.nkx = g.px / 2 + 1;
+    g.kyh = g.py / 2 + 1;
+    g.kzh = 1;
+    g.krow = 8;
+    g.lmax = std::max(g.px, std::max(g.py, 64));
+    g.lglmax = ilog2(g.lmax);
+
+    boris_plan p = new (std::nothrow) boris_plan_s();
+    if (!p) return fail(BORIS_ERR_OOM, "host allocation");
+    auto bail = [&](int code) {
+        boris_plan_destroy(p);
+        return code;
+    };
+    p->g = g;
+    p->dx = hx;
+    p->dy = hy;
+    p->dz = hxyz[2];
+    p->flags = flags;
+    p->stream = (cudaStream_t)cuda_stream;
+    p->ml = true;
+    p->mlt = t;
+    p->ml_unique = (int)h.ua.size();
+    p->yz = YZSchedule{2, 2, 0, 0, 0};
+    int rc;
+    if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "no CUDA device"));
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if (!split_supported<float>(g, max_smem)) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "frame too large"));
+    cudaError_t ce = upload_twiddles_split();
+    if (ce == cudaSuccess) ce = upload_twiddles_fast();
+    if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "twiddle constants"));
+    std::vector<double2> tw(g.lmax);
+    host_twiddles(g.lmax, tw.data());
+    std::vector<float2> twf(g.lmax);
+    for (int i = 0; i < g.lmax; i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+    if ((rc = dev_alloc(p, (void**)&p->tw64, g.lmax * sizeof(double2)))) return bail(rc);
+    if ((rc = dev_alloc(p, &p->tw, g.lmax * sizeof(float2)))) return bail(rc);
+    cudaMemcpy(p->tw64, tw.data(), g.lmax * sizeof(double2), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->tw, twf.data(), g.lmax * sizeof(float2), cudaMemcpyHostToDevice);
+    const size_t kbytes = (size_t)p->ml_unique * g.nkx * g.kyh * 6 * sizeof(float);
+    if ((rc = dev_alloc(p, &p->Kml, kbytes))) return bail(rc);
+    if ((rc = dev_alloc(p, (void**)&p->d_pairs, h.pairs.size() * sizeof(int)))) return bail(rc);
+    cudaMemcpy(p->d_pairs, h.pairs.data(), h.pairs.size() * sizeof(int), cudaMemcpyHostToDevice);
+    ce = ml_build_spectra(h, g, (float*)p->Kml, p->tw64, p->stream);
+    if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("inter-mesh spectra: ") + cudaGetErrorString(ce)));
+    const size_t frame = 3 * (size_t)Z * t.NY * t.NX;
+    if ((rc = dev_alloc(p, (void**)&p->Mf, frame * sizeof(float)))) return bail(rc);
+    if ((rc = dev_alloc(p, (void**)&p->Hf, frame * sizeof(float)))) return bail(rc);
+    if ((rc = dev_alloc(p, &p->X, (size_t)g.nkx * 3 * Z * g.ny * sizeof(float2)))) return bail(rc);
+    if ((rc = dev_alloc(p, &p->Y, (size_t)g.nkx * g.py * 3 * Z * sizeof(float2)))) return bail(rc);
+    if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
+        return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
+    *out = p;
+    return BORIS_OK;
+}
+
+int boris_plan_multimesh_info(boris_plan p, int out[4])
+{
+    if (!p || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (!p->ml) return fail(BORIS_ERR_INVALID_ARG, "not a multi-mesh plan");
+    out[0] = p->mlt.Z;
+    out[1] = p->ml_unique;
+    out[2] = p->mlt.NX;
+    out[3] = p->mlt.NY;
+    return BORIS_OK;
+}
+
 int boris_demag_apply(boris_plan p, const float* M, float* Hd)
 {
     if (!p || !M || !Hd) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
@@ -614,6 +816,7 @@ int boris_energy(boris_plan p, const float* m, const boris_llg_params* prm, doub
 {
     if (!p || !m || !prm || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
     if (p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan");
+    if (p->ml) return fail(BORIS_ERR_INVALID_ARG, "energies of multi-mesh plans are not provided");
     int rc = ensure_llg_workspace<float>(p, false);
     if (rc) return rc;
     LLGArgs<float> a;
@@ -691,7 +894,7 @@ void boris_plan_destroy(boris_plan p)
 {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
-    void* ptrs[] = {p->K, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
+    void* ptrs[] = {p->Kml, p->d_pairs, p->Mf, p->Hf, p->K, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
                     p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);

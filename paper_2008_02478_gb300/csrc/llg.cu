@@ -13,6 +13,7 @@
 // the Fehlberg tableau and the embedded error max |m5 - m4|.
 #include "boris_internal.cuh"
 #include "llg_kernels.cuh"
+#include "multilayer.cuh"
 
 namespace boris {
 
@@ -208,6 +209,97 @@ __global__ void __launch_bounds__(256) energy_kernel(LLGArgs<T> a, const T* __re
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
         atomicAdd(out + threadIdx.x, v * a.V);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Multi-mesh RK4 stage: one launch over all layers' cells (fields concatenated
+// in layer order, each SoA [3][nz][ny][nx]); exchange couples neighbours
+// inside a layer only (Table 1 exchange with Neumann boundaries per mesh).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void ml_field_and_rhs(const LLGArgs<T>& a, const MLTable& t, const T* __restrict__ ms,
+                                                 const T* __restrict__ Hd, size_t idx, size_t vi[3], T m[3], T k[3])
+{
+    int l = 0;
+    while (l + 1 < t.nl && idx >= t.off[l + 1] / 3) l++;
+    const size_t base = t.off[l], cell = idx - base / 3;
+    const int nx = t.nx[l], ny = t.ny[l], nz = t.nz[l];
+    const size_t n = (size_t)nx * ny * nz;
+    const int x = (int)(cell % nx), y = (int)((cell / nx) % ny), z = (int)(cell / ((size_t)nx * ny));
+    for (int c = 0; c < 3; c++) vi[c] = base + c * n + cell;
+    m[0] = ms[vi[0]];
+    m[1] = ms[vi[1]];
+    m[2] = ms[vi[2]];
+    T lap[3] = {T(0), T(0), T(0)};
+    auto nb = [&](size_t j, T w) {
+        lap[0] += w * (ms[vi[0] + j - cell] - m[0]);
+        lap[1] += w * (ms[vi[1] + j - cell] - m[1]);
+        lap[2] += w * (ms[vi[2] + j - cell] - m[2]);
+    };
+    const T ihz2 = T(1) / (T(t.hz[l]) * T(t.hz[l]));
+    const size_t sy = nx, sz = (size_t)nx * ny;
+    if (x > 0) nb(cell - 1, a.ihx2);
+    if (x < nx - 1) nb(cell + 1, a.ihx2);
+    if (y > 0) nb(cell - sy, a.ihy2);
+    if (y < ny - 1) nb(cell + sy, a.ihy2);
+    if (z > 0) nb(cell - sz, ihz2);
+    if (z < nz - 1) nb(cell + sz, ihz2);
+    const T Ms = a.ms_map ? a.ms_map[idx] : a.Ms;
+    const T Ku = a.ku_map ? a.ku_map[idx] : a.Ku;
+    const T inv = T(1) / (T(MU0_D) * Ms);
+    const T cex = T(2) * a.A * inv;
+    const T me = m[0] * a.e[0] + m[1] * a.e[1] + m[2] * a.e[2];
+    const T can = T(2) * Ku * inv * me;
+    T H[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) H[c] = Hd[vi[c]] + cex * lap[c] + can * a.e[c] + a.Hext[c];
+    const T mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
+    const T mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2], m[0] * mxH[1] - m[1] * mxH[0]};
+#pragma unroll
+    for (int c = 0; c < 3; c++) k[c] = -a.gp * (mxH[c] + a.alpha * mmH[c]);
+}
+
+__global__ void __launch_bounds__(256) rk4_stage_ml_kernel(LLGArgs<float> a, MLTable t, int s,
+                                                           const float* __restrict__ ms, const float* __restrict__ Hd,
+                                                           float* __restrict__ m0, float* __restrict__ acc,
+                                                           float* __restrict__ mnext)
+{
+    const size_t n = a.ncell;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        size_t vi[3];
+        float m[3], k[3];
+        ml_field_and_rhs(a, t, ms, Hd, i, vi, m, k);
+        if (s == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                acc[vi[c]] = k[c];
+                mnext[vi[c]] = m[c] + 0.5f * a.dt * k[c];
+            }
+        } else if (s < 3) {
+            const float cdt = s == 1 ? 0.5f * a.dt : a.dt;
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                acc[vi[c]] += 2.f * k[c];
+                mnext[vi[c]] = m0[vi[c]] + cdt * k[c];
+            }
+        } else {
+            float v[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) v[c] = m0[vi[c]] + a.dt * (1.f / 6.f) * (acc[vi[c]] + k[c]);
+            const float inv = rsqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+#pragma unroll
+            for (int c = 0; c < 3; c++) m0[vi[c]] = v[c] * inv;
+        }
+    }
+}
+
+cudaError_t launch_rk4_stage_ml(const LLGArgs<float>& a, const MLTable& t, int s, const float* ms, const float* Hd,
+                                float* m0, float* acc, float* mnext, cudaStream_t st)
+{
+    size_t b = (a.ncell + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    rk4_stage_ml_kernel<<<(int)(b > 0 ? b : 1), 256, 0, st>>>(a, t, s, ms, Hd, m0, acc, mnext);
+    return cudaGetLastError();
 }
 
 static int grid_for(size_t n)

@@ -42,6 +42,9 @@ cudaError_t launch_bwd_local(const LLGArgs<T>& a, const T* ms, const T* Hs, cons
 template <typename T>
 cudaError_t launch_bwd_field(const LLGArgs<T>& a, const T* ms, const T* gH, const T* DgH, const T* gml, T* gm,
                              T* gk_prev, T coef, T* gMs, T* gKu, cudaStream_t st);
+struct MLTable;
+cudaError_t launch_rk4_stage_ml(const LLGArgs<float>& a, const MLTable& t, int s, const float* ms, const float* Hd,
+                                float* m0, float* acc, float* mnext, cudaStream_t st);
 template <typename T>
 cudaError_t launch_energy(const LLGArgs<T>& a, const T* m, const T* Hd, double* out, cudaStream_t st);
 

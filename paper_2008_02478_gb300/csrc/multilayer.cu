@@ -1,0 +1,317 @@
+// Multi-mesh demagnetising field (Eq. 4) for a stack of layers that share the
+// in-plane cell (hx, hy): each layer has its own z cell size, in-plane offset
+// and z position.
+//
+// All layers are embedded in one common in-plane frame (NX x NY cells), so
+// every z plane of every layer is a plane of one batched transform: the x and
+// y transforms of the single-mesh path run once over all Z = sum nz planes.
+// In transform space the inter-mesh sum of Eq. 4 becomes, per (kx, ky),
+//   Hh(p) = sum_q N^(kx, ky; p, q) Mh(q)
+// with N^ the 2D spectrum of the inter-mesh tensor between the cells of plane
+// p (z size a) and plane q (z size b) at z offset dz = z_p - z_q.  Spectra are
+// deduplicated by (a, b, |dz|); dz < 0 flips the xz and yz components (odd in
+// z).  The tensor itself is Newell's construction with the z stencil of two
+// boxes of unequal height, F(z + s) - F(z + d) - F(z - d) + F(z - s),
+// s = (a + b)/2, d = (a - b)/2, normalised by the target volume; beyond 40
+// cell sizes the box-averaged dipole expansion with per-axis variances
+// hx^2/6, hy^2/6, (a^2 + b^2)/12 and the source volume.
+#include <algorithm>
+
+#include "boris_internal.cuh"
+#include "multilayer.cuh"
+#include "newell_fg.cuh"
+
+namespace boris {
+
+// Stencil of one axis: n taps at offsets off with weights w.
+struct Taps {
+    int n;
+    double off[4], w[4];
+};
+__device__ __forceinline__ Taps taps_equal(double h) { return Taps{3, {-h, 0.0, h, 0.0}, {-1.0, 2.0, -1.0, 0.0}}; }
+__device__ __forceinline__ Taps taps_pair(double a, double b)
+{
+    const double s = 0.5 * (a + b), d = 0.5 * (a - b);
+    return Taps{4, {-s, -d, d, s}, {-1.0, 1.0, 1.0, -1.0}};
+}
+
+template <bool G>
+__device__ double pair_sum(double X, double Y, double Z, const Taps& t1, const Taps& t2, const Taps& t3)
+{
+    double acc = 0.0;
+    for (int i = 0; i < t1.n; i++)
+        for (int j = 0; j < t2.n; j++)
+            for (int k = 0; k < t3.n; k++) {
+                const double w = t1.w[i] * t2.w[j] * t3.w[k];
+                const double x = X + t1.off[i], y = Y + t2.off[j], z = Z + t3.off[k];
+                acc += w * (G ? newell_g_dev(x, y, z) : newell_f_dev(x, y, z));
+            }
+    return acc;
+}
+
+__device__ void pair_tensor(double X, double Y, double Z, double hx, double hy, double a, double b, double rs,
+                            double out[6])
+{
+    const double hmax = fmax(fmax(hx, hy), fmax(a, b));
+    const double r2 = X * X + Y * Y + Z * Z;
+    if (sqrt(r2) <= rs * hmax) {
+        const Taps tx = taps_equal(hx), ty = taps_equal(hy), tz = taps_pair(a, b);
+        const double norm = 1.0 / (4.0 * 3.14159265358979323846 * hx * hy * a);
+        out[0] = norm * pair_sum<false>(X, Y, Z, tx, ty, tz);
+        out[1] = norm * pair_sum<false>(Y, X, Z, ty, tx, tz);
+        out[2] = norm * pair_sum<false>(Z, Y, X, tz, ty, tx);
+        out[3] = norm * pair_sum<true>(X, Y, Z, tx, ty, tz);
+        out[4] = norm * pair_sum<true>(X, Z, Y, tx, tz, ty);
+        out[5] = norm * pair_sum<true>(Y, Z, X, ty, tz, tx);
+        return;
+    }
+    // sum_k var_k/2 d_k^2 D_ij with var = (hx^2/6, hy^2/6, (a^2+b^2)/12):
+    // with S2 = sum_k c_k x_k^2, Cs = sum_k c_k (c_k = var_k/2):
+    //   105 x_i x_j S2/r^9 - 15 [x_i x_j (Cs + 2 c_i + 2 c_j) + delta_ij S2]/r^7 + 3 delta_ij (Cs + 2 c_i)/r^5
+    const double x[3] = {X, Y, Z};
+    const double c[3] = {hx * hx / 12.0, hy * hy / 12.0, (a * a + b * b) / 24.0};
+    const double r = sqrt(r2), ir2 = 1.0 / r2, ir5 = ir2 * ir2 / r, ir7 = ir5 * ir2, ir9 = ir7 * ir2;
+    const double S2 = c[0] * X * X + c[1] * Y * Y + c[2] * Z * Z, Cs = c[0] + c[1] + c[2];
+    const double pre = -(hx * hy * b) / (4.0 * 3.14159265358979323846);
+    const int I[6] = {0, 1, 2, 0, 0, 1}, J[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; k++) {
+        const int i = I[k], j = J[k];
+        const double xij = x[i] * x[j], d = i == j ? 1.0 : 0.0;
+        const double D = (3.0 * xij - d * r2) * ir5;
+        const double corr = 105.0 * xij * S2 * ir9 - 15.0 * (xij * (Cs + 2.0 * c[i] + 2.0 * c[j]) + d * S2) * ir7 +
+                            3.0 * d * (Cs + 2.0 * c[i]) * ir5;
+        out[k] = pre * (D + corr);
+    }
+}
+
+// In-plane tensor tables of nu unique (a, b, |dz|) entries: T[u][6][NY][NX].
+__global__ void ml_tensor_kernel(int nu, const double* __restrict__ ua, const double* __restrict__ ub,
+                                 const double* __restrict__ udz, int NX, int NY, double hx, double hy, double rs,
+                                 double* __restrict__ T)
+{
+    const size_t plane = (size_t)NX * NY;
+    const size_t n = (size_t)nu * plane;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+        const int u = (int)(idx / plane);
+        const size_t cell = idx % plane;
+        const int i = (int)(cell % NX), j = (int)(cell / NX);
+        double v[6];
+        pair_tensor(i * hx, j * hy, udz[u], hx, hy, ua[u], ub[u], rs, v);
+        for (int c = 0; c < 6; c++) T[((size_t)u * 6 + c) * plane + cell] = v[c];
+    }
+}
+
+// 2D spectra [6 nu][kyh][nkx] (complex) -> K[u][kx][ky'][6] with the real part of
+// xx, yy, zz, xy and the imaginary part of xz, yz (odd in exactly one in-plane
+// axis), scaled by -1/(px py).
+__global__ void ml_finalize_kernel(const double2* __restrict__ S, float* __restrict__ K, int nu, int nkx, int kyh,
+                                   double scale)
+{
+    const size_t per = (size_t)nkx * kyh;
+    const size_t total = (size_t)nu * per * 6;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx % 6);
+        const size_t rec = idx / 6;  // (u, kx, ky)
+        const int u = (int)(rec / per);
+        const size_t r = rec % per;
+        const int kx = (int)(r / kyh), ky = (int)(r % kyh);
+        const double2 s = S[((size_t)u * 6 + c) * per + (size_t)ky * nkx + kx];
+        K[idx] = (float)(-(c < 4 ? s.x : s.y) * scale);
+    }
+}
+
+// Embed the concatenated layer fields (scaled by Ms) into the frame [3][Z][NY][NX].
+__global__ void ml_embed_kernel(MLTable t, const float* __restrict__ M, const float* __restrict__ ms_map, float ms,
+                                float* __restrict__ F)
+{
+    const size_t fplane = (size_t)t.NX * t.NY;
+    const size_t total = 3 * (size_t)t.Z * fplane;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(idx % t.NX);
+        const int y = (int)((idx / t.NX) % t.NY);
+        const int p = (int)((idx / fplane) % t.Z);
+        const int c = (int)(idx / (fplane * t.Z));
+        const int l = t.plane_layer[p], q = p - t.plane0[l];
+        const int lx = x - t.ox[l], ly = y - t.oy[l];
+        float v = 0.f;
+        if (lx >= 0 && lx < t.nx[l] && ly >= 0 && ly < t.ny[l]) {
+            const size_t n = (size_t)t.nx[l] * t.ny[l] * t.nz[l];
+            const size_t cell = ((size_t)q * t.ny[l] + ly) * t.nx[l] + lx;
+            v = M[t.off[l] + c * n + cell] * (ms_map ? ms_map[t.off[l] / 3 + cell] : ms);
+        }
+        F[idx] = v;
+    }
+}
+
+// Extract the layers' cells of the frame field into the concatenated layout.
+__global__ void ml_extract_kernel(MLTable t, const float* __restrict__ F, float* __restrict__ H)
+{
+    const size_t total = t.total3;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        int l = 0;
+        while (l + 1 < t.nl && idx >= t.off[l + 1]) l++;
+        const size_t local = idx - t.off[l];
+        const size_t n = (size_t)t.nx[l] * t.ny[l] * t.nz[l];
+        const int c = (int)(local / n);
+        const size_t cell = local % n;
+        const int lx = (int)(cell % t.nx[l]), ly = (int)((cell / t.nx[l]) % t.ny[l]), q = (int)(cell / ((size_t)t.nx[l] * t.ny[l]));
+        const int p = t.plane0[l] + q;
+        H[idx] = F[(((size_t)c * t.Z + p) * t.NY + ly + t.oy[l]) * t.NX + lx + t.ox[l]];
+    }
+}
+
+// Inter-plane sum in transform space.  CTA: 32 consecutive ky of one kx; warp w
+// accumulates the target planes p = w, w + 8, ...; lane = column.
+// Y layout [kx][c][p][ky]; pairs[p * Z + q] = u (>= 0) with bit 30 set when
+// z_p < z_q (xz and yz change sign).
+template <int PMAX>
+__global__ void __launch_bounds__(256) ml_mix_kernel(Geometry g, int Z, float2* __restrict__ Y,
+                                                     const float* __restrict__ K, const int* __restrict__ pairs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* Ms = reinterpret_cast<float2*>(smem_raw);  // [Z][3][32]
+    int* pr = reinterpret_cast<int*>(Ms + (size_t)Z * 3 * 32);
+    const int kx = blockIdx.y, ky0 = blockIdx.x * 32, py = g.py;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ky = ky0 + lane;
+    const bool on = ky < py;
+    float2* base = Y + (size_t)kx * 3 * Z * py + ky0;
+    for (int i = threadIdx.x; i < Z * Z; i += 256) pr[i] = pairs[i];
+    for (int i = threadIdx.x; i < 3 * Z * 32; i += 256) {
+        const int line = i >> 5, col = i & 31;  // line = c * Z + p
+        const int c = line / Z, p = line % Z;
+        Ms[(p * 3 + c) * 32 + col] = (ky0 + col < py) ? base[(size_t)line * py + col] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const bool fy = ky > py / 2;
+    const int kyf = fy ? py - ky : ky;
+    const float sy = fy ? -1.f : 1.f;
+    const size_t per = (size_t)g.nkx * g.kyh;
+    const float* Kc = K + ((size_t)kx * g.kyh + kyf) * 6;
+    float2 acc[PMAX][3];
+#pragma unroll
+    for (int j = 0; j < PMAX; j++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) acc[j][c] = make_float2(0.f, 0.f);
+    for (int q = 0; q < Z; q++) {
+        const float2 mx = Ms[(q * 3 + 0) * 32 + lane], my = Ms[(q * 3 + 1) * 32 + lane], mz = Ms[(q * 3 + 2) * 32 + lane];
+#pragma unroll
+        for (int j = 0; j < PMAX; j++) {
+            const int p = warp + 8 * j;
+            if (p < Z) {
+                const int code = pr[p * Z + q];
+                const int u = code & 0x3fffffff;
+                const float sz = (code >> 30) & 1 ? -1.f : 1.f;
+                const float* k = Kc + (size_t)u * per * 6;
+                const float2 k01 = on ? *reinterpret_cast<const float2*>(k) : make_float2(0.f, 0.f);
+                const float2 k23 = on ? *reinterpret_cast<const float2*>(k + 2) : make_float2(0.f, 0.f);
+                const float2 k45 = on ? *reinterpret_cast<const float2*>(k + 4) : make_float2(0.f, 0.f);
+                const float kxx = k01.x, kyy = k01.y, kzz = k23.x, kxy = sy * k23.y;
+                const float kxz = sz * k45.x, kyz = sy * sz * k45.y;  // imaginary parts: i * kxz, i * kyz
+                // x: kxx mx + kxy my + i kxz mz
+                acc[j][0].x += kxx * mx.x + kxy * my.x - kxz * mz.y;
+                acc[j][0].y += kxx * mx.y + kxy * my.y + kxz * mz.x;
+                // y: kxy mx + kyy my + i kyz mz
+                acc[j][1].x += kxy * mx.x + kyy * my.x - kyz * mz.y;
+                acc[j][1].y += kxy * mx.y + kyy * my.y + kyz * mz.x;
+                // z: i kxz mx + i kyz my + kzz mz
+                acc[j][2].x += -kxz * mx.y - kyz * my.y + kzz * mz.x;
+                acc[j][2].y += kxz * mx.x + kyz * my.x + kzz * mz.y;
+            }
+        }
+    }
+    if (!on) return;
+#pragma unroll
+    for (int j = 0; j < PMAX; j++) {
+        const int p = warp + 8 * j;
+        if (p < Z)
+#pragma unroll
+            for (int c = 0; c < 3; c++) base[(size_t)(c * Z + p) * py + lane] = acc[j][c];
+    }
+}
+
+cudaError_t ml_build_spectra(const MLHost& h, const Geometry& g, float* K, const double2* tw64, cudaStream_t st)
+{
+    const int nu = (int)h.ua.size();
+    const int NX = g.nx, NY = g.ny;
+    // process the unique entries in batches that keep the FP64 staging modest
+    const size_t plane = (size_t)NX * NY;
+    int batch = (int)std::max<size_t>(1, ((size_t)1 << 31) / (plane * 6 * sizeof(double) * 3));
+    if (batch > nu) batch = nu;
+    double *ua = nullptr, *ub = nullptr, *udz = nullptr, *T = nullptr;
+    double2 *A = nullptr, *B = nullptr;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMallocAsync((void**)&ua, nu * sizeof(double), st)) != cudaSuccess) break;
+        if ((e = cudaMallocAsync((void**)&ub, nu * sizeof(double), st)) != cudaSuccess) break;
+        if ((e = cudaMallocAsync((void**)&udz, nu * sizeof(double), st)) != cudaSuccess) break;
+        cudaMemcpyAsync(ua, h.ua.data(), nu * sizeof(double), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(ub, h.ub.data(), nu * sizeof(double), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(udz, h.udz.data(), nu * sizeof(double), cudaMemcpyHostToDevice, st);
+        if ((e = cudaMallocAsync((void**)&T, (size_t)batch * 6 * plane * sizeof(double), st)) != cudaSuccess) break;
+        if ((e = cudaMallocAsync((void**)&A, (size_t)batch * 6 * g.nkx * NY * sizeof(double2), st)) != cudaSuccess) break;
+        if ((e = cudaMallocAsync((void**)&B, (size_t)batch * 6 * g.nkx * g.kyh * sizeof(double2), st)) != cudaSuccess) break;
+        for (int u0 = 0; u0 < nu && e == cudaSuccess; u0 += batch) {
+            const int nb = std::min(batch, nu - u0);
+            const size_t tot = (size_t)nb * plane;
+            int blocks = (int)std::min<size_t>((tot + 255) / 256, 152 * 64);
+            ml_tensor_kernel<<<blocks, 256, 0, st>>>(nb, ua + u0, ub + u0, udz + u0, NX, NY, h.hx, h.hy, 40.0, T);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            // x then y transform of the parity-extended in-plane tables
+            if ((e = run_axis_n(T, true, A, 0, NX, NY, 1, NX, g.px, 6 * nb, tw64, g.lglmax, st)) != cudaSuccess) break;
+            if ((e = run_axis_n(A, false, B, 1, g.nkx, NY, 1, NY, g.py, 6 * nb, tw64, g.lglmax, st)) != cudaSuccess) break;
+            const size_t kt = (size_t)nb * g.nkx * g.kyh * 6;
+            blocks = (int)std::min<size_t>((kt + 255) / 256, 152 * 64);
+            ml_finalize_kernel<<<blocks, 256, 0, st>>>(B, K + (size_t)u0 * g.nkx * g.kyh * 6, nb, g.nkx, g.kyh,
+                                                       1.0 / ((double)g.px * g.py));
+            e = cudaGetLastError();
+        }
+    } while (0);
+    if (ua) cudaFreeAsync(ua, st);
+    if (ub) cudaFreeAsync(ub, st);
+    if (udz) cudaFreeAsync(udz, st);
+    if (T) cudaFreeAsync(T, st);
+    if (A) cudaFreeAsync(A, st);
+    if (B) cudaFreeAsync(B, st);
+    return e;
+}
+
+static int grid_n(size_t n)
+{
+    size_t b = (n + 255) / 256;
+    return (int)std::max<size_t>(1, std::min<size_t>(b, 152 * 32));
+}
+
+cudaError_t ml_embed(const MLTable& t, const float* M, const float* ms_map, float ms, float* F, cudaStream_t st)
+{
+    ml_embed_kernel<<<grid_n(3 * (size_t)t.Z * t.NX * t.NY), 256, 0, st>>>(t, M, ms_map, ms, F);
+    return cudaGetLastError();
+}
+
+cudaError_t ml_extract(const MLTable& t, const float* F, float* H, cudaStream_t st)
+{
+    ml_extract_kernel<<<grid_n(t.total3), 256, 0, st>>>(t, F, H);
+    return cudaGetLastError();
+}
+
+cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, cudaStream_t st)
+{
+    const size_t smem = (size_t)Z * 3 * 32 * sizeof(float2) + (size_t)Z * Z * sizeof(int);
+    const dim3 grid((g.py + 31) / 32, g.nkx);
+    const int pmax = (Z + 7) / 8;
+    cudaError_t e;
+#define ML_MIX(P)                                                                                            \
+    e = cudaFuncSetAttribute(ml_mix_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
+    if (e != cudaSuccess) return e;                                                                          \
+    ml_mix_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, pairs);                                            \
+    return cudaGetLastError();
+    if (pmax <= 1) { ML_MIX(1) }
+    if (pmax <= 2) { ML_MIX(2) }
+    if (pmax <= 4) { ML_MIX(4) }
+    if (pmax <= 6) { ML_MIX(6) }
+    if (pmax <= 8) { ML_MIX(8) }
+#undef ML_MIX
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace boris

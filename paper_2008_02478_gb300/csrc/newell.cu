@@ -18,49 +18,9 @@
 //    store -Re / (px py pz) as rows [kx][ky] of kz * 6 + component (row
 //    length padded to a multiple of 4 with zeros) in FP32 or FP64.
 #include "boris_internal.cuh"
+#include "newell_fg.cuh"
 
 namespace boris {
-
-// Newell's f: even in each argument; a term with a vanishing polynomial factor
-// is dropped (its closed-form limit is zero).
-__device__ double newell_f_dev(double x, double y, double z)
-{
-    x = fabs(x); y = fabs(y); z = fabs(z);
-    const double xx = x * x, yy = y * y, zz = z * z;
-    const double R = sqrt(xx + yy + zz);
-    if (R == 0.0) return 0.0;
-    double acc = (2.0 * xx - yy - zz) * R * (1.0 / 6.0);
-    const double t1 = 0.5 * y * (zz - xx);
-    if (t1 != 0.0) acc += t1 * asinh(y / sqrt(xx + zz));
-    const double t2 = 0.5 * z * (yy - xx);
-    if (t2 != 0.0) acc += t2 * asinh(z / sqrt(xx + yy));
-    const double t3 = x * y * z;
-    if (t3 != 0.0) acc -= t3 * atan(y * z / (x * R));
-    return acc;
-}
-
-// Newell's g: odd in x and y, even in z.
-__device__ double newell_g_dev(double x, double y, double z)
-{
-    const double sign = copysign(1.0, x) * copysign(1.0, y);
-    x = fabs(x); y = fabs(y); z = fabs(z);
-    const double xx = x * x, yy = y * y, zz = z * z;
-    const double R = sqrt(xx + yy + zz);
-    if (R == 0.0) return 0.0;
-    double acc = -x * y * R * (1.0 / 3.0);
-    const double xyz = x * y * z;
-    if (xyz != 0.0) acc += xyz * asinh(z / sqrt(xx + yy));
-    const double a = y * (3.0 * zz - yy) * (1.0 / 6.0);
-    if (a != 0.0) acc += a * asinh(x / sqrt(yy + zz));
-    const double b = x * (3.0 * zz - xx) * (1.0 / 6.0);
-    if (b != 0.0) acc += b * asinh(y / sqrt(xx + zz));
-    if (z != 0.0) {
-        acc -= zz * z * (1.0 / 6.0) * atan(x * y / (z * R));
-        if (y != 0.0) acc -= 0.5 * z * yy * atan(x * z / (y * R));
-        if (x != 0.0) acc -= 0.5 * z * xx * atan(y * z / (x * R));
-    }
-    return sign * acc;
-}
 
 // Exact tensor: all six components from one sweep over the 27 shifts.
 __device__ void newell_exact_dev(double X, double Y, double Z, double dx, double dy, double dz, double out[6])
@@ -152,7 +112,7 @@ __device__ __forceinline__ double comp_parity(int c, int a)
 __global__ void __launch_bounds__(256) axis_pass_kernel(const void* __restrict__ in, bool in_real,
                                                         double2* __restrict__ out, int axis, int d0, int d1,
                                                         int d2, int n, int P, int lgP, int NL,
-                                                        const double2* __restrict__ tw, int lglmax)
+                                                        const double2* __restrict__ tw, int lglmax, int ncomp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* buf = reinterpret_cast<double2*>(smem_raw);  // [NL][P]
@@ -162,7 +122,7 @@ __global__ void __launch_bounds__(256) axis_pass_kernel(const void* __restrict__
     od[axis] = kh;
     // line = (c, the two other coordinates)
     const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
-    const long nlines_total = 6L * dims[oa] * dims[ob];
+    const long nlines_total = (long)ncomp * dims[oa] * dims[ob];
     const long line0 = (long)blockIdx.x * NL;
     auto in_index = [&](int c, int u, int v, int e) -> size_t {
         int co[3];
@@ -194,7 +154,7 @@ __global__ void __launch_bounds__(256) axis_pass_kernel(const void* __restrict__
             int src = -1;
             double s = 1.0;
             if (e < n) src = e;
-            else if (e > P - n) { src = P - e; s = comp_parity(c, axis); }
+            else if (e > P - n) { src = P - e; s = comp_parity(c % 6, axis); }
             if (src >= 0) {
                 const size_t ii = in_index(c, u, v, src);
                 if (in_real) val = make_double2(s * reinterpret_cast<const double*>(in)[ii], 0.0);
@@ -261,8 +221,8 @@ cudaError_t newell_octant(int nx, int ny, int nz, double dx, double dy, double d
     return cudaGetLastError();
 }
 
-static cudaError_t run_axis(const void* in, bool in_real, double2* out, int axis, int d0, int d1, int d2, int n,
-                            int P, const double2* tw, int lglmax, cudaStream_t st)
+cudaError_t run_axis_n(const void* in, bool in_real, double2* out, int axis, int d0, int d1, int d2, int n, int P,
+                       int ncomp, const double2* tw, int lglmax, cudaStream_t st)
 {
     const int lgP = ilog2(P);
     int NL = 4096 / P;
@@ -273,11 +233,17 @@ static cudaError_t run_axis(const void* in, bool in_real, double2* out, int axis
     if (e != cudaSuccess) return e;
     const int dims[3] = {d0, d1, d2};
     const int oa = axis == 0 ? 1 : 0, ob = axis == 2 ? 1 : 2;
-    const long nlines = 6L * dims[oa] * dims[ob];
+    const long nlines = (long)ncomp * dims[oa] * dims[ob];
     const long blocks = (nlines + NL - 1) / NL;
     axis_pass_kernel<<<(unsigned)blocks, 256, smem, st>>>(in, in_real, out, axis, d0, d1, d2, n, P, lgP, NL, tw,
-                                                           lglmax);
+                                                           lglmax, ncomp);
     return cudaGetLastError();
+}
+
+static cudaError_t run_axis(const void* in, bool in_real, double2* out, int axis, int d0, int d1, int d2, int n,
+                            int P, const double2* tw, int lglmax, cudaStream_t st)
+{
+    return run_axis_n(in, in_real, out, axis, d0, d1, d2, n, P, 6, tw, lglmax, st);
 }
 
 cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, double dz, double rs, void* K_out,
