@@ -181,6 +181,17 @@ def time_steps(torch, plan, m, prm, K):
     return e0.elapsed_time(e1) / 1e3
 
 
+def time_graph(torch, plan, m, prm, K):
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    plan.llg_run_graph(m, prm, DT, K)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
 def time_demag(torch, plan, M, H, K):
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -208,6 +219,101 @@ def oracle_rk4_rate(nx, ny, nz, steps):
         m = llg.rk4_step(m, DT, prm, dem.apply)
     t = time.perf_counter() - t0
     return nx * ny * nz * steps / t, t, oracle.num_threads()
+
+
+def other_workloads(torch, args, world, max_over_ranks):
+    """Throughput of the other workloads of the build on this GPU (FP32):
+    the six-layer multi-mesh stack (batched, one CUDA graph per RK4 step), the
+    256x64x1 RKF45 film, and forward+adjoint RK4 on the 256x256x8 film with
+    per-cell Ms and Ku maps."""
+    import numpy as np
+
+    from oracle import multilayer as ml
+    from paper_2008_02478_gb300 import inputs
+    from paper_2008_02478_gb300.autograd import trajectory
+    from paper_2008_02478_gb300.binding import RKF45, LLGParams, MultiPlan, Plan
+    out = {}
+    # six-layer stack
+    d = inputs.MULTILAYER
+    st = ml.centred_stack(d["layers"], d["hz"], d["gaps"], d["hxy"])
+    cells = [(st.hx, st.hy, h) for h in st.hz]
+    origins = [(ox * st.hx, oy * st.hy, zb) for ox, oy, zb in zip(st.ox, st.oy, st.zb)]
+    t0 = time.perf_counter()
+    mp = MultiPlan(st.n, cells, origins)
+    t_plan = time.perf_counter() - t0
+    m = np.concatenate([inputs.random_unit(*l, seed=d["seed"] + i).reshape(-1) for i, l in enumerate(st.n)])
+    ms = np.concatenate([np.full(l[0] * l[1] * l[2], d["Ms"][i]) for i, l in enumerate(st.n)])
+    mg = torch.tensor(m, dtype=torch.float32, device="cuda")
+    prm = LLGParams(A=A_EX, alpha=ALPHA, Ms_map=torch.tensor(ms, dtype=torch.float32, device="cuda"))
+    dt_ml = 5e-14
+    mp.llg_run_graph(mg, prm, dt_ml, 3)
+    K = max(4, args.steps)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    mp.llg_run_graph(mg, prm, dt_ml, K)
+    ev1.record()
+    torch.cuda.synchronize()
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    Mf = mg.clone()
+    Hf = torch.empty_like(Mf)
+    mp.apply(Mf, Hf)
+    ev0.record()
+    for _ in range(4 * K):
+        mp.apply(Mf, Hf)
+    ev1.record()
+    torch.cuda.synchronize()
+    td = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    z, nu, NX, NY = mp.info()
+    out["multilayer_6"] = {"cells": st.total(), "z_planes": z, "inter_plane_spectra": nu, "frame": [NX, NY],
+                           "cell_steps_per_s": world * st.total() * K / t, "demag_evals_per_s": world * 4 * K / td,
+                           "plan_build_s": t_plan, "dt": dt_ml, "batched": "all layers per launch, CUDA graph"}
+    mp.close()
+    # RKF45 film 256x64x1
+    fd = inputs.FILM_SP4_MESH
+    fp = Plan(*fd["n"], *fd["cell"])
+    mf = torch.tensor(inputs.uniform(*fd["n"], (1, 1, 1)), dtype=torch.float32, device="cuda")
+    pr = LLGParams(Ms=8e5, A=A_EX, alpha=0.02, Hext=(19894.4 * math.cos(math.radians(170)),
+                                                      19894.4 * math.sin(math.radians(170)), 0.0),
+                   method=RKF45, tol=1e-5, dt_min=1e-16, dt_max=1e-12)
+    h = 1e-14
+    for _ in range(5):
+        h = fp.llg_step(mf, pr, h)
+    torch.cuda.synchronize()
+    n_acc = 200
+    t0 = time.perf_counter()
+    for _ in range(n_acc):
+        h = fp.llg_step(mf, pr, h)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out["rkf45_film_256x64x1"] = {"accepted_steps_per_s": n_acc / t,
+                                  "cell_steps_per_s": n_acc * 256 * 64 / t, "last_dt": h}
+    fp.close()
+    # gradient film 256x256x8: forward + checkpointed adjoint
+    gd = inputs.GRAD_FILM_MESH
+    gp = Plan(*gd["n"], *gd["cell"])
+    nx, ny, nz = gd["n"]
+    Ms = torch.tensor(inputs.smooth_noise(nx, ny, nz, 4.0, 6e5, 1e6, 5), dtype=torch.float32, device="cuda",
+                      requires_grad=True)
+    Ku = torch.tensor(inputs.smooth_noise(nx, ny, nz, 4.0, 0.0, 5e5, 6), dtype=torch.float32, device="cuda",
+                      requires_grad=True)
+    m0 = torch.tensor(inputs.smooth_texture(nx, ny, nz, 4.0, 5), dtype=torch.float32, device="cuda")
+    tgt = torch.tensor(inputs.smooth_texture(nx, ny, nz, 4.0, 3), dtype=torch.float32, device="cuda")
+    base = LLGParams(A=A_EX, alpha=ALPHA, easy=(0.0, 0.0, 1.0))
+    nst = 20
+    L = ((trajectory(m0, Ms, Ku, gp, base, 2, DT, 50) - tgt) ** 2).sum()
+    L.backward()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = ((trajectory(m0, Ms, Ku, gp, base, nst, DT, 10) - tgt) ** 2).sum()
+    L.backward()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out["gradient_film_256x256x8"] = {"steps": nst, "checkpoint_every": 10,
+                                      "forward_plus_adjoint_steps_per_s": nst / t,
+                                      "cell_steps_per_s": nst * nx * ny * nz / t}
+    gp.close()
+    return out
 
 
 def run_reference(args, rank):
@@ -244,6 +350,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -285,6 +392,7 @@ def main():
     m = torch.tensor(m0, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         plan.llg_step(m, prm, DT)
+    plan.llg_run_graph(m, prm, DT, args.warmup)  # capture + warm the graph
     plan.profile_read()  # reset launch counters
 
     # ---- A: headline timing (K RK4 steps, no per-kernel events) ----------
@@ -292,12 +400,14 @@ def main():
         if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
     barrier()
     with ClockSampler(gpu_index) as clk:
-        t_steps = time_steps(torch, plan, m, prm, args.steps)
+        t_steps = time_graph(torch, plan, m, prm, args.steps)
     barrier()
     _, launches = plan.profile_read()
     t_steps = max_over_ranks(t_steps)
     clocks = clk.summary()
     value = world * ncell * args.steps / t_steps
+    # the same steps through one boris_llg_step call each (no graph)
+    t_calls = max_over_ranks(time_steps(torch, plan, m, prm, args.steps))
 
     # ---- demag-only timing ------------------------------------------------
     M = torch.tensor(MS * m0, dtype=torch.float32, device="cuda")
@@ -388,6 +498,11 @@ def main():
             del mt
         del H64
 
+    # ---- other workloads: multi-mesh stack, RKF45 film, gradient film ------
+    extra = {}
+    if not args.no_extra:
+        extra = other_workloads(torch, args, world, max_over_ranks)
+
     # ---- CPU baseline: the oracle on a bounded sample -----------------------
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -407,7 +522,8 @@ def main():
                            "l2": "inputs larger than L2 (m 100.7 MB, spectrum workspace 201.7 MB, kernel "
                                  "spectrum 208.4 MB per evaluation)",
                            "padded": plan.padded(), "yz_schedule": plan.schedule()},
-                "demag_evals_per_s": demag_rate, "fp64": fp64, "mixed_precision": mixed, "roofline": roofline,
+                "demag_evals_per_s": demag_rate, "ms_per_step_without_graph": 1e3 * t_calls / args.steps,
+                "fp64": fp64, "workloads": extra, "mixed_precision": mixed, "roofline": roofline,
                 "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -199,6 +199,17 @@ int boris_llg_step_backward_f64(boris_plan p, const double* m_in, const boris_ll
                                 const double* g_m_out, double* g_m_in, double* g_Ms, double* g_Ku);
 
 /*
+ * boris_llg_run_graph - nsteps RK4 steps of boris_llg_step (FP32 plans,
+ *   single- or multi-mesh), replayed from a CUDA graph: the first call (and
+ *   any call whose m, *prm or dt differ from the captured ones) captures one
+ *   step - all its kernel launches - on a plan-owned stream and instantiates
+ *   it; every step is then one graph launch on the plan's stream.  The device
+ *   pointers in *prm and m must stay valid while the plan keeps the graph.
+ *   The capture synchronises the plan's stream once.
+ */
+int boris_llg_run_graph(boris_plan p, float* m, const boris_llg_params* prm, double dt, int nsteps);
+
+/*
  * boris_llg_run_host - end-to-end form for callers holding host memory:
  *   copies m_host (host [3][nz][ny][nx] float; pinned memory is fastest) to
  *   the device, runs nsteps RK4 steps of size dt, copies the result back to

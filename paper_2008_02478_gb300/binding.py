@@ -28,7 +28,7 @@ GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
 #: entry points declared in include/boris.h
 EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_info", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_apply_noalloc",
            "boris_demag_adjoint",
-           "boris_llg_step", "boris_llg_step_f64", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
+           "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
 KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other", "y_fwd", "z_conv", "y_inv"]
@@ -72,6 +72,7 @@ def lib():
         L.boris_llg_step_backward.argtypes = [vp, vp, P(LLGParamsC), d, vp, vp, vp, vp]
         L.boris_llg_step_backward_f64.argtypes = [vp, vp, P(LLGParamsC), d, vp, vp, vp, vp]
         L.boris_llg_run_host.argtypes = [vp, vp, P(LLGParamsC), d, i]
+        L.boris_llg_run_graph.argtypes = [vp, vp, P(LLGParamsC), d, i]
         L.boris_energy.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_sync_status.argtypes = [vp]
         L.boris_last_error.restype = ctypes.c_char_p
@@ -234,6 +235,12 @@ class Plan:
         check(fn(self._h, _ptr(m_in, self.dtype, self.field_shape), ctypes.byref(c), float(dt),
                  _ptr(g_out, self.dtype, self.field_shape), _ptr(g_in, self.dtype, self.field_shape), gms, gku))
         return g_in
+
+    def llg_run_graph(self, m, prm: LLGParams, dt: float, nsteps: int):
+        """nsteps RK4 steps replayed from a captured CUDA graph (FP32 plans)."""
+        c = self._params(prm)
+        check(lib().boris_llg_run_graph(self._h, _ptr(m, self.dtype, self.field_shape), ctypes.byref(c), float(dt),
+                                        int(nsteps)))
 
     def llg_run_host(self, m_host, prm: LLGParams, dt: float, nsteps: int):
         """m_host: CPU float32 tensor (pinned for speed), updated in place."""

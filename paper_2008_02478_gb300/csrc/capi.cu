@@ -52,6 +52,13 @@ struct boris_plan_s {
     unsigned int* h_err_bits = nullptr;  // pinned
     double* energy = nullptr;
     void* m_dev_e2e = nullptr;
+    // CUDA graph of one RK4 step (boris_llg_run_graph), keyed by its arguments
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    float* g_m = nullptr;
+    boris_llg_params g_prm = {};
+    double g_dt = 0.0;
+    long long g_launches = 0;  // kernel launches inside one captured step
     // multi-mesh plans (boris_multimesh_plan)
     bool ml = false;
     MLTable mlt;
@@ -794,6 +801,68 @@ int boris_llg_step_backward_f64(boris_plan p, const double* m_in, const boris_ll
     return llg_backward_t<double>(p, m_in, prm, dt, g_m_out, g_m_in, g_Ms, g_Ku);
 }
 
+int boris_llg_run_graph(boris_plan p, float* m, const boris_llg_params* prm, double dt, int nsteps)
+{
+    if (!p || !m || !prm) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan");
+    if (prm->method != BORIS_RK4 || nsteps < 0 || !(dt > 0)) return fail(BORIS_ERR_INVALID_ARG, "RK4, nsteps >= 0, dt > 0");
+    if (!aligned16(m)) return fail(BORIS_ERR_INVALID_ARG, "m must be 16-byte aligned");
+    int rc = ensure_llg_workspace<float>(p, false);
+    if (rc) return rc;
+    const bool same = p->gexec && p->g_m == m && p->g_dt == dt && std::memcmp(&p->g_prm, prm, sizeof(*prm)) == 0;
+    if (!same) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        if (!p->gstream) CUDA_TRY(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+        LLGArgs<float> a;
+        if ((rc = check_params<float>(p, prm, &a, dt))) return rc;
+        // capture one step on the plan's private stream (the caller's stream may
+        // be the legacy default stream, which cannot be captured)
+        CUDA_TRY(cudaStreamSynchronize(p->stream));
+        cudaStream_t user = p->stream;
+        const bool prof = p->prof;
+        p->stream = p->gstream;
+        p->prof = false;
+        cudaGraph_t graph = nullptr;
+        const long long before = p->launches;
+        cudaError_t e = cudaStreamBeginCapture(p->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = rk4_step_t<float>(p, m, a);
+            p->g_launches = p->launches - before;
+            p->launches = before;
+            cudaError_t e2 = cudaStreamEndCapture(p->gstream, &graph);
+            if (rc == BORIS_OK && e2 != cudaSuccess) {
+                rc = fail(BORIS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e2));
+            }
+        } else {
+            rc = fail(BORIS_ERR_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+        }
+        p->stream = user;
+        p->prof = prof;
+        if (rc != BORIS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return rc;
+        }
+        e = cudaGraphInstantiate(&p->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            p->gexec = nullptr;
+            return fail(BORIS_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        p->g_m = m;
+        p->g_dt = dt;
+        p->g_prm = *prm;
+    }
+    for (int i = 0; i < nsteps; i++) {
+        CUDA_TRY(cudaGraphLaunch(p->gexec, p->stream));
+        p->launches += p->g_launches;
+    }
+    return BORIS_OK;
+}
+
 int boris_llg_run_host(boris_plan p, float* m_host, const boris_llg_params* prm, double dt, int nsteps)
 {
     if (!p || !m_host || !prm) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
@@ -901,6 +970,8 @@ void boris_plan_destroy(boris_plan p)
     if (p->tw && p->tw != (void*)p->tw64) cudaFree(p->tw);
     if (p->tw64) cudaFree(p->tw64);
     if (p->h_err_bits) cudaFreeHost(p->h_err_bits);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->gstream) cudaStreamDestroy(p->gstream);
     for (auto& u : p->ev_used) {
         cudaEventDestroy(u.second.first);
         cudaEventDestroy(u.second.second);

@@ -106,3 +106,21 @@ def test_energies_match_oracle(per_cell):
     E = plan.energy(to_dev(torch, m0), _gpu_params(torch, prm))
     for e, r in zip(E, ref):
         assert abs(e - r) <= 1e-5 * max(abs(v) for v in ref), (E, ref)
+
+
+@pytest.mark.parametrize("n", [(32, 32, 4), (256, 64, 1)])
+def test_graph_replay_equals_step_calls(n):
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import LLGParams, Plan
+    h = (2e-9, 2e-9, 3e-9)
+    m0 = inputs.random_unit(*n, seed=8)
+    p1, p2 = Plan(*n, *h), Plan(*n, *h)
+    prm = LLGParams(Ms=8e5, A=1.3e-11, alpha=0.02, Hext=(0.0, 1e4, 2e4))
+    a = to_dev(torch, m0)
+    b = to_dev(torch, m0)
+    for _ in range(5):
+        p1.llg_step(a, prm, 1e-13)
+    p2.llg_run_graph(b, prm, 1e-13, 2)
+    p2.llg_run_graph(b, prm, 1e-13, 3)  # reuses the captured graph
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
