@@ -128,7 +128,7 @@ __device__ __forceinline__ void zc_forward(const Geometry& g, const ZcThread<T>&
 #pragma unroll
     for (int z = 0; z < HZ; z++) {
         C x = z < g.nz ? mine[z] : C{T(0), T(0)};
-        if (HP) x = c_mul(x, cw128<C>(z * (64 / HZ)));
+        if (HP) x = c_mul(x, w128lit<C>(z * (64 / HZ)));
         v[z] = x;
     }
     reg_fft<HZ, -1>(v);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(QC * 6, MINB) z_conv_kernel(Geometry g, typena
     __syncthreads();
     if (h) {
 #pragma unroll
-        for (int z = 0; z < HZ; z++) odd[t.col * CS + t.c * HZ + z] = c_mulc(v[z], cw128<C>(z * (64 / HZ)));
+        for (int z = 0; z < HZ; z++) odd[t.col * CS + t.c * HZ + z] = c_mulc(v[z], w128lit<C>(z * (64 / HZ)));
     }
     __syncthreads();
     if (!h) {

@@ -19,6 +19,8 @@
 
 #include <cmath>
 
+#include "twiddle128.h"
+
 namespace boris {
 
 template <typename T> struct Cx;
@@ -191,13 +193,22 @@ template <typename C> __device__ __forceinline__ C cw128(int e);
 template <> __device__ __forceinline__ float2 cw128<float2>(int e) { return c_w128f[e]; }
 template <> __device__ __forceinline__ double2 cw128<double2>(int e) { return c_w128d[e]; }
 
+// w_128^e from the literal table, for indices known at compile time (the
+// values then fold into the multiply instructions).
+template <typename C> __device__ __forceinline__ C w128lit(int e);
+template <> __device__ __forceinline__ float2 w128lit<float2>(int e)
+{
+    return make_float2((float)w128_re(e), (float)w128_im(e));
+}
+template <> __device__ __forceinline__ double2 w128lit<double2>(int e) { return make_double2(w128_re(e), w128_im(e)); }
+
 // v * w_128^e for a compile-time e (exact for e = 0 and e = 32, i.e. 1 and -i).
 template <int DIR, typename C>
 __device__ __forceinline__ C twiddle128(C v, int e)
 {
     if (e == 0) return v;
     if (e == 32) return DIR < 0 ? C{v.y, -v.x} : C{-v.y, v.x};
-    const C w = cw128<C>(e);
+    const C w = w128lit<C>(e);
     return DIR < 0 ? c_mul(v, w) : c_mulc(v, w);
 }
 
