@@ -169,6 +169,16 @@ def llg_algorithmic_bytes(plan) -> float:
     return (48 + 72 + 72 + 60) / 4.0 * (es / 4) * nx * ny * nz
 
 
+def x_c2r_rk4_algorithmic_bytes(plan) -> float:
+    """Inverse x transform fused with the RK4 stage: read the x half spectrum,
+    then the stage's bytes without the H_d read (36, 60, 60, 48 bytes per
+    cell in FP32)."""
+    nx, ny, nz = plan.shape
+    px = plan.padded()[0]
+    es = 8 if plan.fp64 else 4
+    return (px // 2 + 1) * 3 * nz * ny * 2 * es + (36 + 60 + 60 + 48) / 4.0 * (es / 4) * nx * ny * nz
+
+
 def time_steps(torch, plan, m, prm, K):
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -425,7 +435,8 @@ def main():
     dominant = max(kern, key=lambda k: kern[k][0])
     per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in kern.items()}
     algo = {"yz_conv": yz_algorithmic_bytes(plan), "x_r2c": xpass_algorithmic_bytes(plan),
-            "x_c2r": xpass_algorithmic_bytes(plan), "llg_stage": llg_algorithmic_bytes(plan)}
+            "x_c2r": xpass_algorithmic_bytes(plan), "llg_stage": llg_algorithmic_bytes(plan),
+            "x_c2r_rk4": x_c2r_rk4_algorithmic_bytes(plan)}
     algo.update(split_algorithmic_bytes(plan))
     peak, peak_kind = measured_peaks()
     dom_bytes = algo.get(dominant)

@@ -235,11 +235,18 @@ const char* boris_last_error(void);
 /* Padded transform lengths chosen by the plan: out[0..2] = px, py, pz. */
 int boris_plan_padded(boris_plan p, int out[3]);
 
-/* Schedule of the y-z pass chosen by the plan's autotuner: out[0] kind
- * (0: fused, z stage through shared-memory passes, 1: fused, z stage in registers,
- * 2: split), out[1]
- * CTAs per cluster, out[2] threads per CTA, out[3] shared memory per CTA;
- * kind 2: split y-forward / z-convolution / y-inverse kernels). */
+/* Schedule of the y-z pass chosen by the plan's autotuner (CUDA-event
+ * timing of every candidate that fits the mesh): out[0] kind (0: fused, z
+ * stage through shared-memory passes, 1: fused, z stage in registers, 2:
+ * split into y-forward / z-convolution / y-inverse kernels).  Kinds 0 and 1:
+ * out[1] CTAs per cluster, out[2] threads per CTA, out[3] shared memory per
+ * CTA.  Kind 2: out[1] CTAs per SM the z convolution's register budget is
+ * fitted to, out[2] 1 when the z convolution is the persistent bulk-copy
+ * (TMA) pipeline, whose bounded mbarrier waits latch BORIS_ERR_TIMEOUT in the
+ * status word read by boris_sync_status, else 0.
+ * Environment overrides read at plan creation restrict the candidates:
+ * BORIS_YZ_KIND, BORIS_YZ_CLUSTER, BORIS_YZ_THREADS, BORIS_YZ_QC (kind 0
+ * chunk), BORIS_YZ_TMA (kind 2 variant). */
 int boris_plan_schedule(boris_plan p, int out[4]);
 
 /* Bytes of device memory owned by the plan. */
@@ -253,12 +260,14 @@ size_t boris_plan_device_bytes(boris_plan p);
  *   device time in ms and the number of timed launches since the last read:
  *   [0] x real-to-complex, [1] fused y-z pass, [2] x complex-to-real,
  *   [3] LLG stage, [4] other (energies), [5] y forward, [6] z convolution,
- *   [7] y inverse (the last three: split y-z schedule).  *total_launches (may be NULL)
+ *   [7] y inverse (the last three: split y-z schedule), [8] x complex-to-real
+ *   fused with the RK4 stage (FP32 plans with px = 1024 created while the
+ *   environment sets BORIS_FUSE_STAGE=1).  *total_launches (may be NULL)
  *   receives every kernel launch counted since the last read, timed or not.
  *   Resets the counters.
  */
 int boris_profile_enable(boris_plan p, int on);
-int boris_profile_read(boris_plan p, double ms_out[8], long long launches_out[8], long long* total_launches);
+int boris_profile_read(boris_plan p, double ms_out[9], long long launches_out[9], long long* total_launches);
 
 /* Free the plan and everything it owns (NULL is ignored).  Synchronises. */
 void boris_plan_destroy(boris_plan p);

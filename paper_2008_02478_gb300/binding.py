@@ -31,7 +31,7 @@ EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_inf
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
-KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other", "y_fwd", "z_conv", "y_inv"]
+KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other", "y_fwd", "z_conv", "y_inv", "x_c2r_rk4"]
 
 
 class BorisError(RuntimeError):
@@ -261,8 +261,8 @@ class Plan:
 
     def profile_read(self):
         """{kernel class: (ms, timed launches)}, total launches since the last read."""
-        ms = (ctypes.c_double * 8)()
-        cnt = (ctypes.c_longlong * 8)()
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        cnt = (ctypes.c_longlong * len(KERNEL_CLASSES))()
         tot = ctypes.c_longlong()
         check(lib().boris_profile_read(self._h, ms, cnt, ctypes.byref(tot)))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}, tot.value

@@ -96,6 +96,13 @@ cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T
 cudaError_t upload_twiddles_fast();
 // Tensor-core (FP16 / BF16) z stage of the split schedule (zconv_tc.cu), pz = 64.
 bool zconv_tc_supported(const Geometry& g);
+// bulk-copy pipelined z convolution of the split schedule (FP32; zconv_tma.cu);
+// variant 1: one tile stage, three CTAs per SM; 2: two stages, two CTAs per SM
+bool zconv_tma_supported(const Geometry& g, int max_smem, int variant);
+// encodes the tensor map of Y (128 bytes at map) the kernel copies tiles with
+cudaError_t zconv_tma_map(const Geometry& g, float2* Y, void* map);
+cudaError_t launch_zconv_tma(const void* map, const Geometry& g, const float* K, int* status, uint32_t extra_tx,
+                             unsigned long long limit_ns, int nsm, int variant, cudaStream_t st);
 cudaError_t launch_zconv_tc(const Geometry& g, float2* Y, const float* K, const float2* tw, bool bf16, cudaStream_t st);
 cudaError_t upload_twiddles_yz_f32();
 cudaError_t upload_twiddles_yz_f64();
@@ -132,7 +139,7 @@ struct PlanView {
     bool ml;  // multi-mesh plan
 };
 // Number of kernel classes timed by the plan's profiler.
-constexpr int NPROF = 8;
+constexpr int NPROF = 9;
 bool plan_view(boris_plan p, PlanView* v);
 
 // Thread-local last error message (capi.cu).

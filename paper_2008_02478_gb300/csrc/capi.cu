@@ -32,6 +32,16 @@ struct boris_plan_s {
     cudaStream_t stream;
     int device;
     YZSchedule yz;
+    // FP32 RK4 stages fuse the inverse x transform with the stage (px = 1024)
+    bool fuse_rk4 = false;
+    // device status word latched by bounded device-side waits (boris_sync_status)
+    int* d_status = nullptr;
+    int nsm = 0;
+    uint32_t wait_extra_tx = 0;              // test hook: bytes that never arrive
+    unsigned long long wait_limit_ns = 1000000000ull;
+    // tensor map of Y for the bulk-copy z convolution (encoded on first use)
+    alignas(64) unsigned char ymap[128] = {};
+    bool ymap_ready = false;
     // kernel spectrum [kx][ky'][kz'][6] in the plan precision
     void* K = nullptr;
     // twiddles exp(-2 pi i e / lmax) in the plan precision and in FP64
@@ -154,6 +164,15 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
                 if (part == 1 && p->tc)
                     return launch_zconv_tc(p->g, (float2*)p->Y, (const float*)p->K, (const float2*)p->tw, p->tc == 2,
                                            p->stream);
+                if (part == 1 && sc.Qc >= 1) {
+                    if (!p->ymap_ready) {
+                        cudaError_t me = zconv_tma_map(p->g, (float2*)p->Y, p->ymap);
+                        if (me != cudaSuccess) return me;
+                        p->ymap_ready = true;
+                    }
+                    return launch_zconv_tma(p->ymap, p->g, (const float*)p->K, p->d_status, p->wait_extra_tx,
+                                            p->wait_limit_ns, p->nsm, sc.Qc, p->stream);
+                }
                 return launch_split<T>(p->g, (C*)p->X, (C*)p->Y, (const T*)p->K, (const C*)p->tw, p->stream, part,
                                        sc.C);
             });
@@ -177,6 +196,16 @@ int ml_demag_apply(boris_plan p, const float* M, const float* ms_map, float ms_s
     return BORIS_OK;
 }
 
+// Forward x transform and y-z convolution: X holds the x half spectrum of H_d.
+template <typename T>
+int demag_to_spectrum_t(boris_plan p, const T* M, const T* ms_map, T ms_scale)
+{
+    using C = typename Cx<T>::t;
+    CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<T>(p->g, M, ms_map, ms_scale, (C*)p->X, (const C*)p->tw, p->stream); }));
+    CUDA_TRY(yz_stage<T>(p, p->yz));
+    return BORIS_OK;
+}
+
 template <typename T>
 int demag_apply_t(boris_plan p, const T* M, const T* ms_map, T ms_scale, T* H)
 {
@@ -184,8 +213,8 @@ int demag_apply_t(boris_plan p, const T* M, const T* ms_map, T ms_scale, T* H)
     if constexpr (sizeof(T) == 4) {
         if (p->ml) return ml_demag_apply(p, M, ms_map, ms_scale, H);
     }
-    CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<T>(p->g, M, ms_map, ms_scale, (C*)p->X, (const C*)p->tw, p->stream); }));
-    CUDA_TRY(yz_stage<T>(p, p->yz));
+    int rc = demag_to_spectrum_t<T>(p, M, ms_map, ms_scale);
+    if (rc) return rc;
     CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<T>(p->g, (const C*)p->X, H, (const C*)p->tw, p->stream); }));
     return BORIS_OK;
 }
@@ -254,6 +283,17 @@ int rk4_step_t(boris_plan p, T* m, const LLGArgs<T>& a)
     const T* in[4] = {m, sa, sb, sa};
     T* out[4] = {sa, sb, sa, nullptr};
     for (int s = 0; s < 4; s++) {
+        if constexpr (sizeof(T) == 4) {
+            if (p->fuse_rk4) {
+                int rc = demag_to_spectrum_t<T>(p, in[s], ms_map, ms_scale);
+                if (rc) return rc;
+                CUDA_TRY(timed(p, 8, [&] {
+                    return launch_x_c2r_rk4(p->g, (const float2*)p->X, (const float2*)p->tw, a, s, in[s], m, acc,
+                                            out[s], p->stream);
+                }));
+                continue;
+            }
+        }
         int rc = demag_apply_t<T>(p, in[s], ms_map, ms_scale, Hd);
         if (rc) return rc;
         if constexpr (sizeof(T) == 4) {
@@ -495,6 +535,15 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
         return code;
     };
     if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
+    if ((rc = dev_alloc(p, (void**)&p->d_status, sizeof(int)))) return bail(rc);
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "status word"));
+    if (const char* tw = std::getenv("BORIS_TEST_WAIT_TIMEOUT"); tw && std::atoi(tw) == 1) {
+        // test hook: the first bulk-copy wait of each CTA expects 16 bytes that
+        // never arrive and gives up after 2 ms
+        p->wait_extra_tx = 16;
+        p->wait_limit_ns = 2000000ull;
+    }
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     YZSchedule cand[16];
@@ -502,9 +551,13 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     if (p->f64) yz_candidates<double>(g, max_smem, cand, &ncand);
     else yz_candidates<float>(g, max_smem, cand, &ncand);
     const bool split_ok = p->f64 ? split_supported<double>(g, max_smem) : split_supported<float>(g, max_smem);
-    if (split_ok && ncand < 15) {
+    if (split_ok && ncand < 13) {
         cand[ncand++] = YZSchedule{2, 2, 0, 0, 0};
         if (!p->f64) cand[ncand++] = YZSchedule{2, 3, 0, 0, 0};
+        // Qc = 1 / 2 on a split schedule: the bulk-copy pipelined z convolution
+        // with one tile stage and 3 CTAs per SM / two stages and 2 CTAs per SM
+        for (int v = 1; v <= 2; v++)
+            if (!p->f64 && zconv_tma_supported(g, max_smem, v)) cand[ncand++] = YZSchedule{2, v == 1 ? 3 : 2, v, 0, 0};
     }
     if (tc) {
         // the tensor-core z stage runs inside the split schedule only
@@ -520,12 +573,14 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
         const char* sc = std::getenv("BORIS_YZ_CLUSTER");
         const char* st = std::getenv("BORIS_YZ_THREADS");
         const char* sq = std::getenv("BORIS_YZ_QC");
-        if (sk || sc || st) {
+        const char* sp = std::getenv("BORIS_YZ_TMA");
+        if (sk || sc || st || sp) {
             int m = 0;
             for (int i = 0; i < ncand; i++) {
                 if (sk && cand[i].kind != std::atoi(sk)) continue;
                 if (sc && cand[i].C != std::atoi(sc)) continue;
                 if (st && cand[i].threads != std::atoi(st)) continue;
+                if (sp && (cand[i].kind != 2 || cand[i].Qc != std::atoi(sp))) continue;
                 cand[m++] = cand[i];
             }
             if (m == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "no y-z schedule matches the override"));
@@ -542,6 +597,13 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
         }
     }
     p->yz = cand[0];
+    {
+        // BORIS_FUSE_STAGE=1 runs the inverse x transform and the RK4 stage as
+        // one kernel (off by default: two CTAs per SM hide less latency than
+        // the separate kernels do)
+        const char* sf = std::getenv("BORIS_FUSE_STAGE");
+        p->fuse_rk4 = !p->f64 && x_c2r_rk4_ok(g, max_smem) && sf && std::atoi(sf) == 1;
+    }
     cudaError_t ce = p->f64 ? upload_twiddles_yz_f64() : upload_twiddles_yz_f32();
     if (ce == cudaSuccess) ce = upload_twiddles_split();
     if (ce == cudaSuccess) ce = upload_twiddles_fast();
@@ -709,6 +771,15 @@ int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, cons
     p->yz = YZSchedule{2, 2, 0, 0, 0};
     int rc;
     if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
+    if ((rc = dev_alloc(p, (void**)&p->d_status, sizeof(int)))) return bail(rc);
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "status word"));
+    if (const char* tw = std::getenv("BORIS_TEST_WAIT_TIMEOUT"); tw && std::atoi(tw) == 1) {
+        // test hook: the first bulk-copy wait of each CTA expects 16 bytes that
+        // never arrive and gives up after 2 ms
+        p->wait_extra_tx = 16;
+        p->wait_limit_ns = 2000000ull;
+    }
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     if (!split_supported<float>(g, max_smem)) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "frame too large"));
@@ -904,7 +975,14 @@ int boris_sync_status(boris_plan p)
     if (!p) return fail(BORIS_ERR_INVALID_ARG, "NULL plan");
     cudaError_t e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return fail(BORIS_ERR_CUDA, cudaGetErrorString(e));
-    return BORIS_OK;
+    int st = BORIS_OK;
+    if (p->d_status) {
+        if (cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess)
+            return fail(BORIS_ERR_CUDA, "status word");
+    }
+    if (st == BORIS_ERR_TIMEOUT) return fail(BORIS_ERR_TIMEOUT, "a bounded device-side wait gave up");
+    return st;
 }
 
 int boris_plan_schedule(boris_plan p, int out[4])
@@ -912,7 +990,7 @@ int boris_plan_schedule(boris_plan p, int out[4])
     if (!p || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
     out[0] = p->yz.kind;
     out[1] = p->yz.C;
-    out[2] = p->yz.threads;
+    out[2] = p->yz.kind == 2 ? p->yz.Qc : p->yz.threads;
     out[3] = (int)p->yz.smem;
     return BORIS_OK;
 }
@@ -935,7 +1013,7 @@ int boris_profile_enable(boris_plan p, int on)
     return BORIS_OK;
 }
 
-int boris_profile_read(boris_plan p, double ms_out[8], long long launches_out[8], long long* total_launches)
+int boris_profile_read(boris_plan p, double ms_out[9], long long launches_out[9], long long* total_launches)
 {
     if (!p || !ms_out || !launches_out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
     CUDA_TRY(cudaStreamSynchronize(p->stream));

@@ -13,7 +13,7 @@ constexpr int REG1025 = 1025;  // per-warp region stride (complex): one pad elem
 // x real-to-complex, px = 1024: 16 rows (c, z, y0..y0+15) per CTA; warp w packs
 // row w (real part) and row w + 8 (imaginary part) into one complex line.
 template <typename T>
-__global__ void __launch_bounds__(256) x_r2c_1024_kernel(Geometry g, const T* __restrict__ M,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) x_r2c_1024_kernel(Geometry g, const T* __restrict__ M,
                                                          const T* __restrict__ ms_map, T ms_scale,
                                                          typename Cx<T>::t* __restrict__ X,
                                                          const typename Cx<T>::t* __restrict__ tw_g)
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(256) x_r2c_1024_kernel(Geometry g, const T* __
 // x complex-to-real, px = 1024: warp w rebuilds Z = A + i B from the half
 // spectra of rows w and w + 8 and transforms back.
 template <typename T>
-__global__ void __launch_bounds__(256) x_c2r_1024_kernel(Geometry g, const typename Cx<T>::t* __restrict__ X,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) x_c2r_1024_kernel(Geometry g, const typename Cx<T>::t* __restrict__ X,
                                                          T* __restrict__ H,
                                                          const typename Cx<T>::t* __restrict__ tw_g)
 {
@@ -94,13 +94,14 @@ __global__ void __launch_bounds__(256) x_c2r_1024_kernel(Geometry g, const typen
     load_tw1024(tws, tw_g, g.lglmax - 10);
     __syncthreads();
     const int ya = y0 + warp, yb = y0 + warp + 8;
-    // stage the 513 x 16 half-spectrum block ([kx][17]: odd stride, no bank
-    // conflicts when lanes walk kx) with coalesced 128-byte rows
+    // stage the 513 x 16 half-spectrum block with coalesced 128-byte rows;
+    // row kx holds column t at t ^ (kx & 15), so lanes walking kx read
+    // distinct banks without padding (which would cost the third CTA per SM)
     C* S = reg;
     staged_loop<256, C>(513 * 16, [&](int i) {
         const int kx = i >> 4, t = i & 15;
         return y0 + t < ny ? X[(((size_t)kx * 3 + c) * nz + z) * ny + y0 + t] : C{T(0), T(0)};
-    }, [&](int i, C a) { S[(i >> 4) * 17 + (i & 15)] = a; });
+    }, [&](int i, C a) { S[(i >> 4) * 16 + ((i & 15) ^ ((i >> 4) & 15))] = a; });
     __syncthreads();
     C v[32];
 #pragma unroll
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(256) x_c2r_1024_kernel(Geometry g, const typen
         const int k = lane + 32 * d;
         const bool upper = k > 512;
         const int kx = upper ? 1024 - k : k;
-        C A = S[kx * 17 + warp], B = S[kx * 17 + warp + 8];
+        C A = S[kx * 16 + (warp ^ (kx & 15))], B = S[kx * 16 + ((warp + 8) ^ (kx & 15))];
         if (kx == 0 || kx == 512) {
             A.y = T(0);  // DC and Nyquist bins of a real signal are real
             B.y = T(0);
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(256) x_c2r_1024_kernel(Geometry g, const typen
 
 // y forward, py = 1024: X[kx][line][y] -> Y[kx][line][ky], one line per warp.
 template <typename T>
-__global__ void __launch_bounds__(256) y_fwd_1024_kernel(Geometry g, const typename Cx<T>::t* __restrict__ X,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) y_fwd_1024_kernel(Geometry g, const typename Cx<T>::t* __restrict__ X,
                                                          typename Cx<T>::t* __restrict__ Y,
                                                          const typename Cx<T>::t* __restrict__ tw_g)
 {
@@ -195,8 +196,9 @@ __global__ void __launch_bounds__(256) y_inv_1024_kernel(Geometry g, const typen
 template <typename T>
 static size_t smem_1024()
 {
-    // per-warp regions, also used as the 513 x 17 staging block of x_c2r
-    const size_t regions = 8 * (size_t)REG1025 > 513 * 17 ? 8 * (size_t)REG1025 : 513 * 17;
+    // per-warp regions, also used as the 513 x 16 staging block of x_c2r
+    // (74.4 KB in FP32 with the twiddles: three CTAs per SM)
+    const size_t regions = 8 * (size_t)REG1025 > 513 * 16 ? 8 * (size_t)REG1025 : 513 * 16;
     return ((size_t)TW1024_SLOTS + regions) * sizeof(typename Cx<T>::t);
 }
 

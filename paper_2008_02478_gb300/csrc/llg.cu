@@ -13,6 +13,7 @@
 // the Fehlberg tableau and the embedded error max |m5 - m4|.
 #include "boris_internal.cuh"
 #include "llg_kernels.cuh"
+#include "llg_cell.cuh"
 #include "multilayer.cuh"
 
 namespace boris {
@@ -30,42 +31,6 @@ __constant__ double RKF_A[6][5] = {
 __constant__ double RKF_B4[6] = {25.0 / 216, 0.0, 1408.0 / 2565, 2197.0 / 4104, -1.0 / 5, 0.0};
 __constant__ double RKF_B5[6] = {16.0 / 135, 0.0, 6656.0 / 12825, 28561.0 / 56430, -9.0 / 50, 2.0 / 55};
 
-template <typename T>
-__device__ __forceinline__ void field_and_rhs(const LLGArgs<T>& a, const T* __restrict__ ms, const T* __restrict__ Hd,
-                                              size_t i, int x, int y, int z, T m[3], T k[3])
-{
-    const size_t n = a.ncell;
-    m[0] = ms[i];
-    m[1] = ms[n + i];
-    m[2] = ms[2 * n + i];
-    T lap[3] = {T(0), T(0), T(0)};
-    auto nb = [&](size_t j, T w) {
-        lap[0] += w * (ms[j] - m[0]);
-        lap[1] += w * (ms[n + j] - m[1]);
-        lap[2] += w * (ms[2 * n + j] - m[2]);
-    };
-    const size_t sy = a.nx, sz = (size_t)a.nx * a.ny;
-    if (x > 0) nb(i - 1, a.ihx2);
-    if (x < a.nx - 1) nb(i + 1, a.ihx2);
-    if (y > 0) nb(i - sy, a.ihy2);
-    if (y < a.ny - 1) nb(i + sy, a.ihy2);
-    if (z > 0) nb(i - sz, a.ihz2);
-    if (z < a.nz - 1) nb(i + sz, a.ihz2);
-    const T Ms = a.ms_map ? a.ms_map[i] : a.Ms;
-    const T Ku = a.ku_map ? a.ku_map[i] : a.Ku;
-    const T inv = T(1) / (T(MU0_D) * Ms);
-    const T cex = T(2) * a.A * inv;
-    const T me = m[0] * a.e[0] + m[1] * a.e[1] + m[2] * a.e[2];
-    const T can = T(2) * Ku * inv * me;
-    T H[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) H[c] = Hd[c * n + i] + cex * lap[c] + can * a.e[c] + a.Hext[c];
-    const T mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
-    const T mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2], m[0] * mxH[1] - m[1] * mxH[0]};
-#pragma unroll
-    for (int c = 0; c < 3; c++) k[c] = -a.gp * (mxH[c] + a.alpha * mmH[c]);
-}
-
 // stage s in 0..3; ms = stage state (m0 itself for s = 0).
 template <typename T>
 __global__ void __launch_bounds__(256) rk4_stage_kernel(LLGArgs<T> a, int s, const T* __restrict__ ms,
@@ -79,26 +44,119 @@ __global__ void __launch_bounds__(256) rk4_stage_kernel(LLGArgs<T> a, int s, con
         const int z = (int)(i / ((size_t)a.nx * a.ny));
         T m[3], k[3];
         field_and_rhs(a, ms, Hd, i, x, y, z, m, k);
+        rk4_combine(a, s, i, m, k, m0, acc, mnext);
+    }
+}
+
+// FP32 RK4 stage over quads of four consecutive x cells (nx % 4 == 0): one
+// 16-byte load per component and neighbour direction instead of four scalar
+// loads, so each thread keeps several times more bytes in flight.  The x
+// neighbours of the quad's end cells come from scalar loads that hit the
+// lines the adjacent quads bring in.
+__device__ __forceinline__ float q_get(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+__device__ __forceinline__ void q_set(float4& v, int j, float f)
+{
+    if (j == 0) v.x = f;
+    else if (j == 1) v.y = f;
+    else if (j == 2) v.z = f;
+    else v.w = f;
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, const float4& v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void lap_add(float4& L, const float4& u, const float4& v, float w)
+{
+    L.x += w * (u.x - v.x);
+    L.y += w * (u.y - v.y);
+    L.z += w * (u.z - v.z);
+    L.w += w * (u.w - v.w);
+}
+
+__global__ void __launch_bounds__(256, 4) rk4_stage_quad_kernel(LLGArgs<float> a, int s, const float* __restrict__ ms,
+                                                             const float* __restrict__ Hd, float* __restrict__ m0,
+                                                             float* __restrict__ acc, float* __restrict__ mnext)
+{
+    const size_t n = a.ncell, nq = n >> 2;
+    const int nxq = a.nx >> 2;
+    const size_t sy = a.nx, sz = (size_t)a.nx * a.ny;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < nq; q += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = q / nxq;
+        const int x0 = (int)(q - row * nxq) * 4;
+        const int y = (int)(row % a.ny), z = (int)(row / a.ny);
+        const size_t i = q * 4;
+        float4 mv[3], L[3], hv[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float* b = ms + c * n + i;
+            const float4 v = ld4(b);
+            mv[c] = v;
+            hv[c] = ld4(Hd + c * n + i);
+            // x: inner differences of the quad plus the two outer neighbours
+            // (a missing neighbour equals the cell: zero difference)
+            const float xl = x0 > 0 ? b[-1] : v.x;
+            const float xr = x0 + 4 < a.nx ? b[4] : v.w;
+            float4 Lc;
+            Lc.x = a.ihx2 * ((xl - v.x) + (v.y - v.x));
+            Lc.y = a.ihx2 * ((v.x - v.y) + (v.z - v.y));
+            Lc.z = a.ihx2 * ((v.y - v.z) + (v.w - v.z));
+            Lc.w = a.ihx2 * ((v.z - v.w) + (xr - v.w));
+            if (y > 0) lap_add(Lc, ld4(b - sy), v, a.ihy2);
+            if (y < a.ny - 1) lap_add(Lc, ld4(b + sy), v, a.ihy2);
+            if (z > 0) lap_add(Lc, ld4(b - sz), v, a.ihz2);
+            if (z < a.nz - 1) lap_add(Lc, ld4(b + sz), v, a.ihz2);
+            L[c] = Lc;
+        }
+        const float4 Msv = a.ms_map ? ld4(a.ms_map + i) : make_float4(a.Ms, a.Ms, a.Ms, a.Ms);
+        const float4 Kuv = a.ku_map ? ld4(a.ku_map + i) : make_float4(a.Ku, a.Ku, a.Ku, a.Ku);
+        float4 kv[3];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const float m[3] = {q_get(mv[0], j), q_get(mv[1], j), q_get(mv[2], j)};
+            const float lap[3] = {q_get(L[0], j), q_get(L[1], j), q_get(L[2], j)};
+            const float hd[3] = {q_get(hv[0], j), q_get(hv[1], j), q_get(hv[2], j)};
+            float k[3];
+            rhs_local(a, m, lap, hd, q_get(Msv, j), q_get(Kuv, j), k);
+#pragma unroll
+            for (int c = 0; c < 3; c++) q_set(kv[c], j, k[c]);
+        }
         if (s == 0) {
+            const float h = 0.5f * a.dt;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                acc[c * n + i] = k[c];
-                mnext[c * n + i] = m[c] + T(0.5) * a.dt * k[c];
+                st4(acc + c * n + i, kv[c]);
+                const float4 v = mv[c], k = kv[c];
+                st4(mnext + c * n + i, make_float4(v.x + h * k.x, v.y + h * k.y, v.z + h * k.z, v.w + h * k.w));
             }
         } else if (s < 3) {
-            const T cdt = s == 1 ? T(0.5) * a.dt : a.dt;
+            const float h = s == 1 ? 0.5f * a.dt : a.dt;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                acc[c * n + i] += T(2) * k[c];
-                mnext[c * n + i] = m0[c * n + i] + cdt * k[c];
+                float4 ac = ld4(acc + c * n + i);
+                const float4 b = ld4(m0 + c * n + i), k = kv[c];
+                ac.x += 2.f * k.x;
+                ac.y += 2.f * k.y;
+                ac.z += 2.f * k.z;
+                ac.w += 2.f * k.w;
+                st4(acc + c * n + i, ac);
+                st4(mnext + c * n + i, make_float4(b.x + h * k.x, b.y + h * k.y, b.z + h * k.z, b.w + h * k.w));
             }
         } else {
-            T v[3];
+            float4 nv[3];
+            const float h = a.dt * (1.f / 6.f);
 #pragma unroll
-            for (int c = 0; c < 3; c++) v[c] = m0[c * n + i] + a.dt * (T(1) / T(6)) * (acc[c * n + i] + k[c]);
-            const T inv = T(1) / sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            for (int c = 0; c < 3; c++) {
+                const float4 ac = ld4(acc + c * n + i), b = ld4(m0 + c * n + i), k = kv[c];
+                nv[c] = make_float4(b.x + h * (ac.x + k.x), b.y + h * (ac.y + k.y), b.z + h * (ac.z + k.z),
+                                    b.w + h * (ac.w + k.w));
+            }
 #pragma unroll
-            for (int c = 0; c < 3; c++) m0[c * n + i] = v[c] * inv;
+            for (int j = 0; j < 4; j++) {
+                const float vx = q_get(nv[0], j), vy = q_get(nv[1], j), vz = q_get(nv[2], j);
+                const float inv = 1.f / sqrtf(vx * vx + vy * vy + vz * vz);
+#pragma unroll
+                for (int c = 0; c < 3; c++) q_set(nv[c], j, q_get(nv[c], j) * inv);
+            }
+#pragma unroll
+            for (int c = 0; c < 3; c++) st4(m0 + c * n + i, nv[c]);
         }
     }
 }
@@ -313,6 +371,12 @@ template <typename T>
 cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, T* m0, T* acc, T* mnext,
                              cudaStream_t st)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (a.nx % 4 == 0) {
+            rk4_stage_quad_kernel<<<grid_for(a.ncell / 4), 256, 0, st>>>(a, s, ms, Hd, m0, acc, mnext);
+            return cudaGetLastError();
+        }
+    }
     rk4_stage_kernel<T><<<grid_for(a.ncell), 256, 0, st>>>(a, s, ms, Hd, m0, acc, mnext);
     return cudaGetLastError();
 }

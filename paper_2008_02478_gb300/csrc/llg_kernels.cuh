@@ -45,6 +45,11 @@ cudaError_t launch_bwd_field(const LLGArgs<T>& a, const T* ms, const T* gH, cons
 struct MLTable;
 cudaError_t launch_rk4_stage_ml(const LLGArgs<float>& a, const MLTable& t, int s, const float* ms, const float* Hd,
                                 float* m0, float* acc, float* mnext, cudaStream_t st);
+struct Geometry;
+// inverse x transform + RK4 stage in one kernel (FP32, px = 1024; llg_fused.cu)
+bool x_c2r_rk4_ok(const Geometry& g, int max_smem);
+cudaError_t launch_x_c2r_rk4(const Geometry& g, const float2* X, const float2* tw, const LLGArgs<float>& a, int s,
+                             const float* ms, float* m0, float* acc, float* mnext, cudaStream_t st);
 template <typename T>
 cudaError_t launch_energy(const LLGArgs<T>& a, const T* m, const T* Hd, double* out, cudaStream_t st);
 

@@ -49,9 +49,13 @@ SCHEDULE_MESHES = [
     ((30, 16, 3), (1e-9, 2e-9, 3e-9)),    # pz = 8 > 2 nz
     ((20, 48, 2), (2e-9, 2e-9, 2e-9)),    # pz = 4, ny not a power of two
     ((64, 40, 1), (2e-9, 2e-9, 3e-9)),    # 2D mode
+    ((18, 33, 9), (2e-9, 1e-9, 2e-9)),    # pz = 32, ragged nz and ny
+    ((12, 40, 3), (3e-9, 2e-9, 1e-9)),    # pz = 8, py = 128
 ]
+# (kind, CTAs per cluster or per SM, threads | "tma" for the bulk-copy z convolution)
 SCHEDULES = [(0, 1, None), (0, 2, None), (0, 4, None), (0, 8, None), (0, 16, None),
-             (1, 1, 384), (1, 1, 768), (1, 8, 384), (1, 8, 768), (1, 16, 384), (1, 16, 768), (2, 2, None), (2, 3, None)]
+             (1, 1, 384), (1, 1, 768), (1, 8, 384), (1, 8, 768), (1, 16, 384), (1, 16, 768), (2, 2, None), (2, 3, None),
+             (2, 3, "tma1"), (2, 2, "tma2")]
 
 
 @pytest.mark.parametrize("n,h", SCHEDULE_MESHES)
@@ -66,7 +70,9 @@ def test_every_yz_schedule_matches_oracle(n, h, kind, C, NT, monkeypatch):
     ref = oracle.DemagPlan(nx, ny, nz, *h).apply(M)
     monkeypatch.setenv("BORIS_YZ_KIND", str(kind))
     monkeypatch.setenv("BORIS_YZ_CLUSTER", str(C))
-    if NT:
+    if kind == 2:
+        monkeypatch.setenv("BORIS_YZ_TMA", NT[3:] if NT else "0")
+    elif NT:
         monkeypatch.setenv("BORIS_YZ_THREADS", str(NT))
     elif kind == 0:
         monkeypatch.setenv("BORIS_YZ_QC", "7")  # ragged z-stage chunks
@@ -76,7 +82,10 @@ def test_every_yz_schedule_matches_oracle(n, h, kind, C, NT, monkeypatch):
         assert e.code == -4  # this schedule does not fit this mesh
         pytest.skip("schedule does not fit")
     assert plan.schedule()[:2] == (kind, C)
+    if kind == 2:
+        assert plan.schedule()[2] == (int(NT[3:]) if NT else 0)
     H = plan.apply(to_dev(torch, M)).cpu().numpy()
+    plan.sync_status()
     assert rel_l2(H, ref) < 1e-5
 
 

@@ -42,6 +42,7 @@ def _gpu_params(torch, prm, fp64=False):
     ((32, 32, 4), (5e-9, 5e-9, 5e-9), False),   # small cubic-cell mesh, 10 RK4 steps
     ((20, 13, 3), (3e-9, 3e-9, 3e-9), True),    # per-cell Ms and Ku maps, ragged
     ((24, 16, 1), (2e-9, 2e-9, 3e-9), False),   # 2D mode
+    ((21, 10, 2), (3e-9, 2e-9, 4e-9), True),    # nx % 4 != 0: one cell per thread in FP32
 ])
 @pytest.mark.parametrize("fp64", [False, True])
 def test_rk4_steps_match_oracle(n, h, per_cell, fp64):
@@ -114,13 +115,65 @@ def test_graph_replay_equals_step_calls(n):
     from paper_2008_02478_gb300.binding import LLGParams, Plan
     h = (2e-9, 2e-9, 3e-9)
     m0 = inputs.random_unit(*n, seed=8)
-    p1, p2 = Plan(*n, *h), Plan(*n, *h)
+    # one plan for both routes: two plans may autotune different y-z schedules
+    p = Plan(*n, *h)
     prm = LLGParams(Ms=8e5, A=1.3e-11, alpha=0.02, Hext=(0.0, 1e4, 2e4))
     a = to_dev(torch, m0)
     b = to_dev(torch, m0)
     for _ in range(5):
-        p1.llg_step(a, prm, 1e-13)
-    p2.llg_run_graph(b, prm, 1e-13, 2)
-    p2.llg_run_graph(b, prm, 1e-13, 3)  # reuses the captured graph
+        p.llg_step(a, prm, 1e-13)
+    p.llg_run_graph(b, prm, 1e-13, 2)
+    p.llg_run_graph(b, prm, 1e-13, 3)  # reuses the captured graph
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+# Meshes of 257..512 cells along x (transform length 1024) can run the
+# inverse x transform and the RK4 stage as one kernel in FP32; the ragged cases
+# leave a partial group of 8 rows at the top of each plane.
+@pytest.mark.parametrize("n,per_cell", [
+    ((300, 20, 3), True),    # per-cell maps, ny % 8 = 4
+    ((512, 13, 2), False),   # full 512-cell rows, ny % 8 = 5
+    ((257, 8, 1), True),     # shortest row of the 1024-point transform, 2D mode
+])
+def test_fused_inverse_x_rk4_matches_oracle(n, per_cell, monkeypatch):
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan
+    monkeypatch.setenv("BORIS_FUSE_STAGE", "1")
+    h = (3e-9, 3e-9, 3e-9)
+    prm, m0 = _problem(n, h, per_cell, seed=11)
+    dt, steps = 1e-13, 3
+    dem = oracle.DemagPlan(*n, *h)
+    ref = m0.copy()
+    for _ in range(steps):
+        ref = llg.rk4_step(ref, dt, prm, dem.apply)
+    plan = Plan(*n, *h)
+    assert plan.padded()[0] == 1024
+    m = to_dev(torch, m0)
+    gp = _gpu_params(torch, prm)
+    plan.profile(True)
+    for _ in range(steps):
+        plan.llg_step(m, gp, dt)
+    kern, _ = plan.profile_read()
+    assert kern["x_c2r_rk4"][1] == 4 * steps and kern["llg_stage"][1] == 0
+    assert rel_l2(m.cpu().numpy(), ref) < 1e-5
+
+
+def test_fused_and_separate_stage_agree(monkeypatch):
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan
+    n, h = (400, 64, 4), (4e-9, 4e-9, 4e-9)
+    prm, m0 = _problem(n, h, True, seed=12)
+    monkeypatch.setenv("BORIS_FUSE_STAGE", "1")
+    fused = Plan(*n, *h)
+    monkeypatch.setenv("BORIS_FUSE_STAGE", "0")
+    sep = Plan(*n, *h)
+    gp = _gpu_params(torch, prm)
+    a, b = to_dev(torch, m0), to_dev(torch, m0)
+    sep.profile(True)
+    for _ in range(4):
+        fused.llg_step(a, gp, 1e-13)
+        sep.llg_step(b, gp, 1e-13)
+    kern, _ = sep.profile_read()
+    assert kern["x_c2r_rk4"][1] == 0 and kern["llg_stage"][1] == 16
+    assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-6

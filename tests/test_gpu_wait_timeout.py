@@ -1,0 +1,39 @@
+"""Bounded device-side waits: the bulk-copy z convolution waits on mbarriers
+with a time limit.  Through a test hook the first wait of every CTA expects
+16 bytes that never arrive; the kernel must give up after its limit, latch
+BORIS_ERR_TIMEOUT in the plan's status word (read by boris_sync_status) and
+leave the context usable.  No GPU fault is involved: the wait simply runs
+out."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2008_02478_gb300 import inputs
+from tests.gpu_util import rel_l2, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+N, H = (24, 40, 9), (2e-9, 2e-9, 2e-9)
+
+
+def test_wait_that_runs_out_reports_timeout_and_context_survives(monkeypatch):
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import BorisError, Plan
+    M = 7e5 * inputs.random_unit(*N, seed=21)
+    monkeypatch.setenv("BORIS_YZ_KIND", "2")
+    monkeypatch.setenv("BORIS_YZ_TMA", "1")
+    monkeypatch.setenv("BORIS_TEST_WAIT_TIMEOUT", "1")
+    bad = Plan(*N, *H)
+    assert bad.schedule()[0] == 2 and bad.schedule()[2] == 1
+    bad.apply(to_dev(torch, M))
+    with pytest.raises(BorisError) as ei:
+        bad.sync_status()
+    assert ei.value.code == -5
+    bad.sync_status()  # the status word was cleared by the read
+    bad.close()
+    monkeypatch.delenv("BORIS_TEST_WAIT_TIMEOUT")
+    good = Plan(*N, *H)
+    Hd = good.apply(to_dev(torch, M))
+    good.sync_status()
+    ref = oracle.DemagPlan(*N, *H).apply(M)
+    assert rel_l2(Hd.cpu().numpy(), ref) < 1e-5
