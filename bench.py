@@ -39,11 +39,17 @@ WORKLOAD = "512x512x32 film, 4 nm cubic cells, 2621 columnar Voronoi grains (40 
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture on this workload, keyed by kernel class, with a digest of the
-# kernel's sources at capture time; a changed source voids the figure.
+# ncu capture on this workload, keyed by kernel (the z-convolution class names
+# its variant: plain, tma1 one-stage, tma2 two-stage bulk-copy pipeline), with
+# a digest of the kernel's sources at capture time; a changed source voids it.
 TRAFFIC = {
-    "z_conv": (1197.8e6, "10285ab2c5a1155a", ["paper_2008_02478_gb300/csrc/demag_split.cu",
-                                              "paper_2008_02478_gb300/csrc/fft_engine.cuh"]),
+    "z_conv/plain": (1035.0e6, "b51fe8b7759c3a7a", ["paper_2008_02478_gb300/csrc/demag_split.cu",
+                                            "paper_2008_02478_gb300/csrc/fft_engine.cuh",
+                                            "paper_2008_02478_gb300/csrc/twiddle128.h"]),
+    "z_conv/tma2": (964.1e6, "6399403a9bae76bf", ["paper_2008_02478_gb300/csrc/zconv_tma.cu",
+                                           "paper_2008_02478_gb300/csrc/bulk_async.cuh",
+                                           "paper_2008_02478_gb300/csrc/fft_engine.cuh",
+                                           "paper_2008_02478_gb300/csrc/twiddle128.h"]),
 }
 
 
@@ -441,8 +447,11 @@ def main():
     peak, peak_kind = measured_peaks()
     dom_bytes = algo.get(dominant)
     achieved = dom_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9 if dom_bytes else None
-    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic_for(dominant),
+    dom_key = dominant
+    if dominant == "z_conv":
+        dom_key = "z_conv/" + {0: "plain", 1: "tma1", 2: "tma2"}.get(plan.schedule()[2], "plain")
+    roofline = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic_for(dom_key),
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": dom_bytes}
     kernels = {k: {"ms_per_launch": per_launch_ms[k], "launches": kern[k][1],
                    "share": kern[k][0] / max(1e-12, sum(v[0] for v in kern.values())),
