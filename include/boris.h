@@ -111,9 +111,10 @@ int boris_plan_multimesh_info(boris_plan p, int out[4]);
 /*
  * boris_demag_apply - Hd = -N * M (Table 1), FP32 plan.
  *   M, Hd: device [3][nz][ny][nx] float, A/m; may not alias.
- *   Three kernels: zero-padded x real-to-complex transform, fused y-z pass
- *   (y and z transforms, kernel multiply, inverse z and y transforms, one
- *   thread-block cluster per kx plane), x complex-to-real transform.
+ *   Kernels: zero-padded x real-to-complex transform; the y-z pass (y and z
+ *   transforms, kernel multiply, inverse z and y transforms) in the schedule
+ *   the plan's autotuner chose (boris_plan_schedule); x complex-to-real
+ *   transform.  Asynchronous on the plan's stream.
  */
 int boris_demag_apply(boris_plan p, const float* M, float* Hd);
 /* FP64 plan variant (same layout, double). */
