@@ -40,7 +40,8 @@ WORKLOAD = "512x512x32 film, 4 nm cubic cells, 2621 columnar Voronoi grains (40 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture on this workload, keyed by kernel (the z-convolution class names
-# its variant: plain, tma1 one-stage, tma2 two-stage bulk-copy pipeline), with
+# its variant: plain, tma1 one-stage, tma2 two-stage bulk-copy pipeline, res
+# residue-split), with
 # a digest of the kernel's sources at capture time; a changed source voids it.
 TRAFFIC = {
     "z_conv/plain": (1035.0e6, "b51fe8b7759c3a7a", ["paper_2008_02478_gb300/csrc/demag_split.cu",
@@ -88,7 +89,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -361,7 +362,7 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
@@ -449,7 +450,7 @@ def main():
     achieved = dom_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9 if dom_bytes else None
     dom_key = dominant
     if dominant == "z_conv":
-        dom_key = "z_conv/" + {0: "plain", 1: "tma1", 2: "tma2"}.get(plan.schedule()[2], "plain")
+        dom_key = "z_conv/" + {0: "plain", 1: "tma1", 2: "tma2", 3: "res"}.get(plan.schedule()[2], "plain")
     roofline = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic_for(dom_key),
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": dom_bytes}

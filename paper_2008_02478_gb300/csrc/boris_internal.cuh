@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of libboris.
 #pragma once
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -103,6 +104,21 @@ bool zconv_tma_supported(const Geometry& g, int max_smem, int variant);
 cudaError_t zconv_tma_map(const Geometry& g, float2* Y, void* map);
 cudaError_t launch_zconv_tma(const void* map, const Geometry& g, const float* K, int* status, uint32_t extra_tx,
                              unsigned long long limit_ns, int nsm, int variant, cudaStream_t st);
+// residue-split z convolution of the split schedule (FP32; zconv_res.cu):
+// reads the kernel spectrum in the blocked copy K2 [kx][ky'/32][kz'][pair][ky' mod 32]
+// that zconv_res_build_k2 makes from K
+bool zconv_res_supported(const Geometry& g, int max_smem);
+int zconv_res_nkb(const Geometry& g);
+size_t zconv_res_k2_bytes(const Geometry& g);
+cudaError_t zconv_res_build_k2(const Geometry& g, const float* K, float2* K2, cudaStream_t st);
+// encodes the tensor map of K2 (128 bytes at map)
+cudaError_t zconv_res_kmap(const Geometry& g, float2* K2, void* map);
+// ctas_per_sm 3: separate kernel stage and scratch; 4: the scratch overlays the kernel stage
+cudaError_t launch_zconv_res(const void* ymap, const void* kmap, const Geometry& g, float2* Y, int* status,
+                             uint32_t extra_tx, unsigned long long limit_ns, int nsm, int ctas_per_sm, cudaStream_t st);
+// cuTensorMapEncodeTiled from the driver (nullptr if unavailable)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+cudaError_t upload_twiddles_res();
 cudaError_t launch_zconv_tc(const Geometry& g, float2* Y, const float* K, const float2* tw, bool bf16, cudaStream_t st);
 cudaError_t upload_twiddles_yz_f32();
 cudaError_t upload_twiddles_yz_f64();

@@ -44,6 +44,11 @@ struct boris_plan_s {
     bool ymap_ready = false;
     // kernel spectrum [kx][ky'][kz'][6] in the plan precision
     void* K = nullptr;
+    // its column-major copy for the residue-split z convolution (kept only
+    // when that schedule is chosen)
+    void* K2 = nullptr;
+    size_t k2_bytes = 0;
+    alignas(64) unsigned char kmap[128] = {};  // its tensor map
     // twiddles exp(-2 pi i e / lmax) in the plan precision and in FP64
     void* tw = nullptr;
     double2* tw64 = nullptr;
@@ -164,6 +169,15 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
                 if (part == 1 && p->tc)
                     return launch_zconv_tc(p->g, (float2*)p->Y, (const float*)p->K, (const float2*)p->tw, p->tc == 2,
                                            p->stream);
+                if (part == 1 && sc.Qc == 3) {
+                    if (!p->ymap_ready) {
+                        cudaError_t me = zconv_tma_map(p->g, (float2*)p->Y, p->ymap);
+                        if (me != cudaSuccess) return me;
+                        p->ymap_ready = true;
+                    }
+                    return launch_zconv_res(p->ymap, p->kmap, p->g, (float2*)p->Y, p->d_status, p->wait_extra_tx,
+                                            p->wait_limit_ns, p->nsm, sc.C, p->stream);
+                }
                 if (part == 1 && sc.Qc >= 1) {
                     if (!p->ymap_ready) {
                         cudaError_t me = zconv_tma_map(p->g, (float2*)p->Y, p->ymap);
@@ -546,18 +560,23 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     }
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
-    YZSchedule cand[16];
+    YZSchedule cand[20];
     int ncand = 0;
     if (p->f64) yz_candidates<double>(g, max_smem, cand, &ncand);
     else yz_candidates<float>(g, max_smem, cand, &ncand);
     const bool split_ok = p->f64 ? split_supported<double>(g, max_smem) : split_supported<float>(g, max_smem);
-    if (split_ok && ncand < 13) {
+    if (split_ok && ncand < 14) {
         cand[ncand++] = YZSchedule{2, 2, 0, 0, 0};
         if (!p->f64) cand[ncand++] = YZSchedule{2, 3, 0, 0, 0};
         // Qc = 1 / 2 on a split schedule: the bulk-copy pipelined z convolution
         // with one tile stage and 3 CTAs per SM / two stages and 2 CTAs per SM
         for (int v = 1; v <= 2; v++)
             if (!p->f64 && zconv_tma_supported(g, max_smem, v)) cand[ncand++] = YZSchedule{2, v == 1 ? 3 : 2, v, 0, 0};
+        // Qc = 3: the residue-split z convolution, register budgets for 4 and 3 CTAs per SM
+        if (!p->f64 && zconv_res_supported(g, max_smem)) {
+            cand[ncand++] = YZSchedule{2, 4, 3, 0, 0};
+            cand[ncand++] = YZSchedule{2, 3, 3, 0, 0};
+        }
     }
     if (tc) {
         // the tensor-core z stage runs inside the split schedule only
@@ -607,6 +626,7 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     cudaError_t ce = p->f64 ? upload_twiddles_yz_f64() : upload_twiddles_yz_f32();
     if (ce == cudaSuccess) ce = upload_twiddles_split();
     if (ce == cudaSuccess) ce = upload_twiddles_fast();
+    if (ce == cudaSuccess) ce = upload_twiddles_res();
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("twiddle constants: ") + cudaGetErrorString(ce)));
     ce = p->f64 ? yz_set_attributes<double>(p->yz) : yz_set_attributes<float>(p->yz);
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("yz attributes: ") + cudaGetErrorString(ce)));
@@ -651,9 +671,34 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
             p->yz = cand[0];
         }
     }
+    bool want_k2 = false;
+    for (int i = 0; i < ncand; i++) want_k2 |= cand[i].kind == 2 && cand[i].Qc == 3;
+    if (want_k2) {
+        if (dev_alloc(p, &p->K2, zconv_res_k2_bytes(g)) == BORIS_OK) {
+            p->k2_bytes = zconv_res_k2_bytes(g);
+            if ((ce = zconv_res_build_k2(g, (const float*)p->K, (float2*)p->K2, p->stream)) != cudaSuccess ||
+                (ce = zconv_res_kmap(g, (float2*)p->K2, p->kmap)) != cudaSuccess)
+                return bail(fail(BORIS_ERR_CUDA, std::string("kernel spectrum copy: ") + cudaGetErrorString(ce)));
+        } else {
+            // no room for the column-major copy: drop the schedule that reads it
+            cudaGetLastError();
+            int m = 0;
+            for (int i = 0; i < ncand; i++)
+                if (!(cand[i].kind == 2 && cand[i].Qc == 3)) cand[m++] = cand[i];
+            ncand = m;
+            if (ncand == 0) return bail(fail(BORIS_ERR_OOM, "no memory for the kernel spectrum copy"));
+            p->yz = cand[0];
+        }
+    }
     if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
     if (ncand > 1 && (rc = autotune_yz(p, cand, ncand))) return bail(rc);
+    if (p->K2 && !(p->yz.kind == 2 && p->yz.Qc == 3)) {
+        cudaFree(p->K2);
+        p->K2 = nullptr;
+        p->bytes -= p->k2_bytes;
+        p->k2_bytes = 0;
+    }
     *out = p;
     return BORIS_OK;
 }
@@ -785,6 +830,7 @@ int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, cons
     if (!split_supported<float>(g, max_smem)) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "frame too large"));
     cudaError_t ce = upload_twiddles_split();
     if (ce == cudaSuccess) ce = upload_twiddles_fast();
+    if (ce == cudaSuccess) ce = upload_twiddles_res();
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "twiddle constants"));
     std::vector<double2> tw(g.lmax);
     host_twiddles(g.lmax, tw.data());
@@ -1041,7 +1087,7 @@ void boris_plan_destroy(boris_plan p)
 {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
-    void* ptrs[] = {p->Kml, p->d_pairs, p->Mf, p->Hf, p->K, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
+    void* ptrs[] = {p->Kml, p->d_pairs, p->Mf, p->Hf, p->K, p->K2, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
                     p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);

@@ -256,7 +256,7 @@ cudaError_t launch_hz(const CUtensorMap& ymap, const Geometry& g, const float* K
     return launch_v<HZ, 1, 3>(ymap, g, K, status, extra_tx, limit_ns, nsm, st);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn_once()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -286,6 +286,8 @@ size_t tma_smem(int hz, int variant)
 
 }  // namespace
 
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() { return encode_fn_once(); }
+
 bool zconv_tma_supported(const Geometry& g, int max_smem, int variant)
 {
     const int hz = g.pz / 2;
@@ -297,7 +299,7 @@ bool zconv_tma_supported(const Geometry& g, int max_smem, int variant)
 
 cudaError_t zconv_tma_map(const Geometry& g, float2* Y, void* map)
 {
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     // Y[kx][c][z][ky] as a 2D array of complex (8-byte) elements: rows
     // (kx, c, z), py columns; boxes of 32 columns x nz rows

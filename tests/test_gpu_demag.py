@@ -52,10 +52,11 @@ SCHEDULE_MESHES = [
     ((18, 33, 9), (2e-9, 1e-9, 2e-9)),    # pz = 32, ragged nz and ny
     ((12, 40, 3), (3e-9, 2e-9, 1e-9)),    # pz = 8, py = 128
 ]
-# (kind, CTAs per cluster or per SM, threads | "tma" for the bulk-copy z convolution)
+# (kind, CTAs per cluster or per SM, threads | "tma1"/"tma2" for the bulk-copy z
+# convolution | "tma3" for the residue-split z convolution)
 SCHEDULES = [(0, 1, None), (0, 2, None), (0, 4, None), (0, 8, None), (0, 16, None),
              (1, 1, 384), (1, 1, 768), (1, 8, 384), (1, 8, 768), (1, 16, 384), (1, 16, 768), (2, 2, None), (2, 3, None),
-             (2, 3, "tma1"), (2, 2, "tma2")]
+             (2, 3, "tma1"), (2, 2, "tma2"), (2, 4, "tma3"), (2, 3, "tma3")]
 
 
 @pytest.mark.parametrize("n,h", SCHEDULE_MESHES)

@@ -1,4 +1,4 @@
-"""Bounded device-side waits: the bulk-copy z convolution waits on mbarriers
+"""Bounded device-side waits: the bulk-copy and residue-split z convolutions wait on mbarriers
 with a time limit.  Through a test hook the first wait of every CTA expects
 16 bytes that never arrive; the kernel must give up after its limit, latch
 BORIS_ERR_TIMEOUT in the plan's status word (read by boris_sync_status) and
@@ -16,15 +16,16 @@ pytestmark = pytest.mark.gpu
 N, H = (24, 40, 9), (2e-9, 2e-9, 2e-9)
 
 
-def test_wait_that_runs_out_reports_timeout_and_context_survives(monkeypatch):
+@pytest.mark.parametrize("variant", ["1", "3"])  # bulk-copy pipeline, residue-split z convolution
+def test_wait_that_runs_out_reports_timeout_and_context_survives(variant, monkeypatch):
     torch = torch_cuda()
     from paper_2008_02478_gb300.binding import BorisError, Plan
     M = 7e5 * inputs.random_unit(*N, seed=21)
     monkeypatch.setenv("BORIS_YZ_KIND", "2")
-    monkeypatch.setenv("BORIS_YZ_TMA", "1")
+    monkeypatch.setenv("BORIS_YZ_TMA", variant)
     monkeypatch.setenv("BORIS_TEST_WAIT_TIMEOUT", "1")
     bad = Plan(*N, *H)
-    assert bad.schedule()[0] == 2 and bad.schedule()[2] == 1
+    assert bad.schedule()[0] == 2 and bad.schedule()[2] == int(variant)
     bad.apply(to_dev(torch, M))
     with pytest.raises(BorisError) as ei:
         bad.sync_status()
