@@ -58,9 +58,12 @@ cudaError_t launch_x_r2c(const Geometry& g, const T* M, const T* ms_map, T ms_sc
 template <typename T>
 cudaError_t launch_yz_conv(const Geometry& g, const YZSchedule& sc, typename Cx<T>::t* X,
                            const T* K, const typename Cx<T>::t* tw, cudaStream_t st);
+// with a status word (FP32 plans) the tensor-copy form of the length-1024
+// pass may run; its bounded wait latches BORIS_ERR_TIMEOUT there
 template <typename T>
 cudaError_t launch_x_c2r(const Geometry& g, const typename Cx<T>::t* X, T* H,
-                         const typename Cx<T>::t* tw, cudaStream_t st);
+                         const typename Cx<T>::t* tw, cudaStream_t st, int* status = nullptr,
+                         unsigned long long limit_ns = 1000000000ull);
 template <typename T>
 cudaError_t launch_yz_reg(const Geometry& g, const YZSchedule& sc, typename Cx<T>::t* X, const T* K,
                           const typename Cx<T>::t* tw, cudaStream_t st);
@@ -95,6 +98,11 @@ template <typename T>
 cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
                           cudaStream_t st, bool forward);
 cudaError_t upload_twiddles_fast();
+// FP32 x complex-to-real (px = 1024, ny even) with the half-spectrum block
+// fetched by tensor copies; a wait that gives up latches BORIS_ERR_TIMEOUT in *status
+bool x_c2r_tma_ok(const Geometry& g, int max_smem);
+cudaError_t launch_x_c2r_1024_tma(const Geometry& g, const float2* X, float* H, const float2* tw, int* status,
+                                  unsigned long long limit_ns, cudaStream_t st);
 // Tensor-core (FP16 / BF16) z stage of the split schedule (zconv_tc.cu), pz = 64.
 bool zconv_tc_supported(const Geometry& g);
 // bulk-copy pipelined z convolution of the split schedule (FP32; zconv_tma.cu);

@@ -229,7 +229,9 @@ int demag_apply_t(boris_plan p, const T* M, const T* ms_map, T ms_scale, T* H)
     }
     int rc = demag_to_spectrum_t<T>(p, M, ms_map, ms_scale);
     if (rc) return rc;
-    CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<T>(p->g, (const C*)p->X, H, (const C*)p->tw, p->stream); }));
+    CUDA_TRY(timed(p, 2, [&] {
+        return launch_x_c2r<T>(p->g, (const C*)p->X, H, (const C*)p->tw, p->stream, p->d_status, p->wait_limit_ns);
+    }));
     return BORIS_OK;
 }
 

@@ -382,8 +382,11 @@ static cudaError_t launch_c2r_ty(const Geometry& g, const typename Cx<T>::t* X, 
 
 template <typename T>
 cudaError_t launch_x_c2r(const Geometry& g, const typename Cx<T>::t* X, T* H,
-                         const typename Cx<T>::t* tw, cudaStream_t st)
+                         const typename Cx<T>::t* tw, cudaStream_t st, int* status, unsigned long long limit_ns)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (status && x_c2r_tma_ok(g, 227 * 1024)) return launch_x_c2r_1024_tma(g, X, H, tw, status, limit_ns, st);
+    }
     if (x1024_ok<T>(g, 227 * 1024)) return launch_x_c2r_1024<T>(g, X, H, tw, st);
     switch (xrow_tile<T>(g)) {
     case 16: return launch_c2r_ty<T, 16>(g, X, H, tw, st);
@@ -512,7 +515,8 @@ cudaError_t launch_yz_conv(const Geometry& g, const YZSchedule& sc, typename Cx<
                                          cudaStream_t);                                                       \
     template cudaError_t launch_yz_conv<T>(const Geometry&, const YZSchedule&, Cx<T>::t*, const T*,           \
                                            const Cx<T>::t*, cudaStream_t);                                    \
-    template cudaError_t launch_x_c2r<T>(const Geometry&, const Cx<T>::t*, T*, const Cx<T>::t*, cudaStream_t); \
+    template cudaError_t launch_x_c2r<T>(const Geometry&, const Cx<T>::t*, T*, const Cx<T>::t*, cudaStream_t, int*, \
+                                         unsigned long long);                                                  \
     template bool choose_yz_schedule<T>(const Geometry&, int, YZSchedule*);                                   \
     template void yz_candidates<T>(const Geometry&, int, YZSchedule*, int*);                                  \
     template cudaError_t yz_set_attributes<T>(const YZSchedule&);

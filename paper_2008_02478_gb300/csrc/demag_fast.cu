@@ -4,6 +4,7 @@
 // (packed) line in registers (warp_fft.cuh); global loads and stores are
 // 32 consecutive elements per instruction.
 #include "boris_internal.cuh"
+#include "bulk_async.cuh"
 #include "warp_fft.cuh"
 
 namespace boris {
@@ -133,6 +134,135 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) x_c2r_1024_kernel
             if (yb < ny) hb[x] = v[a].y;
         }
     }
+}
+
+// x complex-to-real, px = 1024, FP32, with the 513 x 16 half-spectrum block
+// of the CTA fetched by tensor copies: rows kx < 512 as four 128-row boxes
+// with the 128-byte swizzle (16-byte chunk c of row kx lands at chunk
+// c ^ (kx & 7)), so the whole block is in flight at once and the column reads
+// below spread over the banks; row 512 by plain loads.  The wait for the
+// copies is bounded; when it gives up, the CTA latches BORIS_ERR_TIMEOUT in
+// *status and returns.
+constexpr size_t XC2R_TMA_SMEM = 1024 + 512 * 128 + 128 + (size_t)TW1024_SLOTS * sizeof(float2) + 16;
+
+__global__ void __launch_bounds__(256, 3) x_c2r_1024_tma_kernel(const __grid_constant__ CUtensorMap xmap, Geometry g,
+                                                                 const float2* __restrict__ X, float* __restrict__ H,
+                                                                 const float2* __restrict__ tw_g, int* status,
+                                                                 unsigned long long limit_ns)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    float2* S = reinterpret_cast<float2*>(base);               // rows kx < 512, swizzled
+    float2* R512 = reinterpret_cast<float2*>(base + 512 * 128);  // row kx = 512
+    float2* tws = reinterpret_cast<float2*>(base + 512 * 128 + 128);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(base + 512 * 128 + 128 + TW1024_SLOTS * sizeof(float2));
+    float2* reg = S;  // per-warp transpose regions once the block is consumed
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int y0 = blockIdx.x * 16, z = blockIdx.y, c = blockIdx.z;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int x0 = (c * nz + z) * ny + y0;  // column of the block in the [kx][(c, z, y)] view of X
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(bar, 512 * 128);
+        for (int i = 0; i < 4; i++) tma_load_2d(S + i * 128 * 16, &xmap, x0, i * 128, bar);
+    }
+    load_tw1024(tws, tw_g, g.lglmax - 10);
+    if (warp == 0 && lane < 16) {
+        const size_t plane = (size_t)3 * nz * ny;
+        R512[lane] = y0 + lane < ny ? X[512 * plane + x0 + lane] : float2{0.f, 0.f};
+    }
+    __syncthreads();  // barrier initialised, twiddles and row 512 staged
+    const bool ok = mbar_wait_bounded(bar, 0, limit_ns);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) atomicCAS(status, 0, -5);  // BORIS_ERR_TIMEOUT
+        return;
+    }
+    const int ya = y0 + warp, yb = y0 + warp + 8;
+    // element (kx, t) sits at kx 16 + 2 ((t >> 1) ^ (kx & 7)) + (t & 1); for
+    // k = lane + 32 d the row is kx = k (d < 16, kx & 7 = lane & 7) or
+    // 1024 - k (d > 16, kx & 7 = -lane & 7), so each half reads at fixed
+    // per-thread offsets plus a compile-time 512 d
+    const int wa = warp >> 1, wb = (warp + 8) >> 1, wl = warp & 1;
+    const float2* loA = S + lane * 16 + 2 * (wa ^ (lane & 7)) + wl;
+    const float2* loB = S + lane * 16 + 2 * (wb ^ (lane & 7)) + wl;
+    const float2* hiA = S + (1024 - lane) * 16 + 2 * (wa ^ (-lane & 7)) + wl;
+    const float2* hiB = S + (1024 - lane) * 16 + 2 * (wb ^ (-lane & 7)) + wl;
+    float2 v[32];
+#pragma unroll
+    for (int d = 0; d < 32; d++) {
+        float2 A, B;
+        if (d < 16) {
+            A = loA[512 * d];
+            B = loB[512 * d];
+            if (d == 0 && lane == 0) {
+                A.y = 0.f;  // DC bin of a real signal is real
+                B.y = 0.f;
+            }
+        } else if (d > 16) {
+            A = hiA[-512 * d];
+            B = hiB[-512 * d];
+            A.y = -A.y;
+            B.y = -B.y;
+        } else if (lane == 0) {
+            A = float2{R512[warp].x, 0.f};  // Nyquist bin, real
+            B = float2{R512[warp + 8].x, 0.f};
+        } else {
+            A = hiA[-512 * d];  // k = 512 + lane: kx = 512 - lane
+            B = hiB[-512 * d];
+            A.y = -A.y;
+            B.y = -B.y;
+        }
+        v[brev5(d)] = float2{A.x - B.y, A.y + B.x};
+    }
+    __syncthreads();  // the staging block becomes the warps' transpose tiles
+    warp_fft1024_inv(v, reg + warp * REG1025, tws);
+    const size_t ncell = (size_t)nx * ny * nz;
+    float* ha = H + c * ncell + ((size_t)z * ny + ya) * nx;
+    float* hb = H + c * ncell + ((size_t)z * ny + yb) * nx;
+#pragma unroll
+    for (int a = 0; a < 16; a++) {
+        const int x = 32 * a + lane;
+        if (x < nx) {
+            if (ya < ny) ha[x] = v[a].x;
+            if (yb < ny) hb[x] = v[a].y;
+        }
+    }
+}
+
+// X as a 2D array of 8-byte elements: nkx rows of 3 nz ny columns; boxes of
+// 16 columns x 128 rows, 128-byte swizzle
+static cudaError_t xc2r_map(const Geometry& g, const float2* X, CUtensorMap* map)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)3 * g.nz * g.ny, (cuuint64_t)g.nkx};
+    const cuuint64_t strides[1] = {(cuuint64_t)3 * g.nz * g.ny * sizeof(float2)};
+    const cuuint32_t box[2] = {16, 128};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<float2*>(X), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// the tensor-copy form needs 16-byte aligned block columns and row pitch (ny even)
+bool x_c2r_tma_ok(const Geometry& g, int max_smem)
+{
+    return g.px == 1024 && g.nx <= 512 && g.ny % 2 == 0 && XC2R_TMA_SMEM <= (size_t)max_smem;
+}
+
+cudaError_t launch_x_c2r_1024_tma(const Geometry& g, const float2* X, float* H, const float2* tw, int* status,
+                                  unsigned long long limit_ns, cudaStream_t st)
+{
+    CUtensorMap map;
+    cudaError_t e = xc2r_map(g, X, &map);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(x_c2r_1024_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)XC2R_TMA_SMEM);
+    if (e != cudaSuccess) return e;
+    x_c2r_1024_tma_kernel<<<dim3((g.ny + 15) / 16, g.nz, 3), 256, XC2R_TMA_SMEM, st>>>(map, g, X, H, tw, status,
+                                                                                       limit_ns);
+    return cudaGetLastError();
 }
 
 // y forward, py = 1024: X[kx][line][y] -> Y[kx][line][ky], one line per warp.

@@ -26,6 +26,8 @@ CASES = [
     ((256, 64, 1), (1.953125e-9, 1.953125e-9, 3e-9)),  # SP4-shaped film
     ((300, 280, 3), (3e-9, 3e-9, 3e-9)),    # length-1024 x and y transforms, ragged rows
     ((512, 300, 2), (4e-9, 4e-9, 4e-9)),    # full 512-cell rows
+    ((280, 30, 3), (3e-9, 2e-9, 2e-9)),     # length-1024 x pass, ragged 16-row blocks
+    ((300, 17, 2), (3e-9, 3e-9, 3e-9)),     # odd ny: the x inverse pass without tensor copies
 ]
 
 
