@@ -12,6 +12,9 @@ Paper: "Boris Computational Spintronics" (arXiv 2008.02478).
     side, RK4 / RKF45 steps (Section 2), energies, and the discrete adjoint of
     an RK4 step.
   * ``multilayer.py``   - the multi-mesh convolution sum (Eq. 4).
+  * ``terms.py``        - further Table 1 field terms (second-order uniaxial
+    and cubic anisotropy, bulk and interfacial DMI with their boundary
+    conditions) and the surface exchange of Eq. 5.
 
 The cross-layer tensor for cells of unequal thickness (``multilayer.py``) is
 pinned by its equal-thickness reduction, reciprocity, source splitting and

@@ -45,6 +45,18 @@ class Params:
     Ku: object = 0.0
     easy: tuple = (0.0, 0.0, 1.0)
     Hext: tuple = (0.0, 0.0, 0.0)
+    # further Table 1 terms (oracle/terms.py): second-order uniaxial K2,
+    # cubic K1/K2 with axes e1, e2 (e3 = e1 x e2), bulk or interfacial DMI
+    K2: float = 0.0
+    Kc1: float = 0.0
+    Kc2: float = 0.0
+    cubic_e1: tuple = (1.0, 0.0, 0.0)
+    cubic_e2: tuple = (0.0, 1.0, 0.0)
+    dmi: str = "none"
+    D: float = 0.0
+
+    def has_extra(self):
+        return self.K2 != 0.0 or self.Kc1 != 0.0 or self.Kc2 != 0.0 or (self.dmi != "none" and self.D != 0.0)
 
     def maps(self, shape):
         """Ms and Ku as arrays of the mesh shape [nz][ny][nx]."""
@@ -93,15 +105,28 @@ def anisotropy_field(m, prm: Params, Ms, Ku):
 
 
 def effective_field(m, prm: Params, demag, parts: bool = False):
-    """H = H_d(Ms m) + H_ex + H_an + H_ext.  ``demag`` maps M -> H_d."""
+    """H = H_d(Ms m) + H_ex + H_an + H_ext (+ the further terms of
+    ``oracle/terms.py`` when set).  ``demag`` maps M -> H_d.  With parts,
+    returns (Hd, Hex, Han, Hz) or, with further terms set, (Hd, Hex, Han, Hz,
+    Hdmi) where Han includes the cubic and K2 terms and Hex uses the DMI
+    boundary condition."""
     Ms, Ku = prm.maps(m.shape[1:])
     Hd = demag(Ms[None] * m)
-    Hex = exchange_field(m, prm, Ms)
     Han = anisotropy_field(m, prm, Ms, Ku)
     Hz = np.asarray(prm.Hext, dtype=np.float64).reshape(3, 1, 1, 1) * np.ones_like(m)
+    if not prm.has_extra():
+        Hex = exchange_field(m, prm, Ms)
+        if parts:
+            return Hd, Hex, Han, Hz
+        return Hd + Hex + Han + Hz
+    from . import terms
+    Hex = terms.exchange_field(m, prm.cell, prm.A, Ms, prm.D, prm.dmi)
+    Hdmi = terms.dmi_field(m, prm.cell, prm.A, prm.D, prm.dmi, Ms)
+    Han = Han + terms.uniaxial_k2_field(m, prm.easy, prm.K2, Ms) \
+        + terms.cubic_field(m, prm.cubic_e1, prm.cubic_e2, prm.Kc1, prm.Kc2, Ms)
     if parts:
-        return Hd, Hex, Han, Hz
-    return Hd + Hex + Han + Hz
+        return Hd, Hex, Han, Hz, Hdmi
+    return Hd + Hex + Han + Hz + Hdmi
 
 
 def llg_rhs(m, H, prm: Params):
@@ -162,25 +187,41 @@ def rkf45_next_dt(dt, err, tol, dt_min, dt_max):
 
 def energies(m, prm: Params, demag):
     """(E_demag, E_exchange, E_anisotropy, E_Zeeman) in J."""
+    return energies_terms(m, prm, demag)[:4]
+
+
+def energies_terms(m, prm: Params, demag):
+    """(E_demag, E_exchange, E_anisotropy, E_Zeeman, E_DMI) in J; the
+    anisotropy energy sums the uniaxial (K1, K2) and cubic densities of
+    Table 1, exchange and DMI are -(mu0 Ms V/2) sum m.H of their fields."""
     Ms, Ku = prm.maps(m.shape[1:])
     V = prm.cell[0] * prm.cell[1] * prm.cell[2]
-    Hd, Hex, Han, Hz = effective_field(m, prm, demag, parts=True)
+    f = effective_field(m, prm, demag, parts=True)
+    Hd, Hex, Hz = f[0], f[1], f[3]
     e = np.asarray(prm.easy, dtype=np.float64).reshape(3, 1, 1, 1)
     Ed = -0.5 * MU0 * V * np.sum(Ms * dot(m, Hd))
     Eex = -0.5 * MU0 * V * np.sum(Ms * dot(m, Hex))
     Ean = V * np.sum(Ku * (1.0 - dot(m, e) ** 2))
     Ez = -MU0 * V * np.sum(Ms * dot(m, Hz))
-    return Ed, Eex, Ean, Ez
+    Edmi = 0.0
+    if prm.has_extra():
+        from . import terms
+        Ean += V * np.sum(terms.uniaxial_k2_energy_density(m, prm.easy, prm.K2)
+                          + terms.cubic_energy_density(m, prm.cubic_e1, prm.cubic_e2, prm.Kc1, prm.Kc2))
+        Edmi = -0.5 * MU0 * V * np.sum(Ms * dot(m, f[4]))
+    return Ed, Eex, Ean, Ez, Edmi
 
 
 # --------------------------------------------------------------------------
 # Discrete adjoint of one RK4 step (added by this build; the paper has none)
 # --------------------------------------------------------------------------
 def _field_vjp(m, gH, prm: Params, demag):
-    """Given gH = dL/dH, return (dL/dm, dL/dMs, dL/dKu) through H(m; Ms, Ku).
+    """Given gH = dL/dH, return (dL/dm, dL/dMs, dL/dKu) through H(m; Ms, Ku)
+    (the base terms: demag, exchange, uniaxial K1, applied field).
 
     The demagnetising operator M -> -N*M is self-adjoint (N_ij = N_ji and
     N(-r) = N(r)), so its transpose is the operator itself."""
+    assert not prm.has_extra(), "the adjoint covers the base field terms"
     Ms, Ku = prm.maps(m.shape[1:])
     e = np.asarray(prm.easy, dtype=np.float64).reshape(3, 1, 1, 1)
     DgH = demag(gH)
