@@ -463,6 +463,23 @@ def main():
                    "algorithmic_GBps": (algo[k] / (per_launch_ms[k] * 1e-3) / 1e9) if (k in algo and per_launch_ms[k]) else None}
                for k in kern if kern[k][1]}
 
+    # ---- further field terms on the same film (interfacial DMI, cubic and
+    #      second-order uniaxial anisotropy): one-cell-per-thread stage kernel
+    terms_line = None
+    if not args.no_extra:
+        from paper_2008_02478_gb300.binding import FieldTerms
+        plan.set_field_terms(FieldTerms(K2=1e4, Kc1=4.5e4, cubic_e1=(1.0, 0.0, 0.0), cubic_e2=(0.0, 1.0, 0.0),
+                                        dmi="interfacial", D=3e-3))
+        mt = m.clone()
+        plan.llg_run_graph(mt, prm, DT, 3)
+        t_terms = max_over_ranks(time_graph(torch, plan, mt, prm, args.steps))
+        terms_line = {"terms": "interfacial DMI D=3e-3 J/m^2 (non-homogeneous Neumann boundaries), cubic "
+                               "Kc1=4.5e4 J/m^3, uniaxial K2=1e4 J/m^3",
+                      "cell_steps_per_s": world * ncell * args.steps / t_terms,
+                      "ms_per_step": 1e3 * t_terms / args.steps}
+        plan.set_field_terms(None)
+        del mt
+
     # ---- e2e: pinned host state, H2D + one RK4 step + D2H per step ----------
     m_host = torch.tensor(m0, dtype=torch.float32).pin_memory()
     plan.llg_run_host(m_host, prm, DT, 1)
@@ -548,7 +565,7 @@ def main():
                                  "spectrum 208.4 MB per evaluation)",
                            "padded": plan.padded(), "yz_schedule": plan.schedule()},
                 "demag_evals_per_s": demag_rate, "ms_per_step_without_graph": 1e3 * t_calls / args.steps,
-                "fp64": fp64, "workloads": extra, "mixed_precision": mixed, "roofline": roofline,
+                "fp64": fp64, "workloads": dict(extra, field_terms_512x512x32=terms_line) if terms_line else extra, "mixed_precision": mixed, "roofline": roofline,
                 "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -226,6 +226,52 @@ int boris_llg_run_host(boris_plan p, float* m_host, const boris_llg_params* prm,
  */
 int boris_energy(boris_plan p, const float* m, const boris_llg_params* prm, double out[4]);
 
+/* Further effective-field terms (Table 1 of Appendix A; Eq. 5).  All zero
+ * (or dmi = BORIS_DMI_NONE) leaves the base field of boris_llg_step. */
+#define BORIS_DMI_NONE 0
+#define BORIS_DMI_BULK 1        /* H = -(2D/(mu0 Ms)) curl m, dm/dn = (D/2A) n x m       */
+#define BORIS_DMI_INTERFACIAL 2 /* H = (2D/(mu0 Ms))((div m) z - grad m_z),
+                                   dm/dn = (D/2A)(z x n) x m                          */
+typedef struct {
+    double K2;          /* uniaxial second order (J/m^3), axis boris_llg_params.easy:
+                           eps = K2 (1 - (m.e)^2)^2                                 */
+    double Kc1, Kc2;    /* cubic anisotropy (J/m^3): eps = Kc1 (a^2 b^2 + a^2 c^2 + b^2 c^2)
+                           + Kc2 a^2 b^2 c^2, a = m.e1, b = m.e2, c = m.e3            */
+    double cubic_e1[3]; /* cubic axes e1, e2 (normalised by the call; they must be
+                           orthogonal), e3 = e1 x e2                                  */
+    double cubic_e2[3];
+    int dmi;            /* BORIS_DMI_*; single-mesh plans only, needs A > 0          */
+    double D;           /* DMI constant (J/m^2)                                       */
+    double J1, J2;      /* surface exchange (J/m^2) of Eq. 5 between consecutive layers of
+                           a multi-mesh plan: the top cell plane of layer l and the bottom
+                           plane of layer l + 1 where they overlap in-plane, Delta = the
+                           receiving cell's z size; layers must be listed bottom-up     */
+} boris_field_terms;
+
+/*
+ * boris_set_field_terms - set (t != NULL) or clear (t == NULL) the further
+ *   field terms of plan p; they enter every later boris_llg_step,
+ *   boris_llg_run_graph (a changed set re-captures the graph) and
+ *   boris_energy_terms.  DMI changes the exchange boundary to the
+ *   non-homogeneous Neumann condition of Table 1: a neighbour outside the
+ *   mesh is the ghost m + h dm/dn, which both the exchange Laplacian and the
+ *   central DMI differences use.  Stepping with these terms uses the
+ *   one-cell-per-thread stage kernel; boris_llg_step_backward covers the base
+ *   terms only and fails with BORIS_ERR_INVALID_ARG while terms are set.
+ *   Errors: INVALID_ARG (non-finite values, non-orthogonal cubic axes, unknown
+ *   dmi kind, DMI on a multi-mesh plan, J1/J2 on a single-mesh plan, layers
+ *   not bottom-up).
+ */
+int boris_set_field_terms(boris_plan p, const boris_field_terms* t);
+
+/*
+ * boris_energy_terms - as boris_energy, with out = {E_demag, E_exchange,
+ *   E_anisotropy (uniaxial K1, K2 and cubic), E_Zeeman, E_DMI} in J; the
+ *   exchange and DMI energies are -(mu0 Ms V/2) sum m.H of their fields.
+ *   Single-mesh FP32 plans.  Synchronises the stream.
+ */
+int boris_energy_terms(boris_plan p, const float* m, const boris_llg_params* prm, double out[5]);
+
 /* Device status word: BORIS_OK or the first latched device-side error,
  * which is then cleared.  Synchronises the stream. */
 int boris_sync_status(boris_plan p);

@@ -29,6 +29,7 @@ GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
 EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_info", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_apply_noalloc",
            "boris_demag_adjoint",
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
+           "boris_energy_terms", "boris_set_field_terms",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
 KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other", "y_fwd", "z_conv", "y_inv", "x_c2r_rk4"]
@@ -46,6 +47,38 @@ class LLGParamsC(ctypes.Structure):
                 ("Ku", ctypes.c_double), ("easy", ctypes.c_double * 3), ("Hext", ctypes.c_double * 3),
                 ("method", ctypes.c_int), ("tol", ctypes.c_double), ("dt_min", ctypes.c_double),
                 ("dt_max", ctypes.c_double)]
+
+
+DMI_KINDS = {"none": 0, "bulk": 1, "interfacial": 2}
+
+
+class FieldTermsC(ctypes.Structure):
+    _fields_ = [("K2", ctypes.c_double), ("Kc1", ctypes.c_double), ("Kc2", ctypes.c_double),
+                ("cubic_e1", ctypes.c_double * 3), ("cubic_e2", ctypes.c_double * 3), ("dmi", ctypes.c_int),
+                ("D", ctypes.c_double), ("J1", ctypes.c_double), ("J2", ctypes.c_double)]
+
+
+@dataclass
+class FieldTerms:
+    """Further Table 1 terms and the Eq. 5 surface exchange (boris_field_terms)."""
+    K2: float = 0.0
+    Kc1: float = 0.0
+    Kc2: float = 0.0
+    cubic_e1: tuple = (1.0, 0.0, 0.0)
+    cubic_e2: tuple = (0.0, 1.0, 0.0)
+    dmi: str = "none"
+    D: float = 0.0
+    J1: float = 0.0
+    J2: float = 0.0
+
+    def c(self) -> FieldTermsC:
+        t = FieldTermsC()
+        t.K2, t.Kc1, t.Kc2 = self.K2, self.Kc1, self.Kc2
+        t.cubic_e1 = (ctypes.c_double * 3)(*self.cubic_e1)
+        t.cubic_e2 = (ctypes.c_double * 3)(*self.cubic_e2)
+        t.dmi = DMI_KINDS[self.dmi]
+        t.D, t.J1, t.J2 = self.D, self.J1, self.J2
+        return t
 
 
 _lib = None
@@ -74,6 +107,8 @@ def lib():
         L.boris_llg_run_host.argtypes = [vp, vp, P(LLGParamsC), d, i]
         L.boris_llg_run_graph.argtypes = [vp, vp, P(LLGParamsC), d, i]
         L.boris_energy.argtypes = [vp, vp, P(LLGParamsC), P(d)]
+        L.boris_energy_terms.argtypes = [vp, vp, P(LLGParamsC), P(d)]
+        L.boris_set_field_terms.argtypes = [vp, P(FieldTermsC)]
         L.boris_sync_status.argtypes = [vp]
         L.boris_last_error.restype = ctypes.c_char_p
         L.boris_plan_padded.argtypes = [vp, P(i)]
@@ -254,6 +289,21 @@ class Plan:
         c = self._params(prm)
         out = (ctypes.c_double * 4)()
         check(lib().boris_energy(self._h, _ptr(m, self.dtype, self.field_shape), ctypes.byref(c), out))
+        return tuple(out)
+
+    def set_field_terms(self, terms: "FieldTerms | None"):
+        """Set (or with None clear) the further field terms of the plan."""
+        if terms is None:
+            check(lib().boris_set_field_terms(self._h, None))
+        else:
+            c = terms.c()
+            check(lib().boris_set_field_terms(self._h, ctypes.byref(c)))
+
+    def energy_terms(self, m, prm: LLGParams):
+        """(E_demag, E_exchange, E_anisotropy, E_Zeeman, E_DMI) in J."""
+        c = self._params(prm)
+        out = (ctypes.c_double * 5)()
+        check(lib().boris_energy_terms(self._h, _ptr(m, self.dtype, self.field_shape), ctypes.byref(c), out))
         return tuple(out)
 
     def profile(self, on: bool):

@@ -34,6 +34,10 @@ struct boris_plan_s {
     YZSchedule yz;
     // FP32 RK4 stages fuse the inverse x transform with the stage (px = 1024)
     bool fuse_rk4 = false;
+    // further field terms (boris_set_field_terms) and a counter that keys the CUDA graph
+    boris_field_terms terms = {};
+    bool has_terms = false;
+    long long terms_version = 0;
     // device status word latched by bounded device-side waits (boris_sync_status)
     int* d_status = nullptr;
     int nsm = 0;
@@ -73,10 +77,12 @@ struct boris_plan_s {
     float* g_m = nullptr;
     boris_llg_params g_prm = {};
     double g_dt = 0.0;
+    long long g_terms_version = -1;
     long long g_launches = 0;  // kernel launches inside one captured step
     // multi-mesh plans (boris_multimesh_plan)
     bool ml = false;
     MLTable mlt;
+    double ml_zb[ML_MAX_LAYERS] = {};  // z of each layer's lower face (m)
     void* Kml = nullptr;    // unique inter-plane spectra [u][kx][ky'][6]
     int* d_pairs = nullptr; // [Z * Z]
     float* Mf = nullptr;    // frame fields [3][Z][NY][NX]
@@ -265,6 +271,28 @@ int check_params(boris_plan p, const boris_llg_params* prm, LLGArgs<T>* a, doubl
     a->alpha = (T)prm->alpha;
     a->dt = (T)dt;
     a->V = p->dx * p->dy * p->dz;
+    const boris_field_terms& t = p->terms;
+    a->extra = p->has_terms ? 1 : 0;
+    a->K2 = (T)t.K2;
+    a->Kc1 = (T)t.Kc1;
+    a->Kc2 = (T)t.Kc2;
+    const double e3[3] = {t.cubic_e1[1] * t.cubic_e2[2] - t.cubic_e1[2] * t.cubic_e2[1],
+                          t.cubic_e1[2] * t.cubic_e2[0] - t.cubic_e1[0] * t.cubic_e2[2],
+                          t.cubic_e1[0] * t.cubic_e2[1] - t.cubic_e1[1] * t.cubic_e2[0]};
+    for (int c = 0; c < 3; c++) {
+        a->c1[c] = (T)t.cubic_e1[c];
+        a->c2[c] = (T)t.cubic_e2[c];
+        a->c3[c] = (T)e3[c];
+    }
+    a->dmi = p->has_terms ? t.dmi : 0;
+    a->D = (T)(a->dmi ? t.D : 0.0);
+    if (a->dmi && !(prm->A > 0)) return fail(BORIS_ERR_INVALID_ARG, "DMI needs A > 0 (boundary slope D/2A)");
+    a->kD = (T)(a->dmi ? t.D / (2.0 * prm->A) : 0.0);
+    a->hx = (T)p->dx;
+    a->hy = (T)p->dy;
+    a->hz = (T)p->dz;
+    a->J1 = (T)t.J1;
+    a->J2 = (T)t.J2;
     return BORIS_OK;
 }
 
@@ -300,7 +328,7 @@ int rk4_step_t(boris_plan p, T* m, const LLGArgs<T>& a)
     T* out[4] = {sa, sb, sa, nullptr};
     for (int s = 0; s < 4; s++) {
         if constexpr (sizeof(T) == 4) {
-            if (p->fuse_rk4) {
+            if (p->fuse_rk4 && !a.extra) {
                 int rc = demag_to_spectrum_t<T>(p, in[s], ms_map, ms_scale);
                 if (rc) return rc;
                 CUDA_TRY(timed(p, 8, [&] {
@@ -400,6 +428,7 @@ int llg_backward_t(boris_plan p, const T* m_in, const boris_llg_params* prm, dou
         return fail(BORIS_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
     if (prm->method != BORIS_RK4) return fail(BORIS_ERR_INVALID_ARG, "the adjoint is of the RK4 step");
     if (p->ml) return fail(BORIS_ERR_INVALID_ARG, "the adjoint serves single-mesh plans");
+    if (p->has_terms) return fail(BORIS_ERR_INVALID_ARG, "the adjoint covers the base field terms; clear the further terms");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(BORIS_ERR_INVALID_ARG, "dt must be > 0");
     int rc = ensure_llg_workspace<T>(p, false);
     if (rc) return rc;
@@ -814,6 +843,7 @@ int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, cons
     p->stream = (cudaStream_t)cuda_stream;
     p->ml = true;
     p->mlt = t;
+    for (int l = 0; l < n_layers; l++) p->ml_zb[l] = origin[3 * l + 2];
     p->ml_unique = (int)h.ua.size();
     p->yz = YZSchedule{2, 2, 0, 0, 0};
     int rc;
@@ -928,7 +958,8 @@ int boris_llg_run_graph(boris_plan p, float* m, const boris_llg_params* prm, dou
     if (!aligned16(m)) return fail(BORIS_ERR_INVALID_ARG, "m must be 16-byte aligned");
     int rc = ensure_llg_workspace<float>(p, false);
     if (rc) return rc;
-    const bool same = p->gexec && p->g_m == m && p->g_dt == dt && std::memcmp(&p->g_prm, prm, sizeof(*prm)) == 0;
+    const bool same = p->gexec && p->g_m == m && p->g_dt == dt && p->g_terms_version == p->terms_version &&
+                      std::memcmp(&p->g_prm, prm, sizeof(*prm)) == 0;
     if (!same) {
         if (p->gexec) {
             cudaGraphExecDestroy(p->gexec);
@@ -974,6 +1005,7 @@ int boris_llg_run_graph(boris_plan p, float* m, const boris_llg_params* prm, dou
         p->g_m = m;
         p->g_dt = dt;
         p->g_prm = *prm;
+        p->g_terms_version = p->terms_version;
     }
     for (int i = 0; i < nsteps; i++) {
         CUDA_TRY(cudaGraphLaunch(p->gexec, p->stream));
@@ -1000,7 +1032,7 @@ int boris_llg_run_host(boris_plan p, float* m_host, const boris_llg_params* prm,
     return BORIS_OK;
 }
 
-int boris_energy(boris_plan p, const float* m, const boris_llg_params* prm, double out[4])
+static int energy_impl(boris_plan p, const float* m, const boris_llg_params* prm, double* out, int nout)
 {
     if (!p || !m || !prm || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
     if (p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan");
@@ -1009,12 +1041,69 @@ int boris_energy(boris_plan p, const float* m, const boris_llg_params* prm, doub
     if (rc) return rc;
     LLGArgs<float> a;
     if ((rc = check_params<float>(p, prm, &a, 0.0))) return rc;
-    if (!p->energy && (rc = dev_alloc(p, (void**)&p->energy, 4 * sizeof(double)))) return rc;
+    if (!p->energy && (rc = dev_alloc(p, (void**)&p->energy, 8 * sizeof(double)))) return rc;
     if ((rc = demag_apply_t<float>(p, m, (const float*)prm->Ms_map, (float)prm->Ms, (float*)p->Hd))) return rc;
-    CUDA_TRY(cudaMemsetAsync(p->energy, 0, 4 * sizeof(double), p->stream));
+    CUDA_TRY(cudaMemsetAsync(p->energy, 0, 5 * sizeof(double), p->stream));
     CUDA_TRY(timed(p, 4, [&] { return launch_energy<float>(a, m, (const float*)p->Hd, p->energy, p->stream); }));
-    CUDA_TRY(cudaMemcpyAsync(out, p->energy, 4 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    double tmp[5];
+    CUDA_TRY(cudaMemcpyAsync(tmp, p->energy, 5 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
     CUDA_TRY(cudaStreamSynchronize(p->stream));
+    for (int i = 0; i < nout; i++) out[i] = tmp[i];
+    return BORIS_OK;
+}
+
+int boris_energy(boris_plan p, const float* m, const boris_llg_params* prm, double out[4])
+{
+    return energy_impl(p, m, prm, out, 4);
+}
+
+int boris_energy_terms(boris_plan p, const float* m, const boris_llg_params* prm, double out[5])
+{
+    return energy_impl(p, m, prm, out, 5);
+}
+
+int boris_set_field_terms(boris_plan p, const boris_field_terms* t)
+{
+    if (!p) return fail(BORIS_ERR_INVALID_ARG, "NULL plan");
+    p->terms_version++;
+    if (!t) {
+        p->terms = boris_field_terms{};
+        p->has_terms = false;
+        return BORIS_OK;
+    }
+    boris_field_terms v = *t;
+    const double vals[] = {v.K2, v.Kc1, v.Kc2, v.D, v.J1, v.J2, v.cubic_e1[0], v.cubic_e1[1], v.cubic_e1[2],
+                           v.cubic_e2[0], v.cubic_e2[1], v.cubic_e2[2]};
+    for (double x : vals)
+        if (!std::isfinite(x)) return fail(BORIS_ERR_INVALID_ARG, "field terms must be finite");
+    if (v.dmi < BORIS_DMI_NONE || v.dmi > BORIS_DMI_INTERFACIAL) return fail(BORIS_ERR_INVALID_ARG, "unknown DMI kind");
+    if (v.dmi == BORIS_DMI_NONE) v.D = 0.0;
+    if (v.dmi != BORIS_DMI_NONE && p->ml) return fail(BORIS_ERR_INVALID_ARG, "DMI serves single-mesh plans");
+    if ((v.J1 != 0.0 || v.J2 != 0.0) && !p->ml)
+        return fail(BORIS_ERR_INVALID_ARG, "surface exchange couples the layers of a multi-mesh plan");
+    if (v.J1 != 0.0 || v.J2 != 0.0) {
+        for (int l = 0; l + 1 < p->mlt.nl; l++)
+            if (p->ml_zb[l + 1] < p->ml_zb[l] + p->mlt.nz[l] * (double)p->mlt.hz[l] * (1.0 - 1e-9))
+                return fail(BORIS_ERR_INVALID_ARG, "surface exchange needs the layers listed bottom-up");
+    }
+    if (v.Kc1 != 0.0 || v.Kc2 != 0.0) {
+        double n1 = 0, n2 = 0, d = 0;
+        for (int c = 0; c < 3; c++) {
+            n1 += v.cubic_e1[c] * v.cubic_e1[c];
+            n2 += v.cubic_e2[c] * v.cubic_e2[c];
+        }
+        if (!(n1 > 0) || !(n2 > 0)) return fail(BORIS_ERR_INVALID_ARG, "cubic axes must be nonzero");
+        for (int c = 0; c < 3; c++) {
+            v.cubic_e1[c] /= std::sqrt(n1);
+            v.cubic_e2[c] /= std::sqrt(n2);
+            d += v.cubic_e1[c] * v.cubic_e2[c];
+        }
+        if (std::fabs(d) > 1e-6) return fail(BORIS_ERR_INVALID_ARG, "cubic axes must be orthogonal");
+    }
+    p->terms = v;
+    p->has_terms = v.K2 != 0.0 || v.Kc1 != 0.0 || v.Kc2 != 0.0 || (v.dmi != BORIS_DMI_NONE && v.D != 0.0) ||
+                   v.J1 != 0.0 || v.J2 != 0.0;
+    if (!p->has_terms) p->terms = boris_field_terms{};
     return BORIS_OK;
 }
 

@@ -215,54 +215,46 @@ __global__ void __launch_bounds__(256) rkf45_stage_kernel(LLGArgs<T> a, int s, c
     }
 }
 
-// FP64 energies: E_demag, E_exchange, E_anisotropy, E_Zeeman.
+// FP64 energies: E_demag, E_exchange, E_anisotropy, E_Zeeman, E_DMI.
 template <typename T>
 __global__ void __launch_bounds__(256) energy_kernel(LLGArgs<T> a, const T* __restrict__ m, const T* __restrict__ Hd,
                                                      double* __restrict__ out)
 {
     const size_t n = a.ncell;
-    double e[4] = {0, 0, 0, 0};
+    double e[5] = {0, 0, 0, 0, 0};
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % a.nx);
         const int y = (int)((i / a.nx) % a.ny);
         const int z = (int)(i / ((size_t)a.nx * a.ny));
         const double mc[3] = {(double)m[i], (double)m[n + i], (double)m[2 * n + i]};
-        double lap[3] = {0, 0, 0};
-        auto nb = [&](size_t j, double w) {
-            lap[0] += w * ((double)m[j] - mc[0]);
-            lap[1] += w * ((double)m[n + j] - mc[1]);
-            lap[2] += w * ((double)m[2 * n + j] - mc[2]);
-        };
-        const size_t sy = a.nx, sz = (size_t)a.nx * a.ny;
-        if (x > 0) nb(i - 1, a.ihx2);
-        if (x < a.nx - 1) nb(i + 1, a.ihx2);
-        if (y > 0) nb(i - sy, a.ihy2);
-        if (y < a.ny - 1) nb(i + sy, a.ihy2);
-        if (z > 0) nb(i - sz, a.ihz2);
-        if (z < a.nz - 1) nb(i + sz, a.ihz2);
+        double lap[3], w[3];
+        // neighbours (or boundary ghosts) in FP64; without DMI the ghost is the cell itself
+        ext_exchange_dmi<double>(a, m, i, x, y, z, mc, lap, w);
         const double Ms = a.ms_map ? (double)a.ms_map[i] : (double)a.Ms;
         const double Ku = a.ku_map ? (double)a.ku_map[i] : (double)a.Ku;
         const double me = mc[0] * a.e[0] + mc[1] * a.e[1] + mc[2] * a.e[2];
-        double mHd = 0, mHz = 0, mlap = 0;
+        double mHd = 0, mHz = 0, mlap = 0, mw = 0;
         for (int c = 0; c < 3; c++) {
             mHd += mc[c] * (double)Hd[c * n + i];
             mHz += mc[c] * (double)a.Hext[c];
             mlap += mc[c] * lap[c];
+            mw += mc[c] * w[c];
         }
-        // -(mu0 Ms/2) m.Hex with Hex = (2A/(mu0 Ms)) lap m  ->  -A m.lap m
+        // -(mu0 Ms/2) m.Hex with Hex = (2A/(mu0 Ms)) lap m  ->  -A m.lap m; likewise -D m.w
         e[0] += -0.5 * MU0_D * Ms * mHd;
         e[1] += -(double)a.A * mlap;
-        e[2] += Ku * (1.0 - me * me);
+        e[2] += Ku * (1.0 - me * me) + (a.extra ? ext_local_energy<double>(a, mc) : 0.0);
         e[3] += -MU0_D * Ms * mHz;
+        e[4] += -(double)a.D * mw;
     }
-    __shared__ double red[4][8];
-    for (int c = 0; c < 4; c++) {
+    __shared__ double red[5][8];
+    for (int c = 0; c < 5; c++) {
         double v = e[c];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 5) {
         double v = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) v += red[threadIdx.x][w];
         atomicAdd(out + threadIdx.x, v * a.V);
@@ -311,6 +303,28 @@ __device__ __forceinline__ void ml_field_and_rhs(const LLGArgs<T>& a, const MLTa
     T H[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) H[c] = Hd[vi[c]] + cex * lap[c] + can * a.e[c] + a.Hext[c];
+    if (a.extra) {
+        ext_local_field<T>(a, m, Ms, H);
+        // surface exchange (Eq. 5): the top plane of layer l with the bottom
+        // plane of layer l + 1 where they overlap in-plane, and the reverse;
+        // Delta = this cell's z size
+        if (a.J1 != T(0) || a.J2 != T(0)) {
+            const T cs = inv / T(t.hz[l]);
+            auto couple = [&](int lj, int zj) {
+                const int xj = x + t.ox[l] - t.ox[lj], yj = y + t.oy[l] - t.oy[lj];
+                if (xj < 0 || xj >= t.nx[lj] || yj < 0 || yj >= t.ny[lj]) return;
+                const size_t nj = (size_t)t.nx[lj] * t.ny[lj] * t.nz[lj];
+                const size_t cj = ((size_t)zj * t.ny[lj] + yj) * t.nx[lj] + xj;
+                const T mj[3] = {ms[t.off[lj] + cj], ms[t.off[lj] + nj + cj], ms[t.off[lj] + 2 * nj + cj]};
+                const T d = m[0] * mj[0] + m[1] * mj[1] + m[2] * mj[2];
+                const T f = cs * (a.J1 + T(2) * a.J2 * d);
+#pragma unroll
+                for (int c = 0; c < 3; c++) H[c] += f * mj[c];
+            };
+            if (z == nz - 1 && l + 1 < t.nl) couple(l + 1, 0);
+            if (z == 0 && l > 0) couple(l - 1, t.nz[l - 1] - 1);
+        }
+    }
     const T mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
     const T mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2], m[0] * mxH[1] - m[1] * mxH[0]};
 #pragma unroll
@@ -372,7 +386,7 @@ cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* H
                              cudaStream_t st)
 {
     if constexpr (sizeof(T) == 4) {
-        if (a.nx % 4 == 0) {
+        if (a.nx % 4 == 0 && !a.extra) {
             rk4_stage_quad_kernel<<<grid_for(a.ncell / 4), 256, 0, st>>>(a, s, ms, Hd, m0, acc, mnext);
             return cudaGetLastError();
         }

@@ -26,7 +26,144 @@ __device__ __forceinline__ void rhs_local(const LLGArgs<T>& a, const T m[3], con
     for (int c = 0; c < 3; c++) k[c] = -a.gp * (mxH[c] + a.alpha * mmH[c]);
 }
 
-// m = ms[i]; k = -g' [m x H + alpha m x (m x H)], H = hd + exchange + anisotropy + Hext.
+// ---------------------------------------------------------------------------
+// Further Table 1 terms (boris_field_terms): second-order uniaxial and cubic
+// anisotropy (local), bulk or interfacial DMI with the non-homogeneous
+// Neumann boundary condition dm/dn = (D/2A) u x m (u = n for bulk, z x n for
+// interfacial DMI, n the outward normal).  A neighbour outside the mesh is
+// the ghost m + h (D/2A) u x m; the exchange Laplacian and the central DMI
+// differences both use it (without DMI the ghost is m: homogeneous Neumann).
+// TC is the arithmetic type (T for the stage kernels, double for energies).
+// ---------------------------------------------------------------------------
+template <typename TC, typename T>
+__device__ __forceinline__ void nb_or_ghost(const LLGArgs<T>& a, const T* __restrict__ ms, bool inside, size_t j,
+                                            int axis, int sgn, const TC m[3], TC out[3])
+{
+    const size_t n = a.ncell;
+    if (inside) {
+        out[0] = (TC)ms[j];
+        out[1] = (TC)ms[n + j];
+        out[2] = (TC)ms[2 * n + j];
+        return;
+    }
+    out[0] = m[0];
+    out[1] = m[1];
+    out[2] = m[2];
+    if (a.dmi == 0) return;
+    int ua;
+    TC us;
+    if (a.dmi == 1) {
+        ua = axis;
+        us = (TC)sgn;
+    } else {
+        if (axis == 2) return;  // z x z = 0
+        ua = axis == 0 ? 1 : 0;  // z x x = y, z x y = -x
+        us = axis == 0 ? (TC)sgn : (TC)(-sgn);
+    }
+    const TC h = axis == 0 ? (TC)a.hx : axis == 1 ? (TC)a.hy : (TC)a.hz;
+    const TC f = h * (TC)a.kD * us;
+    if (ua == 0) {  // x x m = (0, -mz, my)
+        out[1] -= f * m[2];
+        out[2] += f * m[1];
+    } else if (ua == 1) {  // y x m = (mz, 0, -mx)
+        out[0] += f * m[2];
+        out[2] -= f * m[0];
+    } else {  // z x m = (-my, mx, 0)
+        out[0] -= f * m[1];
+        out[1] += f * m[0];
+    }
+}
+
+// Exchange Laplacian sum_axes (m_+ + m_- - 2m)/h^2 and the DMI vector w with
+// H_dmi = (2D/(mu0 Ms)) w: bulk w = -curl m, interfacial w = (-dmz/dx,
+// -dmz/dy, dmx/dx + dmy/dy), derivatives (m_+ - m_-)/(2h).
+template <typename TC, typename T>
+__device__ __forceinline__ void ext_exchange_dmi(const LLGArgs<T>& a, const T* __restrict__ ms, size_t i, int x, int y,
+                                                 int z, const TC m[3], TC lap[3], TC w[3])
+{
+    const size_t sy = a.nx, sz = (size_t)a.nx * a.ny;
+    TC xm[3], xp[3], ym[3], yp[3], zm[3], zp[3];
+    nb_or_ghost<TC>(a, ms, x > 0, i - 1, 0, -1, m, xm);
+    nb_or_ghost<TC>(a, ms, x < a.nx - 1, i + 1, 0, 1, m, xp);
+    nb_or_ghost<TC>(a, ms, y > 0, i - sy, 1, -1, m, ym);
+    nb_or_ghost<TC>(a, ms, y < a.ny - 1, i + sy, 1, 1, m, yp);
+    nb_or_ghost<TC>(a, ms, z > 0, i - sz, 2, -1, m, zm);
+    nb_or_ghost<TC>(a, ms, z < a.nz - 1, i + sz, 2, 1, m, zp);
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        lap[c] = (xp[c] + xm[c] - TC(2) * m[c]) * (TC)a.ihx2 + (yp[c] + ym[c] - TC(2) * m[c]) * (TC)a.ihy2 +
+                 (zp[c] + zm[c] - TC(2) * m[c]) * (TC)a.ihz2;
+    w[0] = w[1] = w[2] = TC(0);
+    if (a.dmi == 0) return;
+    TC dx[3], dy[3], dz[3];
+    const TC ix = TC(0.5) / (TC)a.hx, iy = TC(0.5) / (TC)a.hy, iz = TC(0.5) / (TC)a.hz;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        dx[c] = (xp[c] - xm[c]) * ix;
+        dy[c] = (yp[c] - ym[c]) * iy;
+        dz[c] = (zp[c] - zm[c]) * iz;
+    }
+    if (a.dmi == 1) {
+        w[0] = -(dy[2] - dz[1]);
+        w[1] = -(dz[0] - dx[2]);
+        w[2] = -(dx[1] - dy[0]);
+    } else {
+        w[0] = -dx[2];
+        w[1] = -dy[2];
+        w[2] = dx[0] + dy[1];
+    }
+}
+
+// Local further terms added to H: (4 K2/(mu0 Ms)) (1 - (m.e)^2)(m.e) e and the
+// cubic field -(2 Kc1/(mu0 Ms)) [e1 a(b^2 + c^2) + ...] - (2 Kc2/(mu0 Ms)) [e1 a b^2 c^2 + ...].
+template <typename TC, typename T>
+__device__ __forceinline__ void ext_local_field(const LLGArgs<T>& a, const TC m[3], TC Ms, TC H[3])
+{
+    const TC inv = TC(1) / (TC(MU0_D) * Ms);
+    if (a.K2 != T(0)) {
+        const TC me = m[0] * (TC)a.e[0] + m[1] * (TC)a.e[1] + m[2] * (TC)a.e[2];
+        const TC f = TC(4) * (TC)a.K2 * inv * (TC(1) - me * me) * me;
+#pragma unroll
+        for (int c = 0; c < 3; c++) H[c] += f * (TC)a.e[c];
+    }
+    if (a.Kc1 != T(0) || a.Kc2 != T(0)) {
+        const TC p = m[0] * (TC)a.c1[0] + m[1] * (TC)a.c1[1] + m[2] * (TC)a.c1[2];
+        const TC q = m[0] * (TC)a.c2[0] + m[1] * (TC)a.c2[1] + m[2] * (TC)a.c2[2];
+        const TC r = m[0] * (TC)a.c3[0] + m[1] * (TC)a.c3[1] + m[2] * (TC)a.c3[2];
+        const TC f1 = -TC(2) * (TC)a.Kc1 * inv, f2 = -TC(2) * (TC)a.Kc2 * inv;
+        const TC g1 = f1 * p * (q * q + r * r) + f2 * p * q * q * r * r;
+        const TC g2 = f1 * q * (p * p + r * r) + f2 * p * p * q * r * r;
+        const TC g3 = f1 * r * (p * p + q * q) + f2 * p * p * q * q * r;
+#pragma unroll
+        for (int c = 0; c < 3; c++) H[c] += g1 * (TC)a.c1[c] + g2 * (TC)a.c2[c] + g3 * (TC)a.c3[c];
+    }
+}
+
+// Energy densities of the local further terms: K2 (1 - (m.e)^2)^2 and the cubic density.
+template <typename TC, typename T>
+__device__ __forceinline__ TC ext_local_energy(const LLGArgs<T>& a, const TC m[3])
+{
+    const TC me = m[0] * (TC)a.e[0] + m[1] * (TC)a.e[1] + m[2] * (TC)a.e[2];
+    const TC p = m[0] * (TC)a.c1[0] + m[1] * (TC)a.c1[1] + m[2] * (TC)a.c1[2];
+    const TC q = m[0] * (TC)a.c2[0] + m[1] * (TC)a.c2[1] + m[2] * (TC)a.c2[2];
+    const TC r = m[0] * (TC)a.c3[0] + m[1] * (TC)a.c3[1] + m[2] * (TC)a.c3[2];
+    const TC u = TC(1) - me * me;
+    return (TC)a.K2 * u * u + (TC)a.Kc1 * (p * p * q * q + p * p * r * r + q * q * r * r) +
+           (TC)a.Kc2 * p * p * q * q * r * r;
+}
+
+// k = -g' [m x H + alpha m x (m x H)] for a given total field H.
+template <typename T>
+__device__ __forceinline__ void rhs_from_field(const LLGArgs<T>& a, const T m[3], const T H[3], T k[3])
+{
+    const T mxH[3] = {m[1] * H[2] - m[2] * H[1], m[2] * H[0] - m[0] * H[2], m[0] * H[1] - m[1] * H[0]};
+    const T mmH[3] = {m[1] * mxH[2] - m[2] * mxH[1], m[2] * mxH[0] - m[0] * mxH[2], m[0] * mxH[1] - m[1] * mxH[0]};
+#pragma unroll
+    for (int c = 0; c < 3; c++) k[c] = -a.gp * (mxH[c] + a.alpha * mmH[c]);
+}
+
+// m = ms[i]; k = -g' [m x H + alpha m x (m x H)], H = hd + exchange + anisotropy + Hext
+// (+ the further terms when a.extra is set).
 template <typename T>
 __device__ __forceinline__ void cell_rhs(const LLGArgs<T>& a, const T* __restrict__ ms, const T hd[3], size_t i, int x,
                                          int y, int z, T m[3], T k[3])
@@ -35,6 +172,22 @@ __device__ __forceinline__ void cell_rhs(const LLGArgs<T>& a, const T* __restric
     m[0] = ms[i];
     m[1] = ms[n + i];
     m[2] = ms[2 * n + i];
+    if (a.extra) {
+        T lap[3], w[3];
+        ext_exchange_dmi<T>(a, ms, i, x, y, z, m, lap, w);
+        const T Ms = a.ms_map ? a.ms_map[i] : a.Ms;
+        const T Ku = a.ku_map ? a.ku_map[i] : a.Ku;
+        const T inv = T(1) / (T(MU0_D) * Ms);
+        const T cex = T(2) * a.A * inv, cd = T(2) * a.D * inv;
+        const T me = m[0] * a.e[0] + m[1] * a.e[1] + m[2] * a.e[2];
+        const T can = T(2) * Ku * inv * me;
+        T H[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) H[c] = hd[c] + cex * lap[c] + cd * w[c] + can * a.e[c] + a.Hext[c];
+        ext_local_field<T>(a, m, Ms, H);
+        rhs_from_field(a, m, H, k);
+        return;
+    }
     T lap[3] = {T(0), T(0), T(0)};
     auto nb = [&](size_t j, T w) {
         lap[0] += w * (ms[j] - m[0]);

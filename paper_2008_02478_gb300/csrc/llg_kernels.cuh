@@ -22,6 +22,16 @@ struct LLGArgs {
     T alpha;
     T dt;
     double V;  // cell volume (energies)
+    // further Table 1 terms (boris_field_terms); extra = 0 when none is set
+    int extra;
+    T K2;               // uniaxial second order along e
+    T Kc1, Kc2;         // cubic anisotropy
+    T c1[3], c2[3], c3[3];
+    int dmi;            // 0 none, 1 bulk, 2 interfacial
+    T D;                // DMI constant
+    T kD;               // D / (2A): boundary slope of the non-homogeneous Neumann condition
+    T hx, hy, hz;       // cell sizes (central differences, boundary ghosts)
+    T J1, J2;           // surface exchange between consecutive multi-mesh layers (Eq. 5)
 };
 
 template <typename T>
@@ -50,6 +60,7 @@ struct Geometry;
 bool x_c2r_rk4_ok(const Geometry& g, int max_smem);
 cudaError_t launch_x_c2r_rk4(const Geometry& g, const float2* X, const float2* tw, const LLGArgs<float>& a, int s,
                              const float* ms, float* m0, float* acc, float* mnext, cudaStream_t st);
+// out[0..4]: demag, exchange, anisotropy, Zeeman, DMI energies (J), accumulated
 template <typename T>
 cudaError_t launch_energy(const LLGArgs<T>& a, const T* m, const T* Hd, double* out, cudaStream_t st);
 

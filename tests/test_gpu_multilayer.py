@@ -132,3 +132,78 @@ def test_multilayer_rk4_matches_oracle():
     for _ in range(3):
         plan.llg_step(mg, prm, dt)
     assert rel_l2(mg.cpu().numpy(), ref) < 1e-5
+
+
+def test_multilayer_rk4_with_surface_exchange_and_cubic_matches_oracle():
+    """Eq. 5 surface exchange between consecutive layers (top plane of layer l
+    with the bottom plane of layer l + 1 where they overlap in-plane, Delta =
+    the receiving cell's z size) plus cubic anisotropy, against the oracle's
+    RK4 with the same field built from oracle/terms.py."""
+    torch = torch_cuda()
+    from oracle import terms as T
+    from paper_2008_02478_gb300.binding import FieldTerms, LLGParams
+    layers, hz, gaps = [(8, 6, 2), (6, 6, 1), (8, 4, 3)], [2e-9, 3e-9, 1e-9], [1e-9, 2e-9]
+    st, m, M, ms_cells = stack_case(layers, hz, gaps, 3e-9, seed=8)
+    plan = make_plan(st)
+    A, alpha, Hext, dt = 1.3e-11, 0.05, (1e4, 0.0, 2e4), 5e-14
+    J1, J2, Kc1 = -1.2e-3, 2e-4, 3e4
+    e1, e2 = (1.0, 0.0, 0.0), (0.0, 0.6, 0.8)
+    offs = np.cumsum([0] + [a * b * c for a, b, c in layers])
+
+    def views(v):
+        return [v[3 * offs[i]:3 * offs[i + 1]].reshape(3, l[2], l[1], l[0]) for i, l in enumerate(layers)]
+
+    def field(mm):
+        Mc = mm.copy()
+        for i in range(len(layers)):
+            Mc[3 * offs[i]:3 * offs[i + 1]] *= ms_cells[offs[i]]
+        H = ml.direct(st, Mc)
+        Hv, mv = views(H), views(mm)
+        for i, l in enumerate(layers):
+            Ms = ms_cells[offs[i]]
+            prm = llg.Params(cell=(st.hx, st.hy, hz[i]), Ms=Ms, A=A)
+            Hv[i] += llg.exchange_field(mv[i], prm, np.full(l[::-1], Ms))
+            Hv[i] += np.array(Hext).reshape(3, 1, 1, 1)
+            Hv[i] += T.cubic_field(mv[i], e1, e2, Kc1, 0.0, Ms)
+        for i in range(len(layers) - 1):
+            lo, up = mv[i], mv[i + 1]
+            for y in range(layers[i][1]):
+                for x in range(layers[i][0]):
+                    X, Y = x + st.ox[i] - st.ox[i + 1], y + st.oy[i] - st.oy[i + 1]
+                    if 0 <= X < layers[i + 1][0] and 0 <= Y < layers[i + 1][1]:
+                        a, b = lo[:, -1, y, x], up[:, 0, Y, X]
+                        Hv[i][:, -1, y, x] += T.surface_exchange_field(a, b, J1, J2, ms_cells[offs[i]], hz[i])
+                        Hv[i + 1][:, 0, Y, X] += T.surface_exchange_field(b, a, J1, J2, ms_cells[offs[i + 1]],
+                                                                          hz[i + 1])
+        return H
+
+    def rhs(mm):
+        H = field(mm)
+        out = np.zeros_like(mm)
+        for i in range(len(layers)):
+            sl = slice(3 * offs[i], 3 * offs[i + 1])
+            n = offs[i + 1] - offs[i]
+            out[sl] = llg.llg_rhs(mm[sl].reshape(3, n), H[sl].reshape(3, n),
+                                  llg.Params(cell=(1, 1, 1), alpha=alpha)).reshape(-1)
+        return out
+
+    ref = m.copy()
+    for _ in range(2):
+        k1 = rhs(ref)
+        k2 = rhs(ref + 0.5 * dt * k1)
+        k3 = rhs(ref + 0.5 * dt * k2)
+        k4 = rhs(ref + dt * k3)
+        v = ref + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+        for i in range(len(layers)):
+            sl = slice(3 * offs[i], 3 * offs[i + 1])
+            n = offs[i + 1] - offs[i]
+            vv = v[sl].reshape(3, n)
+            v[sl] = (vv / np.linalg.norm(vv, axis=0)).reshape(-1)
+        ref = v
+    mg = torch.tensor(m, dtype=torch.float32, device="cuda")
+    plan.set_field_terms(FieldTerms(J1=J1, J2=J2, Kc1=Kc1, cubic_e1=e1, cubic_e2=e2))
+    prm = LLGParams(A=A, alpha=alpha, Hext=Hext, Ms_map=torch.tensor(ms_cells, dtype=torch.float32, device="cuda"))
+    for _ in range(2):
+        plan.llg_step(mg, prm, dt)
+    assert np.abs(ref - m).max() > 1e-3
+    assert rel_l2(mg.cpu().numpy() - m, ref - m) < 2e-4
