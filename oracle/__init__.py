@@ -6,6 +6,7 @@ of ``bench.py`` may use it.  It shares no code with the CUDA library.
 
 Paper: "Boris Computational Spintronics" (arXiv 2008.02478).
   * ``boris_oracle.c``  - Newell tensor (Table 1, Ref. [50]), far-field form,
+    its sum over periodic images (multiple-images method, Section 4),
     direct-sum demag (Table 1) and convolution-theorem demag with 2x zero
     padding (Section 7), with its own mixed-radix FFT.
   * ``llg.py``          - effective field (Eq. 1 and Table 1), LLG right-hand
@@ -63,6 +64,7 @@ def lib():
             L.orc_newell_exact.argtypes = [d, d, d, d, d, d, vp]
             L.orc_newell_asymptotic.argtypes = [d, d, d, d, d, d, vp]
             L.orc_tensor_table.argtypes = [i, i, i, d, d, d, d, vp]
+            L.orc_tensor_table_pbc.argtypes = [i, i, i, d, d, d, d, i, i, i, vp]
             L.orc_demag_direct.argtypes = [i, i, i, vp, vp, vp]
             L.orc_demag_direct_at.argtypes = [i, i, i, vp, vp, i, vp, vp]
             L.orc_fft1d.argtypes = [vp, i, i]
@@ -119,6 +121,16 @@ def tensor_table(nx, ny, nz, dx, dy, dz, rs: float = RS_DEFAULT) -> np.ndarray:
     """Tensor on the displacement octant, shape [6][nz][ny][nx]."""
     out = np.zeros((6, nz, ny, nx))
     lib().orc_tensor_table(nx, ny, nz, float(dx), float(dy), float(dz), float(rs), _p(out))
+    return out
+
+
+def tensor_table_pbc(nx, ny, nz, dx, dy, dz, images, rs: float = RS_DEFAULT) -> np.ndarray:
+    """Tensor summed over the periodic images (multiple-images method; images =
+    (kx, ky, kz) images on each side along x, y, z, 0 for a non-periodic axis),
+    shape [6][nz][ny][nx]."""
+    out = np.zeros((6, nz, ny, nx))
+    kx, ky, kz = (int(v) for v in images)
+    lib().orc_tensor_table_pbc(nx, ny, nz, float(dx), float(dy), float(dz), float(rs), kx, ky, kz, _p(out))
     return out
 
 

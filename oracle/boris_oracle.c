@@ -171,6 +171,40 @@ void orc_tensor_table(int nx, int ny, int nz, double dx, double dy, double dz, d
             }
 }
 
+/* Periodic boundary conditions by multiple images (Section 4, extending
+ * Eq. 4): the field at a cell of the computational mesh includes the
+ * sources in the images of the mesh displaced by whole periods
+ * (a nx dx, b ny dy, c nz dz), |a| <= kx, |b| <= ky, |c| <= kz.  For a
+ * displacement d between two mesh cells the kernel is therefore the sum of
+ * the cell tensor over the images, N(d + (a Lx, b Ly, c Lz)); the table keeps
+ * the octant form because the image set is symmetric. */
+void orc_tensor_table_pbc(int nx, int ny, int nz, double dx, double dy, double dz, double rs, int kx, int ky, int kz,
+                          double* out)
+{
+    size_t n = (size_t)nx * ny * nz;
+    double hmax = fmax(dx, fmax(dy, dz));
+    double Lx = nx * dx, Ly = ny * dy, Lz = nz * dz;
+#pragma omp parallel for collapse(2) schedule(dynamic)
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                double acc[6] = {0, 0, 0, 0, 0, 0};
+                for (int c = -kz; c <= kz; c++)
+                    for (int b = -ky; b <= ky; b++)
+                        for (int a = -kx; a <= kx; a++) {
+                            double X = i * dx + a * Lx, Y = j * dy + b * Ly, Z = k * dz + c * Lz, v[6];
+                            double r = sqrt(X * X + Y * Y + Z * Z);
+                            if (r <= rs * hmax)
+                                orc_newell_exact(X, Y, Z, dx, dy, dz, v);
+                            else
+                                orc_newell_asymptotic(X, Y, Z, dx, dy, dz, v);
+                            for (int q = 0; q < 6; q++) acc[q] += v[q];
+                        }
+                size_t idx = ((size_t)k * ny + j) * nx + i;
+                for (int q = 0; q < 6; q++) out[q * n + idx] = acc[q];
+            }
+}
+
 /* Tensor entry for a signed displacement (i,j,k) from the octant table:
  * diagonal components are even in every axis; N_xy is odd in x and y, N_xz odd
  * in x and z, N_yz odd in y and z. */

@@ -54,6 +54,9 @@ class Params:
     cubic_e2: tuple = (0.0, 1.0, 0.0)
     dmi: str = "none"
     D: float = 0.0
+    # periodic axes (x, y, z): exchange and DMI neighbours wrap around; the
+    # demagnetising kernel of such a mesh sums the periodic images
+    pbc: tuple = (False, False, False)
 
     def has_extra(self):
         return self.K2 != 0.0 or self.Kc1 != 0.0 or self.Kc2 != 0.0 or (self.dmi != "none" and self.D != 0.0)
@@ -75,12 +78,16 @@ def dot(a, b):
     return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
 
 
-def laplacian(m, cell):
-    """sum over axes and existing neighbours j of (m_j - m_i)/h^2 (Neumann)."""
+def laplacian(m, cell, pbc=(False, False, False)):
+    """sum over axes and existing neighbours j of (m_j - m_i)/h^2 (Neumann);
+    along a periodic axis (pbc[axis]) the neighbours wrap around the mesh."""
     out = np.zeros_like(m)
     # axis order in the array: 1 = z, 2 = y, 3 = x
-    for ax, h in ((3, cell[0]), (2, cell[1]), (1, cell[2])):
+    for ax, h, per in ((3, cell[0], pbc[0]), (2, cell[1], pbc[1]), (1, cell[2], pbc[2])):
         n = m.shape[ax]
+        if per:
+            out += (np.roll(m, 1, axis=ax) + np.roll(m, -1, axis=ax) - 2.0 * m) / (h * h)
+            continue
         if n == 1:
             continue
         d = np.diff(m, axis=ax) / (h * h)  # m[i+1] - m[i]
@@ -95,7 +102,7 @@ def laplacian(m, cell):
 
 def exchange_field(m, prm: Params, Ms):
     c = 2.0 * prm.A / (MU0 * Ms)
-    return c[None] * laplacian(m, prm.cell)
+    return c[None] * laplacian(m, prm.cell, prm.pbc)
 
 
 def anisotropy_field(m, prm: Params, Ms, Ku):
@@ -120,8 +127,8 @@ def effective_field(m, prm: Params, demag, parts: bool = False):
             return Hd, Hex, Han, Hz
         return Hd + Hex + Han + Hz
     from . import terms
-    Hex = terms.exchange_field(m, prm.cell, prm.A, Ms, prm.D, prm.dmi)
-    Hdmi = terms.dmi_field(m, prm.cell, prm.A, prm.D, prm.dmi, Ms)
+    Hex = terms.exchange_field(m, prm.cell, prm.A, Ms, prm.D, prm.dmi, prm.pbc)
+    Hdmi = terms.dmi_field(m, prm.cell, prm.A, prm.D, prm.dmi, Ms, prm.pbc)
     Han = Han + terms.uniaxial_k2_field(m, prm.easy, prm.K2, Ms) \
         + terms.cubic_field(m, prm.cubic_e1, prm.cubic_e2, prm.Kc1, prm.Kc2, Ms)
     if parts:

@@ -108,11 +108,12 @@ def _bc_vector(kind, n):
     return np.zeros(3)
 
 
-def padded(m, cell, A=0.0, D=0.0, kind="none"):
+def padded(m, cell, A=0.0, D=0.0, kind="none", pbc=(False, False, False)):
     """m with one ghost layer on each face (array axes 1 = z, 2 = y, 3 = x).
     Ghost = m_face + h (D/2A) u x m_face (u from the boundary condition);
-    with no DMI the ghost equals the face cell.  Edge and corner entries of
-    the padded array are never read."""
+    with no DMI the ghost equals the face cell; along a periodic axis it is
+    the cell on the opposite face (the neighbour across the period).  Edge
+    and corner entries of the padded array are never read."""
     nz, ny, nx = m.shape[1:]
     p = np.zeros((3, nz + 2, ny + 2, nx + 2))
     p[:, 1:-1, 1:-1, 1:-1] = m
@@ -120,11 +121,17 @@ def padded(m, cell, A=0.0, D=0.0, kind="none"):
     # (array axis, cell size, unit vector of the axis)
     axes = ((3, cell[0], np.array([1.0, 0, 0])), (2, cell[1], np.array([0, 1.0, 0])), (1, cell[2], np.array([0, 0, 1.0])))
     for ax, h, e in axes:
+        per = pbc[3 - ax]
         for side, sgn in ((0, -1.0), (-1, 1.0)):
             face = [slice(None), slice(1, -1), slice(1, -1), slice(1, -1)]
             ghost = list(face)
             face[ax] = slice(1, 2) if side == 0 else slice(-2, -1)
             ghost[ax] = slice(0, 1) if side == 0 else slice(-1, None)
+            if per:
+                far = list(face)
+                far[ax] = slice(-2, -1) if side == 0 else slice(1, 2)
+                p[tuple(ghost)] = p[tuple(far)]
+                continue
             mf = p[tuple(face)]
             u = _bc_vector(kind, sgn * e).reshape(3, 1, 1, 1)
             p[tuple(ghost)] = mf + h * k * _cross(np.broadcast_to(u, mf.shape), mf)
@@ -139,28 +146,28 @@ def _shift(p, ax, d):
     return p[tuple(s)]
 
 
-def exchange_field(m, cell, A, Ms, D=0.0, kind="none"):
+def exchange_field(m, cell, A, Ms, D=0.0, kind="none", pbc=(False, False, False)):
     """(2A/(mu0 Ms)) sum over axes (m_+ + m_- - 2m)/h^2 with boundary ghosts."""
-    p = padded(m, cell, A, D, kind)
+    p = padded(m, cell, A, D, kind, pbc)
     lap = np.zeros_like(m)
     for ax, h in ((3, cell[0]), (2, cell[1]), (1, cell[2])):
         lap += (_shift(p, ax, 1) + _shift(p, ax, -1) - 2.0 * m) / (h * h)
     return (2.0 * A / (MU0 * Ms))[None] * lap if np.ndim(Ms) else 2.0 * A / (MU0 * Ms) * lap
 
 
-def gradients(m, cell, A, D, kind):
+def gradients(m, cell, A, D, kind, pbc=(False, False, False)):
     """d m / d(x, y, z): central differences with boundary ghosts, [axis][comp]..."""
-    p = padded(m, cell, A, D, kind)
+    p = padded(m, cell, A, D, kind, pbc)
     out = []
     for ax, h in ((3, cell[0]), (2, cell[1]), (1, cell[2])):
         out.append((_shift(p, ax, 1) - _shift(p, ax, -1)) / (2.0 * h))
     return out  # out[a][c] = d m_c / d x_a
 
 
-def dmi_field(m, cell, A, D, kind, Ms):
+def dmi_field(m, cell, A, D, kind, Ms, pbc=(False, False, False)):
     if kind == "none" or D == 0.0:
         return np.zeros_like(m)
-    dx, dy, dz = gradients(m, cell, A, D, kind)
+    dx, dy, dz = gradients(m, cell, A, D, kind, pbc)
     c = 2.0 * D / (MU0 * Ms)
     if kind == "bulk":
         curl = np.stack([dy[2] - dz[1], dz[0] - dx[2], dx[1] - dy[0]])
