@@ -83,6 +83,24 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
                      void* cuda_stream, boris_plan* out);
 
 /*
+ * boris_demag_plan_pbc - as boris_demag_plan, with periodic boundary
+ *   conditions by the multiple-images method (Section 4, extending Eq. 4):
+ *   images[a] > 0 makes axis a (0 x, 1 y, 2 z) periodic with period n_a h_a,
+ *   and the field at a mesh cell then includes the sources in the images of
+ *   the mesh displaced by up to images[a] periods on each side.  For a
+ *   displacement d between two mesh cells the kernel becomes the image sum
+ *   sum_k N(d + k L) (|k_a| <= images[a]), built in FP64 on the device with
+ *   the same exact / asymptotic forms; the zero-padded transforms are
+ *   unchanged (the image sum is a linear convolution over one period).  The
+ *   LLG exchange (and DMI) stencil of such a plan wraps around the periodic
+ *   axes.  images[a] = 0 leaves axis a open.  The adjoint
+ *   (boris_llg_step_backward) serves non-periodic plans only.
+ *   Errors: as boris_demag_plan; INVALID_ARG for images NULL or outside 0..1000.
+ */
+int boris_demag_plan_pbc(int nx, int ny, int nz, double dx, double dy, double dz, const int images[3], unsigned flags,
+                         void* cuda_stream, boris_plan* out);
+
+/*
  * boris_multimesh_plan - prepare the multi-mesh demagnetising field of Eq. 4
  *   for a stack of n_layers (1..16) rectangular meshes:
  *     H(r'_kl) = -sum_i sum_{r_ij in V_i} N(r'_kl - r_ij, h_k, h_i) M(r_ij).

@@ -29,7 +29,7 @@ GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
 EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_info", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_apply_noalloc",
            "boris_demag_adjoint",
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
-           "boris_energy_terms", "boris_set_field_terms",
+           "boris_energy_terms", "boris_set_field_terms", "boris_demag_plan_pbc",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
 KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other", "y_fwd", "z_conv", "y_inv", "x_c2r_rk4"]
@@ -94,6 +94,7 @@ def lib():
         i, d, vp, u = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_uint
         P = ctypes.POINTER
         L.boris_demag_plan.argtypes = [i, i, i, d, d, d, u, vp, P(vp)]
+        L.boris_demag_plan_pbc.argtypes = [i, i, i, d, d, d, P(i), u, vp, P(vp)]
         L.boris_demag_apply.argtypes = [vp, vp, vp]
         L.boris_multimesh_plan.argtypes = [i, vp, vp, vp, u, vp, P(vp)]
         L.boris_plan_multimesh_info.argtypes = [vp, P(i)]
@@ -182,7 +183,10 @@ def _ptr(t, dtype, shape=None):
 class Plan:
     """A demag + LLG plan for an nx x ny x nz mesh of dx x dy x dz cells."""
 
-    def __init__(self, nx, ny, nz, dx, dy, dz, fp64: bool = False, stream=None, tc: str | None = None):
+    def __init__(self, nx, ny, nz, dx, dy, dz, fp64: bool = False, stream=None, tc: str | None = None,
+                 images=None):
+        """images: periodic images per axis (x, y, z), 0 for an open axis
+        (boris_demag_plan_pbc); None for no periodic axis."""
         import torch
         self.shape = (nx, ny, nz)
         self.cell = (dx, dy, dz)
@@ -195,8 +199,14 @@ class Plan:
         if tc is not None:
             flags |= {"fp16": FLAG_FP16_TC, "bf16": FLAG_BF16_TC}[tc]
         self.tc = tc
-        check(lib().boris_demag_plan(nx, ny, nz, dx, dy, dz, flags, ctypes.c_void_p(st.cuda_stream),
-                                     ctypes.byref(h)))
+        self.images = tuple(images) if images is not None else (0, 0, 0)
+        if images is not None:
+            im = (ctypes.c_int * 3)(*[int(v) for v in images])
+            check(lib().boris_demag_plan_pbc(nx, ny, nz, dx, dy, dz, im, flags, ctypes.c_void_p(st.cuda_stream),
+                                             ctypes.byref(h)))
+        else:
+            check(lib().boris_demag_plan(nx, ny, nz, dx, dy, dz, flags, ctypes.c_void_p(st.cuda_stream),
+                                         ctypes.byref(h)))
         self._h = h
 
     @property

@@ -142,11 +142,14 @@ cudaError_t yz_set_attributes(const YZSchedule& sc);
 // layout [kx][ky'][krow] with (kz', component) at kz' * 6 + component (octant,
 // FP32 or FP64), already scaled by
 // -1/(px py pz) so that the inverse transforms yield H = -N * M.
+// images (optional, per axis): periodic images on each side summed into the
+// tensor (multiple-images method); NULL or 0 for a non-periodic axis.
 cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, double dz, double rs,
-                                  void* K_out, bool k_is_f64, const double2* tw64, cudaStream_t st);
+                                  void* K_out, bool k_is_f64, const double2* tw64, cudaStream_t st,
+                                  const int* images = nullptr);
 // Exact/asymptotic tensor on the displacement octant, FP64 [6][nz][ny][nx] (for tests).
 cudaError_t newell_octant(int nx, int ny, int nz, double dx, double dy, double dz, double rs,
-                          double* T, cudaStream_t st);
+                          double* T, cudaStream_t st, const int* images = nullptr);
 
 // Twiddle table exp(-2 pi i e / n), e in [0, n), on the host in FP64.
 void host_twiddles(int n, double2* out);

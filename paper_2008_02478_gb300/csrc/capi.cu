@@ -37,6 +37,9 @@ struct boris_plan_s {
     // further field terms (boris_set_field_terms) and a counter that keys the CUDA graph
     boris_field_terms terms = {};
     bool has_terms = false;
+    // periodic axes (multiple-images kernel, wrapping stencil): bit 0 x, 1 y, 2 z
+    int pbc = 0;
+    int images[3] = {0, 0, 0};
     long long terms_version = 0;
     // device status word latched by bounded device-side waits (boris_sync_status)
     int* d_status = nullptr;
@@ -293,6 +296,7 @@ int check_params(boris_plan p, const boris_llg_params* prm, LLGArgs<T>* a, doubl
     a->hz = (T)p->dz;
     a->J1 = (T)t.J1;
     a->J2 = (T)t.J2;
+    a->pbc = p->pbc;
     return BORIS_OK;
 }
 
@@ -328,7 +332,7 @@ int rk4_step_t(boris_plan p, T* m, const LLGArgs<T>& a)
     T* out[4] = {sa, sb, sa, nullptr};
     for (int s = 0; s < 4; s++) {
         if constexpr (sizeof(T) == 4) {
-            if (p->fuse_rk4 && !a.extra) {
+            if (p->fuse_rk4 && !a.extra && !a.pbc) {
                 int rc = demag_to_spectrum_t<T>(p, in[s], ms_map, ms_scale);
                 if (rc) return rc;
                 CUDA_TRY(timed(p, 8, [&] {
@@ -429,6 +433,7 @@ int llg_backward_t(boris_plan p, const T* m_in, const boris_llg_params* prm, dou
     if (prm->method != BORIS_RK4) return fail(BORIS_ERR_INVALID_ARG, "the adjoint is of the RK4 step");
     if (p->ml) return fail(BORIS_ERR_INVALID_ARG, "the adjoint serves single-mesh plans");
     if (p->has_terms) return fail(BORIS_ERR_INVALID_ARG, "the adjoint covers the base field terms; clear the further terms");
+    if (p->pbc) return fail(BORIS_ERR_INVALID_ARG, "the adjoint serves non-periodic meshes");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(BORIS_ERR_INVALID_ARG, "dt must be > 0");
     int rc = ensure_llg_workspace<T>(p, false);
     if (rc) return rc;
@@ -531,8 +536,26 @@ extern "C" {
 
 const char* boris_last_error(void) { return g_last_error.c_str(); }
 
+static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, unsigned flags, void* cuda_stream,
+                       boris_plan* out, const int* images);
+
 int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, unsigned flags, void* cuda_stream,
                      boris_plan* out)
+{
+    return plan_create(nx, ny, nz, dx, dy, dz, flags, cuda_stream, out, nullptr);
+}
+
+int boris_demag_plan_pbc(int nx, int ny, int nz, double dx, double dy, double dz, const int images[3], unsigned flags,
+                         void* cuda_stream, boris_plan* out)
+{
+    if (!images) return fail(BORIS_ERR_INVALID_ARG, "images is NULL");
+    for (int a = 0; a < 3; a++)
+        if (images[a] < 0 || images[a] > 1000) return fail(BORIS_ERR_INVALID_ARG, "images per axis must be 0..1000");
+    return plan_create(nx, ny, nz, dx, dy, dz, flags, cuda_stream, out, images);
+}
+
+static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, unsigned flags, void* cuda_stream,
+                       boris_plan* out, const int* images)
 {
     if (!out) return fail(BORIS_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
@@ -573,6 +596,10 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     p->flags = flags;
     p->f64 = (flags & BORIS_FLAG_F64) != 0;
     p->tc = tc;
+    for (int a = 0; a < 3; a++) {
+        p->images[a] = images ? images[a] : 0;
+        if (p->images[a] > 0) p->pbc |= 1 << a;
+    }
     p->stream = (cudaStream_t)cuda_stream;
     int rc = BORIS_OK;
     auto bail = [&](int code) {
@@ -682,7 +709,7 @@ int boris_demag_plan(int nx, int ny, int nz, double dx, double dy, double dz, un
     const size_t esz = p->f64 ? sizeof(double) : sizeof(float);
     if ((rc = dev_alloc(p, &p->K, kelems * esz))) return bail(rc);
     const double rs = 40.0;
-    ce = build_kernel_spectrum(g, dx, dy, dz, rs, p->K, p->f64, p->tw64, p->stream);
+    ce = build_kernel_spectrum(g, dx, dy, dz, rs, p->K, p->f64, p->tw64, p->stream, p->images);
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("kernel spectrum: ") + cudaGetErrorString(ce)));
     // spectral workspace
     const size_t xelems = (size_t)g.nkx * 3 * g.nz * g.ny;

@@ -91,18 +91,23 @@ __global__ void __launch_bounds__(256, 4) rk4_stage_quad_kernel(LLGArgs<float> a
             mv[c] = v;
             hv[c] = ld4(Hd + c * n + i);
             // x: inner differences of the quad plus the two outer neighbours
-            // (a missing neighbour equals the cell: zero difference)
-            const float xl = x0 > 0 ? b[-1] : v.x;
-            const float xr = x0 + 4 < a.nx ? b[4] : v.w;
+            // (a missing neighbour equals the cell: zero difference; along a
+            // periodic axis the neighbour wraps to the opposite face)
+            const float xl = x0 > 0 ? b[-1] : (a.pbc & 1) ? b[a.nx - 1] : v.x;
+            const float xr = x0 + 4 < a.nx ? b[4] : (a.pbc & 1) ? b[4 - a.nx] : v.w;
             float4 Lc;
             Lc.x = a.ihx2 * ((xl - v.x) + (v.y - v.x));
             Lc.y = a.ihx2 * ((v.x - v.y) + (v.z - v.y));
             Lc.z = a.ihx2 * ((v.y - v.z) + (v.w - v.z));
             Lc.w = a.ihx2 * ((v.z - v.w) + (xr - v.w));
             if (y > 0) lap_add(Lc, ld4(b - sy), v, a.ihy2);
+            else if (a.pbc & 2) lap_add(Lc, ld4(b + (a.ny - 1) * sy), v, a.ihy2);
             if (y < a.ny - 1) lap_add(Lc, ld4(b + sy), v, a.ihy2);
+            else if (a.pbc & 2) lap_add(Lc, ld4(b - (a.ny - 1) * sy), v, a.ihy2);
             if (z > 0) lap_add(Lc, ld4(b - sz), v, a.ihz2);
+            else if (a.pbc & 4) lap_add(Lc, ld4(b + (a.nz - 1) * sz), v, a.ihz2);
             if (z < a.nz - 1) lap_add(Lc, ld4(b + sz), v, a.ihz2);
+            else if (a.pbc & 4) lap_add(Lc, ld4(b - (a.nz - 1) * sz), v, a.ihz2);
             L[c] = Lc;
         }
         const float4 Msv = a.ms_map ? ld4(a.ms_map + i) : make_float4(a.Ms, a.Ms, a.Ms, a.Ms);

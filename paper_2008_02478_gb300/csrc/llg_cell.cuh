@@ -82,13 +82,15 @@ __device__ __forceinline__ void ext_exchange_dmi(const LLGArgs<T>& a, const T* _
                                                  int z, const TC m[3], TC lap[3], TC w[3])
 {
     const size_t sy = a.nx, sz = (size_t)a.nx * a.ny;
+    const bool px = a.pbc & 1, py = a.pbc & 2, pz = a.pbc & 4;
     TC xm[3], xp[3], ym[3], yp[3], zm[3], zp[3];
-    nb_or_ghost<TC>(a, ms, x > 0, i - 1, 0, -1, m, xm);
-    nb_or_ghost<TC>(a, ms, x < a.nx - 1, i + 1, 0, 1, m, xp);
-    nb_or_ghost<TC>(a, ms, y > 0, i - sy, 1, -1, m, ym);
-    nb_or_ghost<TC>(a, ms, y < a.ny - 1, i + sy, 1, 1, m, yp);
-    nb_or_ghost<TC>(a, ms, z > 0, i - sz, 2, -1, m, zm);
-    nb_or_ghost<TC>(a, ms, z < a.nz - 1, i + sz, 2, 1, m, zp);
+    // a periodic axis wraps to the cell on the opposite face
+    nb_or_ghost<TC>(a, ms, x > 0 || px, x > 0 ? i - 1 : i + (a.nx - 1), 0, -1, m, xm);
+    nb_or_ghost<TC>(a, ms, x < a.nx - 1 || px, x < a.nx - 1 ? i + 1 : i - (a.nx - 1), 0, 1, m, xp);
+    nb_or_ghost<TC>(a, ms, y > 0 || py, y > 0 ? i - sy : i + (a.ny - 1) * sy, 1, -1, m, ym);
+    nb_or_ghost<TC>(a, ms, y < a.ny - 1 || py, y < a.ny - 1 ? i + sy : i - (a.ny - 1) * sy, 1, 1, m, yp);
+    nb_or_ghost<TC>(a, ms, z > 0 || pz, z > 0 ? i - sz : i + (a.nz - 1) * sz, 2, -1, m, zm);
+    nb_or_ghost<TC>(a, ms, z < a.nz - 1 || pz, z < a.nz - 1 ? i + sz : i - (a.nz - 1) * sz, 2, 1, m, zp);
 #pragma unroll
     for (int c = 0; c < 3; c++)
         lap[c] = (xp[c] + xm[c] - TC(2) * m[c]) * (TC)a.ihx2 + (yp[c] + ym[c] - TC(2) * m[c]) * (TC)a.ihy2 +
@@ -195,12 +197,20 @@ __device__ __forceinline__ void cell_rhs(const LLGArgs<T>& a, const T* __restric
         lap[2] += w * (ms[2 * n + j] - m[2]);
     };
     const size_t sy = a.nx, sz = (size_t)a.nx * a.ny;
+    // a missing neighbour is the cell itself (homogeneous Neumann), or the
+    // cell on the opposite face along a periodic axis
     if (x > 0) nb(i - 1, a.ihx2);
+    else if (a.pbc & 1) nb(i + (a.nx - 1), a.ihx2);
     if (x < a.nx - 1) nb(i + 1, a.ihx2);
+    else if (a.pbc & 1) nb(i - (a.nx - 1), a.ihx2);
     if (y > 0) nb(i - sy, a.ihy2);
+    else if (a.pbc & 2) nb(i + (a.ny - 1) * sy, a.ihy2);
     if (y < a.ny - 1) nb(i + sy, a.ihy2);
+    else if (a.pbc & 2) nb(i - (a.ny - 1) * sy, a.ihy2);
     if (z > 0) nb(i - sz, a.ihz2);
+    else if (a.pbc & 4) nb(i + (a.nz - 1) * sz, a.ihz2);
     if (z < a.nz - 1) nb(i + sz, a.ihz2);
+    else if (a.pbc & 4) nb(i - (a.nz - 1) * sz, a.ihz2);
     const T Ms = a.ms_map ? a.ms_map[i] : a.Ms;
     const T Ku = a.ku_map ? a.ku_map[i] : a.Ku;
     rhs_local(a, m, lap, hd, Ms, Ku, k);

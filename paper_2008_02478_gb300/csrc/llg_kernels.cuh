@@ -32,6 +32,7 @@ struct LLGArgs {
     T kD;               // D / (2A): boundary slope of the non-homogeneous Neumann condition
     T hx, hy, hz;       // cell sizes (central differences, boundary ghosts)
     T J1, J2;           // surface exchange between consecutive multi-mesh layers (Eq. 5)
+    int pbc;            // periodic axes (bit 0 x, 1 y, 2 z): stencil neighbours wrap around
 };
 
 template <typename T>

@@ -2,7 +2,8 @@
 // using formulas in Ref. [50]": Newell, Williams and Dunlop).
 //
 // 1. newell_octant_kernel: the cell-averaged tensor for every displacement
-//    (i dx, j dy, k dz), 0 <= i < nx etc.  Within rs * max(dx,dy,dz) the exact
+//    (i dx, j dy, k dz), 0 <= i < nx etc. (summed over the periodic images of
+//    a periodic mesh).  Within rs * max(dx,dy,dz) the exact
 //    closed form: N_xx = (1/(4 pi V)) sum over the 27 shifts of prod_axis w(e)
 //    f(...), w(0) = 2, w(+-1) = -1, with Newell's f (xx, yy, zz by permuting
 //    the arguments) and g (xy, xz, yz).  Beyond it the box-averaged dipole
@@ -78,20 +79,32 @@ __device__ void newell_far_dev(double X, double Y, double Z, double dx, double d
     }
 }
 
-__global__ void newell_octant_kernel(int nx, int ny, int nz, double dx, double dy, double dz, double rs,
-                                     double* __restrict__ T)
+// Cell-averaged tensor at displacement (i dx, j dy, k dz), summed over the
+// periodic images (i dx + a nx dx, j dy + b ny dy, k dz + c nz dz) with
+// |a| <= kx, |b| <= ky, |c| <= kz (multiple-images method, Section 4; no
+// images: kx = ky = kz = 0).  The image set is symmetric, so the sum keeps
+// the parities of the octant form.
+__global__ void newell_octant_kernel(int nx, int ny, int nz, double dx, double dy, double dz, double rs, int kx,
+                                     int ky, int kz, double* __restrict__ T)
 {
     const size_t n = (size_t)nx * ny * nz;
     const double hmax = fmax(dx, fmax(dy, dz));
+    const double Lx = nx * dx, Ly = ny * dy, Lz = nz * dz;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(idx % nx);
         const int j = (int)((idx / nx) % ny);
         const int k = (int)(idx / ((size_t)nx * ny));
-        const double X = i * dx, Y = j * dy, Z = k * dz;
-        double v[6];
-        if (sqrt(X * X + Y * Y + Z * Z) <= rs * hmax) newell_exact_dev(X, Y, Z, dx, dy, dz, v);
-        else newell_far_dev(X, Y, Z, dx, dy, dz, v);
-        for (int c = 0; c < 6; c++) T[c * n + idx] = v[c];
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int c = -kz; c <= kz; c++)
+            for (int b = -ky; b <= ky; b++)
+                for (int a = -kx; a <= kx; a++) {
+                    const double X = i * dx + a * Lx, Y = j * dy + b * Ly, Z = k * dz + c * Lz;
+                    double v[6];
+                    if (sqrt(X * X + Y * Y + Z * Z) <= rs * hmax) newell_exact_dev(X, Y, Z, dx, dy, dz, v);
+                    else newell_far_dev(X, Y, Z, dx, dy, dz, v);
+                    for (int q = 0; q < 6; q++) acc[q] += v[q];
+                }
+        for (int q = 0; q < 6; q++) T[q * n + idx] = acc[q];
     }
 }
 
@@ -212,12 +225,13 @@ void host_twiddles(int n, double2* out)
 }
 
 cudaError_t newell_octant(int nx, int ny, int nz, double dx, double dy, double dz, double rs, double* T,
-                          cudaStream_t st)
+                          cudaStream_t st, const int* images)
 {
     const size_t n = (size_t)nx * ny * nz;
     int blocks = (int)((n + 255) / 256);
     if (blocks > 152 * 64) blocks = 152 * 64;
-    newell_octant_kernel<<<blocks, 256, 0, st>>>(nx, ny, nz, dx, dy, dz, rs, T);
+    const int kx = images ? images[0] : 0, ky = images ? images[1] : 0, kz = images ? images[2] : 0;
+    newell_octant_kernel<<<blocks, 256, 0, st>>>(nx, ny, nz, dx, dy, dz, rs, kx, ky, kz, T);
     return cudaGetLastError();
 }
 
@@ -247,7 +261,7 @@ static cudaError_t run_axis(const void* in, bool in_real, double2* out, int axis
 }
 
 cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, double dz, double rs, void* K_out,
-                                  bool k_is_f64, const double2* tw64, cudaStream_t st)
+                                  bool k_is_f64, const double2* tw64, cudaStream_t st, const int* images)
 {
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     double* T = nullptr;
@@ -258,7 +272,7 @@ cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, doubl
     const size_t b_elems = 6 * (size_t)g.nkx * g.kyh * g.nz;
     const size_t c_elems = 6 * (size_t)g.nkx * g.kyh * g.kzh;
     do {
-        if ((e = newell_octant(g.nx, g.ny, g.nz, dx, dy, dz, rs, T, st)) != cudaSuccess) break;
+        if ((e = newell_octant(g.nx, g.ny, g.nz, dx, dy, dz, rs, T, st, images)) != cudaSuccess) break;
         if ((e = cudaMallocAsync((void**)&A, a_elems * sizeof(double2), st)) != cudaSuccess) break;
         if ((e = run_axis(T, true, A, 0, g.nx, g.ny, g.nz, g.nx, g.px, tw64, g.lglmax, st)) != cudaSuccess) break;
         cudaFreeAsync(T, st);
