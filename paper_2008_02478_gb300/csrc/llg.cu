@@ -71,6 +71,9 @@ __device__ __forceinline__ void lap_add(float4& L, const float4& u, const float4
     L.w += w * (u.w - v.w);
 }
 
+// WRAP: some axis is periodic (neighbours wrap around the mesh); the open-mesh
+// instantiation keeps the conditional loads.
+template <bool WRAP>
 __global__ void __launch_bounds__(256, 4) rk4_stage_quad_kernel(LLGArgs<float> a, int s, const float* __restrict__ ms,
                                                              const float* __restrict__ Hd, float* __restrict__ m0,
                                                              float* __restrict__ acc, float* __restrict__ mnext)
@@ -83,6 +86,11 @@ __global__ void __launch_bounds__(256, 4) rk4_stage_quad_kernel(LLGArgs<float> a
         const int x0 = (int)(q - row * nxq) * 4;
         const int y = (int)(row % a.ny), z = (int)(row / a.ny);
         const size_t i = q * 4;
+        const bool wy = WRAP && (a.pbc & 2), wz = WRAP && (a.pbc & 4);
+        const ptrdiff_t oym = y > 0 ? -(ptrdiff_t)sy : wy ? (ptrdiff_t)((a.ny - 1) * sy) : 0;
+        const ptrdiff_t oyp = y < a.ny - 1 ? (ptrdiff_t)sy : wy ? -(ptrdiff_t)((a.ny - 1) * sy) : 0;
+        const ptrdiff_t ozm = z > 0 ? -(ptrdiff_t)sz : wz ? (ptrdiff_t)((a.nz - 1) * sz) : 0;
+        const ptrdiff_t ozp = z < a.nz - 1 ? (ptrdiff_t)sz : wz ? -(ptrdiff_t)((a.nz - 1) * sz) : 0;
         float4 mv[3], L[3], hv[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {
@@ -93,21 +101,27 @@ __global__ void __launch_bounds__(256, 4) rk4_stage_quad_kernel(LLGArgs<float> a
             // x: inner differences of the quad plus the two outer neighbours
             // (a missing neighbour equals the cell: zero difference; along a
             // periodic axis the neighbour wraps to the opposite face)
-            const float xl = x0 > 0 ? b[-1] : (a.pbc & 1) ? b[a.nx - 1] : v.x;
-            const float xr = x0 + 4 < a.nx ? b[4] : (a.pbc & 1) ? b[4 - a.nx] : v.w;
+            const bool wx = WRAP && (a.pbc & 1);
+            const float xl = x0 > 0 ? b[-1] : wx ? b[a.nx - 1] : v.x;
+            const float xr = x0 + 4 < a.nx ? b[4] : wx ? b[4 - a.nx] : v.w;
             float4 Lc;
             Lc.x = a.ihx2 * ((xl - v.x) + (v.y - v.x));
             Lc.y = a.ihx2 * ((v.x - v.y) + (v.z - v.y));
             Lc.z = a.ihx2 * ((v.y - v.z) + (v.w - v.z));
             Lc.w = a.ihx2 * ((v.z - v.w) + (xr - v.w));
-            if (y > 0) lap_add(Lc, ld4(b - sy), v, a.ihy2);
-            else if (a.pbc & 2) lap_add(Lc, ld4(b + (a.ny - 1) * sy), v, a.ihy2);
-            if (y < a.ny - 1) lap_add(Lc, ld4(b + sy), v, a.ihy2);
-            else if (a.pbc & 2) lap_add(Lc, ld4(b - (a.ny - 1) * sy), v, a.ihy2);
-            if (z > 0) lap_add(Lc, ld4(b - sz), v, a.ihz2);
-            else if (a.pbc & 4) lap_add(Lc, ld4(b + (a.nz - 1) * sz), v, a.ihz2);
-            if (z < a.nz - 1) lap_add(Lc, ld4(b + sz), v, a.ihz2);
-            else if (a.pbc & 4) lap_add(Lc, ld4(b - (a.nz - 1) * sz), v, a.ihz2);
+            if (WRAP) {
+                // y and z neighbours as offsets: a missing one is the cell itself
+                // (offset 0, zero difference), so all four loads issue unconditionally
+                lap_add(Lc, ld4(b + oym), v, a.ihy2);
+                lap_add(Lc, ld4(b + oyp), v, a.ihy2);
+                lap_add(Lc, ld4(b + ozm), v, a.ihz2);
+                lap_add(Lc, ld4(b + ozp), v, a.ihz2);
+            } else {
+                if (y > 0) lap_add(Lc, ld4(b - sy), v, a.ihy2);
+                if (y < a.ny - 1) lap_add(Lc, ld4(b + sy), v, a.ihy2);
+                if (z > 0) lap_add(Lc, ld4(b - sz), v, a.ihz2);
+                if (z < a.nz - 1) lap_add(Lc, ld4(b + sz), v, a.ihz2);
+            }
             L[c] = Lc;
         }
         const float4 Msv = a.ms_map ? ld4(a.ms_map + i) : make_float4(a.Ms, a.Ms, a.Ms, a.Ms);
@@ -392,7 +406,8 @@ cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* H
 {
     if constexpr (sizeof(T) == 4) {
         if (a.nx % 4 == 0 && !a.extra) {
-            rk4_stage_quad_kernel<<<grid_for(a.ncell / 4), 256, 0, st>>>(a, s, ms, Hd, m0, acc, mnext);
+            if (a.pbc) rk4_stage_quad_kernel<true><<<grid_for(a.ncell / 4), 256, 0, st>>>(a, s, ms, Hd, m0, acc, mnext);
+            else rk4_stage_quad_kernel<false><<<grid_for(a.ncell / 4), 256, 0, st>>>(a, s, ms, Hd, m0, acc, mnext);
             return cudaGetLastError();
         }
     }
