@@ -13,6 +13,8 @@ Paper: "Boris Computational Spintronics" (arXiv 2008.02478).
     side, RK4 / RKF45 steps (Section 2), energies, and the discrete adjoint of
     an RK4 step.
   * ``multilayer.py``   - the multi-mesh convolution sum (Eq. 4).
+  * ``thermal.py``      - the stochastic thermal field (Philox4x32-10 counter
+    generator, Box-Muller normals, Brown's fluctuation magnitude).
   * ``terms.py``        - further Table 1 field terms (second-order uniaxial
     and cubic anisotropy, bulk and interfacial DMI with their boundary
     conditions) and the surface exchange of Eq. 5.
