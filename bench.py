@@ -497,6 +497,13 @@ def main():
                                "Kc1=4.5e4 J/m^3, uniaxial K2=1e4 J/m^3",
                       "cell_steps_per_s": world * ncell * args.steps / t_terms,
                       "ms_per_step": 1e3 * t_terms / args.steps}
+        # stochastic thermal field at 300 K (Philox normals regenerated in each stage)
+        plan.set_field_terms(FieldTerms(temperature=300.0, seed=7))
+        mt = m.clone()
+        plan.llg_run_graph(mt, prm, DT, 3)
+        t_th = max_over_ranks(time_graph(torch, plan, mt, prm, args.steps))
+        terms_line["thermal_300K"] = {"cell_steps_per_s": world * ncell * args.steps / t_th,
+                                      "ms_per_step": 1e3 * t_th / args.steps}
         plan.set_field_terms(None)
         del mt
 

@@ -264,6 +264,13 @@ typedef struct {
                            a multi-mesh plan: the top cell plane of layer l and the bottom
                            plane of layer l + 1 where they overlap in-plane, Delta = the
                            receiving cell's z size; layers must be listed bottom-up     */
+    double temperature; /* thermal field (K; 0 = off), single-mesh plans, RK4 only:
+                           Brown's field in H_eff, each component of cell i at step s
+                           sigma g with sigma = sqrt(2 alpha kB T / (gamma mu0 Ms V dt)),
+                           g normal from the counter-based generator Philox4x32-10
+                           (counter (i, s mod 2^32, s div 2^32, 0), key = seed,
+                           Box-Muller), held through the step's four stages          */
+    unsigned long long seed;
 } boris_field_terms;
 
 /*
@@ -281,6 +288,14 @@ typedef struct {
  *   not bottom-up).
  */
 int boris_set_field_terms(boris_plan p, const boris_field_terms* t);
+
+/*
+ * boris_thermal_set_step - set the step counter s of the thermal field (it
+ *   starts at 0 and each RK4 step of boris_llg_step / boris_llg_run_graph
+ *   advances it by one on the device, so graph replays draw new fields).
+ *   Asynchronous on the plan's stream.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+int boris_thermal_set_step(boris_plan p, unsigned long long step);
 
 /*
  * boris_energy_terms - as boris_energy, with out = {E_demag, E_exchange,

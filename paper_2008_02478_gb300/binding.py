@@ -30,6 +30,7 @@ EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_inf
            "boris_demag_adjoint",
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
            "boris_energy_terms", "boris_set_field_terms", "boris_demag_plan_pbc",
+           "boris_thermal_set_step",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
 KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other", "y_fwd", "z_conv", "y_inv", "x_c2r_rk4"]
@@ -55,7 +56,8 @@ DMI_KINDS = {"none": 0, "bulk": 1, "interfacial": 2}
 class FieldTermsC(ctypes.Structure):
     _fields_ = [("K2", ctypes.c_double), ("Kc1", ctypes.c_double), ("Kc2", ctypes.c_double),
                 ("cubic_e1", ctypes.c_double * 3), ("cubic_e2", ctypes.c_double * 3), ("dmi", ctypes.c_int),
-                ("D", ctypes.c_double), ("J1", ctypes.c_double), ("J2", ctypes.c_double)]
+                ("D", ctypes.c_double), ("J1", ctypes.c_double), ("J2", ctypes.c_double),
+                ("temperature", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
 
 
 @dataclass
@@ -70,6 +72,8 @@ class FieldTerms:
     D: float = 0.0
     J1: float = 0.0
     J2: float = 0.0
+    temperature: float = 0.0
+    seed: int = 0
 
     def c(self) -> FieldTermsC:
         t = FieldTermsC()
@@ -78,6 +82,7 @@ class FieldTerms:
         t.cubic_e2 = (ctypes.c_double * 3)(*self.cubic_e2)
         t.dmi = DMI_KINDS[self.dmi]
         t.D, t.J1, t.J2 = self.D, self.J1, self.J2
+        t.temperature, t.seed = self.temperature, self.seed
         return t
 
 
@@ -110,6 +115,7 @@ def lib():
         L.boris_energy.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_energy_terms.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_set_field_terms.argtypes = [vp, P(FieldTermsC)]
+        L.boris_thermal_set_step.argtypes = [vp, ctypes.c_ulonglong]
         L.boris_sync_status.argtypes = [vp]
         L.boris_last_error.restype = ctypes.c_char_p
         L.boris_plan_padded.argtypes = [vp, P(i)]
@@ -308,6 +314,9 @@ class Plan:
         else:
             c = terms.c()
             check(lib().boris_set_field_terms(self._h, ctypes.byref(c)))
+
+    def thermal_set_step(self, step: int):
+        check(lib().boris_thermal_set_step(self._h, int(step)))
 
     def energy_terms(self, m, prm: LLGParams):
         """(E_demag, E_exchange, E_anisotropy, E_Zeeman, E_DMI) in J."""

@@ -40,6 +40,8 @@ struct boris_plan_s {
     // periodic axes (multiple-images kernel, wrapping stencil): bit 0 x, 1 y, 2 z
     int pbc = 0;
     int images[3] = {0, 0, 0};
+    // thermal field step counter (device), allocated with the first thermal terms
+    unsigned long long* d_step = nullptr;
     long long terms_version = 0;
     // device status word latched by bounded device-side waits (boris_sync_status)
     int* d_status = nullptr;
@@ -297,6 +299,15 @@ int check_params(boris_plan p, const boris_llg_params* prm, LLGArgs<T>* a, doubl
     a->J1 = (T)t.J1;
     a->J2 = (T)t.J2;
     a->pbc = p->pbc;
+    const double kB = 1.380649e-23;
+    a->th_s0 = (T)((p->has_terms && t.temperature > 0 && dt > 0)
+                       ? std::sqrt(2.0 * prm->alpha * kB * t.temperature / (prm->gamma * MU0_D * a->V * dt))
+                       : 0.0);
+    a->seed_lo = (unsigned int)(t.seed & 0xffffffffull);
+    a->seed_hi = (unsigned int)(t.seed >> 32);
+    a->step = p->d_step;
+    if (a->th_s0 > 0 && !p->d_step) return fail(BORIS_ERR_INVALID_ARG, "thermal step counter missing");
+    if (a->th_s0 > 0) a->extra = 1;
     return BORIS_OK;
 }
 
@@ -354,6 +365,7 @@ int rk4_step_t(boris_plan p, T* m, const LLGArgs<T>& a)
         }
         CUDA_TRY(timed(p, 3, [&] { return launch_rk4_stage<T>(a, s, in[s], Hd, m, acc, out[s], p->stream); }));
     }
+    if (a.th_s0 > T(0)) CUDA_TRY(timed(p, 4, [&] { return launch_thermal_advance(p->d_step, p->stream); }));
     return BORIS_OK;
 }
 
@@ -415,6 +427,8 @@ int llg_step_t(boris_plan p, T* m, const boris_llg_params* prm, double* dt)
     }
     if (prm->method == BORIS_RKF45) {
         if (p->ml) return fail(BORIS_ERR_INVALID_ARG, "multi-mesh plans step with RK4");
+        if (p->has_terms && p->terms.temperature > 0)
+            return fail(BORIS_ERR_INVALID_ARG, "the thermal field steps with RK4 (fixed dt)");
         LLGArgs<T> a;
         if ((rc = check_params<T>(p, prm, &a, 1.0))) return rc;
         return rkf45_step_t<T>(p, m, prm, dt);
@@ -1089,6 +1103,17 @@ int boris_energy_terms(boris_plan p, const float* m, const boris_llg_params* prm
     return energy_impl(p, m, prm, out, 5);
 }
 
+int boris_thermal_set_step(boris_plan p, unsigned long long step)
+{
+    if (!p) return fail(BORIS_ERR_INVALID_ARG, "NULL plan");
+    if (!p->d_step) {
+        int rc = dev_alloc(p, (void**)&p->d_step, sizeof(unsigned long long));
+        if (rc) return rc;
+    }
+    CUDA_TRY(launch_thermal_set(p->d_step, step, p->stream));
+    return BORIS_OK;
+}
+
 int boris_set_field_terms(boris_plan p, const boris_field_terms* t)
 {
     if (!p) return fail(BORIS_ERR_INVALID_ARG, "NULL plan");
@@ -1100,12 +1125,21 @@ int boris_set_field_terms(boris_plan p, const boris_field_terms* t)
     }
     boris_field_terms v = *t;
     const double vals[] = {v.K2, v.Kc1, v.Kc2, v.D, v.J1, v.J2, v.cubic_e1[0], v.cubic_e1[1], v.cubic_e1[2],
-                           v.cubic_e2[0], v.cubic_e2[1], v.cubic_e2[2]};
+                           v.cubic_e2[0], v.cubic_e2[1], v.cubic_e2[2], v.temperature};
     for (double x : vals)
         if (!std::isfinite(x)) return fail(BORIS_ERR_INVALID_ARG, "field terms must be finite");
     if (v.dmi < BORIS_DMI_NONE || v.dmi > BORIS_DMI_INTERFACIAL) return fail(BORIS_ERR_INVALID_ARG, "unknown DMI kind");
     if (v.dmi == BORIS_DMI_NONE) v.D = 0.0;
     if (v.dmi != BORIS_DMI_NONE && p->ml) return fail(BORIS_ERR_INVALID_ARG, "DMI serves single-mesh plans");
+    if (v.temperature < 0) return fail(BORIS_ERR_INVALID_ARG, "temperature must be >= 0");
+    if (v.temperature > 0 && p->ml) return fail(BORIS_ERR_INVALID_ARG, "the thermal field serves single-mesh plans");
+    if (v.temperature > 0 && (size_t)ncell(p) >= ((size_t)1 << 32))
+        return fail(BORIS_ERR_UNSUPPORTED_SIZE, "thermal field: more than 2^32 cells");
+    if (v.temperature > 0 && !p->d_step) {
+        int rc = dev_alloc(p, (void**)&p->d_step, sizeof(unsigned long long));
+        if (rc) return rc;
+        CUDA_TRY(cudaMemsetAsync(p->d_step, 0, sizeof(unsigned long long), p->stream));
+    }
     if ((v.J1 != 0.0 || v.J2 != 0.0) && !p->ml)
         return fail(BORIS_ERR_INVALID_ARG, "surface exchange couples the layers of a multi-mesh plan");
     if (v.J1 != 0.0 || v.J2 != 0.0) {
@@ -1129,7 +1163,7 @@ int boris_set_field_terms(boris_plan p, const boris_field_terms* t)
     }
     p->terms = v;
     p->has_terms = v.K2 != 0.0 || v.Kc1 != 0.0 || v.Kc2 != 0.0 || (v.dmi != BORIS_DMI_NONE && v.D != 0.0) ||
-                   v.J1 != 0.0 || v.J2 != 0.0;
+                   v.J1 != 0.0 || v.J2 != 0.0 || v.temperature > 0.0;
     if (!p->has_terms) p->terms = boris_field_terms{};
     return BORIS_OK;
 }
@@ -1205,7 +1239,7 @@ void boris_plan_destroy(boris_plan p)
 {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
-    void* ptrs[] = {p->Kml, p->d_pairs, p->Mf, p->Hf, p->K, p->K2, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
+    void* ptrs[] = {p->Kml, p->d_pairs, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
                     p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);

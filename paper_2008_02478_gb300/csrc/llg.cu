@@ -393,6 +393,21 @@ cudaError_t launch_rk4_stage_ml(const LLGArgs<float>& a, const MLTable& t, int s
     return cudaGetLastError();
 }
 
+__global__ void thermal_advance_kernel(unsigned long long* step) { *step += 1ull; }
+__global__ void thermal_set_kernel(unsigned long long* step, unsigned long long v) { *step = v; }
+
+cudaError_t launch_thermal_advance(unsigned long long* step, cudaStream_t st)
+{
+    thermal_advance_kernel<<<1, 1, 0, st>>>(step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thermal_set(unsigned long long* step, unsigned long long v, cudaStream_t st)
+{
+    thermal_set_kernel<<<1, 1, 0, st>>>(step, v);
+    return cudaGetLastError();
+}
+
 static int grid_for(size_t n)
 {
     size_t b = (n + 255) / 256;

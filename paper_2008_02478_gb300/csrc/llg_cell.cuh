@@ -154,6 +154,54 @@ __device__ __forceinline__ TC ext_local_energy(const LLGArgs<T>& a, const TC m[3
            (TC)a.Kc2 * p * p * q * q * r * r;
 }
 
+// ---------------------------------------------------------------------------
+// Thermal field: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) from its
+// published definition - ten rounds of (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^
+// k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)), the key bumped by the Weyl
+// constants between rounds - and Box-Muller normals from its four words.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(unsigned int c[4], unsigned int k0, unsigned int k1)
+{
+    constexpr unsigned int M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const unsigned int hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+        const unsigned int hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+        const unsigned int n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+}
+
+// three standard normals of cell i at the plan's current step
+template <typename T>
+__device__ __forceinline__ void thermal_normals(const LLGArgs<T>& a, size_t i, T g[3])
+{
+    const unsigned long long s = *a.step;
+    unsigned int c[4] = {(unsigned int)i, (unsigned int)s, (unsigned int)(s >> 32), 0u};
+    philox4x32_10(c, a.seed_lo, a.seed_hi);
+    T u[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) u[j] = ((T)c[j] + T(0.5)) * T(2.3283064365386963e-10);  // 2^-32
+    const T ra = sqrt(T(-2) * log(u[0])), rb = sqrt(T(-2) * log(u[2]));
+    T s1, c1, s3, c3;
+    if constexpr (sizeof(T) == 4) {
+        sincospif(2.f * u[1], &s1, &c1);
+        sincospif(2.f * u[3], &s3, &c3);
+    } else {
+        sincospi(2.0 * u[1], &s1, &c1);
+        sincospi(2.0 * u[3], &s3, &c3);
+    }
+    (void)s3;
+    g[0] = ra * c1;
+    g[1] = ra * s1;
+    g[2] = rb * c3;
+}
+
 // k = -g' [m x H + alpha m x (m x H)] for a given total field H.
 template <typename T>
 __device__ __forceinline__ void rhs_from_field(const LLGArgs<T>& a, const T m[3], const T H[3], T k[3])
@@ -187,6 +235,13 @@ __device__ __forceinline__ void cell_rhs(const LLGArgs<T>& a, const T* __restric
 #pragma unroll
         for (int c = 0; c < 3; c++) H[c] = hd[c] + cex * lap[c] + cd * w[c] + can * a.e[c] + a.Hext[c];
         ext_local_field<T>(a, m, Ms, H);
+        if (a.th_s0 > T(0)) {
+            T g[3];
+            thermal_normals(a, i, g);
+            const T sg = a.th_s0 / sqrt(Ms);
+#pragma unroll
+            for (int c = 0; c < 3; c++) H[c] += sg * g[c];
+        }
         rhs_from_field(a, m, H, k);
         return;
     }

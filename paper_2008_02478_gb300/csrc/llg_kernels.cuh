@@ -33,7 +33,14 @@ struct LLGArgs {
     T hx, hy, hz;       // cell sizes (central differences, boundary ghosts)
     T J1, J2;           // surface exchange between consecutive multi-mesh layers (Eq. 5)
     int pbc;            // periodic axes (bit 0 x, 1 y, 2 z): stencil neighbours wrap around
+    // thermal field: sigma_i = th_s0 / sqrt(Ms_i) (0: off); Philox key and step counter
+    T th_s0;
+    unsigned int seed_lo, seed_hi;
+    const unsigned long long* step;
 };
+// advances the thermal field's step counter by one (after an RK4 step) / sets it
+cudaError_t launch_thermal_advance(unsigned long long* step, cudaStream_t st);
+cudaError_t launch_thermal_set(unsigned long long* step, unsigned long long v, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, T* m0, T* acc, T* mnext,

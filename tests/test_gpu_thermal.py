@@ -1,0 +1,90 @@
+"""GPU parity of the stochastic thermal field against the oracle: the same
+counter-based generator (Philox4x32-10, Box-Muller) on both sides gives the
+same field for the same (seed, step, cell), so an RK4 step at T > 0 is
+compared like a deterministic one (increment within 2e-4 relative L2 in
+FP32, 1e-9 in FP64); the step counter advances once per RK4 step, also
+inside CUDA-graph replays."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import llg
+from oracle import thermal as th
+from paper_2008_02478_gb300 import inputs
+from tests.gpu_util import rel_l2, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+N, CELL = (20, 12, 3), (2e-9, 2e-9, 2e-9)
+T, SEED, ALPHA = 300.0, 0x1234567890ABCDEF, 0.1
+
+
+def setup(fp64=False):
+    from paper_2008_02478_gb300.binding import FieldTerms, LLGParams, Plan
+    plan = Plan(*N, *CELL, fp64=fp64)
+    plan.set_field_terms(FieldTerms(temperature=T, seed=SEED))
+    prm = LLGParams(Ms=8e5, A=1.3e-11, alpha=ALPHA, Hext=(0.0, 0.0, 5e4))
+    prm_o = llg.Params(cell=CELL, Ms=8e5, A=1.3e-11, alpha=ALPHA, Hext=(0.0, 0.0, 5e4))
+    return plan, prm, prm_o
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_thermal_rk4_steps_match_oracle(fp64):
+    torch = torch_cuda()
+    m0 = inputs.random_unit(*N, seed=51)
+    m0 = m0 + 0.8 * np.roll(m0, 1, axis=3)
+    m0 = (m0 / np.linalg.norm(m0, axis=0)).astype(np.float32).astype(np.float64)
+    plan, prm, prm_o = setup(fp64)
+    demag = oracle.DemagPlan(*N, *CELL).apply
+    dt = 1e-14
+    plan.thermal_set_step(5)
+    m = torch.tensor(m0, dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+    ref = m0
+    for s in (5, 6):
+        prev = ref
+        ref = th.rk4_step_thermal(ref, dt, prm_o, demag, step=s, seed=SEED, T=T)
+        mprev = m.cpu().numpy().astype(np.float64)
+        plan.llg_step(m, prm, dt)
+        got = m.cpu().numpy().astype(np.float64)
+        assert np.abs(ref - prev).max() > 1e-3
+        assert rel_l2(got - mprev, ref - prev) < (1e-9 if fp64 else 2e-4)
+    # without the thermal field the same step is clearly different
+    det = llg.rk4_step(m0, dt, prm_o, demag)
+    first = th.rk4_step_thermal(m0, dt, prm_o, demag, step=5, seed=SEED, T=T)
+    assert rel_l2(det - m0, first - m0) > 0.1
+
+
+def test_thermal_graph_replay_advances_the_counter():
+    torch = torch_cuda()
+    m0 = inputs.random_unit(*N, seed=52)
+    plan, prm, _ = setup()
+    a = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    b = a.clone()
+    plan.thermal_set_step(100)
+    for _ in range(4):
+        plan.llg_step(a, prm, 1e-14)
+    plan.thermal_set_step(100)
+    plan.llg_run_graph(b, prm, 1e-14, 4)
+    torch.cuda.synchronize()
+    assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) < 1e-7
+    # a replay from a different counter draws different fields
+    c = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    plan.thermal_set_step(200)
+    plan.llg_run_graph(c, prm, 1e-14, 4)
+    torch.cuda.synchronize()
+    assert rel_l2(c.cpu().numpy(), a.cpu().numpy()) > 1e-3
+
+
+def test_thermal_argument_checks():
+    torch_cuda()
+    from paper_2008_02478_gb300.binding import RKF45, BorisError, FieldTerms, LLGParams, Plan
+    plan = Plan(*N, *CELL)
+    with pytest.raises(BorisError) as e:
+        plan.set_field_terms(FieldTerms(temperature=-1.0))
+    assert e.value.code == -1
+    plan.set_field_terms(FieldTerms(temperature=300.0))
+    import torch
+    m = torch.tensor(inputs.random_unit(*N, seed=1), dtype=torch.float32, device="cuda")
+    with pytest.raises(BorisError) as e:  # adaptive steps do not take the thermal field
+        plan.llg_step(m, LLGParams(method=RKF45), 1e-14)
+    assert e.value.code == -1
