@@ -13,6 +13,10 @@ Paper: "Boris Computational Spintronics" (arXiv 2008.02478).
     side, RK4 / RKF45 steps (Section 2), energies, and the discrete adjoint of
     an RK4 step.
   * ``multilayer.py``   - the multi-mesh convolution sum (Eq. 4).
+  * ``boris_oracle.c`` also holds the Oersted kernel (Table 1, its Ref. [63]
+    not in the paper): H = J x g with g = -(1/(4 pi V)) grad of the two-box
+    Coulomb integral, obtained as the antiderivative of Newell's N_kk along
+    axis k, and the direct-sum Oersted field.
   * ``thermal.py``      - the stochastic thermal field (Philox4x32-10 counter
     generator, Box-Muller normals, Brown's fluctuation magnitude).
   * ``terms.py``        - further Table 1 field terms (second-order uniaxial
@@ -67,6 +71,9 @@ def lib():
             L.orc_newell_asymptotic.argtypes = [d, d, d, d, d, d, vp]
             L.orc_tensor_table.argtypes = [i, i, i, d, d, d, d, vp]
             L.orc_tensor_table_pbc.argtypes = [i, i, i, d, d, d, d, i, i, i, vp]
+            L.orc_oersted_g.argtypes = [d, d, d, d, d, d, d, vp]
+            L.orc_oersted_table.argtypes = [i, i, i, d, d, d, d, vp]
+            L.orc_oersted_direct.argtypes = [i, i, i, vp, vp, vp]
             L.orc_demag_direct.argtypes = [i, i, i, vp, vp, vp]
             L.orc_demag_direct_at.argtypes = [i, i, i, vp, vp, i, vp, vp]
             L.orc_fft1d.argtypes = [vp, i, i]
@@ -134,6 +141,30 @@ def tensor_table_pbc(nx, ny, nz, dx, dy, dz, images, rs: float = RS_DEFAULT) -> 
     kx, ky, kz = (int(v) for v in images)
     lib().orc_tensor_table_pbc(nx, ny, nz, float(dx), float(dy), float(dz), float(rs), kx, ky, kz, _p(out))
     return out
+
+
+def oersted_g(X, Y, Z, dx, dy, dz, rs: float = RS_DEFAULT) -> np.ndarray:
+    """Cell-averaged Oersted vector g at displacement (X, Y, Z) (target - source):
+    the field of a uniform current density J in the source cell, averaged over
+    the target cell, is J x g."""
+    out = np.zeros(3)
+    lib().orc_oersted_g(float(X), float(Y), float(Z), float(dx), float(dy), float(dz), float(rs), _p(out))
+    return out
+
+
+def oersted_table(nx, ny, nz, dx, dy, dz, rs: float = RS_DEFAULT) -> np.ndarray:
+    out = np.zeros((3, nz, ny, nx))
+    lib().orc_oersted_table(nx, ny, nz, float(dx), float(dy), float(dz), float(rs), _p(out))
+    return out
+
+
+def oersted_direct(J: np.ndarray, G: np.ndarray) -> np.ndarray:
+    """H = sum_r J(r) x g(r0 - r) (A/m) for a current density J [3][nz][ny][nx] (A/m^2)."""
+    J = np.ascontiguousarray(J, dtype=np.float64)
+    _, nz, ny, nx = J.shape
+    H = np.zeros_like(J)
+    lib().orc_oersted_direct(nx, ny, nz, _p(np.ascontiguousarray(G)), _p(J), _p(H))
+    return H
 
 
 # --------------------------------------------------------------------------

@@ -205,6 +205,158 @@ void orc_tensor_table_pbc(int nx, int ny, int nz, double dx, double dy, double d
             }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Oersted kernel (Table 1: H(r0) = sum_r K(r - r0) J_C(r); the formulas of   */
+/* its Ref. [63] are not in the paper and are derived here)                  */
+/* ------------------------------------------------------------------------ */
+/* For a uniform current density J in a source cell, Biot-Savart averaged over
+ * a target cell at centre displacement D (target - source) gives
+ *   H = J x g(D),  g(D) = -(1/(4 pi V)) grad_D P(D),
+ *   P(D) = int_target int_source dr dr' / |r - r'|.
+ * The demagnetising tensor of the same two cells is N_ij = -(1/(4 pi V))
+ * d_i d_j P = d_i g_j, so g_k is an antiderivative of N_kk along axis k and
+ * g -> 0 far away:
+ *   g_k(D) = g_k(D + (t_e - D_k) e_k) - int_{D_k}^{t_e} N_kk(D + (t - D_k) e_k) dt,
+ * with the end point t_e in the far zone, where
+ *   g_k = -(V/4 pi) d_k [1/r + sum_m (h_m^2/12) d_m^2 (1/r)]
+ * (the gradient of the box-averaged potential whose Hessian is the far form
+ * of N).  The integral runs over intervals that end on multiples of h_k
+ * (where N has its kinks), 16-point Gauss-Legendre rules each. */
+static void gl16(double* xs, double* ws)
+{
+    /* nodes and weights on [-1, 1] by Newton iteration on P_16 */
+    const int n = 16;
+    for (int i = 0; i < n; i++) {
+        double x = cos(ORC_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            double dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; k++) {
+            double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        double dp = n * (x * p1 - p0) / (x * x - 1.0);
+        xs[i] = x;
+        ws[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+static void oersted_far(const double* x, const double* h, double V, double* g)
+{
+    double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2], r = sqrt(r2);
+    double r3 = r2 * r, r5 = r3 * r2, r7 = r5 * r2;
+    for (int k = 0; k < 3; k++) {
+        double s = -x[k] / r3;
+        for (int m = 0; m < 3; m++)
+            s += h[m] * h[m] / 12.0 *
+                 ((6.0 * x[m] * (m == k ? 1.0 : 0.0) - 2.0 * x[k]) / r5 - 5.0 * x[k] * (3.0 * x[m] * x[m] - r2) / r7);
+        g[k] = -V / (4.0 * ORC_PI) * s;
+    }
+}
+
+/* N_kk at a point, exact form */
+static double nkk_exact(int k, const double* x, const double* h)
+{
+    double v[6];
+    orc_newell_exact(x[0], x[1], x[2], h[0], h[1], h[2], v);
+    return v[k];
+}
+
+/* g(D) at an arbitrary displacement; rs: far zone beyond rs * max cell size */
+void orc_oersted_g(double X, double Y, double Z, double dx, double dy, double dz, double rs, double* g)
+{
+    double h[3] = {dx, dy, dz}, D[3] = {X, Y, Z};
+    double hmax = fmax(dx, fmax(dy, dz)), V = dx * dy * dz;
+    double r = sqrt(X * X + Y * Y + Z * Z);
+    if (r > rs * hmax) {
+        oersted_far(D, h, V, g);
+        return;
+    }
+    double xs[16], ws[16];
+    gl16(xs, ws);
+    for (int k = 0; k < 3; k++) {
+        /* integrate along +k from |D_k| (g_k is odd in D_k) */
+        double s = D[k] < 0 ? -1.0 : 1.0;
+        double p[3] = {D[0], D[1], D[2]};
+        p[k] = fabs(D[k]);
+        double t = p[k], acc = 0.0;
+        for (;;) {
+            double q[3] = {p[0], p[1], p[2]};
+            q[k] = t;
+            double rq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+            if (rq > rs * hmax) break;
+            /* intervals end on multiples of h_k, where N has its kinks */
+            double b = (floor(t / h[k] * (1.0 + 1e-14)) + 1.0) * h[k];
+            double a = t, half = 0.5 * (b - a), mid = 0.5 * (a + b);
+            for (int i = 0; i < 16; i++) {
+                q[k] = mid + half * xs[i];
+                acc += ws[i] * half * nkk_exact(k, q, h);
+            }
+            t = b;
+        }
+        double e[3] = {p[0], p[1], p[2]}, ge[3];
+        e[k] = t;
+        oersted_far(e, h, V, ge);
+        g[k] = s * (ge[k] - acc);
+    }
+}
+
+/* octant table [3][nz][ny][nx] of g at (i dx, j dy, k dz) */
+void orc_oersted_table(int nx, int ny, int nz, double dx, double dy, double dz, double rs, double* out)
+{
+    size_t n = (size_t)nx * ny * nz;
+#pragma omp parallel for collapse(2) schedule(dynamic)
+    for (int k = 0; k < nz; k++)
+        for (int j = 0; j < ny; j++)
+            for (int i = 0; i < nx; i++) {
+                double g[3];
+                orc_oersted_g(i * dx, j * dy, k * dz, dx, dy, dz, rs, g);
+                size_t idx = ((size_t)k * ny + j) * nx + i;
+                for (int c = 0; c < 3; c++) out[c * n + idx] = g[c];
+            }
+}
+
+/* Direct sum H(r0) = sum_r J(r) x g(r0 - r): g_k is odd in its own axis and
+ * even in the other two, so a signed displacement reads the octant table
+ * with the sign of its k-th coordinate. */
+void orc_oersted_direct(int nx, int ny, int nz, const double* G, const double* J, double* H)
+{
+    size_t n = (size_t)nx * ny * nz;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long t = 0; t < (long)n; t++) {
+        int ti = (int)(t % nx), tj = (int)((t / nx) % ny), tk = (int)(t / ((size_t)nx * ny));
+        double hx = 0, hy = 0, hz = 0;
+        for (int k = 0; k < nz; k++)
+            for (int j = 0; j < ny; j++)
+                for (int i = 0; i < nx; i++) {
+                    int di = ti - i, dj = tj - j, dk = tk - k;
+                    size_t idx = ((size_t)abs(dk) * ny + abs(dj)) * nx + abs(di);
+                    double gx = (di < 0 ? -1.0 : 1.0) * G[idx];
+                    double gy = (dj < 0 ? -1.0 : 1.0) * G[n + idx];
+                    double gz = (dk < 0 ? -1.0 : 1.0) * G[2 * n + idx];
+                    size_t s = ((size_t)k * ny + j) * nx + i;
+                    double jx = J[s], jy = J[n + s], jz = J[2 * n + s];
+                    hx += jy * gz - jz * gy;
+                    hy += jz * gx - jx * gz;
+                    hz += jx * gy - jy * gx;
+                }
+        H[t] = hx;
+        H[n + t] = hy;
+        H[2 * n + t] = hz;
+    }
+}
+
 /* Tensor entry for a signed displacement (i,j,k) from the octant table:
  * diagonal components are even in every axis; N_xy is odd in x and y, N_xz odd
  * in x and z, N_yz odd in y and z. */
