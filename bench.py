@@ -310,6 +310,27 @@ def other_workloads(torch, args, world, max_over_ranks):
                                   "cell_steps_per_s": world * nc * K / t, "ms_per_step": 1e3 * t / K}
     pp.close()
     del mpb
+    # Oersted field of a current density on the 512x512x32 film
+    from paper_2008_02478_gb300.binding import OerstedPlan
+    t0 = time.perf_counter()
+    op = OerstedPlan(*N_MESH, *CELL)
+    t_oe_plan = time.perf_counter() - t0
+    Jd = torch.randn((3, N_MESH[2], N_MESH[1], N_MESH[0]), dtype=torch.float32, device="cuda") * 1e11
+    Hoe = torch.empty_like(Jd)
+    for _ in range(3):
+        op.apply(Jd, Hoe)
+    K = max(4, 4 * args.steps)
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(K):
+        op.apply(Jd, Hoe)
+    ev1.record()
+    torch.cuda.synchronize()
+    t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
+    out["oersted_512x512x32"] = {"evals_per_s": world * K / t, "ms_per_eval": 1e3 * t / K,
+                                 "plan_build_s": t_oe_plan}
+    op.close()
+    del Jd, Hoe
     # RKF45 film 256x64x1
     fd = inputs.FILM_SP4_MESH
     fp = Plan(*fd["n"], *fd["cell"])

@@ -101,6 +101,32 @@ int boris_demag_plan_pbc(int nx, int ny, int nz, double dx, double dy, double dz
                          void* cuda_stream, boris_plan* out);
 
 /*
+ * boris_oersted_plan - prepare the Oersted field of a current density (Table 1:
+ *   H(r0) = sum_r K(r - r0) J(r); the paper takes K from its Ref. [63]).  Here
+ *   K is derived: for a uniform current density J in a source cell the
+ *   target-cell average of the Biot-Savart field is J x g(D), D = target -
+ *   source, with g = -(1/(4 pi V)) grad P, P the two-cell integral of
+ *   1/|r - r'|; since Newell's tensor of the same pair is N_ij = d_i g_j, g_k is
+ *   built in FP64 on the device as the antiderivative of N_kk along axis k
+ *   (Gauss-Legendre over whole cells) closed by the far-field gradient of the
+ *   box-averaged potential beyond 40 cell sizes.  Its zero-padded spectrum is
+ *   imaginary (g_k odd in axis k only), and the convolution runs as
+ *   H^ = i (J^ x G) on the demag transform pipeline (split y-z schedule,
+ *   residue-split z stage; a pointwise multiply when nz = 1).  FP32.
+ *   Supported: nz = 1, or 3 <= nz <= 32 with ny >= 33.
+ *   Errors: INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA.  Synchronises the stream.
+ */
+int boris_oersted_plan(int nx, int ny, int nz, double dx, double dy, double dz, void* cuda_stream, boris_plan* out);
+
+/*
+ * boris_oersted_apply - H = Oersted field (A/m) of the current density J
+ *   (A/m^2); both device SoA [3][nz][ny][nx] FP32, 16-byte aligned, distinct.
+ *   Asynchronous on the plan's stream; a bounded device wait that gives up
+ *   latches BORIS_ERR_TIMEOUT (boris_sync_status).
+ */
+int boris_oersted_apply(boris_plan p, const float* J, float* H);
+
+/*
  * boris_multimesh_plan - prepare the multi-mesh demagnetising field of Eq. 4
  *   for a stack of n_layers (1..16) rectangular meshes:
  *     H(r'_kl) = -sum_i sum_{r_ij in V_i} N(r'_kl - r_ij, h_k, h_i) M(r_ij).
@@ -271,6 +297,10 @@ typedef struct {
                            (counter (i, s mod 2^32, s div 2^32, 0), key = seed,
                            Box-Muller), held through the step's four stages          */
     unsigned long long seed;
+    const void* H_add;  /* additive field map (A/m), device [3][nz][ny][nx] of the plan's
+                           precision, or NULL: added to H_eff like Hext (its energy is
+                           counted with the Zeeman term) - e.g. an Oersted field from
+                           boris_oersted_apply; single-mesh plans                        */
 } boris_field_terms;
 
 /*

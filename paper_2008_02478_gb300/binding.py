@@ -30,7 +30,7 @@ EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_inf
            "boris_demag_adjoint",
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
            "boris_energy_terms", "boris_set_field_terms", "boris_demag_plan_pbc",
-           "boris_thermal_set_step",
+           "boris_thermal_set_step", "boris_oersted_plan", "boris_oersted_apply",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
 KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other", "y_fwd", "z_conv", "y_inv", "x_c2r_rk4"]
@@ -57,7 +57,7 @@ class FieldTermsC(ctypes.Structure):
     _fields_ = [("K2", ctypes.c_double), ("Kc1", ctypes.c_double), ("Kc2", ctypes.c_double),
                 ("cubic_e1", ctypes.c_double * 3), ("cubic_e2", ctypes.c_double * 3), ("dmi", ctypes.c_int),
                 ("D", ctypes.c_double), ("J1", ctypes.c_double), ("J2", ctypes.c_double),
-                ("temperature", ctypes.c_double), ("seed", ctypes.c_ulonglong)]
+                ("temperature", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("H_add", ctypes.c_void_p)]
 
 
 @dataclass
@@ -74,6 +74,7 @@ class FieldTerms:
     J2: float = 0.0
     temperature: float = 0.0
     seed: int = 0
+    H_add: object = None  # torch CUDA tensor [3][nz][ny][nx] of the plan's precision, or None
 
     def c(self) -> FieldTermsC:
         t = FieldTermsC()
@@ -83,6 +84,7 @@ class FieldTerms:
         t.dmi = DMI_KINDS[self.dmi]
         t.D, t.J1, t.J2 = self.D, self.J1, self.J2
         t.temperature, t.seed = self.temperature, self.seed
+        t.H_add = self.H_add.data_ptr() if self.H_add is not None else None
         return t
 
 
@@ -116,6 +118,8 @@ def lib():
         L.boris_energy_terms.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_set_field_terms.argtypes = [vp, P(FieldTermsC)]
         L.boris_thermal_set_step.argtypes = [vp, ctypes.c_ulonglong]
+        L.boris_oersted_plan.argtypes = [i, i, i, d, d, d, vp, P(vp)]
+        L.boris_oersted_apply.argtypes = [vp, vp, vp]
         L.boris_sync_status.argtypes = [vp]
         L.boris_last_error.restype = ctypes.c_char_p
         L.boris_plan_padded.argtypes = [vp, P(i)]
@@ -330,6 +334,57 @@ class Plan:
 
     def profile_read(self):
         """{kernel class: (ms, timed launches)}, total launches since the last read."""
+        ms = (ctypes.c_double * len(KERNEL_CLASSES))()
+        cnt = (ctypes.c_longlong * len(KERNEL_CLASSES))()
+        tot = ctypes.c_longlong()
+        check(lib().boris_profile_read(self._h, ms, cnt, ctypes.byref(tot)))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_CLASSES)}, tot.value
+
+    def sync_status(self):
+        return check(lib().boris_sync_status(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().boris_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class OerstedPlan:
+    """Oersted field H = K * J of a current density on an nx x ny x nz mesh
+    (boris_oersted_plan / boris_oersted_apply), FP32."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, stream=None):
+        import torch
+        self.shape = (nx, ny, nz)
+        self.dtype = torch.float32
+        st = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        check(lib().boris_oersted_plan(nx, ny, nz, dx, dy, dz, ctypes.c_void_p(st.cuda_stream), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def field_shape(self):
+        nx, ny, nz = self.shape
+        return (3, nz, ny, nx)
+
+    def apply(self, J, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.field_shape, dtype=torch.float32, device=J.device)
+        check(lib().boris_oersted_apply(self._h, _ptr(J, torch.float32, self.field_shape),
+                                        _ptr(out, torch.float32, self.field_shape)))
+        return out
+
+    def profile(self, on: bool):
+        check(lib().boris_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
         ms = (ctypes.c_double * len(KERNEL_CLASSES))()
         cnt = (ctypes.c_longlong * len(KERNEL_CLASSES))()
         tot = ctypes.c_longlong()

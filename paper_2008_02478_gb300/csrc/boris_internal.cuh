@@ -151,6 +151,24 @@ cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, doubl
 cudaError_t newell_octant(int nx, int ny, int nz, double dx, double dy, double dz, double rs,
                           double* T, cudaStream_t st, const int* images = nullptr);
 
+// Oersted kernel spectrum (newell.cu): KO[kx][ky'][kz'][4] = (Gx, Gy, Gz, 0),
+// the imaginary parts of the padded g spectra scaled by 1/(px py pz), so that
+// the field of a current density J is H^ = i (J^ x KO) (Gx odd in kx; Gy odd in
+// ky; Gz odd in kz).
+cudaError_t build_oersted_spectrum(const Geometry& g, double dx, double dy, double dz, double rs, float* KO,
+                                   const double2* tw64, cudaStream_t st);
+// Oersted multiply stages (zconv_res.cu): the residue-split z convolution with
+// the curl multiply (pz >= 8; its kernel rows in the blocked copy with two
+// pairs per kz', built by zconv_res_build_k2_curl), and the pointwise multiply
+// for pz = 1.
+bool zconv_res_curl_supported(const Geometry& g, int max_smem);
+size_t zconv_res_k2_curl_bytes(const Geometry& g);
+cudaError_t zconv_res_build_k2_curl(const Geometry& g, const float* KO, float2* K2, cudaStream_t st);
+cudaError_t zconv_res_kmap_curl(const Geometry& g, float2* K2, void* map);
+cudaError_t launch_zconv_res_curl(const void* ymap, const void* kmap, const Geometry& g, float2* Y, int* status,
+                                  unsigned long long limit_ns, int nsm, cudaStream_t st);
+cudaError_t launch_curl_point(const Geometry& g, float2* Y, const float* KO, cudaStream_t st);
+
 // Twiddle table exp(-2 pi i e / n), e in [0, n), on the host in FP64.
 void host_twiddles(int n, double2* out);
 

@@ -42,6 +42,9 @@ struct boris_plan_s {
     int images[3] = {0, 0, 0};
     // thermal field step counter (device), allocated with the first thermal terms
     unsigned long long* d_step = nullptr;
+    // Oersted plan (boris_oersted_plan): K holds the spectrum KO [kx][ky'][kz'][4],
+    // K2 its blocked copy for the residue-split z stage (pz > 1), kmap that copy's tensor map
+    bool oersted = false;
     long long terms_version = 0;
     // device status word latched by bounded device-side waits (boris_sync_status)
     int* d_status = nullptr;
@@ -235,6 +238,7 @@ template <typename T>
 int demag_apply_t(boris_plan p, const T* M, const T* ms_map, T ms_scale, T* H)
 {
     using C = typename Cx<T>::t;
+    if (p->oersted) return fail(BORIS_ERR_INVALID_ARG, "an Oersted plan serves boris_oersted_apply only");
     if constexpr (sizeof(T) == 4) {
         if (p->ml) return ml_demag_apply(p, M, ms_map, ms_scale, H);
     }
@@ -306,6 +310,7 @@ int check_params(boris_plan p, const boris_llg_params* prm, LLGArgs<T>* a, doubl
     a->seed_lo = (unsigned int)(t.seed & 0xffffffffull);
     a->seed_hi = (unsigned int)(t.seed >> 32);
     a->step = p->d_step;
+    a->hadd = p->has_terms ? (const T*)t.H_add : nullptr;
     if (a->th_s0 > 0 && !p->d_step) return fail(BORIS_ERR_INVALID_ARG, "thermal step counter missing");
     if (a->th_s0 > 0) a->extra = 1;
     return BORIS_OK;
@@ -775,6 +780,112 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
     return BORIS_OK;
 }
 
+int boris_oersted_plan(int nx, int ny, int nz, double dx, double dy, double dz, void* cuda_stream, boris_plan* out)
+{
+    if (!out) return fail(BORIS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(BORIS_ERR_INVALID_ARG, "mesh sizes must be >= 1");
+    if (!(dx > 0) || !(dy > 0) || !(dz > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz))
+        return fail(BORIS_ERR_INVALID_ARG, "cell sizes must be finite and > 0");
+    Geometry g;
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.px = padded_len(nx);
+    g.py = padded_len(ny);
+    g.pz = padded_len(nz);
+    if (g.px > 4096 || g.py > 4096 || g.pz > 4096)
+        return fail(BORIS_ERR_UNSUPPORTED_SIZE, "padded transform length above 4096");
+    g.lgx = ilog2(g.px);
+    g.lgy = ilog2(g.py);
+    g.lgz = ilog2(g.pz);
+    g.nkx = g.px / 2 + 1;
+    g.kyh = g.py / 2 + 1;
+    g.kzh = g.pz / 2 + 1;
+    g.krow = (g.kzh * 6 + 3) / 4 * 4;
+    g.lmax = std::max(g.px, std::max(g.py, std::max(g.pz, 32)));
+    g.lglmax = ilog2(g.lmax);
+    if ((size_t)3 * nx * ny * nz > (size_t)1 << 31) return fail(BORIS_ERR_UNSUPPORTED_SIZE, "mesh too large");
+    boris_plan p = new (std::nothrow) boris_plan_s();
+    if (!p) return fail(BORIS_ERR_OOM, "host allocation");
+    p->g = g;
+    p->dx = dx;
+    p->dy = dy;
+    p->dz = dz;
+    p->oersted = true;
+    p->stream = (cudaStream_t)cuda_stream;
+    p->yz = YZSchedule{2, 3, 3, 0, 0};
+    auto bail = [&](int code) {
+        boris_plan_destroy(p);
+        return code;
+    };
+    int rc;
+    if (cudaGetDevice(&p->device) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "no CUDA device"));
+    cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device);
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if (!split_supported<float>(g, max_smem) || !(g.pz == 1 || zconv_res_curl_supported(g, max_smem)))
+        return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE,
+                         "Oersted plans need nz = 1 or 3 <= nz <= 32 with ny >= 33 (padded y >= 64)"));
+    if ((rc = dev_alloc(p, (void**)&p->d_status, sizeof(int)))) return bail(rc);
+    if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "status word"));
+    cudaError_t ce = upload_twiddles_split();
+    if (ce == cudaSuccess) ce = upload_twiddles_fast();
+    if (ce == cudaSuccess) ce = upload_twiddles_res();
+    if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("twiddle constants: ") + cudaGetErrorString(ce)));
+    std::vector<double2> tw(g.lmax);
+    host_twiddles(g.lmax, tw.data());
+    if ((rc = dev_alloc(p, (void**)&p->tw64, g.lmax * sizeof(double2)))) return bail(rc);
+    if (cudaMemcpy(p->tw64, tw.data(), g.lmax * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
+    std::vector<float2> twf(g.lmax);
+    for (int i = 0; i < g.lmax; i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+    if ((rc = dev_alloc(p, &p->tw, g.lmax * sizeof(float2)))) return bail(rc);
+    if (cudaMemcpy(p->tw, twf.data(), g.lmax * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
+    if ((rc = dev_alloc(p, &p->K, (size_t)g.nkx * g.kyh * g.kzh * 4 * sizeof(float)))) return bail(rc);
+    ce = build_oersted_spectrum(g, dx, dy, dz, 40.0, (float*)p->K, p->tw64, p->stream);
+    if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("Oersted spectrum: ") + cudaGetErrorString(ce)));
+    if ((rc = dev_alloc(p, &p->X, (size_t)g.nkx * 3 * g.nz * g.ny * sizeof(float2)))) return bail(rc);
+    if ((rc = dev_alloc(p, &p->Y, (size_t)g.nkx * g.py * 3 * g.nz * sizeof(float2)))) return bail(rc);
+    if (g.pz > 1) {
+        if ((rc = dev_alloc(p, &p->K2, zconv_res_k2_curl_bytes(g)))) return bail(rc);
+        p->k2_bytes = zconv_res_k2_curl_bytes(g);
+        if ((ce = zconv_res_build_k2_curl(g, (const float*)p->K, (float2*)p->K2, p->stream)) != cudaSuccess ||
+            (ce = zconv_res_kmap_curl(g, (float2*)p->K2, p->kmap)) != cudaSuccess ||
+            (ce = zconv_tma_map(g, (float2*)p->Y, p->ymap)) != cudaSuccess)
+            return bail(fail(BORIS_ERR_CUDA, std::string("Oersted spectrum copy: ") + cudaGetErrorString(ce)));
+        p->ymap_ready = true;
+    }
+    if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
+        return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
+    *out = p;
+    return BORIS_OK;
+}
+
+int boris_oersted_apply(boris_plan p, const float* J, float* H)
+{
+    if (!p || !J || !H) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (!p->oersted) return fail(BORIS_ERR_INVALID_ARG, "not an Oersted plan (boris_oersted_plan)");
+    if (!aligned16(J) || !aligned16(H)) return fail(BORIS_ERR_INVALID_ARG, "pointers must be 16-byte aligned");
+    if ((const void*)J == (const void*)H) return fail(BORIS_ERR_INVALID_ARG, "J and H may not alias");
+    const Geometry& g = p->g;
+    float2* X = (float2*)p->X;
+    float2* Y = (float2*)p->Y;
+    const float2* tw = (const float2*)p->tw;
+    CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<float>(g, J, nullptr, 1.0f, X, tw, p->stream); }));
+    CUDA_TRY(timed(p, 5, [&] { return launch_split<float>(g, X, Y, nullptr, tw, p->stream, 0, 2); }));
+    CUDA_TRY(timed(p, 6, [&] {
+        if (g.pz == 1) return launch_curl_point(g, Y, (const float*)p->K, p->stream);
+        return launch_zconv_res_curl(p->ymap, p->kmap, g, Y, p->d_status, p->wait_limit_ns, p->nsm, p->stream);
+    }));
+    CUDA_TRY(timed(p, 7, [&] { return launch_split<float>(g, X, Y, nullptr, tw, p->stream, 2, 2); }));
+    CUDA_TRY(timed(p, 2, [&] {
+        return launch_x_c2r<float>(g, X, H, tw, p->stream, p->d_status, p->wait_limit_ns);
+    }));
+    return BORIS_OK;
+}
+
 int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, const double* origin, unsigned flags,
                          void* cuda_stream, boris_plan* out)
 {
@@ -1132,6 +1243,8 @@ int boris_set_field_terms(boris_plan p, const boris_field_terms* t)
     if (v.dmi == BORIS_DMI_NONE) v.D = 0.0;
     if (v.dmi != BORIS_DMI_NONE && p->ml) return fail(BORIS_ERR_INVALID_ARG, "DMI serves single-mesh plans");
     if (v.temperature < 0) return fail(BORIS_ERR_INVALID_ARG, "temperature must be >= 0");
+    if (v.H_add && (p->ml || ((uintptr_t)v.H_add & 15u)))
+        return fail(BORIS_ERR_INVALID_ARG, "H_add serves single-mesh plans and must be 16-byte aligned");
     if (v.temperature > 0 && p->ml) return fail(BORIS_ERR_INVALID_ARG, "the thermal field serves single-mesh plans");
     if (v.temperature > 0 && (size_t)ncell(p) >= ((size_t)1 << 32))
         return fail(BORIS_ERR_UNSUPPORTED_SIZE, "thermal field: more than 2^32 cells");
@@ -1163,7 +1276,7 @@ int boris_set_field_terms(boris_plan p, const boris_field_terms* t)
     }
     p->terms = v;
     p->has_terms = v.K2 != 0.0 || v.Kc1 != 0.0 || v.Kc2 != 0.0 || (v.dmi != BORIS_DMI_NONE && v.D != 0.0) ||
-                   v.J1 != 0.0 || v.J2 != 0.0 || v.temperature > 0.0;
+                   v.J1 != 0.0 || v.J2 != 0.0 || v.temperature > 0.0 || v.H_add != nullptr;
     if (!p->has_terms) p->terms = boris_field_terms{};
     return BORIS_OK;
 }

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) energy_kernel(LLGArgs<T> a, const T* __re
         double mHd = 0, mHz = 0, mlap = 0, mw = 0;
         for (int c = 0; c < 3; c++) {
             mHd += mc[c] * (double)Hd[c * n + i];
-            mHz += mc[c] * (double)a.Hext[c];
+            mHz += mc[c] * ((double)a.Hext[c] + (a.hadd ? (double)a.hadd[c * n + i] : 0.0));
             mlap += mc[c] * lap[c];
             mw += mc[c] * w[c];
         }

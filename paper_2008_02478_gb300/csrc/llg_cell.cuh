@@ -235,6 +235,10 @@ __device__ __forceinline__ void cell_rhs(const LLGArgs<T>& a, const T* __restric
 #pragma unroll
         for (int c = 0; c < 3; c++) H[c] = hd[c] + cex * lap[c] + cd * w[c] + can * a.e[c] + a.Hext[c];
         ext_local_field<T>(a, m, Ms, H);
+        if (a.hadd) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) H[c] += a.hadd[c * n + i];
+        }
         if (a.th_s0 > T(0)) {
             T g[3];
             thermal_normals(a, i, g);

@@ -37,6 +37,7 @@ struct LLGArgs {
     T th_s0;
     unsigned int seed_lo, seed_hi;
     const unsigned long long* step;
+    const T* hadd;      // additive field map [3][nz][ny][nx] (e.g. an Oersted field) or NULL
 };
 // advances the thermal field's step counter by one (after an RK4 step) / sets it
 cudaError_t launch_thermal_advance(unsigned long long* step, cudaStream_t st);

@@ -33,7 +33,7 @@ struct MLHost {
 };
 
 cudaError_t run_axis_n(const void* in, bool in_real, double2* out, int axis, int d0, int d1, int d2, int n, int P,
-                       int ncomp, const double2* tw, int lglmax, cudaStream_t st);
+                       int ncomp, const double2* tw, int lglmax, cudaStream_t st, int pmode = 0);
 cudaError_t ml_build_spectra(const MLHost& h, const Geometry& g, float* K, const double2* tw64, cudaStream_t st);
 cudaError_t ml_embed(const MLTable& t, const float* M, const float* ms_map, float ms, float* F, cudaStream_t st);
 cudaError_t ml_extract(const MLTable& t, const float* F, float* H, cudaStream_t st);

@@ -122,10 +122,13 @@ __device__ __forceinline__ double comp_parity(int c, int a)
 // the transformed axis of length n (octant); output: same with that axis of
 // length P/2 + 1.  NL lines per CTA, each extended to length P in shared
 // memory with the component's parity.
+// pmode 0: the six demagnetising-tensor components (comp_parity); pmode 1:
+// the three Oersted components, component c odd along axis c only.
 __global__ void __launch_bounds__(256) axis_pass_kernel(const void* __restrict__ in, bool in_real,
                                                         double2* __restrict__ out, int axis, int d0, int d1,
                                                         int d2, int n, int P, int lgP, int NL,
-                                                        const double2* __restrict__ tw, int lglmax, int ncomp)
+                                                        const double2* __restrict__ tw, int lglmax, int ncomp,
+                                                        int pmode)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2* buf = reinterpret_cast<double2*>(smem_raw);  // [NL][P]
@@ -167,7 +170,10 @@ __global__ void __launch_bounds__(256) axis_pass_kernel(const void* __restrict__
             int src = -1;
             double s = 1.0;
             if (e < n) src = e;
-            else if (e > P - n) { src = P - e; s = comp_parity(c % 6, axis); }
+            else if (e > P - n) {
+                src = P - e;
+                s = pmode ? (c == axis ? -1.0 : 1.0) : comp_parity(c % 6, axis);
+            }
             if (src >= 0) {
                 const size_t ii = in_index(c, u, v, src);
                 if (in_real) val = make_double2(s * reinterpret_cast<const double*>(in)[ii], 0.0);
@@ -236,7 +242,7 @@ cudaError_t newell_octant(int nx, int ny, int nz, double dx, double dy, double d
 }
 
 cudaError_t run_axis_n(const void* in, bool in_real, double2* out, int axis, int d0, int d1, int d2, int n, int P,
-                       int ncomp, const double2* tw, int lglmax, cudaStream_t st)
+                       int ncomp, const double2* tw, int lglmax, cudaStream_t st, int pmode)
 {
     const int lgP = ilog2(P);
     int NL = 4096 / P;
@@ -250,14 +256,14 @@ cudaError_t run_axis_n(const void* in, bool in_real, double2* out, int axis, int
     const long nlines = (long)ncomp * dims[oa] * dims[ob];
     const long blocks = (nlines + NL - 1) / NL;
     axis_pass_kernel<<<(unsigned)blocks, 256, smem, st>>>(in, in_real, out, axis, d0, d1, d2, n, P, lgP, NL, tw,
-                                                           lglmax, ncomp);
+                                                           lglmax, ncomp, pmode);
     return cudaGetLastError();
 }
 
 static cudaError_t run_axis(const void* in, bool in_real, double2* out, int axis, int d0, int d1, int d2, int n,
                             int P, const double2* tw, int lglmax, cudaStream_t st)
 {
-    return run_axis_n(in, in_real, out, axis, d0, d1, d2, n, P, 6, tw, lglmax, st);
+    return run_axis_n(in, in_real, out, axis, d0, d1, d2, n, P, 6, tw, lglmax, st, 0);
 }
 
 cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, double dz, double rs, void* K_out,
@@ -289,6 +295,178 @@ cudaError_t build_kernel_spectrum(const Geometry& g, double dx, double dy, doubl
         if (blocks > 152 * 64) blocks = 152 * 64;
         if (k_is_f64) finalize_kernel<double><<<blocks, 256, 0, st>>>(A, (double*)K_out, g.nkx, g.kyh, g.kzh, g.krow, scale);
         else finalize_kernel<float><<<blocks, 256, 0, st>>>(A, (float*)K_out, g.nkx, g.kyh, g.kzh, g.krow, scale);
+        e = cudaGetLastError();
+    } while (0);
+    if (T) cudaFreeAsync(T, st);
+    if (A) cudaFreeAsync(A, st);
+    if (B) cudaFreeAsync(B, st);
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// Oersted kernel (Table 1, "K computed using formulas in Ref. [63]", which
+// the paper does not reproduce).  For a uniform current density J in a source
+// cell, the Biot-Savart field averaged over a target cell at centre
+// displacement D is H = J x g(D), g = -(1/(4 pi V)) grad_D P(D), P the
+// two-cell Coulomb integral of 1/|r - r'|.  The demagnetising tensor of the
+// same pair is N_ij = d_i g_j, so g_k is the antiderivative of N_kk along axis
+// k that vanishes far away:
+//   g_k(D) = gfar_k(D_e) - int_{D_k}^{t_e} N_kk dt,
+// integrated with 16-point Gauss-Legendre rules on whole cells (the kinks of
+// N lie on multiples of h_k) up to the first end point t_e beyond
+// rs max(h), where the far form (the gradient of the box-averaged potential
+// 1/r + sum_m h_m^2/12 d_m^2 (1/r)) takes over.  FP64.
+// ---------------------------------------------------------------------------
+struct GL16 {
+    double x[16], w[16];
+};
+
+// N_kk by Newell's 27-point stencil of f with k's argument first
+__device__ double newell_kk_dev(int k, double X, double Y, double Z, double dx, double dy, double dz)
+{
+    double s = 0.0;
+    for (int a = -1; a <= 1; a++) {
+        const double wa = a == 0 ? 2.0 : -1.0;
+        const double x = X + a * dx;
+        for (int b = -1; b <= 1; b++) {
+            const double wb = b == 0 ? 2.0 : -1.0;
+            const double y = Y + b * dy;
+            for (int c = -1; c <= 1; c++) {
+                const double w = wa * wb * (c == 0 ? 2.0 : -1.0);
+                const double z = Z + c * dz;
+                s += w * (k == 0 ? newell_f_dev(x, y, z) : k == 1 ? newell_f_dev(y, x, z) : newell_f_dev(z, y, x));
+            }
+        }
+    }
+    return s / (4.0 * 3.14159265358979323846 * dx * dy * dz);
+}
+
+__device__ double oersted_far_dev(int k, const double x[3], const double h[3], double V)
+{
+    const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const double r = sqrt(r2);
+    const double ir3 = 1.0 / (r2 * r), ir5 = ir3 / r2, ir7 = ir5 / r2;
+    double s = -x[k] * ir3;  // d_k (1/r)
+    for (int m = 0; m < 3; m++) {
+        // d_k d_m^2 (1/r) = (6 x_m delta_km - 2 x_k)/r^5 - 5 x_k (3 x_m^2 - r^2)/r^7
+        const double d3 = (6.0 * x[m] * (m == k ? 1.0 : 0.0) - 2.0 * x[k]) * ir5 - 5.0 * x[k] * (3.0 * x[m] * x[m] - r2) * ir7;
+        s += h[m] * h[m] * (1.0 / 12.0) * d3;
+    }
+    return -V / (4.0 * 3.14159265358979323846) * s;
+}
+
+// thread per (component, octant displacement): G[c][k][j][i] = g_c(i dx, j dy, k dz)
+__global__ void oersted_octant_kernel(int nx, int ny, int nz, double dx, double dy, double dz, double rs, GL16 gl,
+                                      double* __restrict__ G)
+{
+    const size_t n = (size_t)nx * ny * nz;
+    const double h[3] = {dx, dy, dz};
+    const double hmax = fmax(dx, fmax(dy, dz)), V = dx * dy * dz, rlim = rs * hmax;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < 3 * n; t += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / n);
+        const size_t idx = t - (size_t)c * n;
+        const int i = (int)(idx % nx), j = (int)((idx / nx) % ny), k = (int)(idx / ((size_t)nx * ny));
+        double p[3] = {i * dx, j * dy, k * dz};
+        double val;
+        if (sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) > rlim) {
+            val = oersted_far_dev(c, p, h, V);
+        } else {
+            double acc = 0.0;
+            double tpos = p[c];
+            for (;;) {
+                double q[3] = {p[0], p[1], p[2]};
+                q[c] = tpos;
+                if (sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) > rlim) break;
+                const double half = 0.5 * h[c], mid = tpos + half;
+                for (int g = 0; g < 16; g++) {
+                    q[c] = mid + half * gl.x[g];
+                    acc += gl.w[g] * half * newell_kk_dev(c, q[0], q[1], q[2], dx, dy, dz);
+                }
+                tpos += h[c];
+            }
+            double e[3] = {p[0], p[1], p[2]};
+            e[c] = tpos;
+            val = oersted_far_dev(c, e, h, V) - acc;
+        }
+        G[t] = val;
+    }
+}
+
+// KO[kx][ky'][kz'][4] = (Im gx, Im gy, Im gz, 0) / (px py pz): each spectrum is
+// imaginary (one odd axis), so the convolution is H^ = i (J^ x KO).
+__global__ void oersted_finalize_kernel(const double2* __restrict__ S, float* __restrict__ KO, int nkx, int kyh, int kzh,
+                                        double scale)
+{
+    const size_t n = (size_t)nkx * kyh * kzh;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < 4 * n; idx += (size_t)gridDim.x * blockDim.x) {
+        const int o = (int)(idx % 4);
+        const size_t cell = idx / 4;  // (kx * kyh + ky) * kzh + kz
+        const int kz = (int)(cell % kzh);
+        const size_t row = cell / kzh;
+        const int ky = (int)(row % kyh), kx = (int)(row / kyh);
+        float v = 0.f;
+        if (o < 3) v = (float)(S[(size_t)o * n + ((size_t)kz * kyh + ky) * nkx + kx].y * scale);
+        KO[idx] = v;
+    }
+}
+
+cudaError_t build_oersted_spectrum(const Geometry& g, double dx, double dy, double dz, double rs, float* KO,
+                                   const double2* tw64, cudaStream_t st)
+{
+    GL16 gl;
+    const int nn = 16;
+    for (int i = 0; i < nn; i++) {  // Legendre nodes by Newton iteration, FP64
+        double x = std::cos(3.14159265358979323846 * (i + 0.75) / (nn + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= nn; k++) {
+                const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = nn * (x * p1 - p0) / (x * x - 1.0);
+            const double step = p1 / dp;
+            x -= step;
+            if (std::fabs(step) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= nn; k++) {
+            const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = nn * (x * p1 - p0) / (x * x - 1.0);
+        gl.x[i] = x;
+        gl.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    double* T = nullptr;
+    double2 *A = nullptr, *B = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&T, 3 * n * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const size_t a_elems = 3 * (size_t)g.nkx * g.ny * g.nz;
+    const size_t b_elems = 3 * (size_t)g.nkx * g.kyh * g.nz;
+    const size_t c_elems = 3 * (size_t)g.nkx * g.kyh * g.kzh;
+    do {
+        int blocks = (int)((3 * n + 127) / 128);
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        oersted_octant_kernel<<<blocks, 128, 0, st>>>(g.nx, g.ny, g.nz, dx, dy, dz, rs, gl, T);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = cudaMallocAsync((void**)&A, a_elems * sizeof(double2), st)) != cudaSuccess) break;
+        if ((e = run_axis_n(T, true, A, 0, g.nx, g.ny, g.nz, g.nx, g.px, 3, tw64, g.lglmax, st, 1)) != cudaSuccess) break;
+        cudaFreeAsync(T, st);
+        T = nullptr;
+        if ((e = cudaMallocAsync((void**)&B, b_elems * sizeof(double2), st)) != cudaSuccess) break;
+        if ((e = run_axis_n(A, false, B, 1, g.nkx, g.ny, g.nz, g.ny, g.py, 3, tw64, g.lglmax, st, 1)) != cudaSuccess) break;
+        cudaFreeAsync(A, st);
+        A = nullptr;
+        if ((e = cudaMallocAsync((void**)&A, c_elems * sizeof(double2), st)) != cudaSuccess) break;
+        if ((e = run_axis_n(B, false, A, 2, g.nkx, g.kyh, g.nz, g.nz, g.pz, 3, tw64, g.lglmax, st, 1)) != cudaSuccess) break;
+        const double scale = 1.0 / ((double)g.px * g.py * g.pz);
+        const size_t tot = 4 * (size_t)g.nkx * g.kyh * g.kzh;
+        int fb = (int)((tot + 255) / 256);
+        if (fb > 152 * 64) fb = 152 * 64;
+        oersted_finalize_kernel<<<fb, 256, 0, st>>>(A, KO, g.nkx, g.kyh, g.kzh, scale);
         e = cudaGetLastError();
     } while (0);
     if (T) cudaFreeAsync(T, st);

@@ -48,10 +48,12 @@ constexpr int RTHREADS = 128;       // 4 residue warps
 constexpr int KBW = 34;             // entries per K2 block row (ky' = 32 b .. 32 b + 32, one pad)
 constexpr int STATUS_TIMEOUT = -5;  // BORIS_ERR_TIMEOUT
 
-template <int HZ, bool SEPARATE>
+// NP: kernel pairs per kz' (3 for the symmetric demagnetising tensor, 2 for
+// the Oersted vector: (Gx, Gy), (Gz, 0))
+template <int HZ, bool SEPARATE, int NP = 3>
 struct ResLayout {
     static constexpr int L = HZ / 2;
-    static constexpr int KROWS = (HZ + 1) * 3;
+    static constexpr int KROWS = (HZ + 1) * NP;
     static constexpr size_t stage = (size_t)3 * HZ * RQ * sizeof(float2);      // rows c HZ + z, 32 columns
     static constexpr size_t kstage = (size_t)KROWS * KBW * sizeof(float2);    // rows kz' 3 + pair
     static constexpr size_t scratch = (size_t)L * 4 * RQ * sizeof(float2);    // [z'][r][column]
@@ -95,14 +97,17 @@ __device__ __forceinline__ void recombine(const float2 (&v)[L], float2* scr, flo
     __syncthreads();
 }
 
-// FULL: nz == HZ (no cropped rows: no predicates on the loads and stores)
-template <int HZ, int MINB, bool FULL, bool SEPARATE>
+// FULL: nz == HZ (no cropped rows: no predicates on the loads and stores).
+// CURL: the Oersted multiply H^ = i (J^ x G) instead of the symmetric 3 x 3
+// demagnetising multiply.
+template <int HZ, int MINB, bool FULL, bool SEPARATE, bool CURL = false>
 __global__ void __launch_bounds__(RTHREADS, MINB)
     z_conv_res_kernel(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap kmap, Geometry g,
                       int nkb, float2* __restrict__ Y, int* __restrict__ status, uint32_t extra_tx,
                       unsigned long long limit_ns)
 {
-    using Lay = ResLayout<HZ, SEPARATE>;
+    constexpr int NP = CURL ? 2 : 3;
+    using Lay = ResLayout<HZ, SEPARATE, NP>;
     constexpr int L = Lay::L, LGL = lg2c(L), P = 2 * HZ, S = 128 / P, KROWS = Lay::KROWS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* stage = reinterpret_cast<float2*>(smem_raw);
@@ -202,30 +207,42 @@ __global__ void __launch_bounds__(RTHREADS, MINB)
             const bool fy = ky0 >= py / 2;
             const float sy = fy ? -1.f : 1.f;
             const float2* Kc = kst + (fy ? 32 - col : col);
-            const float2* Kup = Kc + r * 3 * KBW;  // rows 4 j + r
-            const float2* Kdn = Kc - r * 3 * KBW;  // rows P - 4 j - r
+            const float2* Kup = Kc + r * NP * KBW;  // rows 4 j + r
+            const float2* Kdn = Kc - r * NP * KBW;  // rows P - 4 j - r
 #pragma unroll
             for (int pos = 0; pos < L; pos++) {
                 const int j = brevc(pos, LGL);
                 const float2* kp;
                 float sz;
                 if (4 * j < HZ) {
-                    kp = Kup + 4 * j * 3 * KBW;
+                    kp = Kup + 4 * j * NP * KBW;
                     sz = 1.f;
                 } else if (4 * j > HZ) {
-                    kp = Kdn + (P - 4 * j) * 3 * KBW;
+                    kp = Kdn + (P - 4 * j) * NP * KBW;
                     sz = -1.f;
                 } else {
-                    kp = Kdn + HZ * 3 * KBW;  // kz = HZ + r: the Nyquist row for r = 0
+                    kp = Kdn + HZ * NP * KBW;  // kz = HZ + r: the Nyquist row for r = 0
                     sz = r == 0 ? 1.f : -1.f;
                 }
-                const float2 p0 = kp[0], p1 = kp[KBW], p2 = kp[2 * KBW];
-                const float xx = p0.x, yy = p0.y, zz = p1.x;
-                const float xy = p1.y * sy, xz = p2.x * sz, yz = p2.y * (sy * sz);
                 const float2 m0 = v0[pos], m1 = v1[pos], m2 = v2[pos];
-                v0[pos] = float2{xx * m0.x + xy * m1.x + xz * m2.x, xx * m0.y + xy * m1.y + xz * m2.y};
-                v1[pos] = float2{xy * m0.x + yy * m1.x + yz * m2.x, xy * m0.y + yy * m1.y + yz * m2.y};
-                v2[pos] = float2{xz * m0.x + yz * m1.x + zz * m2.x, xz * m0.y + yz * m1.y + zz * m2.y};
+                if (CURL) {
+                    // Gx odd in kx only, Gy odd in ky, Gz odd in kz; H^ = i (J^ x G)
+                    const float2 p0 = kp[0], p1 = kp[KBW];
+                    const float gx = p0.x, gy = p0.y * sy, gz = p1.x * sz;
+                    const float2 c0{m1.x * gz - m2.x * gy, m1.y * gz - m2.y * gy};
+                    const float2 c1{m2.x * gx - m0.x * gz, m2.y * gx - m0.y * gz};
+                    const float2 c2{m0.x * gy - m1.x * gx, m0.y * gy - m1.y * gx};
+                    v0[pos] = float2{-c0.y, c0.x};
+                    v1[pos] = float2{-c1.y, c1.x};
+                    v2[pos] = float2{-c2.y, c2.x};
+                } else {
+                    const float2 p0 = kp[0], p1 = kp[KBW], p2 = kp[2 * KBW];
+                    const float xx = p0.x, yy = p0.y, zz = p1.x;
+                    const float xy = p1.y * sy, xz = p2.x * sz, yz = p2.y * (sy * sz);
+                    v0[pos] = float2{xx * m0.x + xy * m1.x + xz * m2.x, xx * m0.y + xy * m1.y + xz * m2.y};
+                    v1[pos] = float2{xy * m0.x + yy * m1.x + yz * m2.x, xy * m0.y + yy * m1.y + yz * m2.y};
+                    v2[pos] = float2{xz * m0.x + yz * m1.x + zz * m2.x, xz * m0.y + yz * m1.y + zz * m2.y};
+                }
             }
         }
         if (SEPARATE) {
@@ -309,6 +326,69 @@ __global__ void k2_build_kernel(Geometry g, const float* __restrict__ K, float2*
     }
 }
 
+// K2c[kx][b][kz'][p][e] from KO[kx][ky'][kz'][4]: p = 0 (Gx, Gy), p = 1 (Gz, 0);
+// ky' = 32 b + e (e <= 32); zero for e = 33 and ky' >= kyh
+__global__ void k2_curl_build_kernel(Geometry g, const float* __restrict__ KO, float2* __restrict__ K2, int nkb)
+{
+    const size_t total = (size_t)g.nkx * nkb * g.kzh * 2 * KBW;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(i % KBW);
+        size_t rest = i / KBW;
+        const int p = (int)(rest % 2);
+        rest /= 2;
+        const int kz = (int)(rest % g.kzh);
+        rest /= g.kzh;
+        const int b = (int)(rest % nkb);
+        const size_t kx = rest / nkb;
+        const int ky = b * 32 + e;
+        float2 v{0.f, 0.f};
+        if (e <= 32 && ky < g.kyh) {
+            const float* q = KO + ((kx * g.kyh + ky) * g.kzh + kz) * 4;
+            v = p == 0 ? float2{q[0], q[1]} : float2{q[2], 0.f};
+        }
+        K2[i] = v;
+    }
+}
+
+// pz = 1: H^(kx, ky) = i (J^ x G) on Y[kx][c][0][ky] in place; Gy odd in ky
+__global__ void curl_point_kernel(Geometry g, float2* __restrict__ Y, const float* __restrict__ KO)
+{
+    const size_t total = (size_t)g.nkx * g.py;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int ky = (int)(t % g.py);
+        const size_t kx = t / g.py;
+        const bool fy = ky > g.py / 2;
+        const int kyf = fy ? g.py - ky : ky;
+        const float* q = KO + (kx * g.kyh + kyf) * g.kzh * 4;
+        const float gx = q[0], gy = fy ? -q[1] : q[1], gz = q[2];
+        float2* y0 = Y + (kx * 3 + 0) * g.py + ky;
+        float2* y1 = Y + (kx * 3 + 1) * g.py + ky;
+        float2* y2 = Y + (kx * 3 + 2) * g.py + ky;
+        const float2 m0 = *y0, m1 = *y1, m2 = *y2;
+        const float2 c0{m1.x * gz - m2.x * gy, m1.y * gz - m2.y * gy};
+        const float2 c1{m2.x * gx - m0.x * gz, m2.y * gx - m0.y * gz};
+        const float2 c2{m0.x * gy - m1.x * gx, m0.y * gy - m1.y * gx};
+        *y0 = float2{-c0.y, c0.x};
+        *y1 = float2{-c1.y, c1.x};
+        *y2 = float2{-c2.y, c2.x};
+    }
+}
+
+template <int HZ>
+cudaError_t launch_curl_hz(const CUtensorMap& ymap, const CUtensorMap& kmap, const Geometry& g, int nkb, float2* Y,
+                           int* status, unsigned long long limit_ns, int nsm, cudaStream_t st)
+{
+    constexpr int MINB = 3;
+    const size_t smem = ResLayout<HZ, true, 2>::total;
+    auto kern = g.nz == HZ ? z_conv_res_kernel<HZ, MINB, true, true, true> : z_conv_res_kernel<HZ, MINB, false, true, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int ntiles = g.nkx * (g.py / RQ);
+    const int grid = ntiles < MINB * nsm ? ntiles : MINB * nsm;
+    kern<<<grid, RTHREADS, smem, st>>>(ymap, kmap, g, nkb, Y, status, 0u, limit_ns);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // ky' blocks per kx plane of K2: tiles start at block ky0 / 32 (below the
@@ -372,6 +452,69 @@ cudaError_t launch_zconv_res(const void* ymap_p, const void* kmap_p, const Geome
     default: return cudaErrorInvalidValue;
     }
 #undef RES_CASE
+}
+
+bool zconv_res_curl_supported(const Geometry& g, int max_smem)
+{
+    const int hz = g.pz / 2;
+    size_t smem = 0;
+    switch (hz) {
+    case 4: smem = ResLayout<4, true, 2>::total; break;
+    case 8: smem = ResLayout<8, true, 2>::total; break;
+    case 16: smem = ResLayout<16, true, 2>::total; break;
+    case 32: smem = ResLayout<32, true, 2>::total; break;
+    default: return false;
+    }
+    return g.py >= 2 * RQ && g.py % RQ == 0 && g.nz <= hz && smem <= (size_t)max_smem;
+}
+
+size_t zconv_res_k2_curl_bytes(const Geometry& g)
+{
+    return (size_t)g.nkx * zconv_res_nkb(g) * g.kzh * 2 * KBW * sizeof(float2);
+}
+
+cudaError_t zconv_res_build_k2_curl(const Geometry& g, const float* KO, float2* K2, cudaStream_t st)
+{
+    k2_curl_build_kernel<<<1024, 256, 0, st>>>(g, KO, K2, zconv_res_nkb(g));
+    return cudaGetLastError();
+}
+
+cudaError_t zconv_res_kmap_curl(const Geometry& g, float2* K2, void* map)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint64_t rows = (cuuint64_t)g.nkx * zconv_res_nkb(g) * g.kzh * 2;
+    const cuuint64_t dims[2] = {(cuuint64_t)KBW, rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)KBW * sizeof(float2)};
+    const cuuint32_t box[2] = {(cuuint32_t)KBW, (cuuint32_t)(g.kzh * 2)};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, K2, dims, strides,
+                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_zconv_res_curl(const void* ymap_p, const void* kmap_p, const Geometry& g, float2* Y, int* status,
+                                  unsigned long long limit_ns, int nsm, cudaStream_t st)
+{
+    const CUtensorMap& ymap = *reinterpret_cast<const CUtensorMap*>(ymap_p);
+    const CUtensorMap& kmap = *reinterpret_cast<const CUtensorMap*>(kmap_p);
+    const int nkb = zconv_res_nkb(g);
+    switch (g.pz / 2) {
+    case 4: return launch_curl_hz<4>(ymap, kmap, g, nkb, Y, status, limit_ns, nsm, st);
+    case 8: return launch_curl_hz<8>(ymap, kmap, g, nkb, Y, status, limit_ns, nsm, st);
+    case 16: return launch_curl_hz<16>(ymap, kmap, g, nkb, Y, status, limit_ns, nsm, st);
+    case 32: return launch_curl_hz<32>(ymap, kmap, g, nkb, Y, status, limit_ns, nsm, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_curl_point(const Geometry& g, float2* Y, const float* KO, cudaStream_t st)
+{
+    size_t b = ((size_t)g.nkx * g.py + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    curl_point_kernel<<<(int)(b ? b : 1), 256, 0, st>>>(g, Y, KO);
+    return cudaGetLastError();
 }
 
 cudaError_t upload_twiddles_res() { return upload_small_twiddles_here(); }
