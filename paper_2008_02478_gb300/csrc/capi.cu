@@ -91,7 +91,7 @@ struct boris_plan_s {
     bool ml = false;
     MLTable mlt;
     double ml_zb[ML_MAX_LAYERS] = {};  // z of each layer's lower face (m)
-    void* Kml = nullptr;    // unique inter-plane spectra [u][kx][ky'][6]
+    void* Kml = nullptr;    // unique inter-plane spectra [u][kx][c][kyp]
     int* d_pairs = nullptr; // [Z * Z]
     float* Mf = nullptr;    // frame fields [3][Z][NY][NX]
     float* Hf = nullptr;
@@ -219,7 +219,7 @@ int ml_demag_apply(boris_plan p, const float* M, const float* ms_map, float ms_s
     CUDA_TRY(timed(p, 5, [&] { return launch_split<float>(p->g, X, Yb, nullptr, tw, p->stream, 0, 2); }));
     CUDA_TRY(timed(p, 6, [&] { return ml_mix(p->g, p->mlt.Z, Yb, (const float*)p->Kml, p->d_pairs, p->stream); }));
     CUDA_TRY(timed(p, 7, [&] { return launch_split<float>(p->g, X, Yb, nullptr, tw, p->stream, 2, 2); }));
-    CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<float>(p->g, X, p->Hf, tw, p->stream); }));
+    CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<float>(p->g, X, p->Hf, tw, p->stream, p->d_status, p->wait_limit_ns); }));
     CUDA_TRY(timed(p, 4, [&] { return ml_extract(p->mlt, p->Hf, H, p->stream); }));
     return BORIS_OK;
 }
@@ -1024,7 +1024,7 @@ int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, cons
     if ((rc = dev_alloc(p, &p->tw, g.lmax * sizeof(float2)))) return bail(rc);
     cudaMemcpy(p->tw64, tw.data(), g.lmax * sizeof(double2), cudaMemcpyHostToDevice);
     cudaMemcpy(p->tw, twf.data(), g.lmax * sizeof(float2), cudaMemcpyHostToDevice);
-    const size_t kbytes = (size_t)p->ml_unique * g.nkx * g.kyh * 6 * sizeof(float);
+    const size_t kbytes = (size_t)p->ml_unique * g.nkx * 6 * ml_kyp(g) * sizeof(float);
     if ((rc = dev_alloc(p, &p->Kml, kbytes))) return bail(rc);
     if ((rc = dev_alloc(p, (void**)&p->d_pairs, h.pairs.size() * sizeof(int)))) return bail(rc);
     cudaMemcpy(p->d_pairs, h.pairs.data(), h.pairs.size() * sizeof(int), cudaMemcpyHostToDevice);

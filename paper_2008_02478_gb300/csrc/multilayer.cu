@@ -101,22 +101,28 @@ __global__ void ml_tensor_kernel(int nu, const double* __restrict__ ua, const do
     }
 }
 
-// 2D spectra [6 nu][kyh][nkx] (complex) -> K[u][kx][ky'][6] with the real part of
-// xx, yy, zz, xy and the imaginary part of xz, yz (odd in exactly one in-plane
-// axis), scaled by -1/(px py).
+// 2D spectra [6 nu][kyh][nkx] (complex) -> K[u][kx][c][kyp] (component-major,
+// ky' fastest, rows padded to kyp = kyh rounded up to 32 with zeros) with the
+// real part of xx, yy, zz, xy and the imaginary part of xz, yz (odd in exactly
+// one in-plane axis), scaled by -1/(px py).
 __global__ void ml_finalize_kernel(const double2* __restrict__ S, float* __restrict__ K, int nu, int nkx, int kyh,
-                                   double scale)
+                                   int kyp, double scale)
 {
     const size_t per = (size_t)nkx * kyh;
-    const size_t total = (size_t)nu * per * 6;
+    const size_t total = (size_t)nu * nkx * 6 * kyp;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(idx % 6);
-        const size_t rec = idx / 6;  // (u, kx, ky)
-        const int u = (int)(rec / per);
-        const size_t r = rec % per;
-        const int kx = (int)(r / kyh), ky = (int)(r % kyh);
-        const double2 s = S[((size_t)u * 6 + c) * per + (size_t)ky * nkx + kx];
-        K[idx] = (float)(-(c < 4 ? s.x : s.y) * scale);
+        const int ky = (int)(idx % kyp);
+        size_t rest = idx / kyp;
+        const int c = (int)(rest % 6);
+        rest /= 6;
+        const int kx = (int)(rest % nkx);
+        const int u = (int)(rest / nkx);
+        float v = 0.f;
+        if (ky < kyh) {
+            const double2 s = S[((size_t)u * 6 + c) * per + (size_t)ky * nkx + kx];
+            v = (float)(-(c < 4 ? s.x : s.y) * scale);
+        }
+        K[idx] = v;
     }
 }
 
@@ -160,41 +166,52 @@ __global__ void ml_extract_kernel(MLTable t, const float* __restrict__ F, float*
     }
 }
 
-// Inter-plane sum in transform space.  CTA: 32 consecutive ky of one kx; warp w
-// accumulates the target planes p = w, w + 8, ...; lane = column.
-// Y layout [kx][c][p][ky]; pairs[p * Z + q] = u (>= 0) with bit 30 set when
-// z_p < z_q (xz and yz change sign).
+// Inter-plane sum in transform space (Eq. 4 moved to transform space).  CTA:
+// 32 consecutive folded rows ky' = 32 t + lane of one kx; each thread serves
+// column ky = ky' and its mirror py - ky' (which read the same spectrum row,
+// with xy and yz negated), so every spectrum entry is loaded once per kx.
+// Warp w accumulates the target planes p = w, w + 8, ...  Y layout
+// [kx][c][p][ky]; K[u][kx][c][kyp] (one coalesced 128-byte load per component);
+// pairs[p * Z + q] = u (>= 0) with bit 30 set when z_p < z_q (xz and yz change
+// sign).
 template <int PMAX>
 __global__ void __launch_bounds__(256) ml_mix_kernel(Geometry g, int Z, float2* __restrict__ Y,
-                                                     const float* __restrict__ K, const int* __restrict__ pairs)
+                                                     const float* __restrict__ K, int kyp, const int* __restrict__ pairs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2* Ms = reinterpret_cast<float2*>(smem_raw);  // [Z][3][32]
-    int* pr = reinterpret_cast<int*>(Ms + (size_t)Z * 3 * 32);
-    const int kx = blockIdx.y, ky0 = blockIdx.x * 32, py = g.py;
+    float2* Ms = reinterpret_cast<float2*>(smem_raw);  // [Z][3][2][32]: column ky', mirror
+    int* pr = reinterpret_cast<int*>(Ms + (size_t)Z * 3 * 64);
+    const int kx = blockIdx.y, kf0 = blockIdx.x * 32, py = g.py;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ky = ky0 + lane;
-    const bool on = ky < py;
-    float2* base = Y + (size_t)kx * 3 * Z * py + ky0;
+    const int kf = kf0 + lane;
+    const bool onA = kf <= py / 2;                 // column ky = kf
+    const bool onB = kf > 0 && kf < py / 2;        // mirror column py - kf
+    float2* base = Y + (size_t)kx * 3 * Z * py;
     for (int i = threadIdx.x; i < Z * Z; i += 256) pr[i] = pairs[i];
-    for (int i = threadIdx.x; i < 3 * Z * 32; i += 256) {
-        const int line = i >> 5, col = i & 31;  // line = c * Z + p
+    for (int i = threadIdx.x; i < 3 * Z * 64; i += 256) {
+        const int col = i & 31, half = (i >> 5) & 1, line = i >> 6;  // line = c * Z + p
         const int c = line / Z, p = line % Z;
-        Ms[(p * 3 + c) * 32 + col] = (ky0 + col < py) ? base[(size_t)line * py + col] : make_float2(0.f, 0.f);
+        const int f = kf0 + col;
+        const bool ok = half ? (f > 0 && f < py / 2) : (f <= py / 2);
+        const int ky = half ? py - f : f;
+        Ms[((p * 3 + c) * 2 + half) * 32 + col] = ok ? base[(size_t)line * py + ky] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const bool fy = ky > py / 2;
-    const int kyf = fy ? py - ky : ky;
-    const float sy = fy ? -1.f : 1.f;
-    const size_t per = (size_t)g.nkx * g.kyh;
-    const float* Kc = K + ((size_t)kx * g.kyh + kyf) * 6;
-    float2 acc[PMAX][3];
+    const size_t ustride = (size_t)g.nkx * 6 * kyp;
+    const float* Kc = K + (size_t)kx * 6 * kyp + (onA ? kf : 0);
+    float2 acc[PMAX][2][3];
 #pragma unroll
     for (int j = 0; j < PMAX; j++)
 #pragma unroll
-        for (int c = 0; c < 3; c++) acc[j][c] = make_float2(0.f, 0.f);
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[j][h][c] = make_float2(0.f, 0.f);
     for (int q = 0; q < Z; q++) {
-        const float2 mx = Ms[(q * 3 + 0) * 32 + lane], my = Ms[(q * 3 + 1) * 32 + lane], mz = Ms[(q * 3 + 2) * 32 + lane];
+        float2 mv[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) mv[h][c] = Ms[((q * 3 + c) * 2 + h) * 32 + lane];
 #pragma unroll
         for (int j = 0; j < PMAX; j++) {
             const int p = warp + 8 * j;
@@ -202,31 +219,33 @@ __global__ void __launch_bounds__(256) ml_mix_kernel(Geometry g, int Z, float2* 
                 const int code = pr[p * Z + q];
                 const int u = code & 0x3fffffff;
                 const float sz = (code >> 30) & 1 ? -1.f : 1.f;
-                const float* k = Kc + (size_t)u * per * 6;
-                const float2 k01 = on ? *reinterpret_cast<const float2*>(k) : make_float2(0.f, 0.f);
-                const float2 k23 = on ? *reinterpret_cast<const float2*>(k + 2) : make_float2(0.f, 0.f);
-                const float2 k45 = on ? *reinterpret_cast<const float2*>(k + 4) : make_float2(0.f, 0.f);
-                const float kxx = k01.x, kyy = k01.y, kzz = k23.x, kxy = sy * k23.y;
-                const float kxz = sz * k45.x, kyz = sy * sz * k45.y;  // imaginary parts: i * kxz, i * kyz
-                // x: kxx mx + kxy my + i kxz mz
-                acc[j][0].x += kxx * mx.x + kxy * my.x - kxz * mz.y;
-                acc[j][0].y += kxx * mx.y + kxy * my.y + kxz * mz.x;
-                // y: kxy mx + kyy my + i kyz mz
-                acc[j][1].x += kxy * mx.x + kyy * my.x - kyz * mz.y;
-                acc[j][1].y += kxy * mx.y + kyy * my.y + kyz * mz.x;
-                // z: i kxz mx + i kyz my + kzz mz
-                acc[j][2].x += -kxz * mx.y - kyz * my.y + kzz * mz.x;
-                acc[j][2].y += kxz * mx.x + kyz * my.x + kzz * mz.y;
+                const float* k = Kc + (size_t)u * ustride;
+                const float kxx = k[0], kyy = k[kyp], kzz = k[2 * kyp], kxy0 = k[3 * kyp];
+                const float kxz = sz * k[4 * kyp], kyz0 = sz * k[5 * kyp];  // imaginary parts: i kxz, i kyz
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const float kxy = h ? -kxy0 : kxy0, kyz = h ? -kyz0 : kyz0;  // mirror: ky odd entries flip
+                    const float2 mx = mv[h][0], my = mv[h][1], mz = mv[h][2];
+                    acc[j][h][0].x += kxx * mx.x + kxy * my.x - kxz * mz.y;
+                    acc[j][h][0].y += kxx * mx.y + kxy * my.y + kxz * mz.x;
+                    acc[j][h][1].x += kxy * mx.x + kyy * my.x - kyz * mz.y;
+                    acc[j][h][1].y += kxy * mx.y + kyy * my.y + kyz * mz.x;
+                    acc[j][h][2].x += -kxz * mx.y - kyz * my.y + kzz * mz.x;
+                    acc[j][h][2].y += kxz * mx.x + kyz * my.x + kzz * mz.y;
+                }
             }
         }
     }
-    if (!on) return;
 #pragma unroll
     for (int j = 0; j < PMAX; j++) {
         const int p = warp + 8 * j;
-        if (p < Z)
+        if (p < Z) {
 #pragma unroll
-            for (int c = 0; c < 3; c++) base[(size_t)(c * Z + p) * py + lane] = acc[j][c];
+            for (int c = 0; c < 3; c++) {
+                if (onA) base[(size_t)(c * Z + p) * py + kf] = acc[j][0][c];
+                if (onB) base[(size_t)(c * Z + p) * py + (py - kf)] = acc[j][1][c];
+            }
+        }
     }
 }
 
@@ -262,7 +281,10 @@ cudaError_t ml_build_spectra(const MLHost& h, const Geometry& g, float* K, const
             if ((e = run_axis_n(A, false, B, 1, g.nkx, NY, 1, NY, g.py, 6 * nb, tw64, g.lglmax, st)) != cudaSuccess) break;
             const size_t kt = (size_t)nb * g.nkx * g.kyh * 6;
             blocks = (int)std::min<size_t>((kt + 255) / 256, 152 * 64);
-            ml_finalize_kernel<<<blocks, 256, 0, st>>>(B, K + (size_t)u0 * g.nkx * g.kyh * 6, nb, g.nkx, g.kyh,
+            const int kyp = ml_kyp(g);
+            const size_t kt2 = (size_t)nb * g.nkx * 6 * kyp;
+            blocks = (int)std::min<size_t>((kt2 + 255) / 256, 152 * 64);
+            ml_finalize_kernel<<<blocks, 256, 0, st>>>(B, K + (size_t)u0 * g.nkx * 6 * kyp, nb, g.nkx, g.kyh, kyp,
                                                        1.0 / ((double)g.px * g.py));
             e = cudaGetLastError();
         }
@@ -294,16 +316,19 @@ cudaError_t ml_extract(const MLTable& t, const float* F, float* H, cudaStream_t 
     return cudaGetLastError();
 }
 
+int ml_kyp(const Geometry& g) { return (g.kyh + 31) / 32 * 32; }
+
 cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, cudaStream_t st)
 {
-    const size_t smem = (size_t)Z * 3 * 32 * sizeof(float2) + (size_t)Z * Z * sizeof(int);
-    const dim3 grid((g.py + 31) / 32, g.nkx);
+    const size_t smem = (size_t)Z * 3 * 64 * sizeof(float2) + (size_t)Z * Z * sizeof(int);
+    const dim3 grid(g.py / 64 + 1, g.nkx);  // folded rows 0 .. py/2
     const int pmax = (Z + 7) / 8;
+    const int kyp = ml_kyp(g);
     cudaError_t e;
 #define ML_MIX(P)                                                                                            \
     e = cudaFuncSetAttribute(ml_mix_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
     if (e != cudaSuccess) return e;                                                                          \
-    ml_mix_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, pairs);                                            \
+    ml_mix_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, kyp, pairs);                                       \
     return cudaGetLastError();
     if (pmax <= 1) { ML_MIX(1) }
     if (pmax <= 2) { ML_MIX(2) }

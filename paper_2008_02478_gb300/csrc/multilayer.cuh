@@ -38,5 +38,7 @@ cudaError_t ml_build_spectra(const MLHost& h, const Geometry& g, float* K, const
 cudaError_t ml_embed(const MLTable& t, const float* M, const float* ms_map, float ms, float* F, cudaStream_t st);
 cudaError_t ml_extract(const MLTable& t, const float* F, float* H, cudaStream_t st);
 cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, cudaStream_t st);
+// row pitch of the multi-mesh spectra K[u][kx][c][kyp]
+int ml_kyp(const Geometry& g);
 
 }  // namespace boris
