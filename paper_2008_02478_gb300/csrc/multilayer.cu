@@ -249,6 +249,114 @@ __global__ void __launch_bounds__(256) ml_mix_kernel(Geometry g, int Z, float2* 
     }
 }
 
+// The same sum with the spectrum rows staged asynchronously: for each source
+// plane q the 6 x 128-byte rows of every target's spectrum (Z x 6 rows, the
+// CTA's 32 columns) are copied into shared memory by cp.async one source
+// ahead (two buffers), so the loads overlap the previous source's arithmetic
+// instead of stalling each warp (Z <= 64: two buffers plus the columns fit).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int PMAX>
+__global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z, float2* __restrict__ Y,
+                                                            const float* __restrict__ K, int kyp,
+                                                            const int* __restrict__ pairs)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Kb = reinterpret_cast<float*>(smem_raw);             // [2][Z][6][32]
+    float2* Ms = reinterpret_cast<float2*>(Kb + 2 * Z * 6 * 32);  // [Z][3][2][32]
+    int* pr = reinterpret_cast<int*>(Ms + (size_t)Z * 3 * 64);
+    const int kx = blockIdx.y, kf0 = blockIdx.x * 32, py = g.py;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int kf = kf0 + lane;
+    const bool onA = kf <= py / 2;
+    const bool onB = kf > 0 && kf < py / 2;
+    float2* base = Y + (size_t)kx * 3 * Z * py;
+    const size_t ustride = (size_t)g.nkx * 6 * kyp;
+    const float* Kx = K + (size_t)kx * 6 * kyp + kf0;  // + u ustride + c kyp: a 128-byte row
+    for (int i = threadIdx.x; i < Z * Z; i += 256) pr[i] = pairs[i];
+    __syncthreads();
+    auto stage = [&](int q, int b) {
+        float* dst = Kb + (size_t)b * Z * 6 * 32;
+        for (int i = threadIdx.x; i < Z * 48; i += 256) {  // (target, component, 16-byte part)
+            const int p = i / 48, r = i - p * 48, c = r >> 3, part = r & 7;
+            const int u = pr[p * Z + q] & 0x3fffffff;
+            cp_async16(dst + (p * 6 + c) * 32 + part * 4, Kx + (size_t)u * ustride + (size_t)c * kyp + part * 4);
+        }
+        cp_async_commit();
+    };
+    stage(0, 0);
+    for (int i = threadIdx.x; i < 3 * Z * 64; i += 256) {
+        const int col = i & 31, half = (i >> 5) & 1, line = i >> 6;  // line = c * Z + p
+        const int c = line / Z, p = line % Z;
+        const int f = kf0 + col;
+        const bool ok = half ? (f > 0 && f < py / 2) : (f <= py / 2);
+        const int ky = half ? py - f : f;
+        Ms[((p * 3 + c) * 2 + half) * 32 + col] = ok ? base[(size_t)line * py + ky] : make_float2(0.f, 0.f);
+    }
+    float2 acc[PMAX][2][3];
+#pragma unroll
+    for (int j = 0; j < PMAX; j++)
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) acc[j][h][c] = make_float2(0.f, 0.f);
+    for (int q = 0; q < Z; q++) {
+        if (q + 1 < Z) {
+            stage(q + 1, (q + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();  // this source's rows (and, at q = 0, the columns) are in shared memory
+        const float* kb = Kb + (size_t)(q & 1) * Z * 6 * 32;
+        float2 mv[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) mv[h][c] = Ms[((q * 3 + c) * 2 + h) * 32 + lane];
+#pragma unroll
+        for (int j = 0; j < PMAX; j++) {
+            const int p = warp + 8 * j;
+            if (p < Z) {
+                const float sz = (pr[p * Z + q] >> 30) & 1 ? -1.f : 1.f;
+                const float* k = kb + p * 6 * 32 + lane;
+                const float kxx = k[0], kyy = k[32], kzz = k[64], kxy0 = k[96];
+                const float kxz = sz * k[128], kyz0 = sz * k[160];  // imaginary parts: i kxz, i kyz
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    const float kxy = h ? -kxy0 : kxy0, kyz = h ? -kyz0 : kyz0;  // mirror: ky odd entries flip
+                    const float2 mx = mv[h][0], my = mv[h][1], mz = mv[h][2];
+                    acc[j][h][0].x += kxx * mx.x + kxy * my.x - kxz * mz.y;
+                    acc[j][h][0].y += kxx * mx.y + kxy * my.y + kxz * mz.x;
+                    acc[j][h][1].x += kxy * mx.x + kyy * my.x - kyz * mz.y;
+                    acc[j][h][1].y += kxy * mx.y + kyy * my.y + kyz * mz.x;
+                    acc[j][h][2].x += -kxz * mx.y - kyz * my.y + kzz * mz.x;
+                    acc[j][h][2].y += kxz * mx.x + kyz * my.x + kzz * mz.y;
+                }
+            }
+        }
+        __syncthreads();  // buffer q & 1 is free for source q + 2
+    }
+#pragma unroll
+    for (int j = 0; j < PMAX; j++) {
+        const int p = warp + 8 * j;
+        if (p < Z) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                if (onA) base[(size_t)(c * Z + p) * py + kf] = acc[j][0][c];
+                if (onB) base[(size_t)(c * Z + p) * py + (py - kf)] = acc[j][1][c];
+            }
+        }
+    }
+}
+
 cudaError_t ml_build_spectra(const MLHost& h, const Geometry& g, float* K, const double2* tw64, cudaStream_t st)
 {
     const int nu = (int)h.ua.size();
@@ -320,19 +428,30 @@ int ml_kyp(const Geometry& g) { return (g.kyh + 31) / 32 * 32; }
 
 cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, cudaStream_t st)
 {
-    const size_t smem = (size_t)Z * 3 * 64 * sizeof(float2) + (size_t)Z * Z * sizeof(int);
     const dim3 grid(g.py / 64 + 1, g.nkx);  // folded rows 0 .. py/2
     const int pmax = (Z + 7) / 8;
     const int kyp = ml_kyp(g);
+    const size_t smem_s = (size_t)2 * Z * 6 * 32 * sizeof(float) + (size_t)Z * 3 * 64 * sizeof(float2) +
+                          (size_t)Z * Z * sizeof(int);
+    const bool staged = smem_s <= 227 * 1024;
+    const size_t smem = staged ? smem_s : (size_t)Z * 3 * 64 * sizeof(float2) + (size_t)Z * Z * sizeof(int);
     cudaError_t e;
-#define ML_MIX(P)                                                                                            \
-    e = cudaFuncSetAttribute(ml_mix_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);       \
-    if (e != cudaSuccess) return e;                                                                          \
-    ml_mix_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, kyp, pairs);                                       \
+#define ML_MIX(P)                                                                                              \
+    if (staged) {                                                                                              \
+        e = cudaFuncSetAttribute(ml_mix_staged_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e != cudaSuccess) return e;                                                                        \
+        ml_mix_staged_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, kyp, pairs);                              \
+    } else {                                                                                                   \
+        e = cudaFuncSetAttribute(ml_mix_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+        if (e != cudaSuccess) return e;                                                                        \
+        ml_mix_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, kyp, pairs);                                     \
+    }                                                                                                          \
     return cudaGetLastError();
     if (pmax <= 1) { ML_MIX(1) }
     if (pmax <= 2) { ML_MIX(2) }
+    if (pmax <= 3) { ML_MIX(3) }
     if (pmax <= 4) { ML_MIX(4) }
+    if (pmax <= 5) { ML_MIX(5) }
     if (pmax <= 6) { ML_MIX(6) }
     if (pmax <= 8) { ML_MIX(8) }
 #undef ML_MIX
