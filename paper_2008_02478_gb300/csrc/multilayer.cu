@@ -250,10 +250,10 @@ __global__ void __launch_bounds__(256) ml_mix_kernel(Geometry g, int Z, float2* 
 }
 
 // The same sum with the spectrum rows staged asynchronously: for each source
-// plane q the 6 x 128-byte rows of every target's spectrum (Z x 6 rows, the
-// CTA's 32 columns) are copied into shared memory by cp.async one source
-// ahead (two buffers), so the loads overlap the previous source's arithmetic
-// instead of stalling each warp (Z <= 64: two buffers plus the columns fit).
+// plane q every warp copies the 6 x 128-byte rows of its own targets'
+// spectra (the CTA's 32 columns) into its shared-memory buffer by cp.async
+// one source ahead (two buffers), so the loads overlap the previous source's
+// arithmetic and only warp-level synchronisation is needed (Z <= 64).
 __device__ __forceinline__ void cp_async16(void* dst, const void* src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
@@ -265,29 +265,41 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 template <int PMAX>
 __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z, float2* __restrict__ Y,
-                                                            const float* __restrict__ K, int kyp,
-                                                            const int* __restrict__ pairs)
+                                                               const float* __restrict__ K, int kyp,
+                                                               const int* __restrict__ pairs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* Kb = reinterpret_cast<float*>(smem_raw);             // [2][Z][6][32]
-    float2* Ms = reinterpret_cast<float2*>(Kb + 2 * Z * 6 * 32);  // [Z][3][2][32]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // per warp: [2][nt][6][32] rows of its own nt targets p = warp + 8 j (Z
+    // targets over the eight warps: Z x 2 x 6 x 32 floats in all)
+    const int nt = (Z - warp + 7) / 8;
+    int before = 0;
+    for (int v = 0; v < warp; v++) before += (Z - v + 7) / 8;
+    float* Kw = reinterpret_cast<float*>(smem_raw) + (size_t)before * 2 * 6 * 32;
+    float2* Ms = reinterpret_cast<float2*>(reinterpret_cast<float*>(smem_raw) + (size_t)Z * 2 * 6 * 32);
     int* pr = reinterpret_cast<int*>(Ms + (size_t)Z * 3 * 64);
     const int kx = blockIdx.y, kf0 = blockIdx.x * 32, py = g.py;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int kf = kf0 + lane;
     const bool onA = kf <= py / 2;
     const bool onB = kf > 0 && kf < py / 2;
     float2* base = Y + (size_t)kx * 3 * Z * py;
     const size_t ustride = (size_t)g.nkx * 6 * kyp;
-    const float* Kx = K + (size_t)kx * 6 * kyp + kf0;  // + u ustride + c kyp: a 128-byte row
+    // lane's share of a target's six 128-byte rows: 16-byte part lane & 7 of
+    // components lane >> 3 and (lane >> 3) + 4 (the latter for lanes 0..15)
+    const int part = lane & 7, c0 = lane >> 3;
+    const float* Kx = K + (size_t)kx * 6 * kyp + kf0 + part * 4;
     for (int i = threadIdx.x; i < Z * Z; i += 256) pr[i] = pairs[i];
     __syncthreads();
     auto stage = [&](int q, int b) {
-        float* dst = Kb + (size_t)b * Z * 6 * 32;
-        for (int i = threadIdx.x; i < Z * 48; i += 256) {  // (target, component, 16-byte part)
-            const int p = i / 48, r = i - p * 48, c = r >> 3, part = r & 7;
-            const int u = pr[p * Z + q] & 0x3fffffff;
-            cp_async16(dst + (p * 6 + c) * 32 + part * 4, Kx + (size_t)u * ustride + (size_t)c * kyp + part * 4);
+#pragma unroll
+        for (int j = 0; j < PMAX; j++) {
+            const int p = warp + 8 * j;
+            if (p < Z) {
+                const float* src = Kx + (size_t)(pr[p * Z + q] & 0x3fffffff) * ustride;
+                float* dst = Kw + ((size_t)(b * nt + j) * 6) * 32 + part * 4;
+                cp_async16(dst + c0 * 32, src + (size_t)c0 * kyp);
+                if (c0 < 2) cp_async16(dst + (c0 + 4) * 32, src + (size_t)(c0 + 4) * kyp);
+            }
         }
         cp_async_commit();
     };
@@ -300,6 +312,7 @@ __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z
         const int ky = half ? py - f : f;
         Ms[((p * 3 + c) * 2 + half) * 32 + col] = ok ? base[(size_t)line * py + ky] : make_float2(0.f, 0.f);
     }
+    __syncthreads();  // the columns are in shared memory
     float2 acc[PMAX][2][3];
 #pragma unroll
     for (int j = 0; j < PMAX; j++)
@@ -314,8 +327,8 @@ __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z
         } else {
             cp_async_wait<0>();
         }
-        __syncthreads();  // this source's rows (and, at q = 0, the columns) are in shared memory
-        const float* kb = Kb + (size_t)(q & 1) * Z * 6 * 32;
+        __syncwarp();  // every lane's copies of source q are visible to the warp
+        const float* kb = Kw + (size_t)(q & 1) * nt * 6 * 32 + lane;
         float2 mv[2][3];
 #pragma unroll
         for (int h = 0; h < 2; h++)
@@ -326,7 +339,7 @@ __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z
             const int p = warp + 8 * j;
             if (p < Z) {
                 const float sz = (pr[p * Z + q] >> 30) & 1 ? -1.f : 1.f;
-                const float* k = kb + p * 6 * 32 + lane;
+                const float* k = kb + j * 6 * 32;
                 const float kxx = k[0], kyy = k[32], kzz = k[64], kxy0 = k[96];
                 const float kxz = sz * k[128], kyz0 = sz * k[160];  // imaginary parts: i kxz, i kyz
 #pragma unroll
@@ -342,7 +355,7 @@ __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z
                 }
             }
         }
-        __syncthreads();  // buffer q & 1 is free for source q + 2
+        __syncwarp();  // buffer q & 1 is free for source q + 2
     }
 #pragma unroll
     for (int j = 0; j < PMAX; j++) {
@@ -426,12 +439,14 @@ cudaError_t ml_extract(const MLTable& t, const float* F, float* H, cudaStream_t 
 
 int ml_kyp(const Geometry& g) { return (g.kyh + 31) / 32 * 32; }
 
+
+
 cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, cudaStream_t st)
 {
     const dim3 grid(g.py / 64 + 1, g.nkx);  // folded rows 0 .. py/2
     const int pmax = (Z + 7) / 8;
     const int kyp = ml_kyp(g);
-    const size_t smem_s = (size_t)2 * Z * 6 * 32 * sizeof(float) + (size_t)Z * 3 * 64 * sizeof(float2) +
+    const size_t smem_s = (size_t)Z * 2 * 6 * 32 * sizeof(float) + (size_t)Z * 3 * 64 * sizeof(float2) +
                           (size_t)Z * Z * sizeof(int);
     const bool staged = smem_s <= 227 * 1024;
     const size_t smem = staged ? smem_s : (size_t)Z * 3 * 64 * sizeof(float2) + (size_t)Z * Z * sizeof(int);
