@@ -61,7 +61,9 @@ struct ResLayout {
     static constexpr size_t kstage_off = stage;
     static constexpr size_t scratch_off = SEPARATE ? stage + (kstage + 127) / 128 * 128 : stage;
     static constexpr size_t bar_off = (SEPARATE ? scratch_off + scratch : stage + kstage + 15) / 16 * 16;
-    static constexpr size_t total = bar_off + 16;
+    // per residue r: L entries w_P^(z r), L entries w_P^(z r) (-i)^r
+    static constexpr size_t tw_off = bar_off + 16;
+    static constexpr size_t total = tw_off + (size_t)4 * 2 * L * sizeof(float2);
 };
 
 constexpr int lg2c(int v) { return v <= 1 ? 0 : 1 + lg2c(v / 2); }
@@ -85,7 +87,7 @@ __device__ __forceinline__ void recombine(const float2 (&v)[L], float2* scr, flo
 #pragma unroll
     for (int i = 0; i < (L + 3) / 4; i++) {
         const int z = r + 4 * i;
-        if (z < L) {
+        if (L % 4 == 0 || z < L) {  // r < 4: always true when 4 divides L
             const float2 a0 = scr[(z * 4 + 0) * RQ + col], a1 = scr[(z * 4 + 1) * RQ + col];
             const float2 a2 = scr[(z * 4 + 2) * RQ + col], a3 = scr[(z * 4 + 3) * RQ + col];
             const float2 s02 = c_add(a0, a2), d02 = c_sub(a0, a2);
@@ -137,6 +139,14 @@ __global__ void __launch_bounds__(RTHREADS, MINB)
         tma_load_2d(kst, &kmap, 0, (kx * nkb + b) * KROWS, fullK);
     };
 
+    // the warp's twiddle rows at compile-time offsets (no index arithmetic per use)
+    float2* twr = reinterpret_cast<float2*>(smem_raw + Lay::tw_off);
+    for (int i = threadIdx.x; i < 4 * 2 * L; i += RTHREADS) {
+        const int rr = i / (2 * L), k = i - rr * 2 * L, z = k % L;
+        twr[i] = c_w128f[(S * z * rr + (k >= L ? 32 * rr : 0)) & 127];
+    }
+    const float2* twa = twr + r * 2 * L;  // w_P^(z r)
+    const float2* twb = twa + L;          // w_P^(z r) (-i)^r
     if (threadIdx.x == 0) {
         mbar_init(fullY, 1);
         mbar_init(fullK, 1);
@@ -169,8 +179,8 @@ __global__ void __launch_bounds__(RTHREADS, MINB)
             const float2* A = stage + col;
 #pragma unroll
             for (int z = 0; z < L; z++) {
-                const float2 ta = c_w128f[(S * z * r) & 127];
-                const float2 tb = c_w128f[(S * z * r + 32 * r) & 127];
+                const float2 ta = twa[z];
+                const float2 tb = twb[z];
                 const bool lo = FULL || z < nz, hi = FULL || z + L < nz;
                 const float2 f0{0.f, 0.f};
                 const float2 a0 = lo ? A[(0 * HZ + z) * RQ] : f0, b0 = hi ? A[(0 * HZ + z + L) * RQ] : f0;
@@ -257,7 +267,7 @@ __global__ void __launch_bounds__(RTHREADS, MINB)
         reg_fft<L, 1>(v2);
 #pragma unroll
         for (int z = 0; z < L; z++) {
-            const float2 w = c_w128f[(S * z * r) & 127];
+            const float2 w = twa[z];
             v0[z] = c_mulc(v0[z], w);
             v1[z] = c_mulc(v1[z], w);
             v2[z] = c_mulc(v2[z], w);
