@@ -29,6 +29,13 @@ template <> struct Cx<double> { using t = double2; };
 
 template <typename C> __device__ __forceinline__ C c_add(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
 template <typename C> __device__ __forceinline__ C c_sub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+// FP32: the complex sum and difference as one packed FP32x2 instruction each
+// (sm_100 and later), rounded like the two scalar operations.
+template <> __device__ __forceinline__ float2 c_add<float2>(float2 a, float2 b) { return __fadd2_rn(a, b); }
+template <> __device__ __forceinline__ float2 c_sub<float2>(float2 a, float2 b)
+{
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
 template <typename C> __device__ __forceinline__ C c_mul(C a, C b)
 {
     return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
@@ -39,6 +46,7 @@ template <typename C> __device__ __forceinline__ C c_mulc(C a, C b)
     return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
 template <typename C, typename T> __device__ __forceinline__ C c_scale(C a, T s) { return C{a.x * s, a.y * s}; }
+
 
 __device__ __forceinline__ int bitrev(int v, int lg) { return lg == 0 ? 0 : (int)(__brev((unsigned)v) >> (32 - lg)); }
 

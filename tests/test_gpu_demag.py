@@ -53,6 +53,7 @@ SCHEDULE_MESHES = [
     ((64, 40, 1), (2e-9, 2e-9, 3e-9)),    # 2D mode
     ((18, 33, 9), (2e-9, 1e-9, 2e-9)),    # pz = 32, ragged nz and ny
     ((12, 40, 3), (3e-9, 2e-9, 1e-9)),    # pz = 8, py = 128
+    ((24, 20, 32), (2e-9, 2e-9, 2e-9)),   # pz = 64, nz = 32 filling the z tile (no cropped rows)
 ]
 # (kind, CTAs per cluster or per SM, threads | "tma1"/"tma2" for the bulk-copy z
 # convolution | "tma3" for the residue-split z convolution)
