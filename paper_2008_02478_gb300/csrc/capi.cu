@@ -139,6 +139,36 @@ int dev_alloc(boris_plan p, void** ptr, size_t bytes)
 
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
+// The plan's twiddle tables, FP64 (tw64) and in the plan precision (tw):
+// entries e < lmax are exp(-2 pi i e / lmax); the 1024 entries after them are
+// exp(-2 pi i c b / 1024) at c * 32 + b (c, b < 32), the row-per-c table the
+// length-1024 warp transforms copy to shared memory.
+int upload_plan_twiddles(boris_plan p, const Geometry& g, bool f64)
+{
+    const int n = g.lmax + 1024;
+    std::vector<double2> tw(n);
+    host_twiddles(g.lmax, tw.data());
+    const double twopi = 6.283185307179586476925286766559;
+    for (int i = 0; i < 1024; i++) {
+        const double a = twopi * (double)((i >> 5) * (i & 31)) / 1024.0;
+        tw[g.lmax + i] = make_double2(std::cos(a), -std::sin(a));
+    }
+    int rc;
+    if ((rc = dev_alloc(p, (void**)&p->tw64, n * sizeof(double2)))) return rc;
+    if (cudaMemcpy(p->tw64, tw.data(), n * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(BORIS_ERR_CUDA, "twiddle upload");
+    if (f64) {
+        p->tw = p->tw64;
+        return BORIS_OK;
+    }
+    std::vector<float2> twf(n);
+    for (int i = 0; i < n; i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
+    if ((rc = dev_alloc(p, &p->tw, n * sizeof(float2)))) return rc;
+    if (cudaMemcpy(p->tw, twf.data(), n * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(BORIS_ERR_CUDA, "twiddle upload");
+    return BORIS_OK;
+}
+
 size_t ncell(const boris_plan p)
 {
     if (p->ml) return p->mlt.total3 / 3;
@@ -709,20 +739,7 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("yz attributes: ") + cudaGetErrorString(ce)));
 
     // twiddles
-    std::vector<double2> tw(g.lmax);
-    host_twiddles(g.lmax, tw.data());
-    if ((rc = dev_alloc(p, (void**)&p->tw64, g.lmax * sizeof(double2)))) return bail(rc);
-    if (cudaMemcpy(p->tw64, tw.data(), g.lmax * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
-    if (p->f64) {
-        p->tw = p->tw64;
-    } else {
-        std::vector<float2> twf(g.lmax);
-        for (int i = 0; i < g.lmax; i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
-        if ((rc = dev_alloc(p, &p->tw, g.lmax * sizeof(float2)))) return bail(rc);
-        if (cudaMemcpy(p->tw, twf.data(), g.lmax * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
-            return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
-    }
+    if ((rc = upload_plan_twiddles(p, g, p->f64))) return bail(rc);
     // kernel spectrum
     const size_t kelems = (size_t)g.nkx * g.kyh * g.krow;
     const size_t esz = p->f64 ? sizeof(double) : sizeof(float);
@@ -833,16 +850,7 @@ int boris_oersted_plan(int nx, int ny, int nz, double dx, double dy, double dz, 
     if (ce == cudaSuccess) ce = upload_twiddles_fast();
     if (ce == cudaSuccess) ce = upload_twiddles_res();
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("twiddle constants: ") + cudaGetErrorString(ce)));
-    std::vector<double2> tw(g.lmax);
-    host_twiddles(g.lmax, tw.data());
-    if ((rc = dev_alloc(p, (void**)&p->tw64, g.lmax * sizeof(double2)))) return bail(rc);
-    if (cudaMemcpy(p->tw64, tw.data(), g.lmax * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
-    std::vector<float2> twf(g.lmax);
-    for (int i = 0; i < g.lmax; i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
-    if ((rc = dev_alloc(p, &p->tw, g.lmax * sizeof(float2)))) return bail(rc);
-    if (cudaMemcpy(p->tw, twf.data(), g.lmax * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
-        return bail(fail(BORIS_ERR_CUDA, "twiddle upload"));
+    if ((rc = upload_plan_twiddles(p, g, false))) return bail(rc);
     if ((rc = dev_alloc(p, &p->K, (size_t)g.nkx * g.kyh * g.kzh * 4 * sizeof(float)))) return bail(rc);
     ce = build_oersted_spectrum(g, dx, dy, dz, 40.0, (float*)p->K, p->tw64, p->stream);
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, std::string("Oersted spectrum: ") + cudaGetErrorString(ce)));
@@ -1016,14 +1024,7 @@ int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, cons
     if (ce == cudaSuccess) ce = upload_twiddles_fast();
     if (ce == cudaSuccess) ce = upload_twiddles_res();
     if (ce != cudaSuccess) return bail(fail(BORIS_ERR_CUDA, "twiddle constants"));
-    std::vector<double2> tw(g.lmax);
-    host_twiddles(g.lmax, tw.data());
-    std::vector<float2> twf(g.lmax);
-    for (int i = 0; i < g.lmax; i++) twf[i] = make_float2((float)tw[i].x, (float)tw[i].y);
-    if ((rc = dev_alloc(p, (void**)&p->tw64, g.lmax * sizeof(double2)))) return bail(rc);
-    if ((rc = dev_alloc(p, &p->tw, g.lmax * sizeof(float2)))) return bail(rc);
-    cudaMemcpy(p->tw64, tw.data(), g.lmax * sizeof(double2), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->tw, twf.data(), g.lmax * sizeof(float2), cudaMemcpyHostToDevice);
+    if ((rc = upload_plan_twiddles(p, g, false))) return bail(rc);
     const size_t kbytes = (size_t)p->ml_unique * g.nkx * 6 * ml_kyp(g) * sizeof(float);
     if ((rc = dev_alloc(p, &p->Kml, kbytes))) return bail(rc);
     if ((rc = dev_alloc(p, (void**)&p->d_pairs, h.pairs.size() * sizeof(int)))) return bail(rc);

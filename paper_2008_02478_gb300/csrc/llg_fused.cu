@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(FT, 2)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int y0 = blockIdx.x * FY, z = blockIdx.y;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    load_tw1024(tws, tw_g, g.lglmax - 10);
+    load_tw1024(tws, tw_g, g.lmax);
     // stage S[kx][c FY + t] = X[kx][c][z][y0 + t]: each group of FY
     // consecutive threads reads one FY-element run of a spectrum column
     float2* S = reg;

@@ -4,10 +4,10 @@
 //   X[c + 32 d] = sum_b w_32^(b d) w_1024^(b c) sum_a x[32 a + b] w_32^(a c)
 //
 // Forward: a length-32 transform over a in registers, the twiddle
-// w_1024^(b c) (smem table), a transpose through a per-warp 32 x 32 shared
-// tile (column index XOR-swizzled with the row, so both the row-wise writes
-// and the column-wise reads are free of bank conflicts), and a length-32
-// transform over b.  The inverse runs the same steps backwards with
+// w_1024^(b c) (shared-memory table), a transpose through a per-warp 32 x 32
+// shared tile (column index XOR-swizzled with the row, so both the row-wise
+// writes and the column-wise reads are free of bank conflicts), and a
+// length-32 transform over b.  The inverse runs the same steps backwards with
 // conjugate twiddles.  No block-wide barrier is involved: one warp owns the
 // whole line.
 #pragma once
@@ -20,13 +20,24 @@ __device__ __forceinline__ constexpr int brev5(int v)
     return ((v & 1) << 4) | ((v & 2) << 2) | (v & 4) | ((v & 8) >> 2) | ((v & 16) >> 4);
 }
 
-// Twiddle table layout in shared memory: entry e of w_1024^e at e + (e >> 4),
-// which spreads the strided lookups w_1024^(lane * c) over the banks.
-__device__ __forceinline__ int tw1024_slot(int e) { return e + (e >> 4); }
+// Twiddle tables in shared memory (TW1024_SLOTS entries reserved for either):
+//  * rows: w_1024^(c b) at c * 32 + b (c, b < 32), so the lookup of one c by
+//    the 32 lanes (b = lane) reads one contiguous row.  The plan keeps the
+//    same table in global memory right after its length-lmax twiddles, so
+//    filling the shared copy is a contiguous read.
+//  * slots: w_1024^e at e + (e >> 4), filled from the plan's length-lmax
+//    table at stride lmax / 1024.
 constexpr int TW1024_SLOTS = 1024 + 64;
 
 template <typename C>
-__device__ __forceinline__ void load_tw1024(C* tws, const C* __restrict__ tw_g, int shift)
+__device__ __forceinline__ void load_tw1024(C* tws, const C* __restrict__ tw_g, int lmax)
+{
+    const C* src = tw_g + lmax;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) tws[i] = src[i];
+}
+__device__ __forceinline__ int tw1024_slot(int e) { return e + (e >> 4); }
+template <typename C>
+__device__ __forceinline__ void load_tw1024_slots(C* tws, const C* __restrict__ tw_g, int shift)
 {
     for (int e = threadIdx.x; e < 1024; e += blockDim.x) tws[tw1024_slot(e)] = tw_g[e << shift];
 }
@@ -40,7 +51,7 @@ __device__ __forceinline__ void warp_fft1024_fwd(C (&v)[32], C* tile, const C* t
 #pragma unroll
     for (int pos = 0; pos < 32; pos++) {
         const int c = brev5(pos);
-        const C t = c_mul(v[pos], tws[tw1024_slot(lane * c)]);
+        const C t = c_mul(v[pos], tws[c * 32 + lane]);
         tile[c * 32 + (lane ^ c)] = t;  // row c, column lane
     }
     __syncwarp();
@@ -51,14 +62,15 @@ __device__ __forceinline__ void warp_fft1024_fwd(C (&v)[32], C* tile, const C* t
 }
 
 // Inverse (unscaled).  In: v[brev5(d)] = Z[lane + 32 d].  Out: v[a] = z[32 a + lane].
-template <typename C>
+// ROWTAB: tws holds the row table, else the slot table.
+template <typename C, bool ROWTAB = true>
 __device__ __forceinline__ void warp_fft1024_inv(C (&v)[32], C* tile, const C* tws)
 {
     const int lane = threadIdx.x & 31;
     reg_fft<32, 1>(v);  // v[b] = sum_d Z[lane + 32 d] w_32^(-b d)
 #pragma unroll
     for (int b = 0; b < 32; b++) {
-        const C t = c_mulc(v[b], tws[tw1024_slot(lane * b)]);
+        const C t = c_mulc(v[b], ROWTAB ? tws[b * 32 + lane] : tws[tw1024_slot(lane * b)]);
         tile[b * 32 + (lane ^ b)] = t;  // row b, column c = lane
     }
     __syncwarp();
