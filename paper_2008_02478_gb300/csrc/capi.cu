@@ -1171,15 +1171,14 @@ int boris_llg_run_host(boris_plan p, float* m_host, const boris_llg_params* prm,
 {
     if (!p || !m_host || !prm) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
     if (p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan");
-    if (nsteps < 0 || prm->method != BORIS_RK4) return fail(BORIS_ERR_INVALID_ARG, "RK4 with nsteps >= 0 only");
+    if (nsteps < 0 || prm->method != BORIS_RK4 || !(dt > 0))
+        return fail(BORIS_ERR_INVALID_ARG, "RK4 with nsteps >= 0 and dt > 0 only");
     const size_t vb = 3 * ncell(p) * sizeof(float);
     int rc;
     if (!p->m_dev_e2e && (rc = dev_alloc(p, &p->m_dev_e2e, vb))) return rc;
     CUDA_TRY(cudaMemcpyAsync(p->m_dev_e2e, m_host, vb, cudaMemcpyHostToDevice, p->stream));
-    for (int i = 0; i < nsteps; i++) {
-        double h = dt;
-        if ((rc = boris_llg_step(p, (float*)p->m_dev_e2e, prm, &h))) return rc;
-    }
+    // the steps replay the plan's CUDA graph captured for the device copy
+    if (nsteps > 0 && (rc = boris_llg_run_graph(p, (float*)p->m_dev_e2e, prm, dt, nsteps))) return rc;
     CUDA_TRY(cudaMemcpyAsync(m_host, p->m_dev_e2e, vb, cudaMemcpyDeviceToHost, p->stream));
     CUDA_TRY(cudaStreamSynchronize(p->stream));
     return BORIS_OK;

@@ -128,6 +128,27 @@ def test_graph_replay_equals_step_calls(n):
     assert torch.equal(a, b)
 
 
+def test_host_buffer_steps_equal_device_steps():
+    """boris_llg_run_host (pinned host state copied in, steps, copied back) takes
+    the same kernels as the device-resident steps: bit-identical states."""
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import LLGParams, Plan
+    n, h = (48, 20, 3), (3e-9, 3e-9, 3e-9)
+    m0 = inputs.random_unit(*n, seed=9)
+    p = Plan(*n, *h)
+    prm = LLGParams(Ms=8e5, A=1.3e-11, alpha=0.02, Hext=(2e4, 0.0, 1e4))
+    a = to_dev(torch, m0)
+    for _ in range(4):
+        p.llg_step(a, prm, 1e-13)
+    host = torch.tensor(m0, dtype=torch.float32).pin_memory()
+    p.llg_run_host(host, prm, 1e-13, 1)
+    p.llg_run_host(host, prm, 1e-13, 3)  # reuses the captured graph
+    torch.cuda.synchronize()
+    assert torch.equal(a.cpu(), host)
+    p.llg_run_host(host, prm, 1e-13, 0)  # copies in and out only
+    assert torch.equal(a.cpu(), host)
+
+
 # Meshes of 257..512 cells along x (transform length 1024) can run the
 # inverse x transform and the RK4 stage as one kernel in FP32; the ragged cases
 # leave a partial group of 8 rows at the top of each plane.
