@@ -404,6 +404,127 @@ def run_reference(args, rank):
     return 0
 
 
+# FP32 FMA throughput microbenchmark: eight independent FMA chains per thread,
+# scalar (fmaf) and packed (__ffma2_rn) forms; compiled with nvcc at run time.
+FMA_SRC = r"""
+#include <cuda_runtime.h>
+extern "C" __global__ void fma_scalar(float* out, int iters, float a, float b)
+{
+    float x[8];
+    for (int k = 0; k < 8; k++) x[k] = threadIdx.x * 1e-7f + k;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = fmaf(x[k], a, b);
+    }
+    float s = 0.f;
+    for (int k = 0; k < 8; k++) s += x[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+extern "C" __global__ void fma_packed(float* out, int iters, float a, float b)
+{
+    float2 x[8];
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+    for (int k = 0; k < 8; k++) x[k] = make_float2(threadIdx.x * 1e-7f + k, k + 0.5f);
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) x[k] = __ffma2_rn(x[k], a2, b2);
+    }
+    float s = 0.f;
+    for (int k = 0; k < 8; k++) s += x[k].x + x[k].y;
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+extern "C" int fma_run(int packed, int blocks, int threads, int iters, float* ms)
+{
+    float* out;
+    if (cudaMalloc(&out, (size_t)blocks * threads * sizeof(float)) != cudaSuccess) return 1;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int rep = 0; rep < 2; rep++) {  // the first launch warms up
+        cudaEventRecord(e0);
+        if (packed) fma_packed<<<blocks, threads>>>(out, iters, 0.999999f, 1e-6f);
+        else fma_scalar<<<blocks, threads>>>(out, iters, 0.999999f, 1e-6f);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+    }
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int rc = cudaGetLastError() != cudaSuccess;
+    cudaFree(out);
+    return rc;
+}
+"""
+
+
+def fma_peak():
+    """Measured FP32 FMA throughput (TFLOP/s) of the scalar and packed forms."""
+    import ctypes
+    import subprocess
+    import tempfile
+
+    import torch
+    from paper_2008_02478_gb300 import build as bld
+    d = tempfile.mkdtemp(prefix="fma_peak_")
+    src, lib = os.path.join(d, "fma.cu"), os.path.join(d, "fma.so")
+    with open(src, "w") as f:
+        f.write(FMA_SRC)
+    subprocess.run([bld.nvcc(), *bld.ARCH, "-O3", "-shared", "-Xcompiler", "-fPIC", "-o", lib, src], check=True)
+    torch.cuda.init()
+    so = ctypes.CDLL(lib)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, threads, iters = nsm * 8, 256, 1 << 16
+    out = {}
+    for name, packed in (("scalar", 0), ("packed", 1)):
+        ms = ctypes.c_float()
+        if so.fma_run(packed, blocks, threads, iters, ctypes.byref(ms)):
+            raise RuntimeError("FMA microbenchmark failed")
+        lanes = 2 if packed else 1
+        flops = 2.0 * 8 * lanes * iters * blocks * threads
+        out[name] = flops / (ms.value * 1e-3) / 1e12
+    return {"fp32_fma_tflops": out, "sms": nsm, "kernel": "8 independent FMA chains per thread, "
+            f"{blocks} CTAs x {threads} threads x {iters} iterations"}
+
+
+def fig11_sweep(torch, Plan, LLGParams, steps):
+    """Fig. 11-shaped sweep: demag evaluation time and RK4 cell-steps/s for
+    nz in {1, 2, 4, 8, 16, 32} and N = 2^14 .. 2^23 cells, nx = ny (ny = 2 nx
+    where N / nz is not a square), 4 nm cells, perpendicular applied field."""
+    import numpy as np
+    from paper_2008_02478_gb300 import inputs
+    rows = []
+    prm = LLGParams(Ms=MS, A=A_EX, alpha=ALPHA, Hext=HEXT)
+    for nz in (1, 2, 4, 8, 16, 32):
+        for k in range(14, 24):
+            plane = (1 << k) // nz
+            lg = plane.bit_length() - 1
+            nx = 1 << (lg // 2)
+            ny = plane // nx
+            try:
+                plan = Plan(nx, ny, nz, *CELL)
+            except Exception as e:  # noqa: BLE001 - reported per size
+                rows.append({"nz": nz, "nx": nx, "ny": ny, "cells": nx * ny * nz, "error": str(e)[:80]})
+                continue
+            m0 = inputs.random_unit(nx, ny, nz, SEED)
+            M = torch.tensor(MS * m0, dtype=torch.float32, device="cuda")
+            H = torch.empty_like(M)
+            for _ in range(3):
+                plan.apply(M, H)
+            K = max(4, min(200, int(2e8 // (nx * ny * nz))))
+            t_eval = time_demag(torch, plan, M, H, K) / K
+            m = torch.tensor(m0, dtype=torch.float32, device="cuda")
+            plan.llg_run_graph(m, prm, DT, 3)
+            Ks = max(2, K // 4)
+            t_step = time_graph(torch, plan, m, prm, Ks) / Ks
+            rows.append({"nz": nz, "nx": nx, "ny": ny, "cells": nx * ny * nz, "ms_per_eval": 1e3 * t_eval,
+                         "demag_evals_per_s": 1.0 / t_eval, "ms_per_step": 1e3 * t_step,
+                         "cell_steps_per_s": nx * ny * nz / t_step, "yz_schedule": list(plan.schedule())})
+            plan.close()
+            del M, H, m
+            torch.cuda.empty_cache()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,6 +534,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="only the Fig. 11-shaped size sweep and the FP32 FMA peak (one JSON line)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -429,6 +552,12 @@ def main():
     from paper_2008_02478_gb300.binding import LLGParams, Plan
     bld.build()
     torch.cuda.set_device(local)
+    if args.sweep:
+        if rank == 0:
+            rows = fig11_sweep(torch, Plan, LLGParams, args.steps)
+            print(json.dumps({"sweep": "Fig. 11 shape: demag evaluation time and RK4 cell-steps/s vs N and nz, FP32",
+                              "data": "synthetic", "cell": CELL, "rows": rows, "fma_peak": fma_peak()}))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

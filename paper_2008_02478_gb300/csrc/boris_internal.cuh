@@ -98,6 +98,21 @@ template <typename T>
 cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
                           cudaStream_t st, bool forward);
 cudaError_t upload_twiddles_fast();
+// Length-2048 passes (meshes of 513..1024 cells along the axis) from the
+// warp-held length-1024 transform (fft2048.cu).
+template <typename T>
+bool x2048_ok(const Geometry& g, int max_smem);
+template <typename T>
+bool y2048_ok(const Geometry& g, int max_smem);
+template <typename T>
+cudaError_t launch_x_r2c_2048(const Geometry& g, const T* M, const T* ms_map, T ms_scale, typename Cx<T>::t* X,
+                              const typename Cx<T>::t* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_x_c2r_2048(const Geometry& g, const typename Cx<T>::t* X, T* H, const typename Cx<T>::t* tw,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_y_2048(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
+                          cudaStream_t st, bool forward);
 // FP32 x complex-to-real (px = 1024, ny even) with the half-spectrum block
 // fetched by tensor copies; a wait that gives up latches BORIS_ERR_TIMEOUT in *status
 bool x_c2r_tma_ok(const Geometry& g, int max_smem);

@@ -326,6 +326,7 @@ cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>
     dim3 ygrid((lines + YG - 1) / YG, g.nkx);
     cudaError_t e = cudaSuccess;
     if (part != 1 && y1024_ok<T>(g, 227 * 1024)) return launch_y_1024<T>(g, X, Y, tw, st, part == 0);
+    if (part != 1 && y2048_ok<T>(g, 227 * 1024)) return launch_y_2048<T>(g, X, Y, tw, st, part == 0);
     if (part == 0) {
         e = cudaFuncSetAttribute(y_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys);
         if (e != cudaSuccess) return e;

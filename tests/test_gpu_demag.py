@@ -28,6 +28,11 @@ CASES = [
     ((512, 300, 2), (4e-9, 4e-9, 4e-9)),    # full 512-cell rows
     ((280, 30, 3), (3e-9, 2e-9, 2e-9)),     # length-1024 x pass, ragged 16-row blocks
     ((300, 17, 2), (3e-9, 3e-9, 3e-9)),     # odd ny: the x inverse pass without tensor copies
+    ((600, 21, 2), (3e-9, 3e-9, 3e-9)),     # length-2048 x passes, ragged 8-row blocks
+    ((1024, 9, 1), (2e-9, 2e-9, 3e-9)),     # full 1024-cell rows, 2D mode
+    ((601, 6, 3), (2e-9, 3e-9, 2e-9)),      # odd row length on the length-2048 x passes
+    ((24, 700, 3), (3e-9, 2e-9, 2e-9)),     # length-2048 y passes
+    ((520, 530, 2), (4e-9, 4e-9, 4e-9)),    # both in-plane axes of length 2048
 ]
 
 
@@ -54,6 +59,7 @@ SCHEDULE_MESHES = [
     ((18, 33, 9), (2e-9, 1e-9, 2e-9)),    # pz = 32, ragged nz and ny
     ((12, 40, 3), (3e-9, 2e-9, 1e-9)),    # pz = 8, py = 128
     ((24, 20, 32), (2e-9, 2e-9, 2e-9)),   # pz = 64, nz = 32 filling the z tile (no cropped rows)
+    ((12, 600, 4), (2e-9, 2e-9, 2e-9)),   # py = 2048: the length-2048 y passes of the split schedule
 ]
 # (kind, CTAs per cluster or per SM, threads | "tma1"/"tma2" for the bulk-copy z
 # convolution | "tma3" for the residue-split z convolution)
