@@ -113,6 +113,20 @@ cudaError_t launch_x_c2r_2048(const Geometry& g, const typename Cx<T>::t* X, T* 
 template <typename T>
 cudaError_t launch_y_2048(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
                           cudaStream_t st, bool forward);
+// Length-4096 passes (meshes of 1025..2048 cells along the axis), fft4096.cu.
+template <typename T>
+bool x4096_ok(const Geometry& g, int max_smem);
+template <typename T>
+bool y4096_ok(const Geometry& g, int max_smem);
+template <typename T>
+cudaError_t launch_x_r2c_4096(const Geometry& g, const T* M, const T* ms_map, T ms_scale, typename Cx<T>::t* X,
+                              const typename Cx<T>::t* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_x_c2r_4096(const Geometry& g, const typename Cx<T>::t* X, T* H, const typename Cx<T>::t* tw,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_y_4096(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
+                          cudaStream_t st, bool forward);
 // FP32 x complex-to-real (px = 1024, ny even) with the half-spectrum block
 // fetched by tensor copies; a wait that gives up latches BORIS_ERR_TIMEOUT in *status
 bool x_c2r_tma_ok(const Geometry& g, int max_smem);

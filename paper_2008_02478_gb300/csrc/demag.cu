@@ -362,6 +362,7 @@ cudaError_t launch_x_r2c(const Geometry& g, const T* M, const T* ms_map, T ms_sc
 {
     if (x1024_ok<T>(g, 227 * 1024)) return launch_x_r2c_1024<T>(g, M, ms_map, ms_scale, X, tw, st);
     if (x2048_ok<T>(g, 227 * 1024)) return launch_x_r2c_2048<T>(g, M, ms_map, ms_scale, X, tw, st);
+    if (x4096_ok<T>(g, 227 * 1024)) return launch_x_r2c_4096<T>(g, M, ms_map, ms_scale, X, tw, st);
     switch (xrow_tile<T>(g)) {
     case 16: return launch_r2c_ty<T, 16>(g, M, ms_map, ms_scale, X, tw, st);
     case 8: return launch_r2c_ty<T, 8>(g, M, ms_map, ms_scale, X, tw, st);
@@ -390,6 +391,7 @@ cudaError_t launch_x_c2r(const Geometry& g, const typename Cx<T>::t* X, T* H,
     }
     if (x1024_ok<T>(g, 227 * 1024)) return launch_x_c2r_1024<T>(g, X, H, tw, st);
     if (x2048_ok<T>(g, 227 * 1024)) return launch_x_c2r_2048<T>(g, X, H, tw, st);
+    if (x4096_ok<T>(g, 227 * 1024)) return launch_x_c2r_4096<T>(g, X, H, tw, st);
     switch (xrow_tile<T>(g)) {
     case 16: return launch_c2r_ty<T, 16>(g, X, H, tw, st);
     case 8: return launch_c2r_ty<T, 8>(g, X, H, tw, st);

@@ -291,7 +291,9 @@ bool split_supported(const Geometry& g, int max_smem)
 {
     const int hz = g.pz / 2;
     if (!(g.pz == 1 || (hz >= 2 && hz <= 32))) return false;
-    if (split_y_smem<T>(g) > (size_t)max_smem) return false;
+    // the y passes: warp-held transforms of length 1024 / 2048 / 4096, else shared-memory passes
+    const bool ywarp = y1024_ok<T>(g, max_smem) || y2048_ok<T>(g, max_smem) || y4096_ok<T>(g, max_smem);
+    if (!ywarp && split_y_smem<T>(g) > (size_t)max_smem) return false;
     if (g.pz > 1 && split_z_smem<T>(g) > (size_t)max_smem) return false;
     return true;
 }
@@ -327,6 +329,7 @@ cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>
     cudaError_t e = cudaSuccess;
     if (part != 1 && y1024_ok<T>(g, 227 * 1024)) return launch_y_1024<T>(g, X, Y, tw, st, part == 0);
     if (part != 1 && y2048_ok<T>(g, 227 * 1024)) return launch_y_2048<T>(g, X, Y, tw, st, part == 0);
+    if (part != 1 && y4096_ok<T>(g, 227 * 1024)) return launch_y_4096<T>(g, X, Y, tw, st, part == 0);
     if (part == 0) {
         e = cudaFuncSetAttribute(y_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ys);
         if (e != cudaSuccess) return e;

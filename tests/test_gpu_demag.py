@@ -33,6 +33,10 @@ CASES = [
     ((601, 6, 3), (2e-9, 3e-9, 2e-9)),      # odd row length on the length-2048 x passes
     ((24, 700, 3), (3e-9, 2e-9, 2e-9)),     # length-2048 y passes
     ((520, 530, 2), (4e-9, 4e-9, 4e-9)),    # both in-plane axes of length 2048
+    ((1100, 9, 2), (2e-9, 2e-9, 3e-9)),     # length-4096 x passes, ragged 4-row blocks
+    ((2048, 4, 1), (2e-9, 2e-9, 2e-9)),     # full 2048-cell rows, 2D mode
+    ((1301, 6, 2), (2e-9, 3e-9, 2e-9)),     # odd row length on the length-4096 x passes
+    ((10, 1500, 2), (3e-9, 2e-9, 2e-9)),    # length-4096 y passes
 ]
 
 
@@ -60,6 +64,7 @@ SCHEDULE_MESHES = [
     ((12, 40, 3), (3e-9, 2e-9, 1e-9)),    # pz = 8, py = 128
     ((24, 20, 32), (2e-9, 2e-9, 2e-9)),   # pz = 64, nz = 32 filling the z tile (no cropped rows)
     ((12, 600, 4), (2e-9, 2e-9, 2e-9)),   # py = 2048: the length-2048 y passes of the split schedule
+    ((6, 1300, 3), (2e-9, 2e-9, 2e-9)),   # py = 4096: the length-4096 y passes of the split schedule
 ]
 # (kind, CTAs per cluster or per SM, threads | "tma1"/"tma2" for the bulk-copy z
 # convolution | "tma3" for the residue-split z convolution)
