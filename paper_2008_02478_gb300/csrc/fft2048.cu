@@ -31,6 +31,9 @@ namespace boris {
 namespace {
 
 constexpr int R1025 = 1025;  // per-warp region stride (complex)
+// y passes: region stride 1032 (8 mod 16), so the interleaved view
+// q[(j & 1) R1032 + (j >> 1)] of 16 consecutive j falls in 16 distinct bank pairs
+constexpr int R1032 = 1032;
 constexpr int XROWS = 8;     // x passes: rows per CTA (one per warp)
 constexpr int YLINES = 4;    // y passes: lines per CTA (two warps each)
 
@@ -168,29 +171,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tws = reinterpret_cast<C*>(smem_raw);
-    C* reg = tws + TW1024_SLOTS;
+    C* reg = tws + TW1024_SLOTS;  // [8 warps][R1032]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lines = 3 * g.nz, ny = g.ny;
     const int kx = blockIdx.y, line = blockIdx.x * YLINES + (warp >> 1), par = warp & 1;
     load_tw1024(tws, tw_g, g.lmax);
     __syncthreads();
-    if (line >= lines) return;
-    const C* src = X + ((size_t)kx * lines + line) * ny;
-    C v[32];
+    const bool act = line < lines;
+    C* mine = reg + warp * R1032;
+    if (act) {
+        const C* src = X + ((size_t)kx * lines + line) * ny;
+        C v[32];
 #pragma unroll
-    for (int a = 0; a < 32; a++) {
-        const int y = 32 * a + lane;
-        v[a] = y < ny ? src[y] : C{T(0), T(0)};
+        for (int a = 0; a < 32; a++) {
+            const int y = 32 * a + lane;
+            v[a] = y < ny ? src[y] : C{T(0), T(0)};
+        }
+        if (par) {
+            const C wl = tw_g[lane << (g.lglmax - 11)];
+#pragma unroll
+            for (int a = 0; a < 32; a++) v[a] = c_mul(v[a], w2048_at(a, wl));
+        }
+        warp_fft1024_fwd(v, mine, tws);
+#pragma unroll
+        for (int pos = 0; pos < 32; pos++) mine[lane + 32 * brev5(pos)] = v[pos];  // Y[2 k + par] at k
     }
-    if (par) {
-        const C wl = tw_g[lane << (g.lglmax - 11)];
-#pragma unroll
-        for (int a = 0; a < 32; a++) v[a] = c_mul(v[a], w2048_at(a, wl));
+    __syncthreads();  // both halves of every line in shared memory
+    if (!act) return;
+    // warp par stores Y[j], j = 1024 par .. 1024 par + 1023, in 256-byte rows
+    const C* q = reg + (warp & ~1) * R1032;
+    C* dst = Y + ((size_t)kx * lines + line) * 2048;
+#pragma unroll 8
+    for (int i = 0; i < 32; i++) {
+        const int j = 1024 * par + 32 * i + lane;
+        dst[j] = q[(j & 1) * R1032 + (j >> 1)];
     }
-    warp_fft1024_fwd(v, reg + warp * R1025, tws);
-    C* dst = Y + ((size_t)kx * lines + line) * 2048 + par;
-#pragma unroll
-    for (int pos = 0; pos < 32; pos++) dst[2 * (lane + 32 * brev5(pos))] = v[pos];
 }
 
 template <typename T>
@@ -201,19 +216,30 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tws = reinterpret_cast<C*>(smem_raw);
-    C* reg = tws + TW1024_SLOTS;
+    C* reg = tws + TW1024_SLOTS;  // [8 warps][R1032]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lines = 3 * g.nz, ny = g.ny;
     const int kx = blockIdx.y, line = blockIdx.x * YLINES + (warp >> 1), par = warp & 1;
     load_tw1024(tws, tw_g, g.lmax);
-    __syncthreads();
     const bool act = line < lines;
-    C* mine = reg + warp * R1025;
+    C* q = reg + (warp & ~1) * R1032;  // the line's two regions
+    if (act) {
+        // warp par loads Y[j], j = 1024 par .. 1024 par + 1023, in 256-byte rows;
+        // parity j & 1 goes to region j & 1 at j >> 1
+        const C* src = Y + ((size_t)kx * lines + line) * 2048;
+#pragma unroll 8
+        for (int i = 0; i < 32; i++) {
+            const int j = 1024 * par + 32 * i + lane;
+            q[(j & 1) * R1032 + (j >> 1)] = src[j];
+        }
+    }
+    __syncthreads();  // twiddles and both halves of every line staged
+    C* mine = reg + warp * R1032;
     C v[32];
     if (act) {
-        const C* src = Y + ((size_t)kx * lines + line) * 2048 + par;
 #pragma unroll
-        for (int d = 0; d < 32; d++) v[brev5(d)] = src[2 * (lane + 32 * d)];
+        for (int d = 0; d < 32; d++) v[brev5(d)] = mine[lane + 32 * d];
+        __syncwarp();
         warp_fft1024_inv(v, mine, tws);
         if (par) {
             const C wl = tw_g[lane << (g.lglmax - 11)];
@@ -225,7 +251,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     }
     __syncthreads();  // both halves of every line published
     if (!act) return;
-    const C* other = reg + (warp ^ 1) * R1025;
+    const C* other = reg + (warp ^ 1) * R1032;
     C* dst = X + ((size_t)kx * lines + line) * ny;
     // the even warp stores n < 512, the odd one 512 <= n < 1024
     auto store = [&](auto first) {
@@ -252,7 +278,7 @@ size_t smem_x_c2r_2048()
 template <typename T>
 size_t smem_y_2048()
 {
-    return ((size_t)TW1024_SLOTS + 8 * (size_t)R1025) * sizeof(typename Cx<T>::t);
+    return ((size_t)TW1024_SLOTS + 8 * (size_t)R1032) * sizeof(typename Cx<T>::t);
 }
 
 }  // namespace

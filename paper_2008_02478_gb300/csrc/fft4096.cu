@@ -30,6 +30,9 @@ namespace {
 
 constexpr int TWR = 1024;    // the row twiddle table only (no slot layout here)
 constexpr int R1025 = 1025;  // per-warp region stride (complex)
+// y passes: region stride 1028 (4 mod 16), so the interleaved view
+// q[(j & 3) R1028 + (j >> 2)] of 16 consecutive j falls in 16 distinct bank pairs
+constexpr int R1028 = 1028;
 constexpr int XROWS = 4;     // x passes: rows per CTA (two warps each)
 constexpr int YLINES = 2;    // y passes: lines per CTA (four warps each)
 
@@ -45,7 +48,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tws = reinterpret_cast<C*>(smem_raw);
     C* w128s = tws + TWR;  // w^(32 e) = w_128^e
-    C* reg = w128s + 128;
+    C* reg = w128s + 128;  // [8 warps][R1028]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lines = 3 * g.nz, ny = g.ny;
     const int kx = blockIdx.y, line = blockIdx.x * YLINES + (warp >> 2), r = warp & 3;
@@ -53,25 +56,37 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     load_tw1024(tws, tw_g, g.lmax);
     if (threadIdx.x < 128) w128s[threadIdx.x] = tw_g[(32 * threadIdx.x) << sh];
     __syncthreads();
-    if (line >= lines) return;
-    const C* src = X + ((size_t)kx * lines + line) * ny;
-    const C wlr = tw_g[(r * lane) << sh];  // w^(r lane)
-    // (-i)^r = (cr, ci)
-    const T cr = r == 0 ? T(1) : r == 2 ? T(-1) : T(0);
-    const T ci = r == 1 ? T(-1) : r == 3 ? T(1) : T(0);
-    C v[32];
+    const bool act = line < lines;
+    C* mine = reg + warp * R1028;
+    if (act) {
+        const C* src = X + ((size_t)kx * lines + line) * ny;
+        const C wlr = tw_g[(r * lane) << sh];  // w^(r lane)
+        // (-i)^r = (cr, ci)
+        const T cr = r == 0 ? T(1) : r == 2 ? T(-1) : T(0);
+        const T ci = r == 1 ? T(-1) : r == 3 ? T(1) : T(0);
+        C v[32];
 #pragma unroll
-    for (int a = 0; a < 32; a++) {
-        const int m = 32 * a + lane;
-        const C lo = m < ny ? src[m] : C{T(0), T(0)};
-        const C hi = m + 1024 < ny ? src[m + 1024] : C{T(0), T(0)};
-        const C s{lo.x + cr * hi.x - ci * hi.y, lo.y + cr * hi.y + ci * hi.x};
-        v[a] = c_mul(s, c_mul(w128s[(r * a) & 127], wlr));
+        for (int a = 0; a < 32; a++) {
+            const int m = 32 * a + lane;
+            const C lo = m < ny ? src[m] : C{T(0), T(0)};
+            const C hi = m + 1024 < ny ? src[m + 1024] : C{T(0), T(0)};
+            const C s{lo.x + cr * hi.x - ci * hi.y, lo.y + cr * hi.y + ci * hi.x};
+            v[a] = c_mul(s, c_mul(w128s[(r * a) & 127], wlr));
+        }
+        warp_fft1024_fwd(v, mine, tws);
+#pragma unroll
+        for (int pos = 0; pos < 32; pos++) mine[lane + 32 * brev5(pos)] = v[pos];  // Y[4 k + r] at k
     }
-    warp_fft1024_fwd(v, reg + warp * R1025, tws);
-    C* dst = Y + ((size_t)kx * lines + line) * 4096 + r;
-#pragma unroll
-    for (int pos = 0; pos < 32; pos++) dst[4 * (lane + 32 * brev5(pos))] = v[pos];
+    __syncthreads();  // all four residues of every line in shared memory
+    if (!act) return;
+    // warp r stores Y[j], j = 1024 r .. 1024 r + 1023, in 256-byte rows
+    const C* q = reg + (warp & ~3) * R1028;
+    C* dst = Y + ((size_t)kx * lines + line) * 4096;
+#pragma unroll 8
+    for (int i = 0; i < 32; i++) {
+        const int j = 1024 * r + 32 * i + lane;
+        dst[j] = q[(j & 3) * R1028 + (j >> 2)];
+    }
 }
 
 template <typename T>
@@ -83,21 +98,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* tws = reinterpret_cast<C*>(smem_raw);
     C* w128s = tws + TWR;
-    C* reg = w128s + 128;
+    C* reg = w128s + 128;  // [8 warps][R1028]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int lines = 3 * g.nz, ny = g.ny;
     const int kx = blockIdx.y, line = blockIdx.x * YLINES + (warp >> 2), r = warp & 3;
     const int sh = g.lglmax - 12;
     load_tw1024(tws, tw_g, g.lmax);
     if (threadIdx.x < 128) w128s[threadIdx.x] = tw_g[(32 * threadIdx.x) << sh];
-    __syncthreads();
     const bool act = line < lines;
-    C* mine = reg + warp * R1025;
+    C* q = reg + (warp & ~3) * R1028;  // the line's four regions
     if (act) {
-        const C* src = Y + ((size_t)kx * lines + line) * 4096 + r;
-        C v[32];
+        // warp r loads Y[j], j = 1024 r .. 1024 r + 1023, in 256-byte rows; residue
+        // j & 3 goes to region j & 3 at j >> 2
+        const C* src = Y + ((size_t)kx * lines + line) * 4096;
+#pragma unroll 8
+        for (int i = 0; i < 32; i++) {
+            const int j = 1024 * r + 32 * i + lane;
+            q[(j & 3) * R1028 + (j >> 2)] = src[j];
+        }
+    }
+    __syncthreads();  // twiddles and every line's residues staged
+    C* mine = reg + warp * R1028;
+    C v[32];
+    if (act) {
 #pragma unroll
-        for (int d = 0; d < 32; d++) v[brev5(d)] = src[4 * (lane + 32 * d)];
+        for (int d = 0; d < 32; d++) v[brev5(d)] = mine[lane + 32 * d];
+        __syncwarp();
         warp_fft1024_inv(v, mine, tws);
         const C wlr = tw_g[(r * lane) << sh];
 #pragma unroll
@@ -105,13 +131,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
     }
     __syncthreads();  // all four residues of every line published
     if (!act) return;
-    const C* q = reg + (warp & ~3) * R1025;  // the line's four regions
     C* dst = X + ((size_t)kx * lines + line) * ny;
     // warp r stores m = 256 r + 32 i + lane and m + 1024
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const int m = 256 * r + 32 * i + lane;
-        const C v0 = q[m], v1 = q[R1025 + m], v2 = q[2 * R1025 + m], v3 = q[3 * R1025 + m];
+        const C v0 = q[m], v1 = q[R1028 + m], v2 = q[2 * R1028 + m], v3 = q[3 * R1028 + m];
         const C s02 = c_add(v0, v2), d02 = c_sub(v0, v2), s13 = c_add(v1, v3), d13 = c_sub(v1, v3);
         if (m < ny) dst[m] = c_add(s02, s13);
         if (m + 1024 < ny) dst[m + 1024] = C{d02.x - d13.y, d02.y + d13.x};
@@ -261,7 +286,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1)
 template <typename T>
 size_t smem_y_4096()
 {
-    return ((size_t)TWR + 128 + 8 * (size_t)R1025) * sizeof(typename Cx<T>::t);
+    return ((size_t)TWR + 128 + 8 * (size_t)R1028) * sizeof(typename Cx<T>::t);
 }
 template <typename T>
 size_t smem_x_r2c_4096()
