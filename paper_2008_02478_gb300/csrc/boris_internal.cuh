@@ -98,6 +98,21 @@ template <typename T>
 cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
                           cudaStream_t st, bool forward);
 cudaError_t upload_twiddles_fast();
+// Length-512 passes (meshes of 129..256 cells along the axis), two lines per
+// warp through the length-1024 warp transform (fft512.cu).
+template <typename T>
+bool x512_ok(const Geometry& g, int max_smem);
+template <typename T>
+bool y512_ok(const Geometry& g, int max_smem);
+template <typename T>
+cudaError_t launch_x_r2c_512(const Geometry& g, const T* M, const T* ms_map, T ms_scale, typename Cx<T>::t* X,
+                             const typename Cx<T>::t* tw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_x_c2r_512(const Geometry& g, const typename Cx<T>::t* X, T* H, const typename Cx<T>::t* tw,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t launch_y_512(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
+                         cudaStream_t st, bool forward);
 // Length-2048 passes (meshes of 513..1024 cells along the axis) from the
 // warp-held length-1024 transform (fft2048.cu).
 template <typename T>

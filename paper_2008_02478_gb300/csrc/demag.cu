@@ -361,6 +361,7 @@ cudaError_t launch_x_r2c(const Geometry& g, const T* M, const T* ms_map, T ms_sc
                          typename Cx<T>::t* X, const typename Cx<T>::t* tw, cudaStream_t st)
 {
     if (x1024_ok<T>(g, 227 * 1024)) return launch_x_r2c_1024<T>(g, M, ms_map, ms_scale, X, tw, st);
+    if (x512_ok<T>(g, 227 * 1024)) return launch_x_r2c_512<T>(g, M, ms_map, ms_scale, X, tw, st);
     if (x2048_ok<T>(g, 227 * 1024)) return launch_x_r2c_2048<T>(g, M, ms_map, ms_scale, X, tw, st);
     if (x4096_ok<T>(g, 227 * 1024)) return launch_x_r2c_4096<T>(g, M, ms_map, ms_scale, X, tw, st);
     switch (xrow_tile<T>(g)) {
@@ -390,6 +391,7 @@ cudaError_t launch_x_c2r(const Geometry& g, const typename Cx<T>::t* X, T* H,
         if (status && x_c2r_tma_ok(g, 227 * 1024)) return launch_x_c2r_1024_tma(g, X, H, tw, status, limit_ns, st);
     }
     if (x1024_ok<T>(g, 227 * 1024)) return launch_x_c2r_1024<T>(g, X, H, tw, st);
+    if (x512_ok<T>(g, 227 * 1024)) return launch_x_c2r_512<T>(g, X, H, tw, st);
     if (x2048_ok<T>(g, 227 * 1024)) return launch_x_c2r_2048<T>(g, X, H, tw, st);
     if (x4096_ok<T>(g, 227 * 1024)) return launch_x_c2r_4096<T>(g, X, H, tw, st);
     switch (xrow_tile<T>(g)) {

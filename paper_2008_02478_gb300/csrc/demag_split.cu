@@ -292,7 +292,8 @@ bool split_supported(const Geometry& g, int max_smem)
     const int hz = g.pz / 2;
     if (!(g.pz == 1 || (hz >= 2 && hz <= 32))) return false;
     // the y passes: warp-held transforms of length 1024 / 2048 / 4096, else shared-memory passes
-    const bool ywarp = y1024_ok<T>(g, max_smem) || y2048_ok<T>(g, max_smem) || y4096_ok<T>(g, max_smem);
+    const bool ywarp = y512_ok<T>(g, max_smem) || y1024_ok<T>(g, max_smem) || y2048_ok<T>(g, max_smem) ||
+                       y4096_ok<T>(g, max_smem);
     if (!ywarp && split_y_smem<T>(g) > (size_t)max_smem) return false;
     if (g.pz > 1 && split_z_smem<T>(g) > (size_t)max_smem) return false;
     return true;
@@ -328,6 +329,7 @@ cudaError_t launch_split(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>
     dim3 ygrid((lines + YG - 1) / YG, g.nkx);
     cudaError_t e = cudaSuccess;
     if (part != 1 && y1024_ok<T>(g, 227 * 1024)) return launch_y_1024<T>(g, X, Y, tw, st, part == 0);
+    if (part != 1 && y512_ok<T>(g, 227 * 1024)) return launch_y_512<T>(g, X, Y, tw, st, part == 0);
     if (part != 1 && y2048_ok<T>(g, 227 * 1024)) return launch_y_2048<T>(g, X, Y, tw, st, part == 0);
     if (part != 1 && y4096_ok<T>(g, 227 * 1024)) return launch_y_4096<T>(g, X, Y, tw, st, part == 0);
     if (part == 0) {

@@ -33,6 +33,9 @@ CASES = [
     ((601, 6, 3), (2e-9, 3e-9, 2e-9)),      # odd row length on the length-2048 x passes
     ((24, 700, 3), (3e-9, 2e-9, 2e-9)),     # length-2048 y passes
     ((520, 530, 2), (4e-9, 4e-9, 4e-9)),    # both in-plane axes of length 2048
+    ((200, 45, 2), (3e-9, 3e-9, 3e-9)),     # length-512 x passes (two packed lines per warp), ragged 32-row blocks
+    ((131, 7, 3), (2e-9, 3e-9, 2e-9)),      # shortest row of the length-512 passes, odd lengths
+    ((40, 250, 3), (3e-9, 2e-9, 2e-9)),     # length-512 y passes
     ((1100, 9, 2), (2e-9, 2e-9, 3e-9)),     # length-4096 x passes, ragged 4-row blocks
     ((2048, 4, 1), (2e-9, 2e-9, 2e-9)),     # full 2048-cell rows, 2D mode
     ((1301, 6, 2), (2e-9, 3e-9, 2e-9)),     # odd row length on the length-4096 x passes
@@ -65,6 +68,7 @@ SCHEDULE_MESHES = [
     ((24, 20, 32), (2e-9, 2e-9, 2e-9)),   # pz = 64, nz = 32 filling the z tile (no cropped rows)
     ((12, 600, 4), (2e-9, 2e-9, 2e-9)),   # py = 2048: the length-2048 y passes of the split schedule
     ((6, 1300, 3), (2e-9, 2e-9, 2e-9)),   # py = 4096: the length-4096 y passes of the split schedule
+    ((10, 170, 5), (2e-9, 2e-9, 2e-9)),   # py = 512: the length-512 y passes, odd number of lines
 ]
 # (kind, CTAs per cluster or per SM, threads | "tma1"/"tma2" for the bulk-copy z
 # convolution | "tma3" for the residue-split z convolution)
