@@ -36,6 +36,9 @@ CASES = [
     ((200, 45, 2), (3e-9, 3e-9, 3e-9)),     # length-512 x passes (two packed lines per warp), ragged 32-row blocks
     ((131, 7, 3), (2e-9, 3e-9, 2e-9)),      # shortest row of the length-512 passes, odd lengths
     ((40, 250, 3), (3e-9, 2e-9, 2e-9)),     # length-512 y passes
+    ((100, 70, 3), (3e-9, 3e-9, 3e-9)),     # length-256 x and y passes (four lines per warp), ragged 64-row blocks
+    ((128, 5, 2), (2e-9, 2e-9, 3e-9)),      # full 128-cell rows on the length-256 passes
+    ((65, 9, 1), (2e-9, 3e-9, 2e-9)),       # shortest row of the length-256 passes, 2D mode
     ((1100, 9, 2), (2e-9, 2e-9, 3e-9)),     # length-4096 x passes, ragged 4-row blocks
     ((2048, 4, 1), (2e-9, 2e-9, 2e-9)),     # full 2048-cell rows, 2D mode
     ((1301, 6, 2), (2e-9, 3e-9, 2e-9)),     # odd row length on the length-4096 x passes
@@ -69,6 +72,7 @@ SCHEDULE_MESHES = [
     ((12, 600, 4), (2e-9, 2e-9, 2e-9)),   # py = 2048: the length-2048 y passes of the split schedule
     ((6, 1300, 3), (2e-9, 2e-9, 2e-9)),   # py = 4096: the length-4096 y passes of the split schedule
     ((10, 170, 5), (2e-9, 2e-9, 2e-9)),   # py = 512: the length-512 y passes, odd number of lines
+    ((8, 100, 3), (2e-9, 2e-9, 2e-9)),    # py = 256: the length-256 y passes, 9 lines (a partial warp)
 ]
 # (kind, CTAs per cluster or per SM, threads | "tma1"/"tma2" for the bulk-copy z
 # convolution | "tma3" for the residue-split z convolution)
