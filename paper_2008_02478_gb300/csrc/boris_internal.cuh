@@ -172,6 +172,12 @@ cudaError_t launch_zconv_res(const void* ymap, const void* kmap, const Geometry&
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 cudaError_t upload_twiddles_res();
 cudaError_t launch_zconv_tc(const Geometry& g, float2* Y, const float* K, const float2* tw, bool bf16, cudaStream_t st);
+// Tensor-core z stage on tcgen05 (zconv_tc5.cu): pz = 64, 17 <= nz <= 32, py >= 64; reads the
+// blocked kernel copy K2 (kmap) and the tiles of Y (ymap) by tensor copies
+bool zconv_tc5_supported(const Geometry& g, int max_smem);
+cudaError_t launch_zconv_tc5(const void* ymap, const void* kmap, const Geometry& g, float2* Y, const float2* tw,
+                             bool bf16, int* status, uint32_t extra_tx, unsigned long long limit_ns, int nsm,
+                             cudaStream_t st);
 cudaError_t upload_twiddles_yz_f32();
 cudaError_t upload_twiddles_yz_f64();
 // Candidate schedules of the fused y-z pass that fit this geometry.

@@ -29,6 +29,7 @@ struct boris_plan_s {
     unsigned flags;
     bool f64;
     int tc = 0;  // 0: FP32 z stage; 1: FP16 tensor cores; 2: BF16 tensor cores
+    bool tc5 = false;  // tensor-core z stage on tcgen05 (else the mma.sync form)
     cudaStream_t stream;
     int device;
     YZSchedule yz;
@@ -210,6 +211,15 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
         cudaError_t e = cudaSuccess;
         for (int part = 0; part < 3 && e == cudaSuccess; part++)
             e = timed(p, 5 + part, [&] {
+                if (part == 1 && p->tc && p->tc5) {
+                    if (!p->ymap_ready) {
+                        cudaError_t me = zconv_tma_map(p->g, (float2*)p->Y, p->ymap);
+                        if (me != cudaSuccess) return me;
+                        p->ymap_ready = true;
+                    }
+                    return launch_zconv_tc5(p->ymap, p->kmap, p->g, (float2*)p->Y, (const float2*)p->tw, p->tc == 2,
+                                            p->d_status, p->wait_extra_tx, p->wait_limit_ns, p->nsm, p->stream);
+                }
                 if (part == 1 && p->tc)
                     return launch_zconv_tc(p->g, (float2*)p->Y, (const float*)p->K, (const float2*)p->tw, p->tc == 2,
                                            p->stream);
@@ -691,6 +701,10 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
             return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "tensor-core z stage needs pz = 64 (17 <= nz <= 32)"));
         cand[0] = YZSchedule{2, 2, 0, 0, 0};
         ncand = 1;
+        // tcgen05 form where the tile layout allows it; BORIS_TC_MMASYNC=1 keeps
+        // the mma.sync form (for comparisons)
+        const char* ms = std::getenv("BORIS_TC_MMASYNC");
+        p->tc5 = zconv_tc5_supported(g, max_smem) && !(ms && std::atoi(ms) == 1);
     }
     if (ncand == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));
     // optional override for tests and sweeps: BORIS_YZ_KIND / BORIS_YZ_CLUSTER / BORIS_YZ_THREADS / BORIS_YZ_QC
@@ -767,6 +781,7 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
     }
     bool want_k2 = false;
     for (int i = 0; i < ncand; i++) want_k2 |= cand[i].kind == 2 && cand[i].Qc == 3;
+    want_k2 |= p->tc5;
     if (want_k2) {
         if (dev_alloc(p, &p->K2, zconv_res_k2_bytes(g)) == BORIS_OK) {
             p->k2_bytes = zconv_res_k2_bytes(g);
@@ -774,8 +789,9 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
                 (ce = zconv_res_kmap(g, (float2*)p->K2, p->kmap)) != cudaSuccess)
                 return bail(fail(BORIS_ERR_CUDA, std::string("kernel spectrum copy: ") + cudaGetErrorString(ce)));
         } else {
-            // no room for the column-major copy: drop the schedule that reads it
+            // no room for the column-major copy: drop the schedules that read it
             cudaGetLastError();
+            p->tc5 = false;
             int m = 0;
             for (int i = 0; i < ncand; i++)
                 if (!(cand[i].kind == 2 && cand[i].Qc == 3)) cand[m++] = cand[i];
@@ -787,7 +803,7 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
     if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
     if (ncand > 1 && (rc = autotune_yz(p, cand, ncand))) return bail(rc);
-    if (p->K2 && !(p->yz.kind == 2 && p->yz.Qc == 3)) {
+    if (p->K2 && !(p->yz.kind == 2 && p->yz.Qc == 3) && !p->tc5) {
         cudaFree(p->K2);
         p->K2 = nullptr;
         p->bytes -= p->k2_bytes;
@@ -1301,7 +1317,7 @@ int boris_plan_schedule(boris_plan p, int out[4])
     if (!p || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
     out[0] = p->yz.kind;
     out[1] = p->yz.C;
-    out[2] = p->yz.kind == 2 ? p->yz.Qc : p->yz.threads;
+    out[2] = p->yz.kind == 2 ? (p->tc ? (p->tc5 ? 5 : 4) : p->yz.Qc) : p->yz.threads;
     out[3] = (int)p->yz.smem;
     return BORIS_OK;
 }
