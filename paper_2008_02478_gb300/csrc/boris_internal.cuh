@@ -175,6 +175,8 @@ cudaError_t launch_zconv_tc(const Geometry& g, float2* Y, const float* K, const 
 // Tensor-core z stage on tcgen05 (zconv_tc5.cu): pz = 64, 17 <= nz <= 32, py >= 64; reads the
 // blocked kernel copy K2 (kmap) and the tiles of Y (ymap) by tensor copies
 bool zconv_tc5_supported(const Geometry& g, int max_smem);
+// encodes the stage's tensor maps of Y and of the blocked kernel copy K2 (128 bytes each)
+cudaError_t zconv_tc5_maps(const Geometry& g, float2* Y, float2* K2, void* ymap, void* kmap);
 cudaError_t launch_zconv_tc5(const void* ymap, const void* kmap, const Geometry& g, float2* Y, const float2* tw,
                              bool bf16, int* status, uint32_t extra_tx, unsigned long long limit_ns, int nsm,
                              cudaStream_t st);

@@ -211,15 +211,9 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
         cudaError_t e = cudaSuccess;
         for (int part = 0; part < 3 && e == cudaSuccess; part++)
             e = timed(p, 5 + part, [&] {
-                if (part == 1 && p->tc && p->tc5) {
-                    if (!p->ymap_ready) {
-                        cudaError_t me = zconv_tma_map(p->g, (float2*)p->Y, p->ymap);
-                        if (me != cudaSuccess) return me;
-                        p->ymap_ready = true;
-                    }
+                if (part == 1 && p->tc && p->tc5)
                     return launch_zconv_tc5(p->ymap, p->kmap, p->g, (float2*)p->Y, (const float2*)p->tw, p->tc == 2,
                                             p->d_status, p->wait_extra_tx, p->wait_limit_ns, p->nsm, p->stream);
-                }
                 if (part == 1 && p->tc)
                     return launch_zconv_tc(p->g, (float2*)p->Y, (const float*)p->K, (const float2*)p->tw, p->tc == 2,
                                            p->stream);
@@ -786,8 +780,10 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
         if (dev_alloc(p, &p->K2, zconv_res_k2_bytes(g)) == BORIS_OK) {
             p->k2_bytes = zconv_res_k2_bytes(g);
             if ((ce = zconv_res_build_k2(g, (const float*)p->K, (float2*)p->K2, p->stream)) != cudaSuccess ||
-                (ce = zconv_res_kmap(g, (float2*)p->K2, p->kmap)) != cudaSuccess)
+                (ce = p->tc5 ? zconv_tc5_maps(g, (float2*)p->Y, (float2*)p->K2, p->ymap, p->kmap)
+                             : zconv_res_kmap(g, (float2*)p->K2, p->kmap)) != cudaSuccess)
                 return bail(fail(BORIS_ERR_CUDA, std::string("kernel spectrum copy: ") + cudaGetErrorString(ce)));
+            if (p->tc5) p->ymap_ready = true;
         } else {
             // no room for the column-major copy: drop the schedules that read it
             cudaGetLastError();

@@ -5,36 +5,47 @@
 // paper has no mixed-precision path; this is the reduced-precision variant of
 // the split schedule's z convolution).
 //
-// A tile is 32 consecutive ky columns of one kx plane; operand column
-// n = c * 32 + col (component c, column col), N = 96.  With the tile's data
+// A tile is 16 consecutive ky columns of one kx plane; operand column
+// n = c * 16 + col (component c, column col), N = 48.  With the tile's data
 // D[z][n] (z < nz <= 32, complex):
-//   forward  Mh (128 x 96) = A1 (128 x 64) . [Re D; Im D]
+//   forward  Mh (128 x 48) = A1 (128 x 64) . [Re D; Im D]
 //            rows 0..63 Re Mh[kz], rows 64..127 Im Mh[kz];
 //            A1 = [[C, S], [-S, C]], C = cos, S = sin of 2 pi kz z / 64
 //   multiply H[kz][(c, col)] = sum_d N_cd(kx, ky, kz) Mh[kz][(d, col)]; the
 //            kernel spectrum is real, so the real and imaginary rows are
 //            multiplied independently by the same 3 x 3 matrix
-//   inverse  Hz (64 x 96) = A2 (64 x 128) . [Re H; Im H]
+//   inverse  Hz (64 x 48) = A2 (64 x 128) . [Re H; Im H]
 //            rows 0..31 Re Hz[z], rows 32..63 Im Hz[z]; A2 = [[C, -S], [S, C]]
-// Scaling: each forward operand column is divided by its largest magnitude
-// over z before the 16-bit cast, each inverse operand column by its largest
-// magnitude over kz (a per-column slab scale, FP32), and both are undone in
-// FP32 after the products.
+//            = A1 transposed, so the inverse reads A1's storage as an MN-major
+//            operand
+// Scaling: each forward operand column is multiplied by the power of two that
+// brings its largest magnitude over z into [1, 2) before the 16-bit cast, each
+// inverse operand column likewise for its largest magnitude over kz (a per-
+// column slab scale, exact), and both are undone in FP32 after the products.
 //
-// One CTA (8 warps, two CTAs per SM, persistent over tiles): the tile and the
-// kernel block arrive by 2D tensor copies (the blocked kernel-spectrum copy of
-// the residue-split z convolution) one tile ahead; the threads build the
-// scaled 16-bit operand in shared memory; one thread issues the tcgen05.mma
-// instructions (M = 128, N = 96, K = 16 each) into 96 tensor-memory columns
-// and commits them to an mbarrier; every thread then reads its accumulator
-// row (tensor-memory lane) with tcgen05.ld, so the 3 x 3 multiply needs no
-// exchange between threads.  The inverse product reuses the same columns.
-// Outputs go through shared memory and leave as 256-byte rows.
+// One CTA (4 warps, 55 KB of shared memory, four CTAs per SM, persistent over
+// tiles): the tile and its kernel rows arrive by 2D tensor copies (the blocked
+// kernel-spectrum copy of the residue-split z convolution) one tile ahead; the
+// threads build the scaled 16-bit operand in shared memory; one thread issues
+// the tcgen05.mma instructions (M = 128, N = 48, K = 16 each) into 48 tensor-
+// memory columns and commits them to an mbarrier; every thread then reads its
+// accumulator row (tensor-memory lane) with tcgen05.ld, so the 3 x 3 multiply
+// needs no exchange between threads.  The inverse product reuses the same
+// columns.  Outputs go through shared memory and leave as 128-byte rows.
 //
-// Operand layout in shared memory (16-bit, K-major, no swizzle): element
-// (row, k) at (row / 8) SBO + (k / 8) LBO + (row % 8) 16 + (k % 8) 2 bytes,
-// i.e. 8 x 8 core matrices of 128 contiguous bytes.  The data operands use
-// LBO = 160 / 144 so that the threads' stores fall in distinct banks.
+// Operand layout in shared memory (16-bit, no swizzle, 8 x 8 core matrices of
+// 128 contiguous bytes): K-major element (row, k) at (row / 8) SBO + (k / 8)
+// LBO + (row % 8) 16 + (k % 8) 2 bytes (A1 and the forward data operand,
+// whose LBO = 160 spreads the threads' 16-byte stores over the banks); A2 is
+// the MN-major view of A1 (element (m, k) of A2 is element (k, m) of A1); the
+// inverse data operand is MN-major, element (n, k) at (n / 8) SBO + (k / 8) LBO
+// + (k % 8) 16 + (n % 8) 2, so a thread writes its row's 8 consecutive n as one
+// 16-byte store.
+//
+// Accumulator rows are permuted: row m (and m + 64) holds kz = kz_of(m), which
+// puts into each half-warp eight kernel rows kz' with distinct kz' mod 8 (each
+// read by the two lanes of kz and 64 - kz), so the kernel-row loads are free of
+// bank conflicts.  Scales are powers of two (exact, no divisions).
 //
 // Every mbarrier wait is bounded (device timer); when one gives up, the CTA
 // latches BORIS_ERR_TIMEOUT in *status, waits (bounded) for the copies and
@@ -52,38 +63,41 @@ namespace boris {
 
 namespace {
 
-constexpr int Q5 = 32;              // ky columns per tile
-constexpr int N5 = 96;              // operand columns: 3 components x 32
-constexpr int T5 = 256;             // threads per CTA
-constexpr int HZ5 = 32;             // z cells held (pz = 64)
-constexpr int KBW5 = 34;            // blocked kernel row: ky' = 32 b .. 32 b + 32, one pad
+constexpr int Q5 = 16;               // ky columns per tile
+constexpr int N5 = 48;               // operand columns: 3 components x 16
+constexpr int T5 = 128;              // threads per CTA (one per accumulator row)
+constexpr int HZ5 = 32;              // z cells held (pz = 64)
+constexpr int KBW5 = 18;             // kernel-row box: 18 of the blocked copy's 34 entries per row
+constexpr int KBW2 = 34;             // entries per row of the blocked copy (ky' = 32 b .. 32 b + 32, one pad)
 constexpr int KROWS5 = (HZ5 + 1) * 3;
-constexpr uint32_t TMEM_COLS = 128;  // power of two >= 96
+constexpr uint32_t TMEM_COLS = 64;   // power of two >= 48
 constexpr int STATUS_TIMEOUT5 = -5;  // BORIS_ERR_TIMEOUT
 
-constexpr uint32_t A1_LBO = 128, A1_SBO = 1024;  // 128 rows x 64 k
-constexpr uint32_t A2_LBO = 128, A2_SBO = 2048;  // 64 rows x 128 k
-constexpr uint32_t D1_LBO = 160, D1_SBO = 1280;  // 96 rows x 64 k
-constexpr uint32_t D2_LBO = 144, D2_SBO = 2304;  // 96 rows x 128 k
-constexpr int OUT_ROW = 65;                      // floats per (c, z) row of the output stage
+constexpr uint32_t A1_LBO = 128, A1_SBO = 1024;  // K-major, 128 rows x 64 k
+constexpr uint32_t A2_LBO = 1024, A2_SBO = 128;  // MN-major view of A1: 64 (x 128) rows x 128 k
+constexpr uint32_t D1_LBO = 160, D1_SBO = 1280;  // K-major, 48 rows x 64 k
+constexpr uint32_t D2_LBO = 128, D2_SBO = 2048;  // MN-major, 48 n x 128 k
+constexpr int OUT_ROW = 2 * Q5 + 1;               // floats per (c, z) row of the output stage
 
-// shared memory (bytes).  A2 comes first: an M = 128 product reads 128 rows,
-// and rows 64..127 of A2's view fall on A1 (finite values, outputs ignored).
-constexpr size_t OFF_A2 = 0;
-constexpr size_t OFF_A1 = 16384;
-constexpr size_t OFF_STAGE = 32768;                                          // [c][z][col] float2
-constexpr size_t OFF_KST = OFF_STAGE + (size_t)3 * HZ5 * Q5 * 8;              // kernel block
+// shared memory (bytes).  An M = 128 product through the A2 view reads rows
+// 64..127 from A1's other elements and up to 1 KB past A1 (finite data in the
+// stage; those output rows are ignored).
+constexpr size_t OFF_A1 = 0;
+constexpr size_t OFF_STAGE = 16384;                                            // [c][z][col] float2
+constexpr size_t OFF_KST = OFF_STAGE + (size_t)3 * HZ5 * Q5 * 8;                // kernel rows [kz' 3 + p][18]
 constexpr size_t OFF_D = (OFF_KST + (size_t)KROWS5 * KBW5 * 8 + 127) / 128 * 128;  // D1, D2, output stage
-constexpr size_t D_BYTES = (size_t)(N5 / 8) * D2_SBO;
-constexpr size_t OFF_S1 = OFF_D + D_BYTES;  // [col][4] forward column scales (sign of ky fold in .y)
+constexpr size_t D1_BYTES = (size_t)(N5 / 8) * D1_SBO, D2_BYTES = (size_t)(N5 / 8) * D2_SBO;
+constexpr size_t OUT_BYTES = (size_t)3 * HZ5 * OUT_ROW * 4;
+constexpr size_t D_BYTES = OUT_BYTES > D2_BYTES ? OUT_BYTES : D2_BYTES;
+constexpr size_t OFF_S1 = OFF_D + D_BYTES;   // [col][4] forward column scales (sign of ky fold in .y)
 constexpr size_t OFF_S2 = OFF_S1 + Q5 * 16;  // [col][4] inverse column maxima (float bits)
 constexpr size_t OFF_BAR = OFF_S2 + Q5 * 16;
 constexpr size_t OFF_TSLOT = OFF_BAR + 3 * 8;
 constexpr size_t SMEM5 = OFF_TSLOT + 16;
-static_assert((size_t)(N5 / 8) * D1_SBO <= D_BYTES, "D1 fits the operand region");
-static_assert((size_t)3 * HZ5 * OUT_ROW * 4 <= D_BYTES, "output stage fits the operand region");
+static_assert(D1_BYTES <= D_BYTES, "operands fit");
 static_assert(OFF_KST % 128 == 0 && OFF_STAGE % 128 == 0, "tensor-copy destinations");
-static_assert(2 * (SMEM5 + 1024) <= 233472, "two CTAs per SM");
+static_assert(16384 + 1024 <= OFF_D, "the A2 view's ignored rows stay inside the allocation");
+static_assert(4 * (SMEM5 + 1024) <= 233472, "four CTAs per SM");
 
 template <typename H> struct Cvt16;
 template <> struct Cvt16<__half> {
@@ -137,7 +151,7 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// columns taddr + 16 c + j (c < 3 at stride 32, j < 16) of this thread's lane;
+// columns taddr + 16 c + j (c < 3, j < 16) of this thread's lane;
 // the wait sits in the same statement so no use of v can move above it
 __device__ __forceinline__ void tmem_ld48(uint32_t taddr, float (&v)[3][16])
 {
@@ -156,7 +170,7 @@ __device__ __forceinline__ void tmem_ld48(uint32_t taddr, float (&v)[3][16])
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
           "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
           "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47])
-        : "r"(taddr), "r"(taddr + 32), "r"(taddr + 64)
+        : "r"(taddr), "r"(taddr + 16), "r"(taddr + 32)
         : "memory");
 #pragma unroll
     for (int c = 0; c < 3; c++)
@@ -164,46 +178,71 @@ __device__ __forceinline__ void tmem_ld48(uint32_t taddr, float (&v)[3][16])
         for (int j = 0; j < 16; j++) v[c][j] = __uint_as_float(r[16 * c + j]);
 }
 
-// cos and sin of 2 pi e / 64 from the plan's twiddles exp(-2 pi i e / lmax)
-__device__ __forceinline__ float2 cs64(const float2* __restrict__ tw, int shz, int e)
+// kz held by accumulator row m (mod 64): groups of 16 rows take kz' = 8 j + 1 .. 8 j + 8
+// with both signs (j < 3), and kz' = 25 .. 32 with 33 .. 39 and 0 (j = 3)
+__device__ __forceinline__ int kz_of(int m)
 {
-    const float2 w = tw[(e & 63) << shz];
-    return make_float2(w.x, -w.y);
-}
-// A1[m][k]: m = part * 64 + kz, k = kpart * 32 + z
-__device__ __forceinline__ float a1_val(const float2* __restrict__ tw, int shz, int m, int k)
-{
-    const int part = m >> 6, kpart = k >> 5;
-    const float2 cs = cs64(tw, shz, (m & 63) * (k & 31));
-    return part == kpart ? cs.x : (part == 0 ? cs.y : -cs.y);
-}
-// A2[m][k]: m = part * 32 + z, k = kpart * 64 + kz
-__device__ __forceinline__ float a2_val(const float2* __restrict__ tw, int shz, int m, int k)
-{
-    const int part = m >> 5, kpart = k >> 6;
-    const float2 cs = cs64(tw, shz, (k & 63) * (m & 31));
-    return part == kpart ? cs.x : (part == 0 ? -cs.y : cs.y);
+    const int j = m >> 4, i = m & 15;
+    if (j < 3) return i < 8 ? 8 * j + 1 + i : 63 - 8 * j - (i - 8);
+    return i < 8 ? 25 + i : (i < 15 ? 47 - i : 0);
 }
 
+// 2^(e - 127) for the exponent field e of a non-negative float (0 below the
+// normal range), and 2^(127 - e): exact scales that bring |x| into [1, 2)
+__device__ __forceinline__ float pow2_of(uint32_t bits) { return __uint_as_float(bits & 0x7f800000u); }
+__device__ __forceinline__ float inv_pow2_of(uint32_t bits)
+{
+    return __uint_as_float((254u - ((bits >> 23) & 0xffu)) << 23);
+}
+
+// largest |x| over the warp
+__device__ __forceinline__ float warp_max_abs(float x)
+{
+    float r;
+    asm volatile("redux.sync.max.abs.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// mbarrier wait that lets the hardware suspend the thread (up to 20 us per
+// try) instead of spinning; false after limit_ns of device time
+__device__ __forceinline__ bool mbar_wait_hint(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < (1u << 24); it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+// A1[m][k]: m = part * 64 + (row of kz), k = kpart * 32 + z; cs[e] = (cos, sin) of 2 pi e / 64
+__device__ __forceinline__ float a1_val(const float2* cs64, int m, int k)
+{
+    const int part = m >> 6, kpart = k >> 5;
+    const float2 cs = cs64[(kz_of(m & 63) * (k & 31)) & 63];
+    return part == kpart ? cs.x : (part == 0 ? cs.y : -cs.y);
+}
 __device__ __forceinline__ uint32_t op_off(int row, int k, uint32_t lbo, uint32_t sbo)
 {
     return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * lbo + (uint32_t)(row & 7) * 16 + (uint32_t)(k & 7) * 2;
 }
 
-__device__ __forceinline__ float inv_max(uint32_t bits)
-{
-    const float m = __uint_as_float(bits);
-    return m > 0.f ? 1.f / m : 0.f;
-}
 
 template <typename H>
-__global__ void __launch_bounds__(T5, 2)
+__global__ void __launch_bounds__(T5, 4)
     z_conv_tc5_kernel(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap kmap, Geometry g,
                       int nkb, float2* __restrict__ Y, const float2* __restrict__ tw_g, int* __restrict__ status,
                       uint32_t extra_tx, unsigned long long limit_ns)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* A2 = smem_raw + OFF_A2;
     unsigned char* A1 = smem_raw + OFF_A1;
     float2* stage = reinterpret_cast<float2*>(smem_raw + OFF_STAGE);
     float2* kst = reinterpret_cast<float2*>(smem_raw + OFF_KST);
@@ -220,9 +259,11 @@ __global__ void __launch_bounds__(T5, 2)
     const int nty = py / Q5, ntiles = g.nkx * nty, G = gridDim.x;
     const uint32_t ybytes = (uint32_t)lines * Q5 * sizeof(float2);
     constexpr uint32_t kbytes = (uint32_t)KROWS5 * KBW5 * sizeof(float2);
-    // kind::f16, FP32 accumulator, A and B of type H, both K-major, N = 96, M = 128
+    // kind::f16, FP32 accumulator, A and B of type H, N = 48, M = 128; forward:
+    // both K-major; inverse: both MN-major (bits 15 and 16)
     constexpr uint32_t IDESC = (1u << 4) | (Cvt16<H>::fmt << 7) | (Cvt16<H>::fmt << 10) |
                                ((uint32_t)(N5 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    constexpr uint32_t IDESC_MN = IDESC | (1u << 15) | (1u << 16);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -230,17 +271,21 @@ __global__ void __launch_bounds__(T5, 2)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // the DFT operands, once per CTA
-    const int shz = g.lglmax - 6;
-    for (int i = tid; i < 128 * 32; i += T5) {
-        const int m = i >> 5, k = (i & 31) * 2;
-        *reinterpret_cast<uint32_t*>(A1 + op_off(m, k, A1_LBO, A1_SBO)) =
-            Cvt16<H>::two(a1_val(tw_g, shz, m, k), a1_val(tw_g, shz, m, k + 1));
-    }
-    for (int i = tid; i < 64 * 64; i += T5) {
-        const int m = i >> 6, k = (i & 63) * 2;
-        *reinterpret_cast<uint32_t*>(A2 + op_off(m, k, A2_LBO, A2_SBO)) =
-            Cvt16<H>::two(a2_val(tw_g, shz, m, k), a2_val(tw_g, shz, m, k + 1));
+    // the DFT operand, once per CTA, from (cos, sin) of 2 pi e / 64 staged in
+    // the (still unused) operand region; the plan's twiddles are exp(-2 pi i e / lmax)
+    {
+        float2* cs64 = reinterpret_cast<float2*>(Dm);
+        const int shz = g.lglmax - 6;
+        if (tid < 64) {
+            const float2 w = tw_g[tid << shz];
+            cs64[tid] = make_float2(w.x, -w.y);
+        }
+        __syncthreads();
+        for (int i = tid; i < 128 * 32; i += T5) {
+            const int m = i >> 5, k = (i & 31) * 2;
+            *reinterpret_cast<uint32_t*>(A1 + op_off(m, k, A1_LBO, A1_SBO)) =
+                Cvt16<H>::two(a1_val(cs64, m, k), a1_val(cs64, m, k + 1));
+        }
     }
     if (tid == 0) {
         mbar_init(fullY, 1);
@@ -259,12 +304,16 @@ __global__ void __launch_bounds__(T5, 2)
         mbar_arrive_expect_tx(fullY, ybytes + extra);
         for (int c = 0; c < 3; c++) tma_load_2d(stage + c * HZ5 * Q5, &ymap, ky0, kx * lines + c * nz, fullY);
     };
-    // the kernel block of tile t: b = ky0 / 32 below the fold, (py - ky0 - 31) / 32 above it
+    // kernel rows of tile t: block b of the blocked copy and 18 of its 34
+    // entries from x0.  Below the fold entry e = (ky0 mod 32) + col of block
+    // ky0 / 32; above it e = 32 - (ky0 mod 32) - col of block (py - ky0 - 31) / 32.
     auto load_k = [&](int t) {
-        const int kx = t / nty, ky0 = (t - kx * nty) * Q5;
-        const int b = ky0 >= py / 2 ? (py - ky0 - (Q5 - 1)) / 32 : ky0 / 32;
+        const int kx = t / nty, ky0 = (t - kx * nty) * Q5, k32 = ky0 & ~31;
+        const bool up = ky0 >= py / 2;
+        const int b = up ? (py - k32) / 32 - 1 : k32 / 32;
+        const int x0 = up ? 16 - (ky0 & 16) : (ky0 & 16);
         mbar_arrive_expect_tx(fullK, kbytes);
-        tma_load_2d(kst, &kmap, 0, (kx * nkb + b) * KROWS5, fullK);
+        tma_load_2d(kst, &kmap, x0, (kx * nkb + b) * KROWS5, fullK);
     };
     // copies and product groups issued by thread 0 (for the drain after a timeout)
     int ny_issued = 0, nk_issued = 0, nm_issued = 0;
@@ -274,13 +323,12 @@ __global__ void __launch_bounds__(T5, 2)
         ny_issued = nk_issued = 1;
     }
 
-    // this thread's accumulator row (tensor-memory lane) and its columns
-    const int q = warp & 3, wg = warp >> 2;
-    const int r = 32 * q + lane;
-    const int kz = r & 63;
+    // this thread's accumulator row (tensor-memory lane)
+    const int r = tid;
+    const int kz = kz_of(r & 63);
     const int kzf = kz <= HZ5 ? kz : 64 - kz;
     const float sz = kz > HZ5 ? -1.f : 1.f;  // xz and yz are odd in kz
-    const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * wg);
+    const uint32_t trow = tbase + ((uint32_t)(32 * warp) << 16);
     float* outs = reinterpret_cast<float*>(Dm);
 
     bool failed = false;
@@ -290,7 +338,7 @@ __global__ void __launch_bounds__(T5, 2)
         const bool more = t + G < ntiles;
         const bool fy = ky0 >= py / 2;  // ky beyond the fold: xy and yz change sign
         {
-            const bool ok = mbar_wait_bounded(fullY, k & 1, limit_ns);
+            const bool ok = mbar_wait_hint(fullY, k & 1, limit_ns);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
@@ -299,7 +347,7 @@ __global__ void __launch_bounds__(T5, 2)
         // scaled 16-bit forward operand D1[n][k]: k < 32 Re z, k >= 32 Im z;
         // thread pair (2 n, 2 n + 1) takes z < 16 and z >= 16 of column n
         if (tid < 2 * N5) {
-            const int n = tid >> 1, zh = tid & 1, c = n >> 5, col = n & 31;
+            const int n = tid >> 1, zh = tid & 1, c = n >> 4, col = n & 15;
             const float2* src = stage + (c * HZ5 + 16 * zh) * Q5 + col;
             float2 a[16];
             float mx = 0.f;
@@ -309,7 +357,7 @@ __global__ void __launch_bounds__(T5, 2)
                 mx = fmaxf(mx, fmaxf(fabsf(a[i].x), fabsf(a[i].y)));
             }
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-            const float s = mx > 0.f ? 1.f / mx : 0.f;
+            const float s = inv_pow2_of(__float_as_uint(mx));
             unsigned char* row = Dm + (n >> 3) * D1_SBO + (n & 7) * 16;
 #pragma unroll
             for (int h = 0; h < 2; h++) {
@@ -326,7 +374,10 @@ __global__ void __launch_bounds__(T5, 2)
                 *reinterpret_cast<uint4*>(row + (4 + 2 * zh + h) * D1_LBO) = im;
             }
             // the y component carries the sign of the ky fold (see the multiply)
-            if (zh == 0) S1[col * 4 + c] = (c == 1 && fy) ? -mx : mx;
+            if (zh == 0) {
+                const float p2 = pow2_of(__float_as_uint(mx));
+                S1[col * 4 + c] = (c == 1 && fy) ? -p2 : p2;
+            }
         }
         if (tid < 4 * Q5) S2[tid] = 0u;
         fence_proxy_async_smem();
@@ -346,7 +397,7 @@ __global__ void __launch_bounds__(T5, 2)
             nm_issued++;
         }
         {
-            const bool ok = mbar_wait_bounded(fullK, k & 1, limit_ns) && mbar_wait_bounded(mmab, 0, limit_ns);
+            const bool ok = mbar_wait_hint(fullK, k & 1, limit_ns) && mbar_wait_hint(mmab, 0, limit_ns);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
@@ -363,9 +414,8 @@ __global__ void __launch_bounds__(T5, 2)
             const float2* kp = kst + kzf * 3 * KBW5;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int col = 16 * wg + j;
-                const int e = fy ? 32 - col : col;
-                const float4 s = *reinterpret_cast<const float4*>(S1 + col * 4);
+                const int e = fy ? 16 - j : j;
+                const float4 s = *reinterpret_cast<const float4*>(S1 + j * 4);
                 const float m0 = h[0][j] * s.x, m1 = h[1][j] * s.y, m2 = h[2][j] * (s.z * sz);
                 const float2 p0 = kp[e], p1 = kp[KBW5 + e], p2 = kp[2 * KBW5 + e];
                 h[0][j] = p0.x * m0 + p1.y * m1 + p2.x * m2;
@@ -375,20 +425,20 @@ __global__ void __launch_bounds__(T5, 2)
         }
         // largest magnitude of each operand column over the 128 rows
         {
-            uint32_t sel0 = 0, sel1 = 0;
+            float sel0 = 0.f, sel1 = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; c++)
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     const int i = 16 * c + j;
-                    const uint32_t u = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(h[c][j])));
+                    const float u = warp_max_abs(h[c][j]);
                     if (lane == (i & 31)) {
                         if (i < 32) sel0 = u;
                         else sel1 = u;
                     }
                 }
-            atomicMax(S2 + (16 * wg + (lane & 15)) * 4 + (lane >> 4), sel0);
-            if (lane < 16) atomicMax(S2 + (16 * wg + lane) * 4 + 2, sel1);
+            atomicMax(S2 + (lane & 15) * 4 + (lane >> 4), __float_as_uint(sel0));
+            if (lane < 16) atomicMax(S2 + lane * 4 + 2, __float_as_uint(sel1));
         }
         tc_fence_before();
         __syncthreads();
@@ -397,18 +447,30 @@ __global__ void __launch_bounds__(T5, 2)
             load_k(t + G);
             nk_issued++;
         }
-        // scaled 16-bit inverse operand D2[n][k = r]; s_z H2 is turned back into H2 here
+        // scaled 16-bit inverse operand D2[n][k = r] (MN-major: the row's 8
+        // consecutive n per 16-byte store); s_z H2 is turned back into H2 here
         {
-            unsigned short* base = reinterpret_cast<unsigned short*>(Dm + (r >> 3) * D2_LBO + (r & 7) * 2);
+            unsigned char* base = Dm + (r >> 3) * D2_LBO + (r & 7) * 16;
 #pragma unroll
-            for (int j = 0; j < 16; j++) {
-                const int col = 16 * wg + j;
-                const uint4 mb = *reinterpret_cast<const uint4*>(S2 + col * 4);
-                const float i0 = inv_max(mb.x), i1 = inv_max(mb.y), i2 = inv_max(mb.z) * sz;
-                const int n0 = col, n1 = 32 + col, n2 = 64 + col;
-                base[((n0 >> 3) * D2_SBO + (n0 & 7) * 16) / 2] = Cvt16<H>::one(h[0][j] * i0);
-                base[((n1 >> 3) * D2_SBO + (n1 & 7) * 16) / 2] = Cvt16<H>::one(h[1][j] * i1);
-                base[((n2 >> 3) * D2_SBO + (n2 & 7) * 16) / 2] = Cvt16<H>::one(h[2][j] * i2);
+            for (int hh = 0; hh < 2; hh++) {
+                float v[3][8];
+#pragma unroll
+                for (int e = 0; e < 8; e++) {
+                    const int col = 8 * hh + e;
+                    const uint4 mb = *reinterpret_cast<const uint4*>(S2 + col * 4);
+                    v[0][e] = h[0][col] * inv_pow2_of(mb.x);
+                    v[1][e] = h[1][col] * inv_pow2_of(mb.y);
+                    v[2][e] = h[2][col] * (inv_pow2_of(mb.z) * sz);
+                }
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    uint4 w;
+                    w.x = Cvt16<H>::two(v[c][0], v[c][1]);
+                    w.y = Cvt16<H>::two(v[c][2], v[c][3]);
+                    w.z = Cvt16<H>::two(v[c][4], v[c][5]);
+                    w.w = Cvt16<H>::two(v[c][6], v[c][7]);
+                    *reinterpret_cast<uint4*>(base + (2 * c + hh) * D2_SBO) = w;
+                }
             }
         }
         fence_proxy_async_smem();
@@ -417,13 +479,13 @@ __global__ void __launch_bounds__(T5, 2)
             tc_fence_after();
 #pragma unroll
             for (int ks = 0; ks < 8; ks++)
-                umma_f16(tbase, sdesc(A2 + ks * 2 * A2_LBO, A2_LBO, A2_SBO), sdesc(Dm + ks * 2 * D2_LBO, D2_LBO, D2_SBO),
-                         IDESC, ks > 0);
+                umma_f16(tbase, sdesc(A1 + ks * 2 * A2_LBO, A2_LBO, A2_SBO), sdesc(Dm + ks * 2 * D2_LBO, D2_LBO, D2_SBO),
+                         IDESC_MN, ks > 0);
             umma_commit(mmab);
             nm_issued++;
         }
         {
-            const bool ok = mbar_wait_bounded(mmab, 1, limit_ns);
+            const bool ok = mbar_wait_hint(mmab, 1, limit_ns);
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
@@ -432,39 +494,39 @@ __global__ void __launch_bounds__(T5, 2)
         tc_fence_after();
         // rows r < 64: Re (r < 32) and Im (r >= 32) of z = r mod 32; the y
         // component takes back the sign of the ky fold
-        if (q < 2) {
+        if (warp < 2) {
             float o[3][16];
             tmem_ld48(trow, o);
             const int z = r & 31, part = r >> 5;
 #pragma unroll
             for (int j = 0; j < 16; j++) {
-                const int col = 16 * wg + j;
-                const uint4 mb = *reinterpret_cast<const uint4*>(S2 + col * 4);
-                const float s1 = fy ? -__uint_as_float(mb.y) : __uint_as_float(mb.y);
-                outs[(0 * HZ5 + z) * OUT_ROW + 2 * col + part] = o[0][j] * __uint_as_float(mb.x);
-                outs[(1 * HZ5 + z) * OUT_ROW + 2 * col + part] = o[1][j] * s1;
-                outs[(2 * HZ5 + z) * OUT_ROW + 2 * col + part] = o[2][j] * __uint_as_float(mb.z);
+                const uint4 mb = *reinterpret_cast<const uint4*>(S2 + j * 4);
+                const float s1 = fy ? -pow2_of(mb.y) : pow2_of(mb.y);
+                outs[(0 * HZ5 + z) * OUT_ROW + 2 * j + part] = o[0][j] * pow2_of(mb.x);
+                outs[(1 * HZ5 + z) * OUT_ROW + 2 * j + part] = o[1][j] * s1;
+                outs[(2 * HZ5 + z) * OUT_ROW + 2 * j + part] = o[2][j] * pow2_of(mb.z);
             }
         }
         tc_fence_before();
         __syncthreads();
         {
             float2* dst = Y + (size_t)kx * lines * py + ky0;
-            for (int i = tid; i < lines * Q5; i += T5) {
-                const int line = i >> 5, col = i & 31;
-                const int c = line / nz, z = line - c * nz;
-                const float* src = outs + (c * HZ5 + z) * OUT_ROW + 2 * col;
-                dst[(size_t)line * py + col] = make_float2(src[0], src[1]);
-            }
+#pragma unroll
+            for (int c = 0; c < 3; c++)
+                for (int i = tid; i < nz * Q5; i += T5) {
+                    const int z = i >> 4, col = i & 15;
+                    const float* src = outs + (c * HZ5 + z) * OUT_ROW + 2 * col;
+                    dst[(size_t)(c * nz + z) * py + col] = make_float2(src[0], src[1]);
+                }
         }
         // the output stage is rewritten only after the next tile's first barrier
     }
     if (failed && tid == 0) {
         atomicCAS(status, 0, STATUS_TIMEOUT5);
         // let the copies and products still in flight land (bounded)
-        if (ny_issued > 0) mbar_wait_bounded(fullY, (ny_issued - 1) & 1, limit_ns);
-        if (nk_issued > 0) mbar_wait_bounded(fullK, (nk_issued - 1) & 1, limit_ns);
-        if (nm_issued > 0) mbar_wait_bounded(mmab, (nm_issued - 1) & 1, limit_ns);
+        if (ny_issued > 0) mbar_wait_hint(fullY, (ny_issued - 1) & 1, limit_ns);
+        if (nk_issued > 0) mbar_wait_hint(fullK, (nk_issued - 1) & 1, limit_ns);
+        if (nm_issued > 0) mbar_wait_hint(mmab, (nm_issued - 1) & 1, limit_ns);
     }
     tc_fence_before();
     __syncthreads();
@@ -481,7 +543,7 @@ cudaError_t launch5(const CUtensorMap& ymap, const CUtensorMap& kmap, const Geom
     cudaError_t e = cudaFuncSetAttribute(z_conv_tc5_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM5);
     if (e != cudaSuccess) return e;
     const int ntiles = g.nkx * (g.py / Q5);
-    const int grid = std::min(ntiles, 2 * nsm);
+    const int grid = std::min(ntiles, 4 * nsm);
     z_conv_tc5_kernel<H><<<grid, T5, SMEM5, st>>>(ymap, kmap, g, zconv_res_nkb(g), Y, tw, status, extra_tx, limit_ns);
     return cudaGetLastError();
 }
@@ -490,10 +552,39 @@ cudaError_t launch5(const CUtensorMap& ymap, const CUtensorMap& kmap, const Geom
 
 bool zconv_tc5_supported(const Geometry& g, int max_smem)
 {
-    // pz = 64 (17 <= nz <= 32); py >= 64 so that a tile lies wholly on one side
-    // of the ky fold; the blocked kernel copy of the residue-split stage
-    return g.pz == 2 * HZ5 && g.nz >= 17 && g.nz <= HZ5 && g.py >= 2 * Q5 && g.py % Q5 == 0 &&
+    // pz = 64 (17 <= nz <= 32); py >= 64 so that the ky fold falls on a block
+    // boundary of the blocked kernel copy (that of the residue-split stage)
+    return g.pz == 2 * HZ5 && g.nz >= 17 && g.nz <= HZ5 && g.py >= 64 && g.py % 32 == 0 &&
            g.krow == ((HZ5 + 1) * 6 + 3) / 4 * 4 && SMEM5 <= (size_t)max_smem && g.lglmax >= 6;
+}
+
+// Y[kx][c][z][ky] as rows (kx, c, z) of py complex values, boxes of 16 x nz;
+// the blocked kernel copy as rows of 34 entries, boxes of 18 x 3 (HZ + 1)
+cudaError_t zconv_tc5_maps(const Geometry& g, float2* Y, float2* K2, void* ymap, void* kmap)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const cuuint32_t es[2] = {1, 1};
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)g.py, (cuuint64_t)g.nkx * 3 * g.nz};
+        const cuuint64_t strides[1] = {(cuuint64_t)g.py * sizeof(float2)};
+        const cuuint32_t box[2] = {(cuuint32_t)Q5, (cuuint32_t)g.nz};
+        const CUresult r = enc(reinterpret_cast<CUtensorMap*>(ymap), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, Y, dims,
+                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    {
+        const cuuint64_t rows = (cuuint64_t)g.nkx * zconv_res_nkb(g) * g.kzh * 3;
+        const cuuint64_t dims[2] = {(cuuint64_t)KBW2, rows};
+        const cuuint64_t strides[1] = {(cuuint64_t)KBW2 * sizeof(float2)};
+        const cuuint32_t box[2] = {(cuuint32_t)KBW5, (cuuint32_t)KROWS5};
+        const CUresult r = enc(reinterpret_cast<CUtensorMap*>(kmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, K2, dims,
+                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_zconv_tc5(const void* ymap_p, const void* kmap_p, const Geometry& g, float2* Y, const float2* tw,

@@ -1,6 +1,6 @@
 """Run a few demag evaluations (and optionally RK4 steps) on one mesh, for
 profilers: ``python -m paper_2008_02478_gb300.profile_demag --mesh 512,512,32
---evals 3 [--steps 1]``.  Uses random unit magnetisation, 4 nm cells."""
+--evals 3 [--steps 1] [--tc fp16]``.  Uses random unit magnetisation, 4 nm cells."""
 from __future__ import annotations
 
 import argparse
@@ -17,6 +17,7 @@ def main():
     ap.add_argument("--evals", type=int, default=3)
     ap.add_argument("--steps", type=int, default=0)
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--tc", default=None, choices=["fp16", "bf16"], help="tensor-core z stage")
     a = ap.parse_args()
     import torch
 
@@ -24,7 +25,7 @@ def main():
     from paper_2008_02478_gb300.binding import LLGParams, Plan
     n = tuple(int(v) for v in a.mesh.split(","))
     dt = torch.float64 if a.fp64 else torch.float32
-    plan = Plan(*n, a.cell, a.cell, a.cell, fp64=a.fp64)
+    plan = Plan(*n, a.cell, a.cell, a.cell, fp64=a.fp64, tc=a.tc)
     m0 = inputs.random_unit(*n, seed=1)
     M = torch.tensor(8e5 * m0, dtype=dt, device="cuda")
     H = torch.empty_like(M)

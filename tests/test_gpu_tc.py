@@ -64,15 +64,16 @@ def test_tensor_core_random_magnetisation(form, monkeypatch):
 
 
 def test_tcgen05_and_mma_sync_forms_agree(monkeypatch):
-    """Same operands, same scaling: the two forms differ only in the order of
-    the FP32 accumulation, far below the 16-bit rounding."""
+    """The two forms round the same products to 16 bits under different column
+    scales (a power of two against the exact maximum), so they agree to within
+    one unit roundoff of the operand format (2^-11 FP16, 2^-8 BF16)."""
     torch = torch_cuda()
     n, h = (96, 80, 24), (3e-9, 3e-9, 3e-9)
     M = to_dev(torch, 8e5 * inputs.voronoi_columnar(*n, h, 20e-9, seed=7))
     for tc in ("fp16", "bf16"):
         a = tc_plan(monkeypatch, "tcgen05", *n, *h, tc=tc).apply(M).cpu().numpy()
         b = tc_plan(monkeypatch, "mma.sync", *n, *h, tc=tc).apply(M).cpu().numpy()
-        assert rel_l2(a, b) < 1e-4, (tc, rel_l2(a, b))
+        assert rel_l2(a, b) < {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}[tc], (tc, rel_l2(a, b))
 
 
 def test_tcgen05_stage_repeats_and_checks_status(monkeypatch):
