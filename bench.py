@@ -712,7 +712,8 @@ def main():
             mixed[tc] = {"demag_evals_per_s": world * 4 * args.steps / td,
                          "cell_steps_per_s": world * ncell * args.steps / ts,
                          "h_rel_l2_vs_fp64": err,
-                         "z_stage_ms_per_launch": kk["z_conv"][0] / max(1, kk["z_conv"][1])}
+                         "z_stage_ms_per_launch": kk["z_conv"][0] / max(1, kk["z_conv"][1]),
+                         "z_stage": {5: "tcgen05 (tensor memory)", 4: "mma.sync"}.get(pt.schedule()[2], "?")}
             pt.close()
             del mt
         del H64

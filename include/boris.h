@@ -54,10 +54,13 @@ typedef enum {
 #define BORIS_FLAG_F64 0x1u        /* FP64 everywhere: use the *_f64 entry points       */
 /* Mixed-precision z stage (FP32 plans, pz = 64, i.e. 17 <= nz <= 32): the
  * zero-padded z transform and its inverse run as dense matrix products on the
- * tensor cores with FP16 (or BF16) operands, one FP32 scale per (kx, ky,
- * component) column, FP32 accumulation; everything else stays FP32.  The
- * paper has FP32/FP64 only; expected relative L2 error of H_d ~1e-3 (FP16)
- * to ~5e-3 (BF16). */
+ * tensor cores with FP16 (or BF16) operands, one scale per (kx, ky,
+ * component) column, FP32 accumulation; everything else stays FP32.  Where
+ * py >= 64 the products are tcgen05.mma with accumulators in tensor memory
+ * (power-of-two column scales); otherwise, or with BORIS_TC_MMASYNC=1 at plan
+ * creation, mma.sync with the exact column maxima as scales.  The paper has
+ * FP32/FP64 only; expected relative L2 error of H_d ~1e-4 (FP16) to ~1e-3
+ * (BF16). */
 #define BORIS_FLAG_FP16_TC 0x2u
 #define BORIS_FLAG_BF16_TC 0x4u
 
@@ -354,9 +357,12 @@ int boris_plan_padded(boris_plan p, int out[3]);
  * split into y-forward / z-convolution / y-inverse kernels).  Kinds 0 and 1:
  * out[1] CTAs per cluster, out[2] threads per CTA, out[3] shared memory per
  * CTA.  Kind 2: out[1] CTAs per SM the z convolution's register budget is
- * fitted to, out[2] 1 when the z convolution is the persistent bulk-copy
- * (TMA) pipeline, whose bounded mbarrier waits latch BORIS_ERR_TIMEOUT in the
- * status word read by boris_sync_status, else 0.
+ * fitted to, out[2] the z-convolution variant: 1 or 2 for the persistent
+ * bulk-copy (TMA) pipeline with one or two tile stages, 3 for the residue-
+ * split z convolution, 0 for the shared-memory form; on tensor-core plans 5
+ * for the tcgen05 stage and 4 for the mma.sync one.  Variants 1, 2, 3 and 5
+ * bound their mbarrier waits and latch BORIS_ERR_TIMEOUT in the status word
+ * read by boris_sync_status.
  * Environment overrides read at plan creation restrict the candidates:
  * BORIS_YZ_KIND, BORIS_YZ_CLUSTER, BORIS_YZ_THREADS, BORIS_YZ_QC (kind 0
  * chunk), BORIS_YZ_TMA (kind 2 variant). */

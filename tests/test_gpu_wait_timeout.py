@@ -1,4 +1,4 @@
-"""Bounded device-side waits: the bulk-copy and residue-split z convolutions wait on mbarriers
+"""Bounded device-side waits: the bulk-copy, residue-split and tcgen05 z stages wait on mbarriers
 with a time limit.  Through a test hook the first wait of every CTA expects
 16 bytes that never arrive; the kernel must give up after its limit, latch
 BORIS_ERR_TIMEOUT in the plan's status word (read by boris_sync_status) and
@@ -38,3 +38,28 @@ def test_wait_that_runs_out_reports_timeout_and_context_survives(variant, monkey
     good.sync_status()
     ref = oracle.DemagPlan(*N, *H).apply(M)
     assert rel_l2(Hd.cpu().numpy(), ref) < 1e-5
+
+
+def test_tcgen05_stage_wait_that_runs_out(monkeypatch):
+    """The tensor-core z stage (tcgen05) gives up the same way: it latches the
+    timeout, lets its other copies land, frees its tensor memory and returns;
+    a following plan (which allocates tensor memory again) is correct."""
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import BorisError, Plan
+    n, h = (24, 40, 20), (2e-9, 2e-9, 2e-9)
+    M = 7e5 * inputs.random_unit(*n, seed=22)
+    monkeypatch.setenv("BORIS_TEST_WAIT_TIMEOUT", "1")
+    bad = Plan(*n, *h, tc="fp16")
+    assert bad.schedule()[2] == 5
+    bad.apply(to_dev(torch, M))
+    with pytest.raises(BorisError) as ei:
+        bad.sync_status()
+    assert ei.value.code == -5
+    bad.sync_status()
+    bad.close()
+    monkeypatch.delenv("BORIS_TEST_WAIT_TIMEOUT")
+    good = Plan(*n, *h, tc="fp16")
+    Hd = good.apply(to_dev(torch, M))
+    good.sync_status()
+    ref = oracle.DemagPlan(*n, *h).apply(M)
+    assert rel_l2(Hd.cpu().numpy(), ref) < 1e-2
