@@ -628,6 +628,19 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic_for(dom_key),
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": dom_bytes}
+    # the whole RK4 step against the same peak: the bytes this schedule's
+    # kernels move per step (algorithmic bytes per launch x launches per step)
+    # and the compulsory bytes of a step (per evaluation M read, H written and
+    # the kernel octant read; per stage the LLG stage's bytes)
+    step_s = t_steps / args.steps
+    sched_bytes = sum(algo[k] * kern[k][1] for k in kern if k in algo and kern[k][1]) / args.steps
+    kb = split_algorithmic_bytes(plan)["z_conv"] - 2 * (plan.padded()[0] // 2 + 1) * plan.padded()[1] * 3 * nz * 8
+    compulsory = 4 * (2 * 3 * ncell * 4 + kb) + 4 * llg_algorithmic_bytes(plan)
+    step_roofline = {"unit": "GB/s", "peak": peak, "ms_per_step": step_s * 1e3,
+                     "schedule_bytes_per_step": sched_bytes, "schedule_GBps": sched_bytes / step_s / 1e9,
+                     "schedule_frac": sched_bytes / step_s / 1e9 / peak,
+                     "compulsory_bytes_per_step": compulsory, "compulsory_GBps": compulsory / step_s / 1e9,
+                     "compulsory_frac": compulsory / step_s / 1e9 / peak}
     kernels = {k: {"ms_per_launch": per_launch_ms[k], "launches": kern[k][1],
                    "share": kern[k][0] / max(1e-12, sum(v[0] for v in kern.values())),
                    "algorithmic_GBps": (algo[k] / (per_launch_ms[k] * 1e-3) / 1e9) if (k in algo and per_launch_ms[k]) else None}
@@ -743,7 +756,7 @@ def main():
                                  "spectrum 208.4 MB per evaluation)",
                            "padded": plan.padded(), "yz_schedule": plan.schedule()},
                 "demag_evals_per_s": demag_rate, "ms_per_step_without_graph": 1e3 * t_calls / args.steps,
-                "fp64": fp64, "workloads": dict(extra, field_terms_512x512x32=terms_line) if terms_line else extra, "mixed_precision": mixed, "roofline": roofline,
+                "fp64": fp64, "workloads": dict(extra, field_terms_512x512x32=terms_line) if terms_line else extra, "mixed_precision": mixed, "roofline": roofline, "step_roofline": step_roofline,
                 "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
