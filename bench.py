@@ -378,6 +378,47 @@ def other_workloads(torch, args, world, max_over_ranks):
     return out
 
 
+class Replicas:
+    """The ranks of a multi-GPU run (one independent replica per GPU under
+    torchrun, no data-path collective): a barrier and a maximum over ranks for
+    the timing.  backend/device: "nccl"/"cuda" for the bench, "gloo"/"cpu" for
+    the host-side tests.  The process group is set up from the torchrun
+    environment (MASTER_ADDR, MASTER_PORT, RANK, WORLD_SIZE)."""
+
+    def __init__(self, world: int, backend: str = "nccl", device: str = "cuda"):
+        import torch
+        self.torch, self.world, self.device, self.dist = torch, world, device, None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        if self.device == "cuda":
+            self.torch.cuda.synchronize()
+
+    def max(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        t = self.torch.tensor([x], dtype=self.torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.barrier()
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds_max: float) -> float:
+    """Throughput of the whole job: every rank processes units_per_rank in the
+    timed region; the job takes as long as its slowest rank."""
+    return world * units_per_rank / seconds_max
+
+
 def run_reference(args, rank):
     if rank != 0:
         return 0
@@ -558,22 +599,8 @@ def main():
             print(json.dumps({"sweep": "Fig. 11 shape: demag evaluation time and RK4 cell-steps/s vs N and nz, FP32",
                               "data": "synthetic", "cell": CELL, "rows": rows, "fma_peak": fma_peak()}))
         return
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Replicas(world, "nccl", "cuda")
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     nx, ny, nz = N_MESH
     ncell = nx * ny * nz
@@ -596,7 +623,7 @@ def main():
     _, launches = plan.profile_read()
     t_steps = max_over_ranks(t_steps)
     clocks = clk.summary()
-    value = world * ncell * args.steps / t_steps
+    value = whole_job_rate(world, ncell * args.steps, t_steps)
     # the same steps through one boris_llg_step call each (no graph)
     t_calls = max_over_ranks(time_steps(torch, plan, m, prm, args.steps))
 
@@ -761,9 +788,7 @@ def main():
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
