@@ -183,8 +183,8 @@ int boris_demag_apply_f64(boris_plan p, const double* M, double* Hd);
  *   first call before any stream capture.  All calls share the one array:
  *   calls that overlap on the GPU race and corrupt each other's output.
  *   Nothing in the array needs clearing: every call overwrites what it reads.
- *   On a plan made with a tensor-core flag it runs the FP32 z stage (the
- *   result is that of the plan without the flag).
+ *   On a plan made with a tensor-core flag it runs an FP32 z stage, so its
+ *   result has FP32 accuracy rather than that of the 16-bit stage.
  */
 int boris_demag_apply_noalloc(boris_plan p, const float* M, float* Hd);
 
