@@ -249,21 +249,20 @@ def other_workloads(torch, args, world, max_over_ranks):
     per-cell Ms and Ku maps."""
     import numpy as np
 
-    from oracle import multilayer as ml
     from paper_2008_02478_gb300 import inputs
     from paper_2008_02478_gb300.autograd import trajectory
     from paper_2008_02478_gb300.binding import RKF45, LLGParams, MultiPlan, Plan
     out = {}
     # six-layer stack
     d = inputs.MULTILAYER
-    st = ml.centred_stack(d["layers"], d["hz"], d["gaps"], d["hxy"])
-    cells = [(st.hx, st.hy, h) for h in st.hz]
-    origins = [(ox * st.hx, oy * st.hy, zb) for ox, oy, zb in zip(st.ox, st.oy, st.zb)]
+    layers = d["layers"]
+    cells, origins = inputs.stack_geometry(layers, d["hz"], d["gaps"], d["hxy"])
+    total = sum(l[0] * l[1] * l[2] for l in layers)
     t0 = time.perf_counter()
-    mp = MultiPlan(st.n, cells, origins)
+    mp = MultiPlan(layers, cells, origins)
     t_plan = time.perf_counter() - t0
-    m = np.concatenate([inputs.random_unit(*l, seed=d["seed"] + i).reshape(-1) for i, l in enumerate(st.n)])
-    ms = np.concatenate([np.full(l[0] * l[1] * l[2], d["Ms"][i]) for i, l in enumerate(st.n)])
+    m = np.concatenate([inputs.random_unit(*l, seed=d["seed"] + i).reshape(-1) for i, l in enumerate(layers)])
+    ms = np.concatenate([np.full(l[0] * l[1] * l[2], d["Ms"][i]) for i, l in enumerate(layers)])
     mg = torch.tensor(m, dtype=torch.float32, device="cuda")
     prm = LLGParams(A=A_EX, alpha=ALPHA, Ms_map=torch.tensor(ms, dtype=torch.float32, device="cuda"))
     dt_ml = 5e-14
@@ -286,8 +285,8 @@ def other_workloads(torch, args, world, max_over_ranks):
     torch.cuda.synchronize()
     td = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
     z, nu, NX, NY = mp.info()
-    out["multilayer_6"] = {"cells": st.total(), "z_planes": z, "inter_plane_spectra": nu, "frame": [NX, NY],
-                           "cell_steps_per_s": world * st.total() * K / t, "demag_evals_per_s": world * 4 * K / td,
+    out["multilayer_6"] = {"cells": total, "z_planes": z, "inter_plane_spectra": nu, "frame": [NX, NY],
+                           "cell_steps_per_s": world * total * K / t, "demag_evals_per_s": world * 4 * K / td,
                            "plan_build_s": t_plan, "dt": dt_ml, "batched": "all layers per launch, CUDA graph"}
     mp.close()
     # periodic 512x512x32 film: x and y periodic by 8 images each side

@@ -84,6 +84,20 @@ GRAD_FILM_MESH = dict(n=(256, 256, 8), cell=(3e-9, 3e-9, 3e-9), seed=5)
 
 #: six stacked layers: (nx, ny, nz), z cell size (m), Ms (A/m); in-plane cell 4 nm,
 #: gaps between consecutive layers (m); layers laterally centred
+def stack_geometry(layers, hz, gaps, hxy):
+    """Cell sizes and lower-corner origins (m) of layers laterally centred on
+    the largest one (integer cell offsets) and stacked bottom-up with the given
+    gaps between consecutive layers: the layout of the six-layer stack below."""
+    NX = max(l[0] for l in layers)
+    NY = max(l[1] for l in layers)
+    cells, origins, z = [], [], 0.0
+    for i, l in enumerate(layers):
+        cells.append((hxy, hxy, hz[i]))
+        origins.append((((NX - l[0]) // 2) * hxy, ((NY - l[1]) // 2) * hxy, z))
+        z += l[2] * hz[i] + (gaps[i] if i < len(gaps) else 0.0)
+    return cells, origins
+
+
 MULTILAYER = dict(
     layers=[(512, 512, 8), (256, 256, 4), (384, 128, 2), (128, 128, 16), (512, 64, 1), (200, 200, 3)],
     hz=[2e-9, 5e-9, 3e-9, 4e-9, 2e-9, 3e-9],

@@ -7,13 +7,12 @@ import sys
 sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 import numpy as np
 import torch
-from oracle import multilayer as ml
 from paper_2008_02478_gb300 import inputs
 from paper_2008_02478_gb300.binding import MultiPlan
 d = inputs.MULTILAYER
-st = ml.centred_stack(d["layers"], d["hz"], d["gaps"], d["hxy"])
-mp = MultiPlan(st.n, [(st.hx, st.hy, h) for h in st.hz], [(ox * st.hx, oy * st.hy, zb) for ox, oy, zb in zip(st.ox, st.oy, st.zb)])
-M = torch.tensor(np.concatenate([inputs.random_unit(*l, seed=i).reshape(-1) for i, l in enumerate(st.n)]) * 8e5, dtype=torch.float32, device="cuda")
+cells, origins = inputs.stack_geometry(d["layers"], d["hz"], d["gaps"], d["hxy"])
+mp = MultiPlan(d["layers"], cells, origins)
+M = torch.tensor(np.concatenate([inputs.random_unit(*l, seed=i).reshape(-1) for i, l in enumerate(d["layers"])]) * 8e5, dtype=torch.float32, device="cuda")
 H = torch.empty_like(M)
 for _ in range(3): mp.apply(M, H)
 mp.profile(True)

@@ -110,3 +110,16 @@ def test_centred_offsets_and_positions():
     s = ml.centred_stack([(8, 8, 2), (4, 6, 1)], [2e-9, 3e-9], [1e-9], 1e-9)
     assert s.ox == [0, 2] and s.oy == [0, 1]
     assert s.zb[1] == pytest.approx(2 * 2e-9 + 1e-9)
+
+
+def test_input_stack_geometry_matches_the_oracle_layout():
+    """bench.py and the profiling entry lay the six-layer stack out with
+    inputs.stack_geometry (the product side may not import the oracle); it must
+    give the oracle's centred stack: same cell sizes, offsets and z bases."""
+    from paper_2008_02478_gb300 import inputs
+    d = inputs.MULTILAYER
+    st = ml.centred_stack(d["layers"], d["hz"], d["gaps"], d["hxy"])
+    cells, origins = inputs.stack_geometry(d["layers"], d["hz"], d["gaps"], d["hxy"])
+    assert cells == [(st.hx, st.hy, h) for h in st.hz]
+    for (x, y, z), ox, oy, zb in zip(origins, st.ox, st.oy, st.zb):
+        assert x == ox * st.hx and y == oy * st.hy and z == zb
