@@ -17,6 +17,8 @@ CASES = [
     ((48, 40, 32), (4e-9, 4e-9, 4e-9)),    # pz = 64 with nz = 32
     ((37, 29, 20), (3e-9, 3e-9, 2e-9)),    # ragged: nz = 20 still pads to 64, ragged column tiles
     ((64, 300, 17), (4e-9, 4e-9, 4e-9)),   # length-1024 y transforms; several tiles per persistent CTA
+    ((40, 700, 24), (4e-9, 4e-9, 4e-9)),   # py = 2048 (y passes built from the warp transform)
+    ((24, 1100, 18), (4e-9, 4e-9, 4e-9)),  # py = 4096
 ]
 FORMS = {"tcgen05": 5, "mma.sync": 4}
 
