@@ -305,8 +305,9 @@ __global__ void __launch_bounds__(T5, 4)
         for (int c = 0; c < 3; c++) tma_load_2d(stage + c * HZ5 * Q5, &ymap, ky0, kx * lines + c * nz, fullY);
     };
     // kernel rows of tile t: block b of the blocked copy and 18 of its 34
-    // entries from x0.  Below the fold entry e = (ky0 mod 32) + col of block
-    // ky0 / 32; above it e = 32 - (ky0 mod 32) - col of block (py - ky0 - 31) / 32.
+    // entries from x0, with k32 = ky0 rounded down to a multiple of 32.  Below
+    // the fold column col reads entry (ky0 mod 32) + col of block k32 / 32;
+    // above it entry 32 - (ky0 mod 32) - col of block (py - k32) / 32 - 1.
     auto load_k = [&](int t) {
         const int kx = t / nty, ky0 = (t - kx * nty) * Q5, k32 = ky0 & ~31;
         const bool up = ky0 >= py / 2;
