@@ -4,7 +4,8 @@ comparisons.  Generators only: no step of the demag or LLG arithmetic lives here
 Every generator is deterministic in its seed (numpy PCG64) and returns FP64
 numpy arrays in the SoA layout [3][nz][ny][nx] (vector fields) or [nz][ny][nx]
 (scalar maps).  The shapes and value ranges stand in for the paper's workloads
-(thin films, Voronoi grains, multilayer stacks); see the design doc for the recipe.
+(thin films, Voronoi grains, multilayer stacks): the generators below state
+each recipe.
 """
 from __future__ import annotations
 
