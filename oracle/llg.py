@@ -220,7 +220,7 @@ def energies_terms(m, prm: Params, demag):
 
 
 # --------------------------------------------------------------------------
-# Discrete adjoint of one RK4 step (added by this build; the paper has none)
+# Discrete adjoint of one RK4 step (the paper has none; it serves the gradient checks)
 # --------------------------------------------------------------------------
 def _field_vjp(m, gH, prm: Params, demag):
     """Given gH = dL/dH, return (dL/dm, dL/dMs, dL/dKu) through H(m; Ms, Ku)
