@@ -88,3 +88,36 @@ def test_thermal_argument_checks():
     with pytest.raises(BorisError) as e:  # adaptive steps do not take the thermal field
         plan.llg_step(m, LLGParams(method=RKF45), 1e-14)
     assert e.value.code == -1
+
+
+def test_checkpoint_resume_continues_the_thermal_sequence(tmp_path):
+    """Four RK4 steps, a checkpoint, three more: a fresh plan resumed from the
+    checkpoint (counter set back to step 4) ends where the uninterrupted run
+    ends; resumed with the counter left at 0 it draws other fields and does
+    not."""
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import FieldTerms
+    from paper_2008_02478_gb300.state import load_state, resume, save_state
+    m0 = inputs.random_unit(*N, seed=53)
+    dt = 1e-14
+    plan, prm, _ = setup()
+    a = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    for _ in range(4):
+        plan.llg_step(a, prm, dt)
+    path = tmp_path / "run.npz"
+    save_state(path, a, t=4 * dt, dt=dt, step=4, seed=SEED, temperature=T)
+    for _ in range(3):
+        plan.llg_step(a, prm, dt)
+    s = load_state(path)
+    plan2, _, _ = setup()
+    plan2.set_field_terms(FieldTerms(temperature=s["temperature"], seed=s["seed"]))
+    b = resume(plan2, s)
+    assert s["step"] == 4 and abs(s["t"] - 4 * dt) < 1e-30
+    for _ in range(3):
+        plan2.llg_step(b, prm, s["dt"])
+    assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) < 1e-6
+    plan3, _, _ = setup()
+    c = torch.tensor(s["m"], device="cuda")  # counter left at 0
+    for _ in range(3):
+        plan3.llg_step(c, prm, s["dt"])
+    assert rel_l2(c.cpu().numpy(), a.cpu().numpy()) > 1e-4
