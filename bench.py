@@ -242,6 +242,30 @@ def oracle_rk4_rate(nx, ny, nz, steps):
     return nx * ny * nz * steps / t, t, oracle.num_threads()
 
 
+def oracle_demag_rates():
+    """FP64 oracle: FFT-convolution demag evaluations/s on 32x32x4 (5 nm
+    cells, random unit vectors) and 256x256x8 (3 nm cells), one thread and all
+    threads; each figure from at least one evaluation and about 0.5 s."""
+    import oracle
+    from paper_2008_02478_gb300 import inputs
+    allc = oracle.num_threads()
+    out = {}
+    for n, h in (((32, 32, 4), 5e-9), ((256, 256, 8), 3e-9)):
+        M = 8e5 * inputs.random_unit(*n, seed=1)
+        plan = oracle.DemagPlan(*n, h, h, h)
+        row = {}
+        for th in (1, allc):
+            oracle.set_threads(th)
+            t0, k = time.perf_counter(), 0
+            while k == 0 or time.perf_counter() - t0 < 0.5:
+                plan.apply(M)
+                k += 1
+            row["threads_%d" % th] = k / (time.perf_counter() - t0)
+        out["%dx%dx%d" % n] = row
+    oracle.set_threads(allc)
+    return out
+
+
 def other_workloads(torch, args, world, max_over_ranks):
     """Throughput of the other workloads of the build on this GPU (FP32):
     the six-layer multi-mesh stack (batched, one CUDA graph per RK4 step), the
@@ -769,9 +793,11 @@ def main():
         oracle.build()
         blk = (256, 256, 32)
         rate, t, cores = oracle_rk4_rate(*blk, 3)
+        demag_rates = oracle_demag_rates()
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "three RK4 steps (12 FFT demag evaluations) of the FP64 oracle on a %dx%dx%d block of "
-                         "the same film (a quarter of its cells), %.1f s" % (blk + (t,))}
+                         "the same film (a quarter of its cells), %.1f s" % (blk + (t,)),
+               "demag_evals_per_s": demag_rates}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -86,6 +86,7 @@ def lib():
             L.orc_demag_fft.restype = i
             L.orc_demag_fft.argtypes = [vp, vp, vp]
             L.orc_num_threads.restype = i
+            L.orc_set_threads.argtypes = [i]
             L.orc_newell_pair_exact.argtypes = [d, d, d, d, d, d, d, vp]
             L.orc_newell_pair_asymptotic.argtypes = [d, d, d, d, d, d, d, vp]
             L.orc_newell_pair.argtypes = [d, d, d, d, d, d, d, d, vp]
@@ -100,6 +101,11 @@ def _p(a: np.ndarray):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (timing runs)."""
+    lib().orc_set_threads(int(n))
 
 
 # --------------------------------------------------------------------------

@@ -632,6 +632,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* threads of the parallel loops that follow (n >= 1); timing only */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Multi-mesh (Eq. 4): cells of different z thickness                        */
 /* ------------------------------------------------------------------------ */
