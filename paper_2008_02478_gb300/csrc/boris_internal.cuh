@@ -233,7 +233,8 @@ struct PlanView {
     int device;
     const void* K;
     const void* tw;
-    bool ml;  // multi-mesh plan
+    bool ml;       // multi-mesh plan
+    bool oersted;  // Oersted plan: its spectrum is the curl kernel, not the demag tensor
 };
 // Number of kernel classes timed by the plan's profiler.
 constexpr int NPROF = 9;

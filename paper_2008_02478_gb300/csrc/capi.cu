@@ -581,6 +581,7 @@ bool plan_view(boris_plan p, PlanView* v)
     v->K = p->K;
     v->tw = p->tw;
     v->ml = p->ml;
+    v->oersted = p->oersted;
     return true;
 }
 }  // namespace boris

@@ -65,8 +65,8 @@ extern "C" int boris_demag_apply_noalloc(boris_plan p, const float* M, float* Hd
         set_error("NULL argument");
         return BORIS_ERR_INVALID_ARG;
     }
-    if (v.f64 || v.ml) {
-        set_error("boris_demag_apply_noalloc serves FP32 single-mesh plans only");
+    if (v.f64 || v.ml || v.oersted) {
+        set_error("boris_demag_apply_noalloc serves FP32 single-mesh demag plans only");
         return BORIS_ERR_INVALID_ARG;
     }
     if (((uintptr_t)M & 15u) || ((uintptr_t)Hd & 15u) || (const void*)M == (const void*)Hd) {
