@@ -336,6 +336,18 @@ int boris_set_field_terms(boris_plan p, const boris_field_terms* t);
 int boris_thermal_set_step(boris_plan p, unsigned long long step);
 
 /*
+ * boris_philox4x32_10 - the thermal field's random-number generator on given
+ *   inputs: out[4i..4i+3] = Philox4x32-10(counter ctr[4i..4i+3], key
+ *   key[2i..2i+1]) for i < n, the same device function the stage kernels
+ *   draw from (Salmon, Moraes, Dror and Shaw, SC'11; the thermal field of
+ *   Section 1, Eq. 17).  ctr, key, out: device arrays of 32-bit words.
+ *   Asynchronous on cuda_stream (a cudaStream_t or NULL).  It lets a caller
+ *   check the generator against its published known-answer vectors.
+ *   Errors: INVALID_ARG (n < 0, NULL arrays with n > 0), CUDA.
+ */
+int boris_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* cuda_stream);
+
+/*
  * boris_energy_terms - as boris_energy, with out = {E_demag, E_exchange,
  *   E_anisotropy (uniaxial K1, K2 and cubic), E_Zeeman, E_DMI} in J; the
  *   exchange and DMI energies are -(mu0 Ms V/2) sum m.H of their fields.

@@ -30,7 +30,7 @@ EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_inf
            "boris_demag_adjoint",
            "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
            "boris_energy_terms", "boris_set_field_terms", "boris_demag_plan_pbc",
-           "boris_thermal_set_step", "boris_oersted_plan", "boris_oersted_apply",
+           "boris_thermal_set_step", "boris_philox4x32_10", "boris_oersted_plan", "boris_oersted_apply",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
            "boris_profile_enable", "boris_profile_read", "boris_plan_destroy"]
 KERNEL_CLASSES = ["x_r2c", "yz_conv", "x_c2r", "llg_stage", "other", "y_fwd", "z_conv", "y_inv", "x_c2r_rk4"]
@@ -118,6 +118,7 @@ def lib():
         L.boris_energy_terms.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_set_field_terms.argtypes = [vp, P(FieldTermsC)]
         L.boris_thermal_set_step.argtypes = [vp, ctypes.c_ulonglong]
+        L.boris_philox4x32_10.argtypes = [vp, vp, vp, i, vp]
         L.boris_oersted_plan.argtypes = [i, i, i, d, d, d, vp, P(vp)]
         L.boris_oersted_apply.argtypes = [vp, vp, vp]
         L.boris_sync_status.argtypes = [vp]
@@ -135,6 +136,20 @@ def lib():
         L.boris_plan_destroy.restype = None
         _lib = L
     return _lib
+
+
+def philox4x32_10(ctr, key, stream=None):
+    """Device Philox4x32-10 words (boris_philox4x32_10): ctr an int32 CUDA
+    tensor [n][4] and key [n][2] holding the 32-bit words; returns [n][4]."""
+    import torch
+    assert ctr.is_cuda and ctr.dtype == torch.int32 and key.dtype == torch.int32
+    ctr, key = ctr.contiguous(), key.contiguous()
+    n = ctr.shape[0]
+    assert tuple(ctr.shape) == (n, 4) and tuple(key.shape) == (n, 2)
+    out = torch.empty((n, 4), dtype=torch.int32, device=ctr.device)
+    st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    check(lib().boris_philox4x32_10(ctr.data_ptr(), key.data_ptr(), out.data_ptr(), n, st))
+    return out
 
 
 def check(rc):

@@ -1238,6 +1238,14 @@ int boris_thermal_set_step(boris_plan p, unsigned long long step)
     return BORIS_OK;
 }
 
+int boris_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, void* cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!ctr || !key || !out)))
+        return fail(BORIS_ERR_INVALID_ARG, "need n >= 0 and device ctr, key, out");
+    CUDA_TRY(launch_philox_words(ctr, key, out, n, (cudaStream_t)cuda_stream));
+    return BORIS_OK;
+}
+
 int boris_set_field_terms(boris_plan p, const boris_field_terms* t)
 {
     if (!p) return fail(BORIS_ERR_INVALID_ARG, "NULL plan");

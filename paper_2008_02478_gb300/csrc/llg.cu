@@ -393,6 +393,12 @@ cudaError_t launch_rk4_stage_ml(const LLGArgs<float>& a, const MLTable& t, int s
     return cudaGetLastError();
 }
 
+static int grid_for_words(int n)
+{
+    const int b = (n + 255) / 256;
+    return b < 152 * 8 ? b : 152 * 8;
+}
+
 __global__ void thermal_advance_kernel(unsigned long long* step) { *step += 1ull; }
 __global__ void thermal_set_kernel(unsigned long long* step, unsigned long long v) { *step = v; }
 
@@ -405,6 +411,27 @@ cudaError_t launch_thermal_advance(unsigned long long* step, cudaStream_t st)
 cudaError_t launch_thermal_set(unsigned long long* step, unsigned long long v, cudaStream_t st)
 {
     thermal_set_kernel<<<1, 1, 0, st>>>(step, v);
+    return cudaGetLastError();
+}
+
+// The stage kernels' generator on caller-given counters and keys: ctr [n][4],
+// key [n][2], out [n][4] 32-bit words.
+__global__ void philox_words_kernel(const unsigned int* __restrict__ ctr, const unsigned int* __restrict__ key,
+                                    unsigned int* __restrict__ out, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        unsigned int c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+        philox4x32_10(c, key[2 * i], key[2 * i + 1]);
+#pragma unroll
+        for (int j = 0; j < 4; j++) out[4 * i + j] = c[j];
+    }
+}
+
+cudaError_t launch_philox_words(const unsigned int* ctr, const unsigned int* key, unsigned int* out, int n,
+                                cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    philox_words_kernel<<<grid_for_words(n), 256, 0, st>>>(ctr, key, out, n);
     return cudaGetLastError();
 }
 

@@ -42,6 +42,8 @@ struct LLGArgs {
 // advances the thermal field's step counter by one (after an RK4 step) / sets it
 cudaError_t launch_thermal_advance(unsigned long long* step, cudaStream_t st);
 cudaError_t launch_thermal_set(unsigned long long* step, unsigned long long v, cudaStream_t st);
+cudaError_t launch_philox_words(const unsigned int* ctr, const unsigned int* key, unsigned int* out, int n,
+                                cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, T* m0, T* acc, T* mnext,

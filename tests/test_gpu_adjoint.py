@@ -9,7 +9,7 @@ import pytest
 import oracle
 from oracle import llg
 from paper_2008_02478_gb300 import inputs
-from tests.gpu_util import rel_l2, to_dev, torch_cuda
+from tests.gpu_util import assert_close, rel_l2, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -56,9 +56,9 @@ def test_step_backward_matches_oracle(fp64):
     gKu = torch.zeros_like(gMs)
     gm = plan.llg_step_backward(to_dev(torch, m0, fp64), p, dt, to_dev(torch, gout, fp64), None, gMs, gKu)
     tol = 1e-9 if fp64 else 1e-3
-    assert rel_l2(gm.cpu().numpy(), ref_gm) < tol
-    assert rel_l2(gMs.cpu().numpy(), ref_gMs) < tol
-    assert rel_l2(gKu.cpu().numpy(), ref_gKu) < tol
+    assert_close(gm.cpu().numpy(), ref_gm, tol)
+    assert_close(gMs.cpu().numpy(), ref_gMs, tol)
+    assert_close(gKu.cpu().numpy(), ref_gKu, tol)
 
 
 def test_checkpointed_trajectory_gradient():
@@ -78,9 +78,9 @@ def test_checkpointed_trajectory_gradient():
         L = ((out - to_dev(torch, target, fp64)) ** 2).sum()
         L.backward()
         assert abs(float(L) - L_ref) < (1e-9 if fp64 else 1e-4) * L_ref
-        assert rel_l2(Ms.grad.cpu().numpy(), gMs_ref) < tol
-        assert rel_l2(Ku.grad.cpu().numpy(), gKu_ref) < tol
-        assert rel_l2(m.grad.cpu().numpy(), gm_ref) < tol
+        assert_close(Ms.grad.cpu().numpy(), gMs_ref, tol)
+        assert_close(Ku.grad.cpu().numpy(), gKu_ref, tol)
+        assert_close(m.grad.cpu().numpy(), gm_ref, tol)
 
 
 def test_trajectory_gradient_vs_central_differences():

@@ -8,7 +8,7 @@ import pytest
 import oracle
 from oracle import llg
 from paper_2008_02478_gb300 import inputs
-from tests.gpu_util import rel_l2, to_dev, torch_cuda
+from tests.gpu_util import assert_close, rel_l2, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -37,7 +37,7 @@ def test_oersted_matches_direct_sum(n, h):
     plan = OerstedPlan(*n, *h)
     H = plan.apply(to_dev(torch, J)).cpu().numpy()
     plan.sync_status()
-    assert rel_l2(H, ref) < 1e-5
+    assert_close(H, ref, 1e-5)
 
 
 def test_oersted_field_drives_the_llg_step():
@@ -61,7 +61,7 @@ def test_oersted_field_drives_the_llg_step():
     plan.llg_step(m, LLGParams(Ms=8e5, A=1.3e-11, alpha=0.1), dt)
     got = m.cpu().numpy().astype(np.float64)
     assert np.abs(ref - m0).max() > 1e-3
-    assert rel_l2(got - m0, ref - m0) < 2e-4
+    assert_close(got - m0, ref - m0, 2e-4)
     # the Oersted field counts with the Zeeman energy
     E = plan.energy_terms(m, LLGParams(Ms=8e5, A=1.3e-11, alpha=0.1))
     mm = m.cpu().numpy().astype(np.float64)

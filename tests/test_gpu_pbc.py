@@ -10,7 +10,7 @@ import pytest
 import oracle
 from oracle import llg
 from paper_2008_02478_gb300 import inputs
-from tests.gpu_util import rel_l2, to_dev, torch_cuda
+from tests.gpu_util import assert_close, rel_l2, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -32,7 +32,7 @@ def test_pbc_demag_matches_oracle(n, h, images, fp64):
     ref = oracle.DemagPlan(*n, *h, table=table).apply(M)
     plan = Plan(*n, *h, fp64=fp64, images=images)
     H = plan.apply(to_dev(torch, M, fp64)).cpu().numpy()
-    assert rel_l2(H, ref) < (1e-9 if fp64 else 1e-5)
+    assert_close(H, ref, (1e-9 if fp64 else 1e-5))
 
 
 @pytest.mark.parametrize("n,images,dmi", [((16, 12, 3), (3, 2, 0), None), ((15, 12, 3), (2, 2, 0), None),
@@ -59,7 +59,7 @@ def test_pbc_rk4_step_matches_oracle(n, images, dmi):
     plan.llg_step(m, LLGParams(Ms=8e5, A=1.3e-11, alpha=0.1, Hext=(1e4, 0.0, 3e4)), dt)
     got = m.cpu().numpy().astype(np.float64)
     assert np.abs(ref - m0).max() > 1e-3
-    assert rel_l2(got - m0, ref - m0) < 2e-4
+    assert_close(got - m0, ref - m0, 2e-4)
 
 
 def test_pbc_argument_checks():

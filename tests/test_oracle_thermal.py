@@ -6,16 +6,67 @@
     <m.h> = coth(xi) - 1/xi, xi = mu0 Ms V H / (k_B T).  This fixes the
     magnitude of the field (a factor 2 in sigma^2 moves xi by 2) and its
     placement in the LLG equation.
-  * The generator: Philox is a bijection of the counter for a fixed key
+  * The generator: the published known-answer vectors of Philox4x32-10
+    (tests/golden/philox4x32_10_kat.txt, with their source) fix its rounds,
+    multipliers, key schedule and word order bit for bit; beyond that, Philox
+    is a bijection of the counter for a fixed key
     (distinct counters give distinct words), its uniforms are flat and its
     Box-Muller normals have unit variance and no correlation between
     components, cells, steps or seeds.
 """
+import os
+
 import numpy as np
 import pytest
 
 from oracle import llg
 from oracle import thermal as th
+
+KAT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+
+
+def kat_vectors():
+    """(counter words, key words, output words) of each published vector."""
+    rows = []
+    for line in open(KAT):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    rows = kat_vectors()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        got = th.philox4x32_10(*[np.array([c], dtype=np.uint64) for c in ctr], *key)
+        assert [int(g[0]) for g in got] == want, (ctr, key)
+
+
+def test_philox_known_answers_catch_plausible_mistakes():
+    """Each of these slips (swapped output words, nine rounds, a wrong Weyl
+    constant) changes every known-answer output, so the vectors above are a
+    real pin of the round function."""
+    ctr, key, want = kat_vectors()[2]
+
+    def run(rounds=10, w0=th.W0, swap=False):
+        c0, c1, c2, c3 = (np.uint64(x) for x in ctr)
+        k0, k1 = np.uint64(key[0]), np.uint64(key[1])
+        mask = np.uint64(0xFFFFFFFF)
+        for r in range(rounds):
+            p0, p1 = c0 * np.uint64(th.M0), c2 * np.uint64(th.M1)
+            hi0, lo0, hi1, lo1 = p0 >> np.uint64(32), p0 & mask, p1 >> np.uint64(32), p1 & mask
+            if swap:
+                c0, c1, c2, c3 = hi0 ^ c1 ^ k0, lo0, hi1 ^ c3 ^ k1, lo1
+            else:
+                c0, c1, c2, c3 = hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0
+            k0, k1 = (k0 + np.uint64(w0)) & mask, (k1 + np.uint64(th.W1)) & mask
+        return [int(c0), int(c1), int(c2), int(c3)]
+
+    assert run() == want
+    for bad in (run(rounds=9), run(w0=th.W0 + 2), run(swap=True)):
+        assert all(b != w for b, w in zip(bad, want))
 
 
 def test_philox_words_are_distinct_and_uniform():
