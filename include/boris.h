@@ -221,11 +221,19 @@ typedef struct {
  *   + (2Ku/(mu0 Ms))(m.e)e + Hext.
  *   RK4: four field evaluations (four demag applications), *dt is the step
  *   and is not changed; m is renormalised after the step.
- *   RKF45: trial steps with the embedded error max |m5 - m4| until one is
- *   accepted (at most 16 trials, else BORIS_ERR_STEP_CONTROL); *dt is the
- *   step to try on input and, on return, the controller's next step
- *   dt*clip(0.9 (tol/err)^(1/5), 0.2, 2) within [dt_min, dt_max].  RKF45
- *   synchronises the stream once per trial to read the decision.
+ *   RKF45: trial steps with the embedded error max |m5 - m4| (an FP64 max
+ *   over cells) until one is accepted - err <= tol, or dt <= dt_min - at
+ *   most 16 trials, else BORIS_ERR_STEP_CONTROL (also latched in the status
+ *   word) with m unchanged.  The decision and the step size live on the
+ *   device: one step is a CUDA graph whose conditional WHILE node repeats the
+ *   trial until a one-thread controller kernel accepts it; no host decision
+ *   is taken between trials.  *dt is the step to try on input and, on
+ *   return, the controller's next step dt*clip(0.9 (tol/err)^(1/5), 0.2, 2)
+ *   within [dt_min, dt_max]; reading it back synchronises the stream once
+ *   per accepted step (boris_llg_run_rkf45 takes many steps per
+ *   synchronisation).  The graph is captured on the first call and again
+ *   when m, *prm or the field terms change (that capture synchronises the
+ *   stream once).
  */
 int boris_llg_step(boris_plan p, float* m, const boris_llg_params* prm, double* dt);
 int boris_llg_step_f64(boris_plan p, double* m, const boris_llg_params* prm, double* dt);
@@ -258,6 +266,21 @@ int boris_llg_step_backward_f64(boris_plan p, const double* m_in, const boris_ll
  *   The capture synchronises the plan's stream once.
  */
 int boris_llg_run_graph(boris_plan p, float* m, const boris_llg_params* prm, double dt, int nsteps);
+
+/*
+ * boris_llg_run_rkf45 - nsteps accepted RKF45 steps of boris_llg_step (FP32
+ *   single-mesh plans) with the step control on the device (Section 2:
+ *   4th order with an embedded 5th order error estimator): starting from the
+ *   step *dt, each step is one launch of the plan's RKF45 step graph (trial
+ *   loop as a conditional WHILE node, at most 16 trials), and the step size
+ *   carries from step to step in device memory.  The host enqueues the
+ *   launches only and synchronises once at the end, to return in *dt the
+ *   controller's next step and in *t_elapsed (may be NULL) the simulated
+ *   time of the accepted steps.  Returns BORIS_ERR_STEP_CONTROL if any step
+ *   exhausted its trials (m then keeps the state before that step).
+ */
+int boris_llg_run_rkf45(boris_plan p, float* m, const boris_llg_params* prm, double* dt, int nsteps,
+                        double* t_elapsed);
 
 /*
  * boris_llg_run_host - end-to-end form for callers holding host memory:

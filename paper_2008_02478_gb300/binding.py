@@ -28,7 +28,7 @@ GAMMA = MU0 * 2.00231930436256 * 9.2740100783e-24 / 1.054571817e-34
 #: entry points declared in include/boris.h
 EXPORTS = ["boris_demag_plan", "boris_multimesh_plan", "boris_plan_multimesh_info", "boris_demag_apply", "boris_demag_apply_f64", "boris_demag_apply_noalloc",
            "boris_demag_adjoint",
-           "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_energy",
+           "boris_llg_step", "boris_llg_step_f64", "boris_llg_run_graph", "boris_llg_step_backward", "boris_llg_step_backward_f64", "boris_llg_run_host", "boris_llg_run_rkf45", "boris_energy",
            "boris_energy_terms", "boris_set_field_terms", "boris_demag_plan_pbc",
            "boris_thermal_set_step", "boris_philox4x32_10", "boris_oersted_plan", "boris_oersted_apply",
            "boris_sync_status", "boris_last_error", "boris_plan_padded", "boris_plan_schedule", "boris_plan_device_bytes",
@@ -114,6 +114,7 @@ def lib():
         L.boris_llg_step_backward_f64.argtypes = [vp, vp, P(LLGParamsC), d, vp, vp, vp, vp]
         L.boris_llg_run_host.argtypes = [vp, vp, P(LLGParamsC), d, i]
         L.boris_llg_run_graph.argtypes = [vp, vp, P(LLGParamsC), d, i]
+        L.boris_llg_run_rkf45.argtypes = [vp, vp, P(LLGParamsC), P(d), i, P(d)]
         L.boris_energy.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_energy_terms.argtypes = [vp, vp, P(LLGParamsC), P(d)]
         L.boris_set_field_terms.argtypes = [vp, P(FieldTermsC)]
@@ -311,6 +312,15 @@ class Plan:
         c = self._params(prm)
         check(lib().boris_llg_run_graph(self._h, _ptr(m, self.dtype, self.field_shape), ctypes.byref(c), float(dt),
                                         int(nsteps)))
+
+    def llg_run_rkf45(self, m, prm: LLGParams, dt: float, nsteps: int):
+        """nsteps accepted RKF45 steps with device-side step control (FP32 plans);
+        one synchronisation at the end.  Returns (next dt, simulated time)."""
+        c = self._params(prm)
+        h, t = ctypes.c_double(dt), ctypes.c_double(0.0)
+        check(lib().boris_llg_run_rkf45(self._h, _ptr(m, self.dtype, self.field_shape), ctypes.byref(c),
+                                        ctypes.byref(h), int(nsteps), ctypes.byref(t)))
+        return h.value, t.value
 
     def llg_run_host(self, m_host, prm: LLGParams, dt: float, nsteps: int):
         """m_host: CPU float32 tensor (pinned for speed), updated in place."""

@@ -76,8 +76,16 @@ struct boris_plan_s {
     void* acc = nullptr;
     void* kbuf = nullptr;   // RKF45: 6 stage derivatives
     void* mtrial = nullptr; // RKF45: trial solution
-    unsigned int* err_bits = nullptr;
-    unsigned int* h_err_bits = nullptr;  // pinned
+    // RKF45 step control on the device, its pinned host mirror, and the CUDA
+    // graph of one step (trial loop as a conditional WHILE node), keyed by
+    // the state pointer, the parameters and the field terms
+    RKFControl* d_rkf = nullptr;
+    RKFControl* h_rkf = nullptr;
+    cudaGraphExec_t rkf_exec = nullptr;
+    void* rkf_m = nullptr;
+    boris_llg_params rkf_prm = {};
+    long long rkf_terms_version = -1;
+    long long rkf_trial_launches = 0;  // kernel launches of one trial
     double* energy = nullptr;
     void* m_dev_e2e = nullptr;
     // CUDA graph of one RK4 step (boris_llg_run_graph), keyed by its arguments
@@ -345,6 +353,7 @@ int check_params(boris_plan p, const boris_llg_params* prm, LLGArgs<T>* a, doubl
     a->seed_hi = (unsigned int)(t.seed >> 32);
     a->step = p->d_step;
     a->hadd = p->has_terms ? (const T*)t.H_add : nullptr;
+    a->dt_dev = nullptr;
     if (a->th_s0 > 0 && !p->d_step) return fail(BORIS_ERR_INVALID_ARG, "thermal step counter missing");
     if (a->th_s0 > 0) a->extra = 1;
     return BORIS_OK;
@@ -362,8 +371,11 @@ int ensure_llg_workspace(boris_plan p, bool rkf)
     if (rkf) {
         if (!p->kbuf && (rc = dev_alloc(p, &p->kbuf, 6 * vb))) return rc;
         if (!p->mtrial && (rc = dev_alloc(p, &p->mtrial, vb))) return rc;
-        if (!p->err_bits && (rc = dev_alloc(p, (void**)&p->err_bits, 16))) return rc;
-        if (!p->h_err_bits) CUDA_TRY(cudaMallocHost((void**)&p->h_err_bits, 16));
+        if (!p->d_rkf) {
+            if ((rc = dev_alloc(p, (void**)&p->d_rkf, sizeof(RKFControl)))) return rc;
+            CUDA_TRY(cudaMemsetAsync(p->d_rkf, 0, sizeof(RKFControl), p->stream));
+        }
+        if (!p->h_rkf) CUDA_TRY(cudaMallocHost((void**)&p->h_rkf, sizeof(RKFControl)));
     }
     return BORIS_OK;
 }
@@ -408,46 +420,156 @@ int rk4_step_t(boris_plan p, T* m, const LLGArgs<T>& a)
     return BORIS_OK;
 }
 
+// One RKF45 trial (six stages of Fehlberg's tableau) from m into mtrial at the
+// step size held on the device; the embedded error max goes to d_rkf->err_bits.
 template <typename T>
-int rkf45_step_t(boris_plan p, T* m, const boris_llg_params* prm, double* dt)
+int rkf45_trial_t(boris_plan p, const T* m, LLGArgs<T> a)
 {
-    LLGArgs<T> a;
-    double h = *dt;
-    if (!(h > 0)) return fail(BORIS_ERR_INVALID_ARG, "dt must be > 0");
-    if (!(prm->tol > 0) || !(prm->dt_min > 0) || !(prm->dt_max >= prm->dt_min))
-        return fail(BORIS_ERR_INVALID_ARG, "RKF45 needs tol > 0 and 0 < dt_min <= dt_max");
-    T* ms_map = (T*)prm->Ms_map;
+    a.dt_dev = &p->d_rkf->dt;
+    T* ms_map = (T*)a.ms_map;
     T* Hd = (T*)p->Hd;
     T* sa = (T*)p->msa;
+    T* sb = (T*)p->msb;
     T* kb = (T*)p->kbuf;
-    for (int attempt = 0; attempt < 16; attempt++) {
-        int rc = check_params<T>(p, prm, &a, h);
+    // stage states alternate m -> sa -> sb -> sa -> sb -> sa -> (trial)
+    const T* in[6] = {m, sa, sb, sa, sb, sa};
+    T* out[6] = {sa, sb, sa, sb, sa, (T*)p->mtrial};
+    for (int s = 0; s < 6; s++) {
+        int rc = demag_apply_t<T>(p, in[s], ms_map, a.Ms, Hd);
         if (rc) return rc;
-        CUDA_TRY(cudaMemsetAsync(p->err_bits, 0, sizeof(unsigned int), p->stream));
-        // stage states alternate m -> sa -> sb -> sa -> sb -> sa -> (trial)
-        T* sb = (T*)p->msb;
-        const T* in[6] = {m, sa, sb, sa, sb, sa};
-        T* out[6] = {sa, sb, sa, sb, sa, (T*)p->mtrial};
-        for (int s = 0; s < 6; s++) {
-            rc = demag_apply_t<T>(p, in[s], ms_map, a.Ms, Hd);
-            if (rc) return rc;
-            CUDA_TRY(timed(p, 3, [&] { return launch_rkf45_stage<T>(a, s, in[s], Hd, m, kb, out[s], p->err_bits, p->stream); }));
-        }
-        CUDA_TRY(cudaMemcpyAsync(p->h_err_bits, p->err_bits, sizeof(unsigned int), cudaMemcpyDeviceToHost, p->stream));
-        CUDA_TRY(cudaStreamSynchronize(p->stream));
-        float errf;
-        std::memcpy(&errf, p->h_err_bits, sizeof(float));
-        const double err = errf;
-        const double fac = err == 0.0 ? 2.0 : std::fmin(2.0, std::fmax(0.2, 0.9 * std::pow(prm->tol / err, 0.2)));
-        const double hn = std::fmin(prm->dt_max, std::fmax(prm->dt_min, h * fac));
-        if (err <= prm->tol || h <= prm->dt_min) {
-            CUDA_TRY(cudaMemcpyAsync(m, p->mtrial, 3 * ncell(p) * sizeof(T), cudaMemcpyDeviceToDevice, p->stream));
-            *dt = hn;
-            return BORIS_OK;
-        }
-        h = hn;
+        CUDA_TRY(timed(p, 3, [&] {
+            return launch_rkf45_stage<T>(a, s, in[s], Hd, m, kb, out[s], &p->d_rkf->err_bits, p->stream);
+        }));
     }
-    return fail(BORIS_ERR_STEP_CONTROL, "RKF45: 16 trial steps rejected");
+    return BORIS_OK;
+}
+
+// The CUDA graph of one RKF45 step: begin (no trial yet) -> WHILE(trial,
+// controller) -> accept (m = trial if accepted).  The controller ends the loop
+// when a trial is accepted or RKF_MAX_TRIALS were rejected, so one launch of
+// the graph never runs more than RKF_MAX_TRIALS trials and needs no host
+// decision.
+template <typename T>
+int rkf45_graph_t(boris_plan p, T* m, const boris_llg_params* prm, const LLGArgs<T>& a)
+{
+    const bool same = p->rkf_exec && p->rkf_m == (void*)m && p->rkf_terms_version == p->terms_version &&
+                      std::memcmp(&p->rkf_prm, prm, sizeof(*prm)) == 0;
+    if (same) return BORIS_OK;
+    if (p->rkf_exec) {
+        cudaGraphExecDestroy(p->rkf_exec);
+        p->rkf_exec = nullptr;
+    }
+    if (!p->gstream) CUDA_TRY(cudaStreamCreateWithFlags(&p->gstream, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaStream_t user = p->stream;
+    const bool prof = p->prof;
+    const long long before = p->launches;
+    p->stream = p->gstream;  // the caller's stream may be the legacy default stream, which cannot be captured
+    p->prof = false;
+    int rc = BORIS_OK;
+    cudaError_t e = cudaSuccess;
+    cudaGraphNode_t begin = nullptr, loop = nullptr;
+    size_t nn = 0;
+    cudaGraphConditionalHandle cond = 0;
+    auto capture_into = [&](cudaGraph_t target, const cudaGraphNode_t* dep, size_t ndep, auto&& body) -> cudaError_t {
+        cudaError_t ce = cudaStreamBeginCaptureToGraph(p->gstream, target, dep, nullptr, ndep,
+                                                       cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) return ce;
+        body();
+        cudaGraph_t out = nullptr;
+        cudaError_t ce2 = cudaStreamEndCapture(p->gstream, &out);
+        return ce2;
+    };
+    // 1. begin
+    e = capture_into(g, nullptr, 0, [&] {
+        cudaError_t le = launch_rkf45_begin(p->d_rkf, p->gstream);
+        if (le != cudaSuccess) rc = fail(BORIS_ERR_CUDA, std::string("rkf45 begin: ") + cudaGetErrorString(le));
+    });
+    if (e == cudaSuccess && rc == BORIS_OK) e = cudaGraphGetNodes(g, nullptr, &nn);
+    if (e == cudaSuccess && rc == BORIS_OK && nn == 1) e = cudaGraphGetNodes(g, &begin, &nn);
+    // 2. the trial loop
+    if (e == cudaSuccess && rc == BORIS_OK) e = cudaGraphConditionalHandleCreate(&cond, g, 1u, cudaGraphCondAssignDefault);
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess && rc == BORIS_OK) {
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&loop, g, &begin, nullptr, 1, &np);
+        if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
+    }
+    long long trial_launches = 0;
+    if (e == cudaSuccess && rc == BORIS_OK) {
+        const long long b0 = p->launches;
+        e = capture_into(body, nullptr, 0, [&] {
+            rc = rkf45_trial_t<T>(p, m, a);
+            if (rc == BORIS_OK) {
+                cudaError_t le = launch_rkf45_control(p->d_rkf, prm->tol, prm->dt_min, prm->dt_max, p->d_status, cond,
+                                                      p->gstream);
+                if (le != cudaSuccess) rc = fail(BORIS_ERR_CUDA, std::string("rkf45 control: ") + cudaGetErrorString(le));
+                p->launches++;
+            }
+        });
+        trial_launches = p->launches - b0;
+    }
+    // 3. accept
+    if (e == cudaSuccess && rc == BORIS_OK) {
+        e = capture_into(g, &loop, 1, [&] {
+            cudaError_t le = launch_rkf45_accept<T>(p->d_rkf, (const T*)p->mtrial, m, 3 * ncell(p), p->gstream);
+            if (le != cudaSuccess) rc = fail(BORIS_ERR_CUDA, std::string("rkf45 accept: ") + cudaGetErrorString(le));
+        });
+    }
+    p->stream = user;
+    p->prof = prof;
+    p->launches = before;
+    if (rc == BORIS_OK && e != cudaSuccess) rc = fail(BORIS_ERR_CUDA, std::string("RKF45 step graph: ") + cudaGetErrorString(e));
+    if (rc == BORIS_OK) {
+        e = cudaGraphInstantiate(&p->rkf_exec, g, 0);
+        if (e != cudaSuccess) {
+            p->rkf_exec = nullptr;
+            rc = fail(BORIS_ERR_CUDA, std::string("RKF45 graph instantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    cudaGraphDestroy(g);
+    if (rc != BORIS_OK) {
+        cudaGetLastError();
+        return rc;
+    }
+    p->rkf_m = (void*)m;
+    p->rkf_prm = *prm;
+    p->rkf_terms_version = p->terms_version;
+    p->rkf_trial_launches = trial_launches;
+    return BORIS_OK;
+}
+
+// nsteps accepted RKF45 steps from *dt (device-side control; graph launches
+// only), then one copy of the controller state to the host and one
+// synchronisation.  *dt receives the controller's next step.
+template <typename T>
+int rkf45_run_t(boris_plan p, T* m, const boris_llg_params* prm, double* dt, int nsteps, double* t_elapsed)
+{
+    if (!(*dt > 0) || !std::isfinite(*dt)) return fail(BORIS_ERR_INVALID_ARG, "dt must be > 0");
+    if (!(prm->tol > 0) || !(prm->dt_min > 0) || !(prm->dt_max >= prm->dt_min))
+        return fail(BORIS_ERR_INVALID_ARG, "RKF45 needs tol > 0 and 0 < dt_min <= dt_max");
+    LLGArgs<T> a;
+    int rc = check_params<T>(p, prm, &a, 1.0);
+    if (rc) return rc;
+    if ((rc = rkf45_graph_t<T>(p, m, prm, a))) return rc;
+    CUDA_TRY(launch_rkf45_set_dt(p->d_rkf, *dt, true, p->stream));
+    for (int i = 0; i < nsteps; i++) CUDA_TRY(cudaGraphLaunch(p->rkf_exec, p->stream));
+    CUDA_TRY(cudaMemcpyAsync(p->h_rkf, p->d_rkf, sizeof(RKFControl), cudaMemcpyDeviceToHost, p->stream));
+    CUDA_TRY(cudaStreamSynchronize(p->stream));
+    const RKFControl& c = *p->h_rkf;
+    p->launches += 1 + (long long)nsteps * 2 + (long long)c.trials * p->rkf_trial_launches;
+    *dt = c.dt;
+    if (t_elapsed) *t_elapsed = c.t;
+    if (c.failed_steps > 0)
+        return fail(BORIS_ERR_STEP_CONTROL, "RKF45: " + std::to_string(c.failed_steps) + " step(s) rejected " +
+                                                std::to_string(RKF_MAX_TRIALS) + " trials in a row");
+    return BORIS_OK;
 }
 
 template <typename T>
@@ -468,9 +590,7 @@ int llg_step_t(boris_plan p, T* m, const boris_llg_params* prm, double* dt)
         if (p->ml) return fail(BORIS_ERR_INVALID_ARG, "multi-mesh plans step with RK4");
         if (p->has_terms && p->terms.temperature > 0)
             return fail(BORIS_ERR_INVALID_ARG, "the thermal field steps with RK4 (fixed dt)");
-        LLGArgs<T> a;
-        if ((rc = check_params<T>(p, prm, &a, 1.0))) return rc;
-        return rkf45_step_t<T>(p, m, prm, dt);
+        return rkf45_run_t<T>(p, m, prm, dt, 1, nullptr);
     }
     return fail(BORIS_ERR_INVALID_ARG, "unknown method");
 }
@@ -1180,6 +1300,21 @@ int boris_llg_run_graph(boris_plan p, float* m, const boris_llg_params* prm, dou
     return BORIS_OK;
 }
 
+int boris_llg_run_rkf45(boris_plan p, float* m, const boris_llg_params* prm, double* dt, int nsteps, double* t_elapsed)
+{
+    if (!p || !m || !prm || !dt) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
+    if (p->f64) return fail(BORIS_ERR_INVALID_ARG, "FP64 plan: use boris_llg_step_f64");
+    if (p->oersted) return fail(BORIS_ERR_INVALID_ARG, "an Oersted plan serves boris_oersted_apply only");
+    if (prm->method != BORIS_RKF45 || nsteps < 0) return fail(BORIS_ERR_INVALID_ARG, "RKF45 with nsteps >= 0");
+    if (p->ml) return fail(BORIS_ERR_INVALID_ARG, "multi-mesh plans step with RK4");
+    if (p->has_terms && p->terms.temperature > 0)
+        return fail(BORIS_ERR_INVALID_ARG, "the thermal field steps with RK4 (fixed dt)");
+    if (!aligned16(m)) return fail(BORIS_ERR_INVALID_ARG, "m must be 16-byte aligned");
+    int rc = ensure_llg_workspace<float>(p, true);
+    if (rc) return rc;
+    return rkf45_run_t<float>(p, m, prm, dt, nsteps, t_elapsed);
+}
+
 int boris_llg_run_host(boris_plan p, float* m_host, const boris_llg_params* prm, double dt, int nsteps)
 {
     if (!p || !m_host || !prm) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
@@ -1373,14 +1508,15 @@ void boris_plan_destroy(boris_plan p)
 {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
-    void* ptrs[] = {p->Kml, p->d_pairs, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->err_bits, p->energy,
+    void* ptrs[] = {p->Kml, p->d_pairs, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->d_rkf, p->energy,
                     p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (p->tw && p->tw != (void*)p->tw64) cudaFree(p->tw);
     if (p->tw64) cudaFree(p->tw64);
-    if (p->h_err_bits) cudaFreeHost(p->h_err_bits);
+    if (p->h_rkf) cudaFreeHost(p->h_rkf);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->rkf_exec) cudaGraphExecDestroy(p->rkf_exec);
     if (p->gstream) cudaStreamDestroy(p->gstream);
     for (auto& u : p->ev_used) {
         cudaEventDestroy(u.second.first);

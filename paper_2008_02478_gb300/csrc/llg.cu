@@ -187,10 +187,11 @@ template <typename T>
 __global__ void __launch_bounds__(256) rkf45_stage_kernel(LLGArgs<T> a, int s, const T* __restrict__ ms,
                                                           const T* __restrict__ Hd, const T* __restrict__ m0,
                                                           T* __restrict__ kbuf, T* __restrict__ mnext,
-                                                          unsigned int* __restrict__ err_bits)
+                                                          unsigned long long* __restrict__ err_bits)
 {
     const size_t n = a.ncell;
-    float local_err = 0.f;
+    const T dt = a.dt_dev ? (T)*a.dt_dev : a.dt;
+    double local_err = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const int x = (int)(i % a.nx);
         const int y = (int)((i / a.nx) % a.ny);
@@ -203,35 +204,92 @@ __global__ void __launch_bounds__(256) rkf45_stage_kernel(LLGArgs<T> a, int s, c
 #pragma unroll
             for (int c = 0; c < 3; c++) {
                 T v = m0[c * n + i];
-                for (int j = 0; j < s; j++) v += a.dt * T(RKF_A[s + 1][j]) * kbuf[((size_t)j * 3 + c) * n + i];
-                v += a.dt * T(RKF_A[s + 1][s]) * k[c];
+                for (int j = 0; j < s; j++) v += dt * T(RKF_A[s + 1][j]) * kbuf[((size_t)j * 3 + c) * n + i];
+                v += dt * T(RKF_A[s + 1][s]) * k[c];
                 mnext[c * n + i] = v;
             }
         } else {
-            T v4[3], d[3];
+            T v4[3];
+            double e2 = 0.0;
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                T s4 = T(0), s5 = T(0);
+                T s4 = T(0);
+                double d = 0.0;  // m5 - m4 = dt sum_j (b5_j - b4_j) k_j, accumulated in FP64
                 for (int j = 0; j < 6; j++) {
                     const T kj = j == 5 ? k[c] : kbuf[((size_t)j * 3 + c) * n + i];
                     s4 += T(RKF_B4[j]) * kj;
-                    s5 += T(RKF_B5[j]) * kj;
+                    d += (RKF_B5[j] - RKF_B4[j]) * (double)kj;
                 }
-                v4[c] = m0[c * n + i] + a.dt * s4;
-                d[c] = a.dt * (s5 - s4);
+                v4[c] = m0[c * n + i] + dt * s4;
+                d *= (double)dt;
+                e2 += d * d;
             }
-            const T e = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            local_err = fmaxf(local_err, (float)e);
+            local_err = fmax(local_err, sqrt(e2));
             const T inv = T(1) / sqrt(v4[0] * v4[0] + v4[1] * v4[1] + v4[2] * v4[2]);
 #pragma unroll
             for (int c = 0; c < 3; c++) mnext[c * n + i] = v4[c] * inv;
         }
     }
     if (s == 5) {
-        // non-negative floats order like their bit patterns
-        for (int o = 16; o > 0; o >>= 1) local_err = fmaxf(local_err, __shfl_xor_sync(0xffffffffu, local_err, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(err_bits, __float_as_uint(local_err));
+        // non-negative doubles order like their bit patterns read as unsigned integers
+        for (int o = 16; o > 0; o >>= 1) local_err = fmax(local_err, __shfl_xor_sync(0xffffffffu, local_err, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(err_bits, (unsigned long long)__double_as_longlong(local_err));
     }
+}
+
+__global__ void rkf45_set_dt_kernel(RKFControl* c, double dt, int reset)
+{
+    c->dt = dt;
+    if (reset) {
+        c->t = 0.0;
+        c->trials = 0ull;
+        c->accepted_steps = 0ull;
+        c->failed_steps = 0ull;
+    }
+}
+
+__global__ void rkf45_begin_kernel(RKFControl* c)
+{
+    c->attempts = 0u;
+    c->accepted = 0;
+    c->err_bits = 0ull;
+}
+
+__global__ void rkf45_control_kernel(RKFControl* c, double tol, double dt_min, double dt_max, int* status,
+                                     cudaGraphConditionalHandle loop)
+{
+    const double err = __longlong_as_double((long long)c->err_bits);
+    const double h = c->dt;
+    const double fac = err == 0.0 ? 2.0 : fmin(2.0, fmax(0.2, 0.9 * pow(tol / err, 0.2)));
+    const double hn = fmin(dt_max, fmax(dt_min, h * fac));
+    const bool acc = err <= tol || h <= dt_min;
+    const unsigned int tries = c->attempts + 1u;
+    c->attempts = tries;
+    c->err = err;
+    c->trials += 1ull;
+    c->err_bits = 0ull;
+    c->dt = hn;
+    if (acc) {
+        c->accepted = 1;
+        c->dt_used = h;
+        c->t += h;
+        c->accepted_steps += 1ull;
+    } else if (tries >= RKF_MAX_TRIALS) {
+        c->failed_steps += 1ull;
+        if (status) atomicCAS(status, 0, -6);  // BORIS_ERR_STEP_CONTROL
+    }
+    // repeat the trial only while it is rejected and trials remain: the loop
+    // ends after at most RKF_MAX_TRIALS passes whatever the error is
+    cudaGraphSetConditional(loop, (!acc && tries < RKF_MAX_TRIALS) ? 1u : 0u);
+}
+
+template <typename T>
+__global__ void rkf45_accept_kernel(const RKFControl* __restrict__ c, const T* __restrict__ trial, T* __restrict__ m,
+                                    size_t n)
+{
+    if (!c->accepted) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        m[i] = trial[i];
 }
 
 // FP64 energies: E_demag, E_exchange, E_anisotropy, E_Zeeman, E_DMI.
@@ -459,11 +517,39 @@ cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* H
 
 template <typename T>
 cudaError_t launch_rkf45_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, const T* m0, T* kbuf, T* mnext,
-                               unsigned int* err_bits, cudaStream_t st)
+                               unsigned long long* err_bits, cudaStream_t st)
 {
     rkf45_stage_kernel<T><<<grid_for(a.ncell), 256, 0, st>>>(a, s, ms, Hd, m0, kbuf, mnext, err_bits);
     return cudaGetLastError();
 }
+
+cudaError_t launch_rkf45_set_dt(RKFControl* c, double dt, bool reset_counters, cudaStream_t st)
+{
+    rkf45_set_dt_kernel<<<1, 1, 0, st>>>(c, dt, reset_counters ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rkf45_begin(RKFControl* c, cudaStream_t st)
+{
+    rkf45_begin_kernel<<<1, 1, 0, st>>>(c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rkf45_control(RKFControl* c, double tol, double dt_min, double dt_max, int* status,
+                                 cudaGraphConditionalHandle loop, cudaStream_t st)
+{
+    rkf45_control_kernel<<<1, 1, 0, st>>>(c, tol, dt_min, dt_max, status, loop);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_rkf45_accept(const RKFControl* c, const T* trial, T* m, size_t n, cudaStream_t st)
+{
+    rkf45_accept_kernel<T><<<grid_for(n), 256, 0, st>>>(c, trial, m, n);
+    return cudaGetLastError();
+}
+template cudaError_t launch_rkf45_accept<float>(const RKFControl*, const float*, float*, size_t, cudaStream_t);
+template cudaError_t launch_rkf45_accept<double>(const RKFControl*, const double*, double*, size_t, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_energy(const LLGArgs<T>& a, const T* m, const T* Hd, double* out, cudaStream_t st)
@@ -477,9 +563,9 @@ template cudaError_t launch_rk4_stage<float>(const LLGArgs<float>&, int, const f
 template cudaError_t launch_rk4_stage<double>(const LLGArgs<double>&, int, const double*, const double*, double*,
                                               double*, double*, cudaStream_t);
 template cudaError_t launch_rkf45_stage<float>(const LLGArgs<float>&, int, const float*, const float*, const float*,
-                                               float*, float*, unsigned int*, cudaStream_t);
+                                               float*, float*, unsigned long long*, cudaStream_t);
 template cudaError_t launch_rkf45_stage<double>(const LLGArgs<double>&, int, const double*, const double*,
-                                                const double*, double*, double*, unsigned int*, cudaStream_t);
+                                                const double*, double*, double*, unsigned long long*, cudaStream_t);
 template cudaError_t launch_energy<float>(const LLGArgs<float>&, const float*, const float*, double*, cudaStream_t);
 template cudaError_t launch_energy<double>(const LLGArgs<double>&, const double*, const double*, double*,
                                            cudaStream_t);

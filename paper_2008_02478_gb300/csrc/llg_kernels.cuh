@@ -38,7 +38,42 @@ struct LLGArgs {
     unsigned int seed_lo, seed_hi;
     const unsigned long long* step;
     const T* hadd;      // additive field map [3][nz][ny][nx] (e.g. an Oersted field) or NULL
+    // RKF45 trial steps read their step size here (device memory, set by the
+    // step controller) when non-NULL, else use dt
+    const double* dt_dev;
 };
+
+// Device-side RKF45 step control (Section 2: 4th order with an embedded 5th
+// order error estimate).  One trial = six stages; after it a one-thread
+// controller kernel reads the FP64 error max |m5 - m4| (err_bits: the bit
+// pattern of a non-negative double, which orders like the value), accepts
+// when err <= tol or dt <= dt_min, sets the next step
+// dt clip(0.9 (tol/err)^(1/5), 0.2, 2) within [dt_min, dt_max], and decides
+// whether the trial loop of the captured step graph repeats.
+struct RKFControl {
+    double dt;                     // step of the next trial
+    double dt_used;                // the step that was accepted
+    double err;                    // error of the last trial
+    double t;                      // sum of accepted steps
+    unsigned long long err_bits;   // running max over cells of the trial in flight
+    unsigned int attempts;         // trials of the current step
+    int accepted;                  // the current step was accepted
+    unsigned long long trials;     // all trials since the last reset of the counters
+    unsigned long long accepted_steps;
+    unsigned long long failed_steps;  // steps that ran out of trials
+};
+constexpr unsigned int RKF_MAX_TRIALS = 16;
+// the next step to try
+cudaError_t launch_rkf45_set_dt(RKFControl* c, double dt, bool reset_counters, cudaStream_t st);
+// start of a step: no trial yet, error max cleared
+cudaError_t launch_rkf45_begin(RKFControl* c, cudaStream_t st);
+// after a trial; sets the trial loop's condition (1: repeat) and latches
+// BORIS_ERR_STEP_CONTROL in *status when RKF_MAX_TRIALS trials were rejected
+cudaError_t launch_rkf45_control(RKFControl* c, double tol, double dt_min, double dt_max, int* status,
+                                 cudaGraphConditionalHandle loop, cudaStream_t st);
+// end of a step: m = trial when the step was accepted (else m is unchanged)
+template <typename T>
+cudaError_t launch_rkf45_accept(const RKFControl* c, const T* trial, T* m, size_t n, cudaStream_t st);
 // advances the thermal field's step counter by one (after an RK4 step) / sets it
 cudaError_t launch_thermal_advance(unsigned long long* step, cudaStream_t st);
 cudaError_t launch_thermal_set(unsigned long long* step, unsigned long long v, cudaStream_t st);
@@ -50,7 +85,7 @@ cudaError_t launch_rk4_stage(const LLGArgs<T>& a, int s, const T* ms, const T* H
                              cudaStream_t st);
 template <typename T>
 cudaError_t launch_rkf45_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, const T* m0, T* kbuf, T* mnext,
-                               unsigned int* err_bits, cudaStream_t st);
+                               unsigned long long* err_bits, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fwd_stage(const LLGArgs<T>& a, int s, const T* ms, const T* Hd, const T* m0, T* Hs, T* ks,
                              T* mnext, cudaStream_t st);

@@ -62,7 +62,10 @@ def test_rk4_steps_match_oracle(n, h, per_cell, fp64):
     assert_close(m.cpu().numpy(), ref, 1e-10 if fp64 else 1e-5)
 
 
-def test_rkf45_step_matches_oracle():
+@pytest.mark.parametrize("fp64", [False, True])
+def test_rkf45_step_matches_oracle(fp64):
+    """One accepted RKF45 step (tol large enough to accept the first trial):
+    the 4th-order state and the controller's next step against the oracle."""
     torch = torch_cuda()
     from paper_2008_02478_gb300.binding import Plan, RKF45
     n, h = (24, 12, 2), (2e-9, 2e-9, 3e-9)
@@ -70,13 +73,97 @@ def test_rkf45_step_matches_oracle():
     dem = oracle.DemagPlan(*n, *h)
     dt = 5e-14
     ref, err_ref = llg.rkf45_step(m0, dt, prm, dem.apply)
+    plan = Plan(*n, *h, fp64=fp64)
+    m = to_dev(torch, m0, fp64)
+    gp = _gpu_params(torch, prm, fp64)
+    gp.method, gp.tol, gp.dt_min, gp.dt_max = RKF45, 1.0, 1e-16, 1e-12
+    nxt = plan.llg_step(m, gp, dt)
+    assert_close(m.cpu().numpy(), ref, 1e-10 if fp64 else 1e-5)
+    assert nxt == pytest.approx(llg.rkf45_next_dt(dt, err_ref, 1.0, 1e-16, 1e-12), rel=1e-5 if fp64 else 1e-3)
+
+
+def _oracle_rkf45_run(m, dt, nsteps, prm, demag, tol, dt_min, dt_max):
+    """The oracle's adaptive RKF45 (Section 2 evaluator; controller of the
+    stated reading): accepted states, the accepted steps and the next step."""
+    t, dts, trials = 0.0, [], 0
+    for _ in range(nsteps):
+        for _attempt in range(16):
+            m_new, err = llg.rkf45_step(m, dt, prm, demag)
+            trials += 1
+            hn = llg.rkf45_next_dt(dt, err, tol, dt_min, dt_max)
+            if err <= tol or dt <= dt_min:
+                m, t = m_new, t + dt
+                dts.append(dt)
+                dt = hn
+                break
+            dt = hn
+        else:
+            raise AssertionError("oracle controller ran out of trials")
+    return m, dt, t, dts, trials
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_rkf45_frozen_controller_matches_oracle(fp64):
+    """Parity with the controller frozen: the GPU steps with the oracle's
+    accepted step sequence (every trial accepted), 8 steps."""
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan, RKF45
+    n, h = (24, 12, 2), (3e-9, 3e-9, 3e-9)
+    prm, m0 = _problem(n, h, True, seed=5)
+    dem = oracle.DemagPlan(*n, *h)
+    ref, _, _, dts, _ = _oracle_rkf45_run(m0, 1e-13, 8, prm, dem.apply, 1e-6, 1e-16, 1e-12)
+    plan = Plan(*n, *h, fp64=fp64)
+    m = to_dev(torch, m0, fp64)
+    gp = _gpu_params(torch, prm, fp64)
+    gp.method, gp.tol, gp.dt_min, gp.dt_max = RKF45, 1e30, 1e-16, 1e-12
+    for dt in dts:
+        plan.llg_step(m, gp, dt)
+    assert_close(m.cpu().numpy(), ref, 1e-10 if fp64 else 1e-5)
+
+
+def test_rkf45_device_controller_matches_oracle():
+    """Adaptive RKF45 with rejected trials (the first step is far too long):
+    the device controller's accept/reject decisions, step sizes, simulated
+    time and final state equal the oracle's (FP64 plan, one host
+    synchronisation for all steps)."""
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan, RKF45
+    n, h = (24, 12, 2), (3e-9, 3e-9, 3e-9)
+    prm, m0 = _problem(n, h, False, seed=6)
+    dem = oracle.DemagPlan(*n, *h)
+    tol, dmin, dmax, dt0, nsteps = 1e-5, 1e-16, 1e-12, 3e-12, 6
+    ref, dt_ref, t_ref, dts, trials = _oracle_rkf45_run(m0, dt0, nsteps, prm, dem.apply, tol, dmin, dmax)
+    assert trials > nsteps  # the test exercises rejections
     plan = Plan(*n, *h, fp64=True)
     m = to_dev(torch, m0, True)
     gp = _gpu_params(torch, prm, True)
-    gp.method, gp.tol, gp.dt_min, gp.dt_max = RKF45, 1.0, 1e-16, 1e-12
-    nxt = plan.llg_step(m, gp, dt)
+    gp.method, gp.tol, gp.dt_min, gp.dt_max = RKF45, tol, dmin, dmax
+    dt = dt0
+    for _ in range(nsteps):
+        dt = plan.llg_step(m, gp, dt)
+    assert dt == pytest.approx(dt_ref, rel=1e-8)
     assert_close(m.cpu().numpy(), ref, 1e-10)
-    assert nxt == pytest.approx(llg.rkf45_next_dt(dt, err_ref, 1.0, 1e-16, 1e-12), rel=1e-5)
+
+
+def test_rkf45_run_equals_single_steps():
+    """boris_llg_run_rkf45 (all steps enqueued, one synchronisation) takes the
+    same decisions as step-by-step calls: identical state, step and time."""
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import Plan, RKF45
+    n, h = (40, 24, 3), (3e-9, 3e-9, 3e-9)
+    prm, m0 = _problem(n, h, True, seed=7)
+    plan = Plan(*n, *h)
+    gp = _gpu_params(torch, prm)
+    gp.method, gp.tol, gp.dt_min, gp.dt_max = RKF45, 1e-5, 1e-16, 1e-12
+    a, b = to_dev(torch, m0), to_dev(torch, m0)
+    dt_a = 2e-12
+    for _ in range(5):
+        dt_a = plan.llg_step(a, gp, dt_a)
+    dt_b, t_b = plan.llg_run_rkf45(b, gp, 2e-12, 5)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    assert dt_a == dt_b and t_b > 0
+    assert plan.sync_status() == 0
 
 
 def test_rkf45_rejects_then_accepts():
