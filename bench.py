@@ -266,53 +266,209 @@ def oracle_demag_rates():
     return out
 
 
-def other_workloads(torch, args, world, max_over_ranks):
-    """Throughput of the other workloads of the build on this GPU (FP32):
-    the six-layer multi-mesh stack (batched, one CUDA graph per RK4 step), the
-    256x64x1 RKF45 film, and forward+adjoint RK4 on the 256x256x8 film with
-    per-cell Ms and Ku maps."""
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _gather_stack_cells(H, counts, cells):
+    """Field values [len(cells)][3] at flat cell indices of a concatenated
+    multi-layer field (each layer SoA [3][nz][ny][nx])."""
+    import numpy as np
+    offs = np.cumsum([0] + list(counts))
+    out = []
+    for g in cells:
+        l = int(np.searchsorted(offs, g, side="right") - 1)
+        n, loc, base = counts[l], g - offs[l], 3 * offs[l]
+        out.append([H[base + c * n + loc] for c in range(3)])
+    return np.array(out)
+
+
+def _errs(got, ref):
+    import numpy as np
+    got, ref = np.asarray(got, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_rel": float(np.abs(got - ref).max() / np.abs(ref).max())}
+
+
+def multilayer_workload(torch, args, world, max_over_ranks, check_oracle):
+    """Six-layer stack (Eq. 4): 500 RK4 steps of the batched plan (all layers
+    in each launch, one CUDA graph per step), its demag rate against the plain
+    FP32 alternatives - the six layers as separate single-mesh plans applied in
+    turn (self terms only, no cross-layer field) and the same batched plan with
+    the layers pulled 1 mm apart (self terms only, like-for-like cost) - and
+    the H_d error of each against the oracle's direct Eq. 4 sum at sampled
+    cells."""
     import numpy as np
 
+    from oracle import multilayer as ml
     from paper_2008_02478_gb300 import inputs
-    from paper_2008_02478_gb300.autograd import trajectory
-    from paper_2008_02478_gb300.binding import RKF45, LLGParams, MultiPlan, Plan
-    out = {}
-    # six-layer stack
+    from paper_2008_02478_gb300.binding import LLGParams, MultiPlan, Plan
     d = inputs.MULTILAYER
     layers = d["layers"]
     cells, origins = inputs.stack_geometry(layers, d["hz"], d["gaps"], d["hxy"])
-    total = sum(l[0] * l[1] * l[2] for l in layers)
+    counts = [l[0] * l[1] * l[2] for l in layers]
+    total = sum(counts)
     t0 = time.perf_counter()
     mp = MultiPlan(layers, cells, origins)
     t_plan = time.perf_counter() - t0
     m = np.concatenate([inputs.random_unit(*l, seed=d["seed"] + i).reshape(-1) for i, l in enumerate(layers)])
-    ms = np.concatenate([np.full(l[0] * l[1] * l[2], d["Ms"][i]) for i, l in enumerate(layers)])
+    ms = np.concatenate([np.full(c, d["Ms"][i]) for i, c in enumerate(counts)])
     mg = torch.tensor(m, dtype=torch.float32, device="cuda")
     prm = LLGParams(A=A_EX, alpha=ALPHA, Ms_map=torch.tensor(ms, dtype=torch.float32, device="cuda"))
     dt_ml = 5e-14
     mp.llg_run_graph(mg, prm, dt_ml, 3)
-    K = max(4, args.steps)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nsteps = 500 if not args.short else 20
+    ev0, ev1 = _events(torch)
     torch.cuda.synchronize()
     ev0.record()
-    mp.llg_run_graph(mg, prm, dt_ml, K)
+    mp.llg_run_graph(mg, prm, dt_ml, nsteps)
     ev1.record()
     torch.cuda.synchronize()
     t = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
-    Mf = mg.clone()
-    Hf = torch.empty_like(Mf)
-    mp.apply(Mf, Hf)
+    nrm = torch.sqrt((mg.view(-1)[:3 * counts[0]].view(3, -1) ** 2).sum(0))
+    M = np.concatenate([(m[3 * o:3 * (o + c)].reshape(3, c) * d["Ms"][i]).reshape(-1)
+                        for i, (o, c) in enumerate(zip(np.cumsum([0] + counts[:-1]), counts))])
+    Md = torch.tensor(M, dtype=torch.float32, device="cuda")
+    Hb = torch.empty_like(Md)
+    K = 40 if not args.short else 8
+
+    def rate(fn):
+        for _ in range(2):
+            fn()
+        a, b = _events(torch)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(K):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return world * K / max_over_ranks(a.elapsed_time(b) / 1e3)
+    batched_rate = rate(lambda: mp.apply(Md, Hb))
+    z, nu, NX, NY = mp.info()
+    # the six layers as separate single-mesh FP32 plans (self terms only)
+    singles = [Plan(*l, *cells[i]) for i, l in enumerate(layers)]
+    offs = np.cumsum([0] + counts)
+    Hs = torch.empty_like(Md)
+    views = [(Md[3 * offs[i]:3 * offs[i + 1]].view(3, l[2], l[1], l[0]),
+              Hs[3 * offs[i]:3 * offs[i + 1]].view(3, l[2], l[1], l[0])) for i, l in enumerate(layers)]
+
+    def per_layer():
+        for p, (a, b) in zip(singles, views):
+            p.apply(a, b)
+    single_rate = rate(per_layer)
+    # self terms only, batched: the same layers 1 mm apart (cross terms ~0)
+    far = [(o[0], o[1], o[2] + 1e-3 * i) for i, o in enumerate(origins)]
+    mpf = MultiPlan(layers, cells, far)
+    Hf = torch.empty_like(Md)
+    self_batched_rate = rate(lambda: mpf.apply(Md, Hf))
+    out = {"cells": total, "z_planes": z, "inter_plane_spectra": nu, "frame": [NX, NY], "steps": nsteps,
+           "cell_steps_per_s": world * total * nsteps / t, "ms_per_step": 1e3 * t / nsteps,
+           "max_norm_deviation_layer0": float((nrm - 1).abs().max()),
+           "plan_build_s": t_plan, "dt": dt_ml,
+           "demag_evals_per_s": {"batched_eq4": batched_rate, "per_layer_single_mesh_self_only": single_rate,
+                                 "batched_self_only_layers_1mm_apart": self_batched_rate},
+           "batched": "all layers in each launch, one CUDA graph per RK4 step"}
+    if check_oracle:
+        st = ml.centred_stack(layers, d["hz"], d["gaps"], d["hxy"])
+        sample = inputs.rng(9).integers(0, total, 12)
+        ref = ml.direct_at(st, M, sample)
+        out["h_error_vs_oracle_eq4_at_12_cells"] = {
+            "batched_eq4": _errs(_gather_stack_cells(Hb.cpu().numpy(), counts, sample), ref),
+            "per_layer_single_mesh_self_only": _errs(_gather_stack_cells(Hs.cpu().numpy(), counts, sample), ref),
+            "batched_self_only_vs_per_layer": _errs(_gather_stack_cells(Hf.cpu().numpy(), counts, sample),
+                                                    _gather_stack_cells(Hs.cpu().numpy(), counts, sample))}
+    for p in singles:
+        p.close()
+    mpf.close()
+    mp.close()
+    return out
+
+
+def rkf45_film_workload(torch, args):
+    """256x64x1 film (the shape of muMAG standard problem 4): relaxation from
+    (1,1,1)/sqrt3 at alpha = 0.5 in zero field (chunks of 200 accepted steps
+    until the energy changes by less than 1e-6 relative over a chunk, or 5 ns),
+    then alpha = 0.02 with 25 mT at 170 degrees in-plane and 10000 timed
+    accepted RKF45 steps with the step control on the device (one host
+    synchronisation for all of them)."""
+    from paper_2008_02478_gb300 import inputs
+    from paper_2008_02478_gb300.binding import RKF45, LLGParams, Plan
+    fd = inputs.FILM_SP4_MESH
+    fp = Plan(*fd["n"], *fd["cell"])
+    mf = torch.tensor(inputs.uniform(*fd["n"], (1, 1, 1)), dtype=torch.float32, device="cuda")
+    relax = LLGParams(Ms=8e5, A=A_EX, alpha=0.5, method=RKF45, tol=1e-5, dt_min=1e-16, dt_max=1e-12)
+    h, t_sim, e_prev, chunks = 1e-14, 0.0, None, 0
+    t0 = time.perf_counter()
+    while t_sim < 5e-9:
+        h, dts = fp.llg_run_rkf45(mf, relax, h, 200)
+        t_sim += dts
+        chunks += 1
+        e = sum(fp.energy(mf, relax))
+        if e_prev is not None and abs(e - e_prev) < 1e-6 * abs(e):
+            break
+        e_prev = e
+        if args.short and chunks >= 3:
+            break
+    t_relax = time.perf_counter() - t0
+    drive = LLGParams(Ms=8e5, A=A_EX, alpha=0.02, Hext=(19894.4 * math.cos(math.radians(170)),
+                                                       19894.4 * math.sin(math.radians(170)), 0.0),
+                      method=RKF45, tol=1e-5, dt_min=1e-16, dt_max=1e-12)
+    h, _ = fp.llg_run_rkf45(mf, drive, 1e-14, 20)  # capture the drive's step graph
+    n_acc = 10000 if not args.short else 500
+    fp.profile_read()
+    ev0, ev1 = _events(torch)
+    torch.cuda.synchronize()
     ev0.record()
-    for _ in range(4 * K):
-        mp.apply(Mf, Hf)
+    h, t_drive = fp.llg_run_rkf45(mf, drive, h, n_acc)
     ev1.record()
     torch.cuda.synchronize()
-    td = max_over_ranks(ev0.elapsed_time(ev1) / 1e3)
-    z, nu, NX, NY = mp.info()
-    out["multilayer_6"] = {"cells": total, "z_planes": z, "inter_plane_spectra": nu, "frame": [NX, NY],
-                           "cell_steps_per_s": world * total * K / t, "demag_evals_per_s": world * 4 * K / td,
-                           "plan_build_s": t_plan, "dt": dt_ml, "batched": "all layers per launch, CUDA graph"}
-    mp.close()
+    t = ev0.elapsed_time(ev1) / 1e3
+    _, launches = fp.profile_read()
+    out = {"relax": {"alpha": 0.5, "accepted_steps": 200 * chunks, "simulated_ns": 1e9 * t_sim,
+                     "converged": t_sim < 5e-9, "wall_s": t_relax},
+           "accepted_steps": n_acc, "accepted_steps_per_s": n_acc / t, "cell_steps_per_s": n_acc * 256 * 64 / t,
+           "simulated_ns": 1e9 * t_drive, "last_dt": h, "kernel_launches": launches,
+           "host_syncs": 1, "step_control": "on the device (graph WHILE node per step)"}
+    fp.close()
+    return out
+
+
+def gradient_film_workload(torch, args):
+    """256x256x8 film, 3 nm cells, learnable per-cell Ms and Ku: forward +
+    checkpointed adjoint over 2000 RK4 steps with a checkpoint every 50."""
+    from paper_2008_02478_gb300 import inputs
+    from paper_2008_02478_gb300.autograd import trajectory
+    from paper_2008_02478_gb300.binding import LLGParams, Plan
+    gd = inputs.GRAD_FILM_MESH
+    gp = Plan(*gd["n"], *gd["cell"])
+    nx, ny, nz = gd["n"]
+    Ms = torch.tensor(inputs.smooth_noise(nx, ny, nz, 4.0, 6e5, 1e6, 5), dtype=torch.float32, device="cuda",
+                      requires_grad=True)
+    Ku = torch.tensor(inputs.smooth_noise(nx, ny, nz, 4.0, 0.0, 5e5, 6), dtype=torch.float32, device="cuda",
+                      requires_grad=True)
+    m0 = torch.tensor(inputs.smooth_texture(nx, ny, nz, 4.0, 5), dtype=torch.float32, device="cuda")
+    tgt = torch.tensor(inputs.smooth_texture(nx, ny, nz, 4.0, 3), dtype=torch.float32, device="cuda")
+    base = LLGParams(A=A_EX, alpha=ALPHA, easy=(0.0, 0.0, 1.0))
+    L = ((trajectory(m0, Ms, Ku, gp, base, 2, DT, 50) - tgt) ** 2).sum()
+    L.backward()
+    nst, ck = (2000, 50) if not args.short else (100, 50)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = ((trajectory(m0, Ms, Ku, gp, base, nst, DT, ck) - tgt) ** 2).sum()
+    L.backward()
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    out = {"steps": nst, "checkpoint_every": ck, "loss": float(L.detach()),
+           "forward_plus_adjoint_steps_per_s": nst / t, "cell_steps_per_s": nst * nx * ny * nz / t,
+           "grad_norms": {"Ms": float(Ms.grad.norm()), "Ku": float(Ku.grad.norm())}}
+    gp.close()
+    return out
+
+
+def other_workloads(torch, args, world, max_over_ranks, rank):
+    """Throughput of the other workloads of the build on this GPU (FP32)."""
+    from paper_2008_02478_gb300.binding import LLGParams, Plan
+    out = {"multilayer_6": multilayer_workload(torch, args, world, max_over_ranks, rank == 0 and not args.no_cpu)}
     # periodic 512x512x32 film: x and y periodic by 8 images each side
     t0 = time.perf_counter()
     pp = Plan(*N_MESH, *CELL, images=(8, 8, 0))
@@ -321,7 +477,7 @@ def other_workloads(torch, args, world, max_over_ranks):
     prm_p = LLGParams(Ms=MS, A=A_EX, alpha=ALPHA, Hext=HEXT)
     pp.llg_run_graph(mpb, prm_p, DT, 3)
     K = max(4, args.steps)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0, ev1 = _events(torch)
     torch.cuda.synchronize()
     ev0.record()
     pp.llg_run_graph(mpb, prm_p, DT, K)
@@ -354,50 +510,8 @@ def other_workloads(torch, args, world, max_over_ranks):
                                  "plan_build_s": t_oe_plan}
     op.close()
     del Jd, Hoe
-    # RKF45 film 256x64x1
-    fd = inputs.FILM_SP4_MESH
-    fp = Plan(*fd["n"], *fd["cell"])
-    mf = torch.tensor(inputs.uniform(*fd["n"], (1, 1, 1)), dtype=torch.float32, device="cuda")
-    pr = LLGParams(Ms=8e5, A=A_EX, alpha=0.02, Hext=(19894.4 * math.cos(math.radians(170)),
-                                                      19894.4 * math.sin(math.radians(170)), 0.0),
-                   method=RKF45, tol=1e-5, dt_min=1e-16, dt_max=1e-12)
-    h = 1e-14
-    for _ in range(5):
-        h = fp.llg_step(mf, pr, h)
-    torch.cuda.synchronize()
-    n_acc = 200
-    t0 = time.perf_counter()
-    for _ in range(n_acc):
-        h = fp.llg_step(mf, pr, h)
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    out["rkf45_film_256x64x1"] = {"accepted_steps_per_s": n_acc / t,
-                                  "cell_steps_per_s": n_acc * 256 * 64 / t, "last_dt": h}
-    fp.close()
-    # gradient film 256x256x8: forward + checkpointed adjoint
-    gd = inputs.GRAD_FILM_MESH
-    gp = Plan(*gd["n"], *gd["cell"])
-    nx, ny, nz = gd["n"]
-    Ms = torch.tensor(inputs.smooth_noise(nx, ny, nz, 4.0, 6e5, 1e6, 5), dtype=torch.float32, device="cuda",
-                      requires_grad=True)
-    Ku = torch.tensor(inputs.smooth_noise(nx, ny, nz, 4.0, 0.0, 5e5, 6), dtype=torch.float32, device="cuda",
-                      requires_grad=True)
-    m0 = torch.tensor(inputs.smooth_texture(nx, ny, nz, 4.0, 5), dtype=torch.float32, device="cuda")
-    tgt = torch.tensor(inputs.smooth_texture(nx, ny, nz, 4.0, 3), dtype=torch.float32, device="cuda")
-    base = LLGParams(A=A_EX, alpha=ALPHA, easy=(0.0, 0.0, 1.0))
-    nst = 20
-    L = ((trajectory(m0, Ms, Ku, gp, base, 2, DT, 50) - tgt) ** 2).sum()
-    L.backward()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    L = ((trajectory(m0, Ms, Ku, gp, base, nst, DT, 10) - tgt) ** 2).sum()
-    L.backward()
-    torch.cuda.synchronize()
-    t = time.perf_counter() - t0
-    out["gradient_film_256x256x8"] = {"steps": nst, "checkpoint_every": 10,
-                                      "forward_plus_adjoint_steps_per_s": nst / t,
-                                      "cell_steps_per_s": nst * nx * ny * nz / t}
-    gp.close()
+    out["rkf45_film_256x64x1"] = rkf45_film_workload(torch, args)
+    out["gradient_film_256x256x8"] = gradient_film_workload(torch, args)
     return out
 
 
@@ -589,6 +703,114 @@ def fig11_sweep(torch, Plan, LLGParams, steps):
     return rows
 
 
+def profile_run(args):
+    """--profile demag: a few demag evaluations (and optional RK4 steps) on one
+    mesh, random unit magnetisation; --profile multilayer: a few evaluations
+    of the six-layer stack with the per-kernel-class CUDA-event times.  Small,
+    self-contained runs for ncu captures."""
+    import numpy as np
+    import torch
+
+    from paper_2008_02478_gb300 import build as bld
+    from paper_2008_02478_gb300 import inputs
+    from paper_2008_02478_gb300.binding import LLGParams, MultiPlan, Plan
+    bld.build()
+    if args.profile == "multilayer":
+        d = inputs.MULTILAYER
+        cells, origins = inputs.stack_geometry(d["layers"], d["hz"], d["gaps"], d["hxy"])
+        mp = MultiPlan(d["layers"], cells, origins)
+        M = torch.tensor(np.concatenate([inputs.random_unit(*l, seed=i).reshape(-1)
+                                         for i, l in enumerate(d["layers"])]) * 8e5, dtype=torch.float32,
+                         device="cuda")
+        H = torch.empty_like(M)
+        for _ in range(3):
+            mp.apply(M, H)
+        mp.profile(True)
+        for _ in range(max(1, args.evals)):
+            mp.apply(M, H)
+        k, _ = mp.profile_read()
+        print(json.dumps({kk: round(v[0] / max(v[1], 1), 4) for kk, v in k.items() if v[1]}))
+        return 0
+    n = tuple(int(v) for v in args.mesh.split(","))
+    dt = torch.float64 if args.fp64 else torch.float32
+    plan = Plan(*n, args.cell, args.cell, args.cell, fp64=args.fp64, tc=args.tc)
+    m0 = inputs.random_unit(*n, seed=1)
+    M = torch.tensor(8e5 * m0, dtype=dt, device="cuda")
+    H = torch.empty_like(M)
+    for _ in range(args.evals):
+        plan.apply(M, H)
+    m = torch.tensor(m0, dtype=dt, device="cuda")
+    for _ in range(args.llg_steps):
+        plan.llg_step(m, LLGParams(), 1e-13)
+    torch.cuda.synchronize()
+    print("ok mesh=%s padded=%s schedule=%s" % (n, plan.padded(), plan.schedule()))
+    return 0
+
+
+def demag_row_bytes(plan):
+    """Algorithmic bytes of the hot-path rows per demag evaluation (FP32 or
+    FP64 per the plan): X^ = the x half spectrum [kx][3][nz][ny] complex, N^ =
+    the kernel-spectrum octant (6 reals per (kx, ky', kz')), M and H the real
+    fields.  a2 (x R2C) = M + X^, a3 (y-z pass) = X^ + N^ + Y^ with Y^ the
+    same size as X^, a4 (x C2R) = X^ + H; compulsory = M + H + N^."""
+    nx, ny, nz = plan.shape
+    px, py, pz = plan.padded()
+    es = 8 if plan.fp64 else 4
+    nkx, kyh, kzh = px // 2 + 1, py // 2 + 1, pz // 2 + 1
+    field = 3 * nx * ny * nz * es
+    xhat = nkx * 3 * nz * ny * 2 * es
+    khat = nkx * kyh * kzh * 6 * es
+    return {"a2": field + xhat, "a3": 2 * xhat + khat, "a4": xhat + field, "compulsory": 2 * field + khat,
+            "field": field, "xhat": xhat, "khat": khat}
+
+
+# kernel class -> the hot-path row it realises
+ROW_OF = {"x_r2c": "a2", "yz_conv": "a3", "y_fwd": "a3", "z_conv": "a3", "y_inv": "a3", "x_c2r": "a4",
+          "llg_stage": "a5/a6", "x_c2r_rk4": "a4+a5/a6"}
+DEMAG_KERNELS = ("x_r2c", "yz_conv", "y_fwd", "z_conv", "y_inv", "x_c2r")
+
+
+def film_accuracy_check(torch, plan, prm, m0, nsteps, cpu_threads):
+    """The 512x512x32 film after nsteps RK4 steps (CUDA graph): energies every
+    nsteps/10 steps (damped and driven by a constant field, the total must not
+    rise), the largest deviation of |m| from 1, and H_d of the final state from
+    the FP32 plan against the FP64 oracle's FFT convolution of the same state
+    (one oracle evaluation on the host cores, timed)."""
+    import numpy as np
+
+    import oracle
+    from oracle import llg
+    m = torch.tensor(m0, dtype=torch.float32, device="cuda")
+    energies = [sum(plan.energy(m, prm))]
+    chunk = max(1, nsteps // 10)
+    done = 0
+    while done < nsteps:
+        k = min(chunk, nsteps - done)
+        plan.llg_run_graph(m, prm, DT, k)
+        done += k
+        energies.append(sum(plan.energy(m, prm)))
+    mh = m.cpu().numpy().astype(np.float64)
+    nrm_dev = float(np.abs(np.sqrt((mh * mh).sum(0)) - 1.0).max())
+    M = torch.tensor(MS * mh, dtype=torch.float32, device="cuda")
+    Hg = plan.apply(M).cpu().numpy().astype(np.float64)
+    oracle.set_threads(cpu_threads)
+    t0 = time.perf_counter()
+    dem = oracle.DemagPlan(*N_MESH, *CELL)
+    t_plan = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Ho = dem.apply(MS * mh)
+    t_eval = time.perf_counter() - t0
+    e_or = llg.energies(mh, llg.Params(cell=CELL, Ms=MS, A=A_EX, alpha=ALPHA, Hext=HEXT), lambda _M: Ho)
+    e_gpu = plan.energy(m, prm)
+    de = np.diff(np.array(energies))
+    return {"steps": nsteps, "h_d_vs_oracle": _errs(Hg, Ho),
+            "energies_J_gpu": list(e_gpu), "energies_J_oracle": list(e_or),
+            "energy_rel_err": float(abs(sum(e_gpu) - sum(e_or)) / abs(sum(e_or))),
+            "energy_trace_J": energies, "energy_never_rises": bool((de <= 1e-9 * abs(energies[0])).all()),
+            "max_abs_norm_deviation": nrm_dev,
+            "oracle_512x512x32_eval_s": t_eval, "oracle_plan_s": t_plan, "oracle_threads": cpu_threads}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,14 +820,25 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--short", action="store_true", help="shorter extra workloads (quick checks)")
     ap.add_argument("--sweep", action="store_true",
                     help="only the Fig. 11-shaped size sweep and the FP32 FMA peak (one JSON line)")
+    ap.add_argument("--profile", choices=["demag", "multilayer"], default=None,
+                    help="a small run for profilers (no JSON line): see --mesh, --evals, --llg-steps")
+    ap.add_argument("--mesh", default="512,512,32")
+    ap.add_argument("--cell", type=float, default=4e-9)
+    ap.add_argument("--evals", type=int, default=3)
+    ap.add_argument("--llg-steps", type=int, default=0)
+    ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--tc", default=None, choices=["fp16", "bf16"])
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.profile:
+        return profile_run(args)
     if args.warmup < 3:
         raise SystemExit("need --warmup >= 3")
 
@@ -636,17 +869,29 @@ def main():
     plan.llg_run_graph(m, prm, DT, args.warmup)  # capture + warm the graph
     plan.profile_read()  # reset launch counters
 
-    # ---- A: headline timing (K RK4 steps, no per-kernel events) ----------
+    # ---- A: headline timing (exactly K RK4 steps), then the same K-step
+    #      window repeated until at least 1 s has been timed; the clock sampler
+    #      spans both
     gpu_index = int((os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",") + ["0"])[local]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
     barrier()
     with ClockSampler(gpu_index) as clk:
         t_steps = time_graph(torch, plan, m, prm, args.steps)
+        barrier()
+        _, launches = plan.profile_read()
+        sus_t, sus_windows = 0.0, 0
+        while sus_t < 1.0:
+            sus_t += time_graph(torch, plan, m, prm, args.steps)
+            sus_windows += 1
     barrier()
-    _, launches = plan.profile_read()
+    plan.profile_read()
     t_steps = max_over_ranks(t_steps)
+    sus_t = max_over_ranks(sus_t)
     clocks = clk.summary()
     value = whole_job_rate(world, ncell * args.steps, t_steps)
+    sustained = {"windows": sus_windows, "steps": sus_windows * args.steps, "seconds": sus_t,
+                 "ms_per_step": 1e3 * sus_t / (sus_windows * args.steps),
+                 "value": whole_job_rate(world, ncell * sus_windows * args.steps, sus_t)}
     # the same steps through one boris_llg_step call each (no graph)
     t_calls = max_over_ranks(time_steps(torch, plan, m, prm, args.steps))
 
@@ -658,9 +903,11 @@ def main():
     t_dem = max_over_ranks(time_demag(torch, plan, M, H, 4 * args.steps))
     demag_rate = world * 4 * args.steps / t_dem
 
-    # ---- B: per-kernel CUDA-event durations over K steps -------------------
+    # ---- B: per-kernel CUDA-event durations over at least 1 s of steps ------
+    step_s = t_steps / args.steps
+    n_prof = max(args.steps, int(math.ceil(1.0 / step_s)))
     plan.profile(True)
-    time_steps(torch, plan, m, prm, args.steps)
+    time_steps(torch, plan, m, prm, n_prof)
     kern, _ = plan.profile_read()
     plan.profile(False)
     dominant = max(kern, key=lambda k: kern[k][0])
@@ -669,32 +916,53 @@ def main():
             "x_c2r": xpass_algorithmic_bytes(plan), "llg_stage": llg_algorithmic_bytes(plan),
             "x_c2r_rk4": x_c2r_rk4_algorithmic_bytes(plan)}
     algo.update(split_algorithmic_bytes(plan))
+    rows = demag_row_bytes(plan)
     peak, peak_kind = measured_peaks()
-    dom_bytes = algo.get(dominant)
-    achieved = dom_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9 if dom_bytes else None
+    row = ROW_OF.get(dominant)
+    row_bytes = {"a2": rows["a2"], "a3": rows["a3"], "a4": rows["a4"]}.get(row, algo.get(dominant))
+    achieved = row_bytes / (per_launch_ms[dominant] * 1e-3) / 1e9 if row_bytes else None
     dom_key = dominant
     if dominant == "z_conv":
         dom_key = "z_conv/" + {0: "plain", 1: "tma1", 2: "tma2", 3: "res"}.get(plan.schedule()[2], "plain")
-    roofline = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": peak, "unit": "GB/s",
+    # per demag evaluation: the kernels that realise row a3, and all demag kernels
+    evals = max(1, kern["x_r2c"][1]) if kern.get("x_r2c") else 1
+    a3_ms = sum(kern[k][0] for k in ("yz_conv", "y_fwd", "z_conv", "y_inv") if k in kern) / evals
+    demag_ms = sum(kern[k][0] for k in DEMAG_KERNELS if k in kern) / evals
+    sched_demag = sum(algo[k] * kern[k][1] for k in DEMAG_KERNELS if k in kern and kern[k][1]) / evals
+    roofline = {"bound": "hbm", "kernel": dom_key, "row": row, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic_for(dom_key),
-                "peak_source": peak_kind, "algorithmic_bytes_per_launch": dom_bytes}
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": row_bytes,
+                "bytes_basis": "SURVEY 8(d) bytes of the row the kernel realises, per evaluation",
+                "kernel_own_bytes_per_launch": algo.get(dominant),
+                "a3_pass": {"kernels": [k for k in ("yz_conv", "y_fwd", "z_conv", "y_inv") if k in kern],
+                            "bytes": rows["a3"], "ms_per_eval": a3_ms,
+                            "GBps": rows["a3"] / (a3_ms * 1e-3) / 1e9 if a3_ms else None,
+                            "frac": rows["a3"] / (a3_ms * 1e-3) / 1e9 / peak if a3_ms else None},
+                "demag_eval": {"compulsory_bytes": rows["compulsory"], "schedule_bytes": sched_demag,
+                               "ms_per_eval": demag_ms,
+                               "compulsory_frac": rows["compulsory"] / (demag_ms * 1e-3) / 1e9 / peak,
+                               "schedule_frac": sched_demag / (demag_ms * 1e-3) / 1e9 / peak,
+                               "wasted_traffic_ratio": sched_demag / rows["compulsory"]}}
     # the whole RK4 step against the same peak: the bytes this schedule's
     # kernels move per step (algorithmic bytes per launch x launches per step)
     # and the compulsory bytes of a step (per evaluation M read, H written and
     # the kernel octant read; per stage the LLG stage's bytes)
-    step_s = t_steps / args.steps
-    sched_bytes = sum(algo[k] * kern[k][1] for k in kern if k in algo and kern[k][1]) / args.steps
-    kb = split_algorithmic_bytes(plan)["z_conv"] - 2 * (plan.padded()[0] // 2 + 1) * plan.padded()[1] * 3 * nz * 8
-    compulsory = 4 * (2 * 3 * ncell * 4 + kb) + 4 * llg_algorithmic_bytes(plan)
+    prof_step = n_prof
+    sched_bytes = sum(algo[k] * kern[k][1] for k in kern if k in algo and kern[k][1]) / prof_step
+    compulsory = 4 * rows["compulsory"] + 4 * llg_algorithmic_bytes(plan)
+    three_pass = 4 * (rows["a2"] + rows["a3"] + rows["a4"]) + 4 * llg_algorithmic_bytes(plan)
     step_roofline = {"unit": "GB/s", "peak": peak, "ms_per_step": step_s * 1e3,
                      "schedule_bytes_per_step": sched_bytes, "schedule_GBps": sched_bytes / step_s / 1e9,
                      "schedule_frac": sched_bytes / step_s / 1e9 / peak,
+                     "three_pass_bytes_per_step": three_pass, "three_pass_frac": three_pass / step_s / 1e9 / peak,
                      "compulsory_bytes_per_step": compulsory, "compulsory_GBps": compulsory / step_s / 1e9,
-                     "compulsory_frac": compulsory / step_s / 1e9 / peak}
-    kernels = {k: {"ms_per_launch": per_launch_ms[k], "launches": kern[k][1],
+                     "compulsory_frac": compulsory / step_s / 1e9 / peak,
+                     "wasted_traffic_ratio": sched_bytes / compulsory}
+    kernels = {k: {"ms_per_launch": per_launch_ms[k], "launches": kern[k][1], "row": ROW_OF.get(k),
                    "share": kern[k][0] / max(1e-12, sum(v[0] for v in kern.values())),
                    "algorithmic_GBps": (algo[k] / (per_launch_ms[k] * 1e-3) / 1e9) if (k in algo and per_launch_ms[k]) else None}
                for k in kern if kern[k][1]}
+    kernels_window = {"steps": n_prof, "seconds": sum(v[0] for v in kern.values()) / 1e3}
 
     # ---- further field terms on the same film (interfacial DMI, cubic and
     #      second-order uniaxial anisotropy): one-cell-per-thread stage kernel
@@ -756,26 +1024,33 @@ def main():
         def rel_err(Hx):
             d = (Hx.double() - H64).norm() / H64.norm()
             return float(d)
+
+        def max_err(Hx):
+            return float((Hx.double() - H64).abs().max() / H64.abs().max())
         plan.apply(M, H)
         fp64["h_rel_l2_fp32_vs_fp64"] = rel_err(H)
+        fp64["h_max_rel_fp32_vs_fp64"] = max_err(H)
         mixed = {}
         for tc in ("fp16", "bf16"):
             pt = Plan(nx, ny, nz, *CELL, tc=tc)
             pt.apply(M, H)
-            err = rel_err(H)
+            err, merr = rel_err(H), max_err(H)
             for _ in range(3):
                 pt.apply(M, H)
             td = max_over_ranks(time_demag(torch, pt, M, H, 4 * args.steps))
             mt = torch.tensor(m0, dtype=torch.float32, device="cuda")
-            for _ in range(2):
-                pt.llg_step(mt, prm, DT)
+            pt.llg_run_graph(mt, prm, DT, 3)
+            ts = max_over_ranks(time_graph(torch, pt, mt, prm, args.steps))
             pt.profile(True)
-            ts = max_over_ranks(time_steps(torch, pt, mt, prm, args.steps))
+            time_steps(torch, pt, mt, prm, max(4, args.steps // 4))
             kk, _ = pt.profile_read()
             mixed[tc] = {"demag_evals_per_s": world * 4 * args.steps / td,
                          "cell_steps_per_s": world * ncell * args.steps / ts,
-                         "h_rel_l2_vs_fp64": err,
+                         "ms_per_step": 1e3 * ts / args.steps,
+                         "speedup_vs_fp32_step": (ncell * args.steps / ts) / (value / world),
+                         "h_rel_l2_vs_fp64": err, "h_max_rel_vs_fp64": merr,
                          "z_stage_ms_per_launch": kk["z_conv"][0] / max(1, kk["z_conv"][1]),
+                         "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in kk.items() if v[1]},
                          "z_stage": {5: "tcgen05 (tensor memory)", 4: "mma.sync"}.get(pt.schedule()[2], "?")}
             pt.close()
             del mt
@@ -784,20 +1059,31 @@ def main():
     # ---- other workloads: multi-mesh stack, RKF45 film, gradient film ------
     extra = {}
     if not args.no_extra:
-        extra = other_workloads(torch, args, world, max_over_ranks)
+        extra = other_workloads(torch, args, world, max_over_ranks, rank)
 
     # ---- CPU baseline: the oracle on a bounded sample -----------------------
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
+        allc = oracle.num_threads()
         blk = (256, 256, 32)
         rate, t, cores = oracle_rk4_rate(*blk, 3)
+        oracle.set_threads(1)
+        blk1 = (64, 64, 8)
+        rate1, t1, _ = oracle_rk4_rate(*blk1, 2)
+        oracle.set_threads(allc)
         demag_rates = oracle_demag_rates()
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "three RK4 steps (12 FFT demag evaluations) of the FP64 oracle on a %dx%dx%d block of "
                          "the same film (a quarter of its cells), %.1f s" % (blk + (t,)),
+               "one_thread": {"value": rate1, "unit": UNIT, "sample": "two RK4 steps on a %dx%dx%d block, %.1f s"
+                              % (blk1 + (t1,))},
                "demag_evals_per_s": demag_rates}
+        # the film after 1000 RK4 steps, checked by one oracle evaluation of the full mesh
+        acc = film_accuracy_check(torch, plan, prm, m0, 1000 if not args.short else 50, allc)
+        cpu["demag_evals_per_s"]["512x512x32"] = {"threads_%d" % allc: 1.0 / acc["oracle_512x512x32_eval_s"]}
+        extra["film_512x512x32_after_steps"] = acc
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -807,9 +1093,11 @@ def main():
                            "l2": "inputs larger than L2 (m 100.7 MB, spectrum workspace 201.7 MB, kernel "
                                  "spectrum 208.4 MB per evaluation)",
                            "padded": plan.padded(), "yz_schedule": plan.schedule()},
+                "sustained": sustained,
                 "demag_evals_per_s": demag_rate, "ms_per_step_without_graph": 1e3 * t_calls / args.steps,
-                "fp64": fp64, "workloads": dict(extra, field_terms_512x512x32=terms_line) if terms_line else extra, "mixed_precision": mixed, "roofline": roofline, "step_roofline": step_roofline,
-                "kernels": kernels,
+                "fp64": fp64, "workloads": dict(extra, field_terms_512x512x32=terms_line) if terms_line else extra,
+                "mixed_precision": mixed, "roofline": roofline, "step_roofline": step_roofline,
+                "kernels": kernels, "kernels_window": kernels_window,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()

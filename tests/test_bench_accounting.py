@@ -40,3 +40,14 @@ def test_rk4_stage_bytes_and_fp64():
 
 def test_whole_job_rate_is_all_ranks_work_over_the_slowest():
     assert bench.whole_job_rate(4, 8388608 * 60, 0.165) == pytest.approx(4 * 8388608 * 60 / 0.165)
+
+
+def test_hot_path_row_bytes():
+    """Per-evaluation bytes of the rows: a3 = X^ + N^ + Y^ = 611.8 MB and the
+    compulsory M + H + N^ = 409.8 MB (the figures the roofline reports)."""
+    r = bench.demag_row_bytes(film_plan())
+    assert r["a3"] == 2 * 513 * 3 * 32 * 512 * 8 + 513 * 513 * 33 * 6 * 4
+    assert r["a3"] == pytest.approx(611.8e6, rel=1e-3)
+    assert r["compulsory"] == pytest.approx(409.8e6, rel=1e-3)
+    assert r["a2"] == r["a4"] == bench.xpass_algorithmic_bytes(film_plan())
+    assert bench.ROW_OF["z_conv"] == "a3" and bench.ROW_OF["x_r2c"] == "a2"

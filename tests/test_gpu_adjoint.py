@@ -115,3 +115,37 @@ def test_trajectory_gradient_vs_central_differences():
                  (loss(Ms.detach(), tp) - loss(Ms.detach(), tm)) / (2 * eps)
             g = float(G[idx])
             assert abs(fd - g) <= 1e-5 * float(G.abs().max()) + 1e-5 * abs(fd), (which, fd, g)
+
+
+# meshes where the backward step runs the production kernels: length-1024 x
+# passes with the four-cells-per-thread stage (300 x 64 x 3), length-1024 y
+# passes of the split y-z schedule (64 x 300 x 4), and pz = 64 with a ragged
+# nz (48 x 40 x 17), where the residue-split z stage is a candidate
+BIG = [((300, 64, 3), (3e-9, 3e-9, 3e-9)), ((64, 300, 4), (3e-9, 3e-9, 3e-9)), ((48, 40, 17), (3e-9, 3e-9, 3e-9))]
+
+
+@pytest.mark.parametrize("n,h", BIG)
+@pytest.mark.parametrize("fp64", [False, True])
+def test_step_backward_matches_oracle_on_production_kernels(n, h, fp64):
+    """g_m, g_Ms and g_Ku of one RK4 step against the oracle's discrete adjoint
+    on meshes that take the length-1024 warp transforms, the split y-z
+    schedule and the quad stage kernel."""
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import LLGParams, Plan
+    Ms = inputs.smooth_noise(*n, 2.0, 6e5, 1e6, 15)
+    Ku = inputs.smooth_noise(*n, 2.0, 0.0, 5e5, 16)
+    prm = llg.Params(cell=h, Ms=Ms, A=1.3e-11, alpha=0.02, Ku=Ku, easy=(0.0, 0.0, 1.0), Hext=(0.0, 0.0, 2e4))
+    m0 = inputs.smooth_texture(*n, 1.5, 17)
+    gout = inputs.random_unit(*n, seed=18)
+    dt = 1e-13
+    ref_gm, ref_gMs, ref_gKu = llg.rk4_step_vjp(m0, dt, prm, oracle.DemagPlan(*n, *h).apply, gout)
+    plan = Plan(*n, *h, fp64=fp64)
+    p = LLGParams(A=prm.A, alpha=prm.alpha, gamma=prm.gamma, easy=prm.easy, Hext=prm.Hext,
+                  Ms_map=to_dev(torch, Ms, fp64), Ku_map=to_dev(torch, Ku, fp64))
+    gMs = torch.zeros(n[::-1], dtype=plan.dtype, device="cuda")
+    gKu = torch.zeros_like(gMs)
+    gm = plan.llg_step_backward(to_dev(torch, m0, fp64), p, dt, to_dev(torch, gout, fp64), None, gMs, gKu)
+    tol = 1e-9 if fp64 else 1e-3
+    assert_close(gm.cpu().numpy(), ref_gm, tol)
+    assert_close(gMs.cpu().numpy(), ref_gMs, tol)
+    assert_close(gKu.cpu().numpy(), ref_gKu, tol)

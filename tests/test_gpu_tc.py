@@ -104,3 +104,31 @@ def test_tensor_core_rejects_unsupported_depth():
     with pytest.raises(BorisError) as e:
         Plan(32, 32, 8, 1e-9, 1e-9, 1e-9, tc="fp16")
     assert e.value.code == -4
+
+
+_FILM = {}
+
+
+def _large_film_reference():
+    """512 x 512 x 32 film of 4 nm cells with 2621 columnar Voronoi grains,
+    and the oracle's O(N) direct sums at 24 sampled cells (cached)."""
+    if not _FILM:
+        n, cell, seed = inputs.LARGE_FILM_MESH["n"], inputs.LARGE_FILM_MESH["cell"], inputs.LARGE_FILM_MESH["seed"]
+        M = 8e5 * inputs.voronoi_columnar(*n, cell, 40e-9, seed)
+        T = oracle.tensor_table(*n, *cell)
+        cells = inputs.rng(13).integers(0, n[0] * n[1] * n[2], 24)
+        _FILM.update(n=n, cell=cell, M=M, cells=cells, ref=oracle.demag_direct_at(M, T, cells))
+    return _FILM
+
+
+@pytest.mark.parametrize("tc", ["fp16", "bf16"])
+def test_large_film_tensor_core_stage_sampled_direct_sum(tc, monkeypatch):
+    """The configuration the benchmark times: the tcgen05 z stage on the
+    512 x 512 x 32 film, against the oracle's direct sum at sampled cells."""
+    torch = torch_cuda()
+    f = _large_film_reference()
+    plan = tc_plan(monkeypatch, "tcgen05", *f["n"], *f["cell"], tc=tc)
+    assert plan.schedule()[2] == FORMS["tcgen05"]
+    H = plan.apply(to_dev(torch, f["M"])).cpu().numpy().reshape(3, -1)
+    assert plan.sync_status() == 0
+    assert_close(H[:, f["cells"]].T, f["ref"], 1e-2)
