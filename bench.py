@@ -911,7 +911,11 @@ def main():
     kern, _ = plan.profile_read()
     plan.profile(False)
     dominant = max(kern, key=lambda k: kern[k][0])
-    per_launch_ms = {k: (v[0] / v[1] if v[1] else None) for k, v in kern.items()}
+    # demag kernel classes are timed per evaluation (a chunked schedule
+    # launches them several times per evaluation); the LLG stage per launch
+    evals = max(1, kern["x_r2c"][1]) if kern.get("x_r2c") and kern["x_r2c"][1] else 1
+    units = {k: (evals if k in DEMAG_KERNELS else v[1]) for k, v in kern.items()}
+    per_launch_ms = {k: (v[0] / units[k] if v[1] else None) for k, v in kern.items()}
     algo = {"yz_conv": yz_algorithmic_bytes(plan), "x_r2c": xpass_algorithmic_bytes(plan),
             "x_c2r": xpass_algorithmic_bytes(plan), "llg_stage": llg_algorithmic_bytes(plan),
             "x_c2r_rk4": x_c2r_rk4_algorithmic_bytes(plan)}
@@ -925,10 +929,9 @@ def main():
     if dominant == "z_conv":
         dom_key = "z_conv/" + {0: "plain", 1: "tma1", 2: "tma2", 3: "res"}.get(plan.schedule()[2], "plain")
     # per demag evaluation: the kernels that realise row a3, and all demag kernels
-    evals = max(1, kern["x_r2c"][1]) if kern.get("x_r2c") else 1
     a3_ms = sum(kern[k][0] for k in ("yz_conv", "y_fwd", "z_conv", "y_inv") if k in kern) / evals
     demag_ms = sum(kern[k][0] for k in DEMAG_KERNELS if k in kern) / evals
-    sched_demag = sum(algo[k] * kern[k][1] for k in DEMAG_KERNELS if k in kern and kern[k][1]) / evals
+    sched_demag = sum(algo[k] * units[k] for k in DEMAG_KERNELS if k in kern and kern[k][1]) / evals
     roofline = {"bound": "hbm", "kernel": dom_key, "row": row, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic_for(dom_key),
                 "peak_source": peak_kind, "algorithmic_bytes_per_launch": row_bytes,
@@ -948,7 +951,7 @@ def main():
     # and the compulsory bytes of a step (per evaluation M read, H written and
     # the kernel octant read; per stage the LLG stage's bytes)
     prof_step = n_prof
-    sched_bytes = sum(algo[k] * kern[k][1] for k in kern if k in algo and kern[k][1]) / prof_step
+    sched_bytes = sum(algo[k] * units[k] for k in kern if k in algo and kern[k][1]) / prof_step
     compulsory = 4 * rows["compulsory"] + 4 * llg_algorithmic_bytes(plan)
     three_pass = 4 * (rows["a2"] + rows["a3"] + rows["a4"]) + 4 * llg_algorithmic_bytes(plan)
     step_roofline = {"unit": "GB/s", "peak": peak, "ms_per_step": step_s * 1e3,
@@ -959,6 +962,7 @@ def main():
                      "compulsory_frac": compulsory / step_s / 1e9 / peak,
                      "wasted_traffic_ratio": sched_bytes / compulsory}
     kernels = {k: {"ms_per_launch": per_launch_ms[k], "launches": kern[k][1], "row": ROW_OF.get(k),
+                   "per": "evaluation" if k in DEMAG_KERNELS else "launch",
                    "share": kern[k][0] / max(1e-12, sum(v[0] for v in kern.values())),
                    "algorithmic_GBps": (algo[k] / (per_launch_ms[k] * 1e-3) / 1e9) if (k in algo and per_launch_ms[k]) else None}
                for k in kern if kern[k][1]}

@@ -64,17 +64,33 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) x_r2c_1024_kernel
 #pragma unroll
     for (int pos = 0; pos < 32; pos++) mine[lane + 32 * brev5(pos)] = v[pos];
     __syncthreads();
-    // unpack: A_k = (Z_k + conj Z_{N-k})/2 (row w), B_k = (Z_k - conj Z_{N-k})/(2i) (row w + 8)
-    for (int i = threadIdx.x; i < 513 * 16; i += 256) {
-        const int t = i & 15, kx = i >> 4;
+    // unpack: A_k = (Z_k + conj Z_{N-k})/2 (row w), B_k = (Z_k - conj Z_{N-k})/(2i) (row w + 8).
+    // A thread keeps its row t = tid mod 16 and walks kx = tid / 16 + 16 j, so
+    // its shared and global addresses advance by fixed strides.
+    {
+        const int t = threadIdx.x & 15, kx0 = threadIdx.x >> 4;
         const int y = y0 + t;
-        if (y >= ny) continue;
-        const C* line = reg + (t & 7) * REG1025;
-        const C zk = line[kx], zm = line[(1024 - kx) & 1023];
-        C out;
-        if (t < 8) out = C{T(0.5) * (zk.x + zm.x), T(0.5) * (zk.y - zm.y)};
-        else out = C{T(0.5) * (zk.y + zm.y), T(-0.5) * (zk.x - zm.x)};
-        X[(((size_t)kx * 3 + c) * nz + z) * ny + y] = out;
+        if (y < ny) {
+            const C* line = reg + (t & 7) * REG1025;
+            const size_t xstride = (size_t)3 * nz * ny;  // one kx step in X
+            C* dst = X + ((size_t)kx0 * 3 + c) * nz * ny + (size_t)z * ny + y;
+            const bool lo = t < 8;
+            // kx = 0 (with N - kx = 1024 -> 0) is the only index whose mirror wraps
+            const C* lk = line + kx0;
+            const C* lm = line + (1024 - kx0);
+            if (kx0 == 0) lm = line;
+#pragma unroll 4
+            for (int kx = kx0; kx < 513; kx += 16) {
+                const C zk = *lk, zm = *lm;
+                // row w: (Re zk + Re zm, Im zk - Im zm) / 2; row w + 8: (Im zk + Im zm, Re zm - Re zk) / 2
+                const T a0 = lo ? zk.x : zk.y, a1 = lo ? zm.x : zm.y;
+                const T b0 = lo ? zk.y : zm.x, b1 = lo ? zm.y : zk.x;
+                *dst = C{T(0.5) * (a0 + a1), T(0.5) * (b0 - b1)};
+                dst += 16 * xstride;
+                lk += 16;
+                lm = (kx == 0) ? line + (1024 - 16) : lm - 16;
+            }
+        }
     }
 }
 
