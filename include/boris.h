@@ -140,8 +140,14 @@ int boris_oersted_apply(boris_plan p, const float* J, float* H);
  *   inter-mesh tensor between cells of z size a (target) and b (source) is
  *   Newell's construction with the two-box z stencil, normalised by the
  *   target volume (a far-field dipole expansion beyond 40 cell sizes), built
- *   in FP64 on the device for every distinct (a, b, |dz|) and stored as its
- *   2D in-plane spectrum.  flags: BORIS_FLAG_F32 only.  The plan works with
+ *   in FP64 on the device.  The stencil is symmetric in a and b, so
+ *   a N_ab = b N_ba: the plan stores the 2D in-plane spectrum of a N_ab once
+ *   per distinct (min(a, b), max(a, b), |dz|) and divides by the target's a
+ *   in the sum.  The inter-plane sum in transform space is one kernel over
+ *   all layer pairs; the plan times its variants (one CTA per tile, staged
+ *   rows, or one persistent launch at one or two CTAs per SM) and keeps the
+ *   fastest (boris_plan_schedule out[2]; BORIS_ML_MIX=v at plan creation
+ *   forces variant v).  flags: BORIS_FLAG_F32 only.  The plan works with
  *   boris_demag_apply on the layers' fields concatenated in layer order, each
  *   SoA [3][nz][ny][nx], and with boris_llg_step (per-cell maps concatenated
  *   the same way).  Synchronises the stream.
@@ -391,7 +397,10 @@ int boris_plan_padded(boris_plan p, int out[3]);
 /* Schedule of the y-z pass chosen by the plan's autotuner (CUDA-event
  * timing of every candidate that fits the mesh): out[0] kind (0: fused, z
  * stage through shared-memory passes, 1: fused, z stage in registers, 2:
- * split into y-forward / z-convolution / y-inverse kernels).  Kinds 0 and 1:
+ * split into y-forward / z-convolution / y-inverse kernels; multi-mesh plans
+ * report kind 2 with out[2] the inter-plane sum variant: 0 one CTA per tile,
+ * 1 staged rows, 2 or 3 one persistent launch with 1 or 2 CTAs per SM).
+ * Kinds 0 and 1:
  * out[1] CTAs per cluster, out[2] threads per CTA, out[3] shared memory per
  * CTA.  Kind 2: out[1] CTAs per SM the z convolution's register budget is
  * fitted to, out[2] the z-convolution variant: 1 or 2 for the persistent

@@ -102,6 +102,9 @@ struct boris_plan_s {
     double ml_zb[ML_MAX_LAYERS] = {};  // z of each layer's lower face (m)
     void* Kml = nullptr;    // unique inter-plane spectra [u][kx][c][kyp]
     int* d_pairs = nullptr; // [Z * Z]
+    unsigned* d_pcode = nullptr;  // [Z * Z] spectrum row offsets / 32, kz sign in bit 31
+    float* d_invhz = nullptr;     // [Z] 1 / z size of each plane
+    int ml_variant = 1;           // inter-plane sum kernel (ml_mix), chosen by timing at plan time
     float* Mf = nullptr;    // frame fields [3][Z][NY][NX]
     float* Hf = nullptr;
     int ml_unique = 0;
@@ -259,7 +262,10 @@ int ml_demag_apply(boris_plan p, const float* M, const float* ms_map, float ms_s
     CUDA_TRY(timed(p, 4, [&] { return ml_embed(p->mlt, M, ms_map, ms_scale, p->Mf, p->stream); }));
     CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<float>(p->g, p->Mf, nullptr, 1.0f, X, tw, p->stream); }));
     CUDA_TRY(timed(p, 5, [&] { return launch_split<float>(p->g, X, Yb, nullptr, tw, p->stream, 0, 2); }));
-    CUDA_TRY(timed(p, 6, [&] { return ml_mix(p->g, p->mlt.Z, Yb, (const float*)p->Kml, p->d_pairs, p->stream); }));
+    CUDA_TRY(timed(p, 6, [&] {
+        return ml_mix(p->g, p->mlt.Z, Yb, (const float*)p->Kml, p->d_pairs, p->d_pcode, p->d_invhz, p->ml_variant,
+                      p->nsm, p->stream);
+    }));
     CUDA_TRY(timed(p, 7, [&] { return launch_split<float>(p->g, X, Yb, nullptr, tw, p->stream, 2, 2); }));
     CUDA_TRY(timed(p, 2, [&] { return launch_x_c2r<float>(p->g, X, p->Hf, tw, p->stream, p->d_status, p->wait_limit_ns); }));
     CUDA_TRY(timed(p, 4, [&] { return ml_extract(p->mlt, p->Hf, H, p->stream); }));
@@ -1080,7 +1086,8 @@ int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, cons
     }
     t.off[n_layers] = off;
     t.total3 = off;
-    // unique inter-plane spectra keyed by (target size, source size, |dz|)
+    // unique inter-plane spectra: a N_ab keyed by (min(a, b), max(a, b), |dz|)
+    // (a N_ab = b N_ba: the stencil of two boxes is symmetric in a and b)
     MLHost h;
     h.hx = hx;
     h.hy = hy;
@@ -1090,14 +1097,15 @@ int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, cons
     for (int pp = 0; pp < Z; pp++)
         for (int q = 0; q < Z; q++) {
             const double dz = zc[pp] - zc[q];
-            auto key = std::make_tuple(std::llround(hzp[pp] / qz), std::llround(hzp[q] / qz), std::llround(std::fabs(dz) / qz));
+            const double lo = std::min(hzp[pp], hzp[q]), hi = std::max(hzp[pp], hzp[q]);
+            auto key = std::make_tuple(std::llround(lo / qz), std::llround(hi / qz), std::llround(std::fabs(dz) / qz));
             auto it = uniq.find(key);
             int u;
             if (it == uniq.end()) {
                 u = (int)h.ua.size();
                 uniq[key] = u;
-                h.ua.push_back(hzp[pp]);
-                h.ub.push_back(hzp[q]);
+                h.ua.push_back(lo);
+                h.ub.push_back(hi);
                 h.udz.push_back(std::fabs(dz));
             } else {
                 u = it->second;
@@ -1169,6 +1177,72 @@ int boris_multimesh_plan(int n_layers, const int* nxyz, const double* hxyz, cons
     if ((rc = dev_alloc(p, (void**)&p->Hf, frame * sizeof(float)))) return bail(rc);
     if ((rc = dev_alloc(p, &p->X, (size_t)g.nkx * 3 * Z * g.ny * sizeof(float2)))) return bail(rc);
     if ((rc = dev_alloc(p, &p->Y, (size_t)g.nkx * g.py * 3 * Z * sizeof(float2)))) return bail(rc);
+    // the persistent inter-plane sum reads 32-bit row offsets (128-byte units)
+    {
+        const size_t ustride32 = (size_t)g.nkx * 6 * ml_kyp(g) / 32;
+        const bool fits = (size_t)p->ml_unique * ustride32 < ((size_t)1 << 31);
+        std::vector<unsigned> pcode((size_t)Z * Z);
+        std::vector<float> invhz(Z);
+        for (size_t i = 0; i < pcode.size(); i++) {
+            const int code = h.pairs[i];
+            pcode[i] = (unsigned)((size_t)(code & 0x3fffffff) * ustride32) | ((code >> 30) & 1 ? 0x80000000u : 0u);
+        }
+        for (int i = 0; i < Z; i++) invhz[i] = (float)(1.0 / hzp[i]);
+        if ((rc = dev_alloc(p, (void**)&p->d_pcode, pcode.size() * sizeof(unsigned)))) return bail(rc);
+        if ((rc = dev_alloc(p, (void**)&p->d_invhz, invhz.size() * sizeof(float)))) return bail(rc);
+        cudaMemcpy(p->d_pcode, pcode.data(), pcode.size() * sizeof(unsigned), cudaMemcpyHostToDevice);
+        cudaMemcpy(p->d_invhz, invhz.data(), invhz.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
+            return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
+        // multi-mesh autotuner: time each inter-plane sum kernel that fits on the
+        // (zeroed) padded spectrum and keep the fastest; BORIS_ML_MIX forces one
+        std::vector<int> vars = {0, 1};
+        if (fits && ml_mix_v2_smem(Z) <= (size_t)max_smem) {
+            vars.push_back(2);
+            if (2 * (ml_mix_v2_smem(Z) + 1024) <= 233472) vars.push_back(3);
+        }
+        const size_t staged = (size_t)Z * 2 * 6 * 32 * 4 + (size_t)Z * 3 * 64 * 8 + (size_t)Z * Z * 4;
+        if (staged > (size_t)max_smem) vars.erase(std::remove(vars.begin(), vars.end(), 1), vars.end());
+        if (const char* sv = std::getenv("BORIS_ML_MIX")) {
+            const int want = std::atoi(sv);
+            if (std::find(vars.begin(), vars.end(), want) == vars.end())
+                return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "the requested inter-plane sum kernel does not fit"));
+            vars = {want};
+        }
+        CUDA_TRY(cudaMemsetAsync(p->Y, 0, (size_t)g.nkx * g.py * 3 * Z * sizeof(float2), p->stream));
+        cudaEvent_t a, b;
+        CUDA_TRY(cudaEventCreate(&a));
+        CUDA_TRY(cudaEventCreate(&b));
+        float best = 1e30f;
+        p->ml_variant = vars[0];
+        for (int v : vars) {
+            if (vars.size() == 1) break;
+            cudaError_t e = ml_mix(g, Z, (float2*)p->Y, (const float*)p->Kml, p->d_pairs, p->d_pcode, p->d_invhz, v,
+                                   p->nsm, p->stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaEventRecord(a, p->stream);
+            for (int r = 0; r < 3 && e == cudaSuccess; r++)
+                e = ml_mix(g, Z, (float2*)p->Y, (const float*)p->Kml, p->d_pairs, p->d_pcode, p->d_invhz, v, p->nsm,
+                           p->stream);
+            cudaEventRecord(b, p->stream);
+            if (cudaEventSynchronize(b) != cudaSuccess || e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < best) {
+                best = ms;
+                p->ml_variant = v;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        p->yz.Qc = p->ml_variant;
+    }
     if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
     *out = p;
@@ -1508,7 +1582,7 @@ void boris_plan_destroy(boris_plan p)
 {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
-    void* ptrs[] = {p->Kml, p->d_pairs, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->d_rkf, p->energy,
+    void* ptrs[] = {p->Kml, p->d_pairs, p->d_pcode, p->d_invhz, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->d_rkf, p->energy,
                     p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);

@@ -8,9 +8,12 @@
 // In transform space the inter-mesh sum of Eq. 4 becomes, per (kx, ky),
 //   Hh(p) = sum_q N^(kx, ky; p, q) Mh(q)
 // with N^ the 2D spectrum of the inter-mesh tensor between the cells of plane
-// p (z size a) and plane q (z size b) at z offset dz = z_p - z_q.  Spectra are
-// deduplicated by (a, b, |dz|); dz < 0 flips the xz and yz components (odd in
-// z).  The tensor itself is Newell's construction with the z stencil of two
+// p (z size a) and plane q (z size b) at z offset dz = z_p - z_q.  The two-box
+// stencil below is the same for (a, b) and (b, a), and only the volume of the
+// target box normalises it, so a N_ab = b N_ba at every displacement (the
+// reciprocity of Eq. 4's tensor): the plan stores Nt = a N_ab once per
+// (min(a, b), max(a, b), |dz|) and the sum divides by the target's a.  dz < 0
+// flips the xz and yz components (odd in z).  The tensor itself is Newell's construction with the z stencil of two
 // boxes of unequal height, F(z + s) - F(z + d) - F(z - d) + F(z - s),
 // s = (a + b)/2, d = (a - b)/2, normalised by the target volume; beyond 40
 // cell sizes the box-averaged dipole expansion with per-axis variances
@@ -84,7 +87,8 @@ __device__ void pair_tensor(double X, double Y, double Z, double hx, double hy, 
     }
 }
 
-// In-plane tensor tables of nu unique (a, b, |dz|) entries: T[u][6][NY][NX].
+// In-plane tables of nu unique (a, b, |dz|) entries, a N_ab (the reciprocal
+// form, symmetric in a and b): T[u][6][NY][NX].
 __global__ void ml_tensor_kernel(int nu, const double* __restrict__ ua, const double* __restrict__ ub,
                                  const double* __restrict__ udz, int NX, int NY, double hx, double hy, double rs,
                                  double* __restrict__ T)
@@ -97,7 +101,7 @@ __global__ void ml_tensor_kernel(int nu, const double* __restrict__ ua, const do
         const int i = (int)(cell % NX), j = (int)(cell / NX);
         double v[6];
         pair_tensor(i * hx, j * hy, udz[u], hx, hy, ua[u], ub[u], rs, v);
-        for (int c = 0; c < 6; c++) T[((size_t)u * 6 + c) * plane + cell] = v[c];
+        for (int c = 0; c < 6; c++) T[((size_t)u * 6 + c) * plane + cell] = ua[u] * v[c];
     }
 }
 
@@ -176,7 +180,8 @@ __global__ void ml_extract_kernel(MLTable t, const float* __restrict__ F, float*
 // sign).
 template <int PMAX>
 __global__ void __launch_bounds__(256) ml_mix_kernel(Geometry g, int Z, float2* __restrict__ Y,
-                                                     const float* __restrict__ K, int kyp, const int* __restrict__ pairs)
+                                                     const float* __restrict__ K, int kyp, const int* __restrict__ pairs,
+                                                     const float* __restrict__ inv_hz)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* Ms = reinterpret_cast<float2*>(smem_raw);  // [Z][3][2][32]: column ky', mirror
@@ -240,10 +245,12 @@ __global__ void __launch_bounds__(256) ml_mix_kernel(Geometry g, int Z, float2* 
     for (int j = 0; j < PMAX; j++) {
         const int p = warp + 8 * j;
         if (p < Z) {
+            const float ia = inv_hz[p];  // the spectra hold a N: divide by the target's a
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                if (onA) base[(size_t)(c * Z + p) * py + kf] = acc[j][0][c];
-                if (onB) base[(size_t)(c * Z + p) * py + (py - kf)] = acc[j][1][c];
+                if (onA) base[(size_t)(c * Z + p) * py + kf] = make_float2(acc[j][0][c].x * ia, acc[j][0][c].y * ia);
+                if (onB)
+                    base[(size_t)(c * Z + p) * py + (py - kf)] = make_float2(acc[j][1][c].x * ia, acc[j][1][c].y * ia);
             }
         }
     }
@@ -266,7 +273,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 template <int PMAX>
 __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z, float2* __restrict__ Y,
                                                                const float* __restrict__ K, int kyp,
-                                                               const int* __restrict__ pairs)
+                                                               const int* __restrict__ pairs,
+                                                               const float* __restrict__ inv_hz)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -361,12 +369,136 @@ __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z
     for (int j = 0; j < PMAX; j++) {
         const int p = warp + 8 * j;
         if (p < Z) {
+            const float ia = inv_hz[p];  // the spectra hold a N: divide by the target's a
 #pragma unroll
             for (int c = 0; c < 3; c++) {
-                if (onA) base[(size_t)(c * Z + p) * py + kf] = acc[j][0][c];
-                if (onB) base[(size_t)(c * Z + p) * py + (py - kf)] = acc[j][1][c];
+                if (onA) base[(size_t)(c * Z + p) * py + kf] = make_float2(acc[j][0][c].x * ia, acc[j][0][c].y * ia);
+                if (onB)
+                    base[(size_t)(c * Z + p) * py + (py - kf)] = make_float2(acc[j][1][c].x * ia, acc[j][1][c].y * ia);
             }
         }
+    }
+}
+
+// The inter-plane sum as one persistent launch over all work items (kx,
+// 32-column tile of folded ky'), tiles of one kx consecutive.  Per item: the
+// Z planes' 32 columns and their mirrors go to shared memory; then for each
+// source plane q every warp stages, by cp.async one source ahead, the 6 x
+// 128-byte spectrum rows of its own targets p = warp + 8 j, whose offsets
+// (in 128-byte units, the kz sign in bit 31) come precomputed in pcode; the
+// 3 x 3 products run as packed FP32x2 multiply-adds on (Re, Im) pairs.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int PMAX>
+__global__ void __launch_bounds__(256, 2) ml_mix_v2_kernel(Geometry g, int Z, float2* __restrict__ Y,
+                                                           const float* __restrict__ K, int kyp,
+                                                           const unsigned* __restrict__ pcode,
+                                                           const float* __restrict__ inv_hz, int ntile, int nwork)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nt = (Z - warp + 7) / 8;
+    int before = 0;
+    for (int v = 0; v < warp; v++) before += (Z - v + 7) / 8;
+    float* Kw = reinterpret_cast<float*>(smem_raw) + (size_t)before * 2 * 6 * 32;
+    float2* Ms = reinterpret_cast<float2*>(reinterpret_cast<float*>(smem_raw) + (size_t)Z * 2 * 6 * 32);
+    unsigned* pc = reinterpret_cast<unsigned*>(Ms + (size_t)Z * 3 * 64);
+    float* ih = reinterpret_cast<float*>(pc + (size_t)Z * Z);
+    const int py = g.py;
+    const int part = lane & 7, c0 = lane >> 3;
+    for (int i = threadIdx.x; i < Z * Z; i += 256) pc[i] = pcode[i];
+    for (int i = threadIdx.x; i < Z; i += 256) ih[i] = inv_hz[i];
+    __syncthreads();
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int kx = w / ntile, kf0 = (w - kx * ntile) * 32;
+        const int kf = kf0 + lane;
+        const bool onA = kf <= py / 2;
+        const bool onB = kf > 0 && kf < py / 2;
+        float2* base = Y + (size_t)kx * 3 * Z * py;
+        const float* Kx = K + (size_t)kx * 6 * kyp + kf0 + part * 4;
+        auto stage = [&](int q, int b) {
+#pragma unroll
+            for (int j = 0; j < PMAX; j++) {
+                const int p = warp + 8 * j;
+                if (p < Z) {
+                    const float* src = Kx + (size_t)(pc[p * Z + q] & 0x7fffffffu) * 32;
+                    float* dst = Kw + ((size_t)(b * nt + j) * 6) * 32 + part * 4;
+                    cp_async16(dst + c0 * 32, src + (size_t)c0 * kyp);
+                    if (c0 < 2) cp_async16(dst + (c0 + 4) * 32, src + (size_t)(c0 + 4) * kyp);
+                }
+            }
+            cp_async_commit();
+        };
+        stage(0, 0);
+        for (int i = threadIdx.x; i < 3 * Z * 64; i += 256) {
+            const int col = i & 31, half = (i >> 5) & 1, line = i >> 6;  // line = c * Z + p
+            const int c = line / Z, p = line - c * Z;
+            const int f = kf0 + col;
+            const bool ok = half ? (f > 0 && f < py / 2) : (f <= py / 2);
+            const int ky = half ? py - f : f;
+            Ms[((p * 3 + c) * 2 + half) * 32 + col] = ok ? base[(size_t)line * py + ky] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();  // the columns are in shared memory
+        float2 acc[PMAX][2][3];
+#pragma unroll
+        for (int j = 0; j < PMAX; j++)
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) acc[j][h][c] = make_float2(0.f, 0.f);
+        for (int q = 0; q < Z; q++) {
+            if (q + 1 < Z) {
+                stage(q + 1, (q + 1) & 1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();  // every lane's copies of source q are visible to the warp
+            const float* kb = Kw + (size_t)(q & 1) * nt * 6 * 32 + lane;
+            // source columns m and i m (i times, for the imaginary xz and yz entries)
+            float2 m[2][3], im[2][3];
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    m[h][c] = Ms[((q * 3 + c) * 2 + h) * 32 + lane];
+                    im[h][c] = make_float2(-m[h][c].y, m[h][c].x);
+                }
+#pragma unroll
+            for (int j = 0; j < PMAX; j++) {
+                const int p = warp + 8 * j;
+                if (p < Z) {
+                    const float sz = (pc[p * Z + q] >> 31) ? -1.f : 1.f;
+                    const float* k = kb + j * 6 * 32;
+                    const float kxx = k[0], kyy = k[32], kzz = k[64], kxy = k[96];
+                    const float kxz = sz * k[128], kyz = sz * k[160];
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        // the mirror column ky -> py - ky flips the ky-odd entries xy and yz
+                        const float2 bxx = f2(kxx), byy = f2(kyy), bzz = f2(kzz), bxz = f2(kxz);
+                        const float2 bxy = f2(h ? -kxy : kxy), byz = f2(h ? -kyz : kyz);
+                        acc[j][h][0] = ffma2(bxx, m[h][0], ffma2(bxy, m[h][1], ffma2(bxz, im[h][2], acc[j][h][0])));
+                        acc[j][h][1] = ffma2(bxy, m[h][0], ffma2(byy, m[h][1], ffma2(byz, im[h][2], acc[j][h][1])));
+                        acc[j][h][2] = ffma2(bxz, im[h][0], ffma2(byz, im[h][1], ffma2(bzz, m[h][2], acc[j][h][2])));
+                    }
+                }
+            }
+            __syncwarp();  // buffer q & 1 is free for source q + 2
+        }
+#pragma unroll
+        for (int j = 0; j < PMAX; j++) {
+            const int p = warp + 8 * j;
+            if (p < Z) {
+                const float2 ia = f2(ih[p]);  // the spectra hold a N: divide by the target's a
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    if (onA) base[(size_t)(c * Z + p) * py + kf] = __fmul2_rn(acc[j][0][c], ia);
+                    if (onB) base[(size_t)(c * Z + p) * py + (py - kf)] = __fmul2_rn(acc[j][1][c], ia);
+                }
+            }
+        }
+        __syncthreads();  // the column stage is reused by the next item
     }
 }
 
@@ -441,25 +573,52 @@ int ml_kyp(const Geometry& g) { return (g.kyh + 31) / 32 * 32; }
 
 
 
-cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, cudaStream_t st)
+size_t ml_mix_v2_smem(int Z)
+{
+    return (size_t)Z * 2 * 6 * 32 * sizeof(float) + (size_t)Z * 3 * 64 * sizeof(float2) +
+           (size_t)Z * Z * sizeof(unsigned) + (size_t)Z * sizeof(float);
+}
+
+cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, const unsigned* pcode,
+                   const float* inv_hz, int variant, int nsm, cudaStream_t st)
 {
     const dim3 grid(g.py / 64 + 1, g.nkx);  // folded rows 0 .. py/2
     const int pmax = (Z + 7) / 8;
     const int kyp = ml_kyp(g);
+    cudaError_t e;
+    if (variant >= 2) {
+        // persistent: (variant - 1) CTAs per SM over all (kx, tile) items
+        const size_t smem = ml_mix_v2_smem(Z);
+        const int ntile = g.py / 64 + 1, nwork = ntile * g.nkx;
+        const int G = std::min(nwork, (variant - 1) * nsm);
+#define ML_V2(P)                                                                                             \
+    e = cudaFuncSetAttribute(ml_mix_v2_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);   \
+    if (e != cudaSuccess) return e;                                                                          \
+    ml_mix_v2_kernel<P><<<G, 256, smem, st>>>(g, Z, Y, K, kyp, pcode, inv_hz, ntile, nwork);                 \
+    return cudaGetLastError();
+        if (pmax <= 1) { ML_V2(1) }
+        if (pmax <= 2) { ML_V2(2) }
+        if (pmax <= 3) { ML_V2(3) }
+        if (pmax <= 4) { ML_V2(4) }
+        if (pmax <= 5) { ML_V2(5) }
+        if (pmax <= 6) { ML_V2(6) }
+        if (pmax <= 8) { ML_V2(8) }
+#undef ML_V2
+        return cudaErrorInvalidValue;
+    }
     const size_t smem_s = (size_t)Z * 2 * 6 * 32 * sizeof(float) + (size_t)Z * 3 * 64 * sizeof(float2) +
                           (size_t)Z * Z * sizeof(int);
-    const bool staged = smem_s <= 227 * 1024;
+    const bool staged = variant == 1;
     const size_t smem = staged ? smem_s : (size_t)Z * 3 * 64 * sizeof(float2) + (size_t)Z * Z * sizeof(int);
-    cudaError_t e;
 #define ML_MIX(P)                                                                                              \
     if (staged) {                                                                                              \
         e = cudaFuncSetAttribute(ml_mix_staged_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
         if (e != cudaSuccess) return e;                                                                        \
-        ml_mix_staged_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, kyp, pairs);                              \
+        ml_mix_staged_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, kyp, pairs, inv_hz);                      \
     } else {                                                                                                   \
         e = cudaFuncSetAttribute(ml_mix_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
         if (e != cudaSuccess) return e;                                                                        \
-        ml_mix_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, kyp, pairs);                                     \
+        ml_mix_kernel<P><<<grid, 256, smem, st>>>(g, Z, Y, K, kyp, pairs, inv_hz);                             \
     }                                                                                                          \
     return cudaGetLastError();
     if (pmax <= 1) { ML_MIX(1) }

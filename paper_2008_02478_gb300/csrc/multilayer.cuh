@@ -37,7 +37,16 @@ cudaError_t run_axis_n(const void* in, bool in_real, double2* out, int axis, int
 cudaError_t ml_build_spectra(const MLHost& h, const Geometry& g, float* K, const double2* tw64, cudaStream_t st);
 cudaError_t ml_embed(const MLTable& t, const float* M, const float* ms_map, float ms, float* F, cudaStream_t st);
 cudaError_t ml_extract(const MLTable& t, const float* F, float* H, cudaStream_t st);
-cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, cudaStream_t st);
+// The inter-plane sum in transform space.  variant 0: one CTA per (kx, tile),
+// spectrum rows read by the threads; 1: the same with the rows staged by
+// cp.async; v >= 2: one persistent launch of (v - 1) CTAs per SM over all
+// (kx, tile) items, precomputed row offsets, packed FP32x2 products.  pairs:
+// [p Z + q] unique index (bit 30: z_p < z_q); pcode: the same as the row
+// offset u nkx 6 kyp / 32 with the sign in bit 31; inv_hz[p] = 1 / (z size of
+// plane p) (the spectra hold a N_ab).
+cudaError_t ml_mix(const Geometry& g, int Z, float2* Y, const float* K, const int* pairs, const unsigned* pcode,
+                   const float* inv_hz, int variant, int nsm, cudaStream_t st);
+size_t ml_mix_v2_smem(int Z);
 // row pitch of the multi-mesh spectra K[u][kx][c][kyp]
 int ml_kyp(const Geometry& g);
 

@@ -49,6 +49,33 @@ def test_multilayer_demag_matches_direct_sum(layers, hz, gaps):
     assert_close(H, ref, 1e-5)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("layers,hz,gaps", CASES[:2])
+def test_every_inter_plane_sum_kernel_matches_direct_sum(layers, hz, gaps, variant, monkeypatch):
+    """Each variant of the inter-plane sum (one CTA per tile, staged rows, one
+    persistent launch at one or two CTAs per SM) against Eq. 4's direct sum;
+    the layers have unequal z sizes, so the spectra shared by (a, b) and
+    (b, a) through a N_ab = b N_ba are exercised."""
+    torch = torch_cuda()
+    st, m, M, _ = stack_case(layers, hz, gaps, 4e-9, seed=6)
+    ref = ml.direct(st, M)
+    monkeypatch.setenv("BORIS_ML_MIX", str(variant))
+    plan = make_plan(st)
+    assert plan.schedule()[2] == variant
+    H = plan.apply(torch.tensor(M, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert_close(H, ref, 1e-5)
+
+
+def test_reciprocal_spectra_halve_the_cross_layer_set():
+    """Spectra are stored once per (min(a, b), max(a, b), |dz|): two layers of
+    z sizes 2 and 3 nm, one plane each, need 3 spectra (a = b = 2, a = b = 3,
+    and one shared by (2, 3) and (3, 2)), not 4."""
+    torch_cuda()
+    st, m, M, _ = stack_case([(8, 8, 1), (8, 8, 1)], [2e-9, 3e-9], [1e-9], 4e-9, seed=1)
+    plan = make_plan(st)
+    assert plan.info()[1] == 3
+
+
 def test_six_layer_stack_sampled():
     """The six-layer stack (512x512x8 ... 200x200x3 cells, 4 nm in-plane,
     z cells 2-5 nm, gaps 1-10 nm, Ms 4e5-1.4e6): 12 target cells against the
