@@ -98,6 +98,20 @@ template <typename T>
 cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
                           cudaStream_t st, bool forward);
 cudaError_t upload_twiddles_fast();
+// y passes of length 1024 on the BF16 spectrum of the mixed-precision split
+// schedule (layout [kx][c][ky/8][part][z][ky%8])
+cudaError_t launch_y_1024_b16(const Geometry& g, float2* X, void* Y16, const float2* tw, cudaStream_t st,
+                              bool forward);
+// Mixed-precision z stage with the spectrum stored in BF16 (zconv_tc6.cu):
+// pz = 64, py >= 256 in 128-column tiles; reads the FP16 kernel pairs K16
+bool zconv_tc6_supported(const Geometry& g, int max_smem);
+int zconv_tc6_kyp16(const Geometry& g);
+size_t zconv_tc6_y16_bytes(const Geometry& g);
+size_t zconv_tc6_k16_bytes(const Geometry& g);
+cudaError_t zconv_tc6_build_k16(const Geometry& g, const float* K, void* K16, cudaStream_t st);
+cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, void* kmap);
+cudaError_t launch_zconv_tc6(const void* ymap, const void* kmap, const Geometry& g, void* Y16, const float2* tw,
+                             int* status, unsigned long long limit_ns, int nsm, cudaStream_t st);
 // Length-512 passes (meshes of 129..256 cells along the axis), two lines per
 // warp through the length-1024 warp transform (fft512.cu).
 template <typename T>

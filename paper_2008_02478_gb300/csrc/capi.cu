@@ -30,6 +30,13 @@ struct boris_plan_s {
     bool f64;
     int tc = 0;  // 0: FP32 z stage; 1: FP16 tensor cores; 2: BF16 tensor cores
     bool tc5 = false;  // tensor-core z stage on tcgen05 (else the mma.sync form)
+    // BF16 plans: the padded y-z spectrum stored in BF16 (Y16), the z stage on
+    // tcgen05 with the data as the 128-row operand, FP16 kernel pairs (K16)
+    bool tc6 = false;
+    void* Y16 = nullptr;
+    void* K16 = nullptr;
+    alignas(64) unsigned char ymap16[128] = {};
+    alignas(64) unsigned char kmap16[128] = {};
     cudaStream_t stream;
     int device;
     YZSchedule yz;
@@ -218,6 +225,17 @@ template <typename T>
 cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
 {
     using C = typename Cx<T>::t;
+    if (sc.kind == 2 && p->tc6) {
+        cudaError_t e = timed(p, 5, [&] { return launch_y_1024_b16(p->g, (float2*)p->X, p->Y16, (const float2*)p->tw, p->stream, true); });
+        if (e == cudaSuccess)
+            e = timed(p, 6, [&] {
+                return launch_zconv_tc6(p->ymap16, p->kmap16, p->g, p->Y16, (const float2*)p->tw, p->d_status,
+                                        p->wait_limit_ns, p->nsm, p->stream);
+            });
+        if (e == cudaSuccess)
+            e = timed(p, 7, [&] { return launch_y_1024_b16(p->g, (float2*)p->X, p->Y16, (const float2*)p->tw, p->stream, false); });
+        return e;
+    }
     if (sc.kind == 2) {
         cudaError_t e = cudaSuccess;
         for (int part = 0; part < 3 && e == cudaSuccess; part++)
@@ -826,6 +844,12 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
         // the mma.sync form (for comparisons)
         const char* ms = std::getenv("BORIS_TC_MMASYNC");
         p->tc5 = zconv_tc5_supported(g, max_smem) && !(ms && std::atoi(ms) == 1);
+        // BF16 plans store the padded spectrum in BF16 where the length-1024 y
+        // passes and the 128-column tiles apply (BORIS_TC_STORE16=0 keeps the
+        // FP32 spectrum with the tcgen05 stage of 16-column tiles)
+        const char* s16 = std::getenv("BORIS_TC_STORE16");
+        p->tc6 = tc == 2 && p->tc5 && zconv_tc6_supported(g, max_smem) && y1024_ok<float>(g, max_smem) &&
+                 !(s16 && std::atoi(s16) == 0);
     }
     if (ncand == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));
     // optional override for tests and sweeps: BORIS_YZ_KIND / BORIS_YZ_CLUSTER / BORIS_YZ_THREADS / BORIS_YZ_QC
@@ -922,6 +946,13 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
             if (ncand == 0) return bail(fail(BORIS_ERR_OOM, "no memory for the kernel spectrum copy"));
             p->yz = cand[0];
         }
+    }
+    if (p->tc6) {
+        if ((rc = dev_alloc(p, &p->Y16, zconv_tc6_y16_bytes(g)))) return bail(rc);
+        if ((rc = dev_alloc(p, &p->K16, zconv_tc6_k16_bytes(g)))) return bail(rc);
+        if ((ce = zconv_tc6_build_k16(g, (const float*)p->K, p->K16, p->stream)) != cudaSuccess ||
+            (ce = zconv_tc6_maps(g, p->Y16, p->K16, p->ymap16, p->kmap16)) != cudaSuccess)
+            return bail(fail(BORIS_ERR_CUDA, std::string("16-bit spectrum set-up: ") + cudaGetErrorString(ce)));
     }
     if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
         return bail(fail(BORIS_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(ce)));
@@ -1531,7 +1562,7 @@ int boris_plan_schedule(boris_plan p, int out[4])
     if (!p || !out) return fail(BORIS_ERR_INVALID_ARG, "NULL argument");
     out[0] = p->yz.kind;
     out[1] = p->yz.C;
-    out[2] = p->yz.kind == 2 ? (p->tc ? (p->tc5 ? 5 : 4) : p->yz.Qc) : p->yz.threads;
+    out[2] = p->yz.kind == 2 ? (p->tc ? (p->tc6 ? 6 : p->tc5 ? 5 : 4) : p->yz.Qc) : p->yz.threads;
     out[3] = (int)p->yz.smem;
     return BORIS_OK;
 }
@@ -1582,7 +1613,7 @@ void boris_plan_destroy(boris_plan p)
 {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
-    void* ptrs[] = {p->Kml, p->d_pairs, p->d_pcode, p->d_invhz, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->d_rkf, p->energy,
+    void* ptrs[] = {p->Y16, p->K16, p->Kml, p->d_pairs, p->d_pcode, p->d_invhz, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->d_rkf, p->energy,
                     p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);

@@ -3,6 +3,8 @@
 // y forward / inverse passes of the split schedule.  Each warp owns one
 // (packed) line in registers (warp_fft.cuh); global loads and stores are
 // 32 consecutive elements per instruction.
+#include <cuda_bf16.h>
+
 #include "boris_internal.cuh"
 #include "bulk_async.cuh"
 #include "warp_fft.cuh"
@@ -341,6 +343,74 @@ __global__ void __launch_bounds__(256) y_inv_1024_kernel(Geometry g, const typen
     }
 }
 
+// The same y passes on the 16-bit spectrum of the mixed-precision split schedule
+// (BF16, line-contiguous layout [kx][c][part][z][ky], see zconv_tc6.cu): each
+// (part, z) line of a kx plane is py consecutive values, so a warp moves 32
+// consecutive ky (64 bytes) per instruction.
+__device__ __forceinline__ size_t y16_index(int kx, int c, int part, int z, int ky, int nz, int py)
+{
+    return ((((size_t)kx * 3 + c) * 2 + part) * nz + z) * (size_t)py + ky;
+}
+
+__global__ void __launch_bounds__(256, 3) y_fwd_1024_b16_kernel(Geometry g, const float2* __restrict__ X,
+                                                                __nv_bfloat16* __restrict__ Y16,
+                                                                const float2* __restrict__ tw_g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tws = reinterpret_cast<float2*>(smem_raw);
+    float2* reg = tws + TW1024_SLOTS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lines = 3 * g.nz, ny = g.ny, nz = g.nz;
+    const int kx = blockIdx.y, line = blockIdx.x * 8 + warp;
+    load_tw1024(tws, tw_g, g.lmax);
+    __syncthreads();
+    if (line >= lines) return;
+    const int c = line / nz, z = line - c * nz;
+    const float2* src = X + ((size_t)kx * lines + line) * ny;
+    float2 v[32];
+#pragma unroll
+    for (int a = 0; a < 32; a++) {
+        const int y = 32 * a + lane;
+        v[a] = (a < 16 && y < ny) ? src[y] : float2{0.f, 0.f};
+    }
+    warp_fft1024_fwd(v, reg + warp * REG1025, tws);
+    // v[pos] = Y[ky], ky = lane + 32 brev5(pos)
+    __nv_bfloat16* re = Y16 + y16_index(kx, c, 0, z, lane, nz, 1024);
+    __nv_bfloat16* im = Y16 + y16_index(kx, c, 1, z, lane, nz, 1024);
+#pragma unroll
+    for (int pos = 0; pos < 32; pos++) {
+        re[32 * brev5(pos)] = __float2bfloat16_rn(v[pos].x);
+        im[32 * brev5(pos)] = __float2bfloat16_rn(v[pos].y);
+    }
+}
+
+__global__ void __launch_bounds__(256) y_inv_1024_b16_kernel(Geometry g, const __nv_bfloat16* __restrict__ Y16,
+                                                             float2* __restrict__ X, const float2* __restrict__ tw_g)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2* tws = reinterpret_cast<float2*>(smem_raw);
+    float2* reg = tws + TW1024_SLOTS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lines = 3 * g.nz, ny = g.ny, nz = g.nz;
+    const int kx = blockIdx.y, line = blockIdx.x * 8 + warp;
+    load_tw1024_slots(tws, tw_g, g.lglmax - 10);
+    __syncthreads();
+    if (line >= lines) return;
+    const int c = line / nz, z = line - c * nz;
+    const __nv_bfloat16* re = Y16 + y16_index(kx, c, 0, z, lane, nz, 1024);
+    const __nv_bfloat16* im = Y16 + y16_index(kx, c, 1, z, lane, nz, 1024);
+    float2 v[32];
+#pragma unroll
+    for (int d = 0; d < 32; d++) v[brev5(d)] = float2{__bfloat162float(re[32 * d]), __bfloat162float(im[32 * d])};
+    warp_fft1024_inv<float2, false>(v, reg + warp * REG1025, tws);
+    float2* dst = X + ((size_t)kx * lines + line) * ny;
+#pragma unroll
+    for (int a = 0; a < 16; a++) {
+        const int y = 32 * a + lane;
+        if (y < ny) dst[y] = v[a];
+    }
+}
+
 template <typename T>
 static size_t smem_1024()
 {
@@ -395,6 +465,24 @@ cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T
         cudaError_t e = cudaFuncSetAttribute(y_inv_1024_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         y_inv_1024_kernel<T><<<grid, 256, smem, st>>>(g, Y, X, tw);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_y_1024_b16(const Geometry& g, float2* X, void* Y16, const float2* tw, cudaStream_t st,
+                              bool forward)
+{
+    const size_t smem = smem_1024<float>();
+    const dim3 grid((3 * g.nz + 7) / 8, g.nkx);
+    if (forward) {
+        cudaError_t e = cudaFuncSetAttribute(y_fwd_1024_b16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        y_fwd_1024_b16_kernel<<<grid, 256, smem, st>>>(g, X, (__nv_bfloat16*)Y16, tw);
+    } else {
+        cudaError_t e =
+            cudaFuncSetAttribute(y_inv_1024_b16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        y_inv_1024_b16_kernel<<<grid, 256, smem, st>>>(g, (const __nv_bfloat16*)Y16, X, tw);
     }
     return cudaGetLastError();
 }

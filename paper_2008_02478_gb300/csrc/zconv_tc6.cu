@@ -1,0 +1,427 @@
+// Mixed-precision z stage with 16-bit storage of the padded y-z spectrum: the
+// zero-padded length-64 z transform of the pipelined convolution (Section 7)
+// and its inverse as dense products on the tcgen05 tensor cores, BF16
+// operands, FP32 accumulation in tensor memory (the paper has FP32 and FP64
+// only; this is the reduced-precision variant of the split schedule).
+//
+// Layout of the 16-bit spectrum Y16 (written by the y forward pass, read by
+// the y inverse): [kx][c][part][z][ky], part 0 = Re, 1 = Im, each (part, z)
+// line of a kx plane py consecutive values.  A 5D tensor-copy view of it -
+// (ky mod 8, z, part, ky / 8, (kx, c)) with the ky / 8 dimension at a stride of
+// 16 bytes, boxes of (8, 32, 2, 16, 1) - lands in shared memory as the
+// no-swizzle MN-major operand of a 128-row product: element (m = ky in the
+// tile, k = 32 part + z) at (m / 8) 1024 + (k / 8) 128 + (k % 8) 16 + (m % 8) 2.
+// z >= nz is filled with zeros by the copy (the zero padding of the z
+// transform).
+//
+// A tile is 128 ky columns of one kx plane.  Per component c:
+//   forward  D_c (128 x 128) = A_c (128 x 64) . F (64 x 128): the data are the
+//            A operand (rows = ky columns), F the DFT matrix,
+//            n = 64 q + kz (q: Re / Im of X^(kz)), k = 32 p + z (p: Re / Im of
+//            x(z)), F = [[C, S], [-S, C]] with C, S = cos, sin(2 pi kz z / 64)
+//   multiply H_c(kz) = sum_d N_cd(kx, ky, kz) M_d(kz): thread t owns
+//            accumulator row t (one ky column) for all three components and
+//            all kz, so the 3 x 3 product needs no exchange between threads;
+//            the kernel spectrum is real, Re and Im are multiplied alike
+//   inverse  out_c^T (64 x 128) = F^T (64 x 128) . H_c^T (128 x 128): F^T is
+//            F's storage read as an MN-major operand (M = 64 rows (part, z):
+//            row m of the result lands in tensor-memory lane 32 (m / 16) +
+//            m mod 16), the products H_c the K-major B operand (rows = ky
+//            columns); the thread of row (part, z < nz) then stores its 128 ky
+//            as 16-byte pieces
+// The kernel spectrum arrives as FP16 pairs (xx, yy), (zz, xy), (xz, yz) of
+// the octant scaled by px py pz (the fold of the normalisation is undone on
+// the output).  Everything runs in one persistent CTA of eight warps per SM
+// (tensor memory: 3 x 128 accumulator columns); warps w and w + 4 read the
+// same tensor-memory lanes and split the kz chunks of the multiply and the ky
+// halves of the output; tensor-memory loads are issued in groups with one
+// wait each.  The next tile's data and kernel rows are copied in while the
+// current tile is multiplied.
+//
+// Every mbarrier wait is bounded (device timer); when one gives up the CTA
+// latches BORIS_ERR_TIMEOUT in *status, waits (bounded) for its copies and
+// products in flight, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "boris_internal.cuh"
+#include "tcgen05.cuh"
+
+namespace boris {
+
+namespace {
+
+constexpr int T6 = 256;       // threads: two per accumulator row (ky column), warps w and w + 4 share lanes
+constexpr int MT = 128;       // ky columns per tile
+constexpr int HZ6 = 32;       // z cells held (pz = 64)
+constexpr int KZH6 = HZ6 + 1;  // kz' rows of the kernel octant
+constexpr int KW6 = 136;      // kernel-spectrum box width (ky' entries, 16-byte multiple)
+constexpr uint32_t TMEM6 = 512;
+constexpr int STATUS_TIMEOUT6 = -5;
+
+constexpr uint32_t F_LBO = 128, F_SBO = 1024;    // F: K-major, 128 n x 64 k
+constexpr uint32_t FI_LBO = 1024, FI_SBO = 128;  // F^T as an MN-major operand: 64 rows x 128 k
+constexpr uint32_t AF_LBO = 128, AF_SBO = 1024;  // data: MN-major, 128 m x 64 k (tensor copy)
+constexpr uint32_t AI_LBO = 128, AI_SBO = 2048;  // products: K-major, 128 m x 128 k
+
+constexpr size_t F_BYTES = 128 * 64 * 2;
+constexpr size_t AF_COMP = (size_t)MT * 64 * 2;   // 16 KB per component
+constexpr size_t AI_COMP = (size_t)MT * 128 * 2;  // 32 KB per component
+constexpr size_t K_BYTES = (size_t)KZH6 * 3 * KW6 * 4;
+constexpr size_t OFF_F = 0;
+constexpr size_t OFF_AF = OFF_F + F_BYTES;
+constexpr size_t OFF_AI = OFF_AF + 3 * AF_COMP;
+constexpr size_t OFF_K = OFF_AI + 3 * AI_COMP;
+constexpr size_t OFF_BAR = (OFF_K + K_BYTES + 15) / 16 * 16;
+constexpr size_t OFF_TSLOT = OFF_BAR + 4 * 8;
+constexpr size_t SMEM6 = OFF_TSLOT + 16 + 1024;  // + alignment of the base to 1024 bytes
+static_assert(SMEM6 <= 232448, "one CTA per SM");
+static_assert(OFF_AF % 1024 == 0 && OFF_AI % 1024 == 0 && OFF_K % 128 == 0, "operand and copy alignment");
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__global__ void __launch_bounds__(T6, 1)
+    z_conv_tc6_kernel(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap kmap, Geometry g,
+                      __nv_bfloat16* __restrict__ Y16, const float2* __restrict__ tw_g, float out_scale,
+                      int* __restrict__ status, unsigned long long limit_ns)
+{
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* F = base + OFF_F;
+    unsigned char* AF = base + OFF_AF;
+    unsigned char* AI = base + OFF_AI;
+    const __half2* kst = reinterpret_cast<const __half2*>(base + OFF_K);
+    uint64_t* fullA = reinterpret_cast<uint64_t*>(base + OFF_BAR);
+    uint64_t* fullK = fullA + 1;
+    uint64_t* mmab = fullA + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(base + OFF_TSLOT);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lq = warp & 3, half = warp >> 2;  // tensor-memory lane quarter, work half
+    const int row = 32 * lq + lane;             // accumulator row of the multiply (ky column in the tile)
+    const int py = g.py;
+    const int nty = py / MT, ntiles = g.nkx * nty, G = gridDim.x;
+    constexpr uint32_t abytes = 3 * (uint32_t)AF_COMP;
+    constexpr uint32_t kbytes = (uint32_t)K_BYTES;
+    constexpr uint32_t IDESC_F = tc::idesc_f16(1, true, false, 128, 128);  // data MN-major, F K-major
+    constexpr uint32_t IDESC_I = tc::idesc_f16(1, true, false, 64, 128);   // F^T MN-major, products K-major
+
+    if (warp == 0) tc::alloc(tslot, TMEM6);
+    // the forward DFT matrix F, once per CTA; the plan's twiddles are exp(-2 pi i e / lmax)
+    {
+        float2* cs64 = reinterpret_cast<float2*>(AI);  // scratch: AI is written only later
+        const int shz = g.lglmax - 6;
+        if (tid < 64) {
+            const float2 w = tw_g[tid << shz];
+            cs64[tid] = make_float2(w.x, -w.y);
+        }
+        __syncthreads();
+        for (int i = tid; i < 128 * 32; i += T6) {
+            const int n = i >> 5, k = (i & 31) * 2;  // two consecutive k of row n
+            const int q = n >> 6, kz = n & 63;
+            float v[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int kk = k + h, p = kk >> 5, z = kk & 31;
+                const float2 cs = cs64[(kz * z) & 63];
+                v[h] = q == p ? cs.x : (q == 0 ? cs.y : -cs.y);
+            }
+            *reinterpret_cast<uint32_t*>(F + (n >> 3) * F_SBO + (k >> 3) * F_LBO + (n & 7) * 16 + (k & 7) * 2) =
+                pack_bf16(v[0], v[1]);
+        }
+    }
+    if (tid == 0) {
+        mbar_init(fullA, 1);
+        mbar_init(fullK, 1);
+        mbar_init(mmab, 1);
+        fence_mbar_init();
+    }
+    fence_proxy_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = *tslot;
+
+    auto load_a = [&](int t) {
+        const int kx = t / nty, ky0 = (t - kx * nty) * MT;
+        mbar_arrive_expect_tx(fullA, abytes);
+        for (int c = 0; c < 3; c++) tc::tma_load_5d(AF + c * AF_COMP, &ymap, 0, 0, 0, ky0 / 8, kx * 3 + c, fullA);
+    };
+    // kernel rows of tile t: ky' = ky below the fold, py - ky above it (a box
+    // starting 128 entries below py - ky0, so that ky' = x + 128 - t)
+    auto load_k = [&](int t) {
+        const int kx = t / nty, ky0 = (t - kx * nty) * MT;
+        const int x = ky0 < py / 2 ? ky0 : py - ky0 - MT;
+        mbar_arrive_expect_tx(fullK, kbytes);
+        tc::tma_load_3d(base + OFF_K, &kmap, x, 0, kx, fullK);
+    };
+    int na = 0, nk = 0, nm = 0;  // copies and product groups issued by thread 0 (drained after a timeout)
+    if (tid == 0 && (int)blockIdx.x < ntiles) {
+        load_a(blockIdx.x);
+        load_k(blockIdx.x);
+        na = nk = 1;
+    }
+
+    const uint32_t trow = tbase + ((uint32_t)(32 * lq) << 16);
+    bool failed = false;
+    uint32_t mp = 0;  // parity of the next product-group completion
+    int it = 0;
+    for (int t = blockIdx.x; t < ntiles; t += G, it++) {
+        const int kx = t / nty, ky0 = (t - kx * nty) * MT;
+        const bool more = t + G < ntiles;
+        const bool up = ky0 >= py / 2;  // above the ky fold: xy and yz change sign
+        const int ke = up ? MT - row : row;
+        {
+            const bool ok = tc::wait(fullA, it & 1, limit_ns);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+        }
+        if (tid == 0) {
+            tc::fence_after();
+            for (int c = 0; c < 3; c++)
+#pragma unroll
+                for (int ks = 0; ks < 4; ks++)
+                    tc::mma_f16(tbase + c * 128, tc::sdesc(AF + c * AF_COMP + ks * 2 * AF_LBO, AF_LBO, AF_SBO),
+                                tc::sdesc(F + ks * 2 * F_LBO, F_LBO, F_SBO), IDESC_F, ks > 0);
+            tc::commit(mmab);
+            nm++;
+        }
+        {
+            const bool ok = tc::wait(mmab, mp, limit_ns) && tc::wait(fullK, it & 1, limit_ns);
+            mp ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+        }
+        // the data operand is consumed: copy the next tile's data in
+        if (tid == 0 && more) {
+            load_a(t + G);
+            na++;
+        }
+        tc::fence_after();
+        // kernel multiply, eight kz at a time (this warp's half of the chunks);
+        // products to the inverse operand
+        for (int j = 4 * half; j < 4 * half + 4; j++) {
+            const int kz0 = 8 * j;
+            float mr[3][8], mi[3][8];
+            {
+                const uint32_t a[6] = {trow + kz0, trow + 64 + kz0, trow + 128 + kz0, trow + 192 + kz0,
+                                       trow + 256 + kz0, trow + 320 + kz0};
+                float v6[6][8];
+                tc::ld8x6(a, v6);
+#pragma unroll
+                for (int c = 0; c < 3; c++)
+#pragma unroll
+                    for (int e = 0; e < 8; e++) {
+                        mr[c][e] = v6[2 * c][e];
+                        mi[c][e] = v6[2 * c + 1][e];
+                    }
+            }
+            float hr[3][8], hi[3][8];
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const int kz = kz0 + e;
+                const int kzp = kz <= HZ6 ? kz : 64 - kz;
+                const float sz = kz > HZ6 ? -1.f : 1.f;  // xz and yz are odd in kz
+                const __half2* kp = kst + (kzp * 3) * KW6 + ke;
+                const float2 p0 = __half22float2(kp[0]), p1 = __half22float2(kp[KW6]), p2 = __half22float2(kp[2 * KW6]);
+                const float xx = p0.x, yy = p0.y, zz = p1.x;
+                const float xy = up ? -p1.y : p1.y, xz = sz * p2.x, yz = (up ? -sz : sz) * p2.y;
+                hr[0][e] = xx * mr[0][e] + xy * mr[1][e] + xz * mr[2][e];
+                hi[0][e] = xx * mi[0][e] + xy * mi[1][e] + xz * mi[2][e];
+                hr[1][e] = xy * mr[0][e] + yy * mr[1][e] + yz * mr[2][e];
+                hi[1][e] = xy * mi[0][e] + yy * mi[1][e] + yz * mi[2][e];
+                hr[2][e] = xz * mr[0][e] + yz * mr[1][e] + zz * mr[2][e];
+                hi[2][e] = xz * mi[0][e] + yz * mi[1][e] + zz * mi[2][e];
+            }
+            // row `row`, k = kz (Re) and 64 + kz (Im): one 16-byte store each
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                unsigned char* arow = AI + c * AI_COMP + (row >> 3) * AI_SBO + (row & 7) * 16;
+                uint4 wr, wi;
+                wr.x = pack_bf16(hr[c][0], hr[c][1]);
+                wr.y = pack_bf16(hr[c][2], hr[c][3]);
+                wr.z = pack_bf16(hr[c][4], hr[c][5]);
+                wr.w = pack_bf16(hr[c][6], hr[c][7]);
+                wi.x = pack_bf16(hi[c][0], hi[c][1]);
+                wi.y = pack_bf16(hi[c][2], hi[c][3]);
+                wi.z = pack_bf16(hi[c][4], hi[c][5]);
+                wi.w = pack_bf16(hi[c][6], hi[c][7]);
+                *reinterpret_cast<uint4*>(arow + j * AI_LBO) = wr;
+                *reinterpret_cast<uint4*>(arow + (8 + j) * AI_LBO) = wi;
+            }
+        }
+        fence_proxy_async_smem();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            // the kernel rows are consumed: copy the next tile's in
+            if (more) {
+                load_k(t + G);
+                nk++;
+            }
+            tc::fence_after();
+            for (int c = 0; c < 3; c++)
+#pragma unroll
+                for (int ks = 0; ks < 8; ks++)
+                    tc::mma_f16(tbase + c * 128, tc::sdesc(F + ks * 2 * FI_LBO, FI_LBO, FI_SBO),
+                                tc::sdesc(AI + c * AI_COMP + ks * 2 * AI_LBO, AI_LBO, AI_SBO), IDESC_I, ks > 0);
+            tc::commit(mmab);
+            nm++;
+        }
+        {
+            const bool ok = tc::wait(mmab, mp, limit_ns);
+            mp ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+        }
+        tc::fence_after();
+        // outputs: the thread of result row m = 16 lq + lane (lane < 16; part = m / 32,
+        // z = m mod 32) holds that row for the tile's 128 ky in columns c 128 + ky; warps
+        // w and w + 4 store the two 64-column halves
+        {
+            const int m = 16 * lq + (lane & 15), part = m >> 5, z = m & 31;
+            const bool keep = lane < 16 && z < g.nz;
+#pragma unroll 1
+            for (int c = 0; c < 3; c++) {
+                // line (kx, c, part, z), 64 consecutive ky from ky0 + 64 half
+                __nv_bfloat16* dst =
+                    Y16 + ((((size_t)kx * 3 + c) * 2 + part) * g.nz + z) * (size_t)py + ky0 + 64 * half;
+#pragma unroll
+                for (int hq = 0; hq < 2; hq++) {
+                float v[32];
+                tc::ld32(trow + c * 128 + 64 * half + 32 * hq, v);
+                if (keep) {
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        uint4 w;
+                        w.x = pack_bf16(v[8 * q + 0] * out_scale, v[8 * q + 1] * out_scale);
+                        w.y = pack_bf16(v[8 * q + 2] * out_scale, v[8 * q + 3] * out_scale);
+                        w.z = pack_bf16(v[8 * q + 4] * out_scale, v[8 * q + 5] * out_scale);
+                        w.w = pack_bf16(v[8 * q + 6] * out_scale, v[8 * q + 7] * out_scale);
+                        *reinterpret_cast<uint4*>(dst + 32 * hq + 8 * q) = w;
+                    }
+                }
+                }
+            }
+        }
+        tc::fence_before();
+        __syncthreads();
+    }
+
+    if (failed && tid == 0) {
+        atomicCAS(status, 0, STATUS_TIMEOUT6);
+        if (na > 0) tc::wait(fullA, (na - 1) & 1, limit_ns);
+        if (nk > 0) tc::wait(fullK, (nk - 1) & 1, limit_ns);
+        if (nm > 0) tc::wait(mmab, (nm - 1) & 1, limit_ns);
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::dealloc(tbase, TMEM6);
+    }
+}
+
+// K16 [kx][kz'][pair][ky'] of FP16 pairs (xx, yy), (zz, xy), (xz, yz) from the
+// octant K [kx][ky'][kz' 6 + comp], scaled by s; rows padded to kyp16 entries
+__global__ void k16_build_kernel(Geometry g, const float* __restrict__ K, __half2* __restrict__ K16, int kyp16, float s)
+{
+    const size_t total = (size_t)g.nkx * g.kzh * 3 * kyp16;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int kyp = (int)(i % kyp16);
+        size_t r = i / kyp16;
+        const int pair = (int)(r % 3);
+        r /= 3;
+        const int kzp = (int)(r % g.kzh);
+        const int kx = (int)(r / g.kzh);
+        float a = 0.f, b = 0.f;
+        if (kyp < g.kyh) {
+            const float* row = K + ((size_t)kx * g.kyh + kyp) * g.krow + kzp * 6 + 2 * pair;
+            a = row[0] * s;
+            b = row[1] * s;
+        }
+        K16[i] = __floats2half2_rn(a, b);
+    }
+}
+
+}  // namespace
+
+bool zconv_tc6_supported(const Geometry& g, int max_smem)
+{
+    // pz = 64 (17 <= nz <= 32), whole 128-column tiles on both sides of the ky fold
+    return g.pz == 2 * HZ6 && g.nz >= 17 && g.nz <= HZ6 && g.py >= 2 * MT && g.py % MT == 0 && g.kzh == KZH6 &&
+           SMEM6 <= (size_t)max_smem && g.lglmax >= 6;
+}
+
+int zconv_tc6_kyp16(const Geometry& g) { return g.py / 2 + 8; }
+size_t zconv_tc6_y16_bytes(const Geometry& g) { return (size_t)g.nkx * 3 * 2 * g.nz * g.py * 2; }
+size_t zconv_tc6_k16_bytes(const Geometry& g) { return (size_t)g.nkx * g.kzh * 3 * zconv_tc6_kyp16(g) * 4; }
+
+cudaError_t zconv_tc6_build_k16(const Geometry& g, const float* K, void* K16, cudaStream_t st)
+{
+    const size_t total = (size_t)g.nkx * g.kzh * 3 * zconv_tc6_kyp16(g);
+    const int blocks = (int)std::min<size_t>((total + 255) / 256, 152 * 32);
+    const float s = (float)((double)g.px * g.py * g.pz);
+    k16_build_kernel<<<blocks, 256, 0, st>>>(g, K, (__half2*)K16, zconv_tc6_kyp16(g), s);
+    return cudaGetLastError();
+}
+
+// Y16 [kx][c][part][z][ky] as the 5D tensor (ky%8, z, part, ky/8, kx c), boxes of
+// (8, 32, 2, 16, 1); K16 as (ky', kz' pair, kx) of 32-bit pairs, boxes of (136, 99, 1)
+cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, void* kmap)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    {
+        const cuuint64_t dims[5] = {8, (cuuint64_t)g.nz, 2, (cuuint64_t)g.py / 8, (cuuint64_t)g.nkx * 3};
+        const cuuint64_t strides[4] = {(cuuint64_t)g.py * 2, (cuuint64_t)g.nz * g.py * 2, 16,
+                                       (cuuint64_t)2 * g.nz * g.py * 2};
+        const cuuint32_t box[5] = {8, (cuuint32_t)HZ6, 2, (cuuint32_t)MT / 8, 1};
+        const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        const CUresult r = enc(reinterpret_cast<CUtensorMap*>(ymap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, Y16, dims,
+                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    {
+        const int kyp16 = zconv_tc6_kyp16(g);
+        const cuuint64_t dims[3] = {(cuuint64_t)kyp16, (cuuint64_t)g.kzh * 3, (cuuint64_t)g.nkx};
+        const cuuint64_t strides[2] = {(cuuint64_t)kyp16 * 4, (cuuint64_t)kyp16 * 4 * g.kzh * 3};
+        const cuuint32_t box[3] = {(cuuint32_t)KW6, (cuuint32_t)(g.kzh * 3), 1};
+        const cuuint32_t es[3] = {1, 1, 1};
+        const CUresult r = enc(reinterpret_cast<CUtensorMap*>(kmap), CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, K16, dims,
+                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_zconv_tc6(const void* ymap_p, const void* kmap_p, const Geometry& g, void* Y16, const float2* tw,
+                             int* status, unsigned long long limit_ns, int nsm, cudaStream_t st)
+{
+    const CUtensorMap& ymap = *reinterpret_cast<const CUtensorMap*>(ymap_p);
+    const CUtensorMap& kmap = *reinterpret_cast<const CUtensorMap*>(kmap_p);
+    cudaError_t e = cudaFuncSetAttribute(z_conv_tc6_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM6);
+    if (e != cudaSuccess) return e;
+    const int ntiles = g.nkx * (g.py / MT);
+    const int grid = std::min(ntiles, nsm);
+    const float out_scale = (float)(1.0 / ((double)g.px * g.py * g.pz));
+    z_conv_tc6_kernel<<<grid, T6, SMEM6, st>>>(ymap, kmap, g, (__nv_bfloat16*)Y16, tw, out_scale, status, limit_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace boris

@@ -24,13 +24,17 @@ FORMS = {"tcgen05": 5, "mma.sync": 4}
 
 
 def tc_plan(monkeypatch, form, *args, **kw):
+    """Plan with the tensor-core z stage in the given form; "tcgen05" keeps the
+    FP32 spectrum (BORIS_TC_STORE16=0), "store16" the BF16 one (BF16 plans)."""
     from paper_2008_02478_gb300.binding import Plan
     if form == "mma.sync":
         monkeypatch.setenv("BORIS_TC_MMASYNC", "1")
     else:
         monkeypatch.delenv("BORIS_TC_MMASYNC", raising=False)
+    monkeypatch.setenv("BORIS_TC_STORE16", "1" if form == "store16" else "0")
     plan = Plan(*args, **kw)
     monkeypatch.delenv("BORIS_TC_MMASYNC", raising=False)
+    monkeypatch.delenv("BORIS_TC_STORE16", raising=False)
     return plan
 
 
@@ -132,3 +136,61 @@ def test_large_film_tensor_core_stage_sampled_direct_sum(tc, monkeypatch):
     H = plan.apply(to_dev(torch, f["M"])).cpu().numpy().reshape(3, -1)
     assert plan.sync_status() == 0
     assert_close(H[:, f["cells"]].T, f["ref"], 1e-2)
+
+
+# meshes for the BF16-storage z stage: length-1024 y passes (257 <= ny <= 512), pz = 64
+STORE16 = [
+    ((64, 300, 17), (4e-9, 4e-9, 4e-9)),    # ragged nz, partial 128-column tiles of ny
+    ((48, 512, 32), (3e-9, 3e-9, 3e-9)),    # full z tile and full y lines
+    ((130, 400, 24), (3e-9, 2e-9, 3e-9)),   # anisotropic cells, odd nx
+]
+
+
+@pytest.mark.parametrize("n,h", STORE16)
+def test_bf16_storage_stage_matches_oracle(n, h, monkeypatch):
+    """BF16 plans store the padded y-z spectrum in BF16 and run the tcgen05
+    z stage with the data as the 128-row operand: H_d against the FP64 oracle
+    (bound 1e-2 on both norms), twice in a row (the persistent CTAs leave no
+    state behind), with no bounded wait giving up."""
+    torch = torch_cuda()
+    M = 8e5 * inputs.voronoi_columnar(*n, h, 20e-9, seed=5)
+    ref = oracle.DemagPlan(*n, *h).apply(M)
+    plan = tc_plan(monkeypatch, "store16", *n, *h, tc="bf16")
+    assert plan.schedule()[2] == 6
+    Md = to_dev(torch, M)
+    a = plan.apply(Md).cpu().numpy()
+    b = plan.apply(Md).cpu().numpy()
+    assert plan.sync_status() == 0
+    assert np.array_equal(a, b)
+    err, _ = assert_close(a, ref, 1e-2)
+    # it is the reduced-precision path, not an FP32 one
+    H32 = __import__("paper_2008_02478_gb300.binding", fromlist=["Plan"]).Plan(*n, *h).apply(Md).cpu().numpy()
+    assert err > 10 * rel_l2(H32, ref)
+
+
+def test_bf16_storage_stage_on_large_film(monkeypatch):
+    """The 512 x 512 x 32 film with the BF16-storage stage against the
+    oracle's direct sums at sampled cells."""
+    torch = torch_cuda()
+    f = _large_film_reference()
+    plan = tc_plan(monkeypatch, "store16", *f["n"], *f["cell"], tc="bf16")
+    assert plan.schedule()[2] == 6
+    H = plan.apply(to_dev(torch, f["M"])).cpu().numpy().reshape(3, -1)
+    assert plan.sync_status() == 0
+    assert_close(H[:, f["cells"]].T, f["ref"], 1e-2)
+
+
+def test_bf16_storage_rk4_step_matches_oracle(monkeypatch):
+    """One RK4 step of a BF16-storage plan (four evaluations through the new
+    stage) against the FP64 oracle: the change of m within 1e-2."""
+    torch = torch_cuda()
+    from oracle import llg
+    from paper_2008_02478_gb300.binding import LLGParams
+    n, h = (64, 300, 17), (4e-9, 4e-9, 4e-9)
+    m0 = inputs.voronoi_columnar(*n, h, 20e-9, seed=6)
+    prm = llg.Params(cell=h, Ms=8e5, A=1.3e-11, alpha=0.02, Hext=(0.0, 0.0, 8e4))
+    ref = llg.rk4_step(m0, 1e-13, prm, oracle.DemagPlan(*n, *h).apply)
+    plan = tc_plan(monkeypatch, "store16", *n, *h, tc="bf16")
+    m = to_dev(torch, m0)
+    plan.llg_step(m, LLGParams(Ms=8e5, A=1.3e-11, alpha=0.02, Hext=(0.0, 0.0, 8e4)), 1e-13)
+    assert_close(m.cpu().numpy() - m0, ref - m0, 1e-2)
