@@ -76,7 +76,7 @@ constexpr size_t OFF_AF = OFF_F + F_BYTES;
 constexpr size_t OFF_AI = OFF_AF + 3 * AF_COMP;
 constexpr size_t OFF_K = OFF_AI + 3 * AI_COMP;
 constexpr size_t OFF_BAR = (OFF_K + K_BYTES + 15) / 16 * 16;
-constexpr size_t OFF_TSLOT = OFF_BAR + 4 * 8;
+constexpr size_t OFF_TSLOT = OFF_BAR + 6 * 8;
 constexpr size_t SMEM6 = OFF_TSLOT + 16 + 1024;  // + alignment of the base to 1024 bytes
 static_assert(SMEM6 <= 232448, "one CTA per SM");
 static_assert(OFF_AF % 1024 == 0 && OFF_AI % 1024 == 0 && OFF_K % 128 == 0, "operand and copy alignment");
@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(T6, 1)
     const __half2* kst = reinterpret_cast<const __half2*>(base + OFF_K);
     uint64_t* fullA = reinterpret_cast<uint64_t*>(base + OFF_BAR);
     uint64_t* fullK = fullA + 1;
-    uint64_t* mmab = fullA + 2;
+    uint64_t* mmab = fullA + 2;  // forward products
+    uint64_t* invb = fullA + 3;  // inverse products of component c: invb[c] (one phase per tile each)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(base + OFF_TSLOT);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(T6, 1)
         mbar_init(fullA, 1);
         mbar_init(fullK, 1);
         mbar_init(mmab, 1);
+        for (int c = 0; c < 3; c++) mbar_init(invb + c, 1);
         fence_mbar_init();
     }
     fence_proxy_async_smem();
@@ -162,7 +164,9 @@ __global__ void __launch_bounds__(T6, 1)
         mbar_arrive_expect_tx(fullK, kbytes);
         tc::tma_load_3d(base + OFF_K, &kmap, x, 0, kx, fullK);
     };
-    int na = 0, nk = 0, nm = 0;  // copies and product groups issued by thread 0 (drained after a timeout)
+    // copies, forward product groups and inverse product groups (tiles) issued by
+    // thread 0 (drained after a timeout)
+    int na = 0, nk = 0, nm = 0, ni = 0;
     if (tid == 0 && (int)blockIdx.x < ntiles) {
         load_a(blockIdx.x);
         load_k(blockIdx.x);
@@ -213,6 +217,18 @@ __global__ void __launch_bounds__(T6, 1)
         // products to the inverse operand
         for (int j = 4 * half; j < 4 * half + 4; j++) {
             const int kz0 = 8 * j;
+            // this chunk's kernel pairs first: their shared-memory latency then
+            // overlaps that of the tensor-memory loads below
+            __half2 kq[8][3];
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const int kz = kz0 + e;
+                const int kzp = kz <= HZ6 ? kz : 64 - kz;
+                const __half2* kp = kst + (kzp * 3) * KW6 + ke;
+                kq[e][0] = kp[0];
+                kq[e][1] = kp[KW6];
+                kq[e][2] = kp[2 * KW6];
+            }
             float mr[3][8], mi[3][8];
             {
                 const uint32_t a[6] = {trow + kz0, trow + 64 + kz0, trow + 128 + kz0, trow + 192 + kz0,
@@ -231,10 +247,8 @@ __global__ void __launch_bounds__(T6, 1)
 #pragma unroll
             for (int e = 0; e < 8; e++) {
                 const int kz = kz0 + e;
-                const int kzp = kz <= HZ6 ? kz : 64 - kz;
                 const float sz = kz > HZ6 ? -1.f : 1.f;  // xz and yz are odd in kz
-                const __half2* kp = kst + (kzp * 3) * KW6 + ke;
-                const float2 p0 = __half22float2(kp[0]), p1 = __half22float2(kp[KW6]), p2 = __half22float2(kp[2 * KW6]);
+                const float2 p0 = __half22float2(kq[e][0]), p1 = __half22float2(kq[e][1]), p2 = __half22float2(kq[e][2]);
                 const float xx = p0.x, yy = p0.y, zz = p1.x;
                 const float xy = up ? -p1.y : p1.y, xz = sz * p2.x, yz = (up ? -sz : sz) * p2.y;
                 hr[0][e] = xx * mr[0][e] + xy * mr[1][e] + xz * mr[2][e];
@@ -271,23 +285,17 @@ __global__ void __launch_bounds__(T6, 1)
                 nk++;
             }
             tc::fence_after();
-            for (int c = 0; c < 3; c++)
+            // one commit (and barrier) per component: the stores of component c
+            // overlap the products of the later components
+            for (int c = 0; c < 3; c++) {
 #pragma unroll
                 for (int ks = 0; ks < 8; ks++)
                     tc::mma_f16(tbase + c * 128, tc::sdesc(F + ks * 2 * FI_LBO, FI_LBO, FI_SBO),
                                 tc::sdesc(AI + c * AI_COMP + ks * 2 * AI_LBO, AI_LBO, AI_SBO), IDESC_I, ks > 0);
-            tc::commit(mmab);
-            nm++;
-        }
-        {
-            const bool ok = tc::wait(mmab, mp, limit_ns);
-            mp ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
+                tc::commit(invb + c);
             }
+            ni++;
         }
-        tc::fence_after();
         // outputs: the thread of result row m = 16 lq + lane (lane < 16; part = m / 32,
         // z = m mod 32) holds that row for the tile's 128 ky in columns c 128 + ky; warps
         // w and w + 4 store the two 64-column halves
@@ -296,6 +304,12 @@ __global__ void __launch_bounds__(T6, 1)
             const bool keep = lane < 16 && z < g.nz;
 #pragma unroll 1
             for (int c = 0; c < 3; c++) {
+                {
+                    // the products of component c
+                    const bool ok = tc::wait(invb + c, it & 1, limit_ns);
+                    if (!ok) failed = true;
+                }
+                tc::fence_after();
                 // line (kx, c, part, z), 64 consecutive ky from ky0 + 64 half
                 __nv_bfloat16* dst =
                     Y16 + ((((size_t)kx * 3 + c) * 2 + part) * g.nz + z) * (size_t)py + ky0 + 64 * half;
@@ -318,7 +332,10 @@ __global__ void __launch_bounds__(T6, 1)
             }
         }
         tc::fence_before();
-        __syncthreads();
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
     }
 
     if (failed && tid == 0) {
@@ -326,6 +343,7 @@ __global__ void __launch_bounds__(T6, 1)
         if (na > 0) tc::wait(fullA, (na - 1) & 1, limit_ns);
         if (nk > 0) tc::wait(fullK, (nk - 1) & 1, limit_ns);
         if (nm > 0) tc::wait(mmab, (nm - 1) & 1, limit_ns);
+        for (int c = 0; c < 3 && ni > 0; c++) tc::wait(invb + c, (ni - 1) & 1, limit_ns);
     }
     tc::fence_before();
     __syncthreads();
