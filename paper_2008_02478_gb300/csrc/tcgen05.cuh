@@ -23,6 +23,13 @@ __device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t 
            (1ull << 46);
 }
 
+// the same with the 128-byte swizzle (atoms of 8 rows of 128 bytes, 16-byte
+// chunks XOR-permuted by the row index; atoms 1024-byte aligned)
+__device__ __forceinline__ uint64_t sdesc_sw128(const void* p, uint32_t lbo, uint32_t sbo)
+{
+    return sdesc(p, lbo, sbo) | (2ull << 61);
+}
+
 // instruction descriptor of kind::f16 with an FP32 accumulator: a_fmt / b_fmt
 // 0 = FP16, 1 = BF16; a_mn / b_mn: operand MN-major (else K-major)
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t fmt, bool a_mn, bool b_mn, int M, int N)

@@ -64,7 +64,10 @@ constexpr int STATUS_TIMEOUT6 = -5;
 
 constexpr uint32_t F_LBO = 128, F_SBO = 1024;    // F: K-major, 128 n x 64 k
 constexpr uint32_t FI_LBO = 1024, FI_SBO = 128;  // F^T as an MN-major operand: 64 rows x 128 k
-constexpr uint32_t AF_LBO = 128, AF_SBO = 1024;  // data: MN-major, 128 m x 64 k (tensor copy)
+// data: MN-major with the 128-byte swizzle, 128 m x 64 k (tensor copy): atoms of
+// 64 m (128 bytes) x 8 k; LBO = stride between the two 64-m atom columns,
+// SBO = stride between groups of 8 k
+constexpr uint32_t AF_LBO = 8192, AF_SBO = 1024;
 constexpr uint32_t AI_LBO = 128, AI_SBO = 2048;  // products: K-major, 128 m x 128 k
 
 constexpr size_t F_BYTES = 128 * 64 * 2;
@@ -154,7 +157,7 @@ __global__ void __launch_bounds__(T6, 1)
     auto load_a = [&](int t) {
         const int kx = t / nty, ky0 = (t - kx * nty) * MT;
         mbar_arrive_expect_tx(fullA, abytes);
-        for (int c = 0; c < 3; c++) tc::tma_load_5d(AF + c * AF_COMP, &ymap, 0, 0, 0, ky0 / 8, kx * 3 + c, fullA);
+        for (int c = 0; c < 3; c++) tc::tma_load_5d(AF + c * AF_COMP, &ymap, 0, 0, 0, ky0 / 64, kx * 3 + c, fullA);
     };
     // kernel rows of tile t: ky' = ky below the fold, py - ky above it (a box
     // starting 128 entries below py - ky0, so that ky' = x + 128 - t)
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(T6, 1)
             for (int c = 0; c < 3; c++)
 #pragma unroll
                 for (int ks = 0; ks < 4; ks++)
-                    tc::mma_f16(tbase + c * 128, tc::sdesc(AF + c * AF_COMP + ks * 2 * AF_LBO, AF_LBO, AF_SBO),
+                    tc::mma_f16(tbase + c * 128, tc::sdesc_sw128(AF + c * AF_COMP + ks * 2 * AF_SBO, AF_LBO, AF_SBO),
                                 tc::sdesc(F + ks * 2 * F_LBO, F_LBO, F_SBO), IDESC_F, ks > 0);
             tc::commit(mmab);
             nm++;
@@ -404,13 +407,13 @@ cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, 
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
     {
-        const cuuint64_t dims[5] = {8, (cuuint64_t)g.nz, 2, (cuuint64_t)g.py / 8, (cuuint64_t)g.nkx * 3};
-        const cuuint64_t strides[4] = {(cuuint64_t)g.py * 2, (cuuint64_t)g.nz * g.py * 2, 16,
+        const cuuint64_t dims[5] = {64, (cuuint64_t)g.nz, 2, (cuuint64_t)g.py / 64, (cuuint64_t)g.nkx * 3};
+        const cuuint64_t strides[4] = {(cuuint64_t)g.py * 2, (cuuint64_t)g.nz * g.py * 2, 128,
                                        (cuuint64_t)2 * g.nz * g.py * 2};
-        const cuuint32_t box[5] = {8, (cuuint32_t)HZ6, 2, (cuuint32_t)MT / 8, 1};
+        const cuuint32_t box[5] = {64, (cuuint32_t)HZ6, 2, (cuuint32_t)MT / 64, 1};
         const cuuint32_t es[5] = {1, 1, 1, 1, 1};
         const CUresult r = enc(reinterpret_cast<CUtensorMap*>(ymap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, Y16, dims,
-                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     }
