@@ -406,9 +406,12 @@ int boris_plan_padded(boris_plan p, int out[3]);
  * fitted to, out[2] the z-convolution variant: 1 or 2 for the persistent
  * bulk-copy (TMA) pipeline with one or two tile stages, 3 for the residue-
  * split z convolution, 0 for the shared-memory form; on tensor-core plans 5
- * for the tcgen05 stage and 4 for the mma.sync one.  Variants 1, 2, 3 and 5
- * bound their mbarrier waits and latch BORIS_ERR_TIMEOUT in the status word
- * read by boris_sync_status.
+ * for the tcgen05 stage, 4 for the mma.sync one and 6 for the BF16 plan whose
+ * y passes store the spectrum in BF16 and whose tcgen05 z stage takes the
+ * data as the 128-row operand (BORIS_TC_STORE16=0 at plan creation keeps
+ * the FP32 spectrum and variant 5).  Variants 1, 2, 3, 5 and 6 bound their
+ * mbarrier waits and latch BORIS_ERR_TIMEOUT in the status word read by
+ * boris_sync_status.
  * Environment overrides read at plan creation restrict the candidates:
  * BORIS_YZ_KIND, BORIS_YZ_CLUSTER, BORIS_YZ_THREADS, BORIS_YZ_QC (kind 0
  * chunk), BORIS_YZ_TMA (kind 2 variant). */

@@ -120,6 +120,24 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32])
     for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
 }
 
+// two 16x32bx2 loads of eight columns each with one wait: threads 0-15 read
+// lanes base..base+15 at columns c .. c + 7, threads 16-31 the same lanes at
+// c + 8 .. c + 15 (c = column of ta, then of tb); v[0..7] from ta, v[8..15] from tb
+__device__ __forceinline__ void ld16x2_8x2(uint32_t ta, uint32_t tb, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x32bx2.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16], 8;\n\t"
+        "tcgen05.ld.sync.aligned.16x32bx2.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17], 8;\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta), "r"(tb)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
 // mbarrier wait that lets the hardware suspend the thread (up to 20 us per
 // try); false after limit_ns of device time
 __device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)

@@ -27,16 +27,17 @@
 //            F's storage read as an MN-major operand (M = 64 rows (part, z):
 //            row m of the result lands in tensor-memory lane 32 (m / 16) +
 //            m mod 16), the products H_c the K-major B operand (rows = ky
-//            columns); the thread of row (part, z < nz) then stores its 128 ky
-//            as 16-byte pieces
+//            columns); the rows (part, z < nz) are read back by half-warp
+//            loads (16 lanes, two column runs) and stored as 16-byte pieces
 // The kernel spectrum arrives as FP16 pairs (xx, yy), (zz, xy), (xz, yz) of
 // the octant scaled by px py pz (the fold of the normalisation is undone on
-// the output).  Everything runs in one persistent CTA of eight warps per SM
-// (tensor memory: 3 x 128 accumulator columns); warps w and w + 4 read the
-// same tensor-memory lanes and split the kz chunks of the multiply and the ky
-// halves of the output; tensor-memory loads are issued in groups with one
-// wait each.  The next tile's data and kernel rows are copied in while the
-// current tile is multiplied.
+// the output).  Everything runs in one persistent CTA of sixteen warps per SM
+// (tensor memory: 3 x 128 accumulator columns); the four warps of a
+// tensor-memory lane quarter split the kz range of the multiply (sixteen kz
+// each, so that the fold signs are fixed per warp and tile) and the ky
+// columns of the output (32 each); tensor-memory loads are issued in groups
+// with one wait each.  The next tile's data and kernel rows are copied in
+// while the current tile is multiplied.
 //
 // Every mbarrier wait is bounded (device timer); when one gives up the CTA
 // latches BORIS_ERR_TIMEOUT in *status, waits (bounded) for its copies and
@@ -54,7 +55,7 @@ namespace boris {
 
 namespace {
 
-constexpr int T6 = 256;       // threads: two per accumulator row (ky column), warps w and w + 4 share lanes
+constexpr int T6 = 512;       // threads: four warps per tensor-memory lane quarter
 constexpr int MT = 128;       // ky columns per tile
 constexpr int HZ6 = 32;       // z cells held (pz = 64)
 constexpr int KZH6 = HZ6 + 1;  // kz' rows of the kernel octant
@@ -90,6 +91,65 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// The kernel multiply of one chunk of eight kz for accumulator row `row`
+// (kernel entry ke of the staged rows): the forward products of the three
+// components from tensor memory, H_c = sum_d N_cd M_d with the fold signs
+// known at compile time (UP: above the ky fold, xy and yz odd in ky; NEGZ:
+// kz > 32, xz and yz odd in kz, whose kz = 32 entries vanish), BF16 products
+// to the K-major inverse operand (k = kz for Re, 64 + kz for Im).
+template <bool UP, bool NEGZ>
+__device__ __forceinline__ void tc6_multiply_chunk(int j, uint32_t trow, const __half2* __restrict__ kst, int ke,
+                                                   unsigned char* AI, int row)
+{
+    const int kz0 = 8 * j;
+    // this chunk's kernel pairs first: their shared-memory latency then
+    // overlaps that of the tensor-memory loads below
+    __half2 kq[8][3];
+#pragma unroll
+    for (int e = 0; e < 8; e++) {
+        const int kz = kz0 + e;
+        const int kzp = kz <= HZ6 ? kz : 64 - kz;
+        const __half2* kp = kst + (kzp * 3) * KW6 + ke;
+        kq[e][0] = kp[0];
+        kq[e][1] = kp[KW6];
+        kq[e][2] = kp[2 * KW6];
+    }
+    float v6[6][8];
+    {
+        const uint32_t a[6] = {trow + kz0, trow + 64 + kz0, trow + 128 + kz0, trow + 192 + kz0,
+                               trow + 256 + kz0, trow + 320 + kz0};
+        tc::ld8x6(a, v6);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        float hr[8], hi[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const float2 p0 = __half22float2(kq[e][0]), p1 = __half22float2(kq[e][1]), p2 = __half22float2(kq[e][2]);
+            const float xx = p0.x, yy = p0.y, zz = p1.x;
+            const float xy = UP ? -p1.y : p1.y, xz = NEGZ ? -p2.x : p2.x, yz = (UP != NEGZ) ? -p2.y : p2.y;
+            const float n0 = c == 0 ? xx : c == 1 ? xy : xz;
+            const float n1 = c == 0 ? xy : c == 1 ? yy : yz;
+            const float n2 = c == 0 ? xz : c == 1 ? yz : zz;
+            hr[e] = n0 * v6[0][e] + n1 * v6[2][e] + n2 * v6[4][e];
+            hi[e] = n0 * v6[1][e] + n1 * v6[3][e] + n2 * v6[5][e];
+        }
+        // row `row`, k = kz (Re) and 64 + kz (Im): one 16-byte store each
+        unsigned char* arow = AI + c * AI_COMP + (row >> 3) * AI_SBO + (row & 7) * 16;
+        uint4 wr, wi;
+        wr.x = pack_bf16(hr[0], hr[1]);
+        wr.y = pack_bf16(hr[2], hr[3]);
+        wr.z = pack_bf16(hr[4], hr[5]);
+        wr.w = pack_bf16(hr[6], hr[7]);
+        wi.x = pack_bf16(hi[0], hi[1]);
+        wi.y = pack_bf16(hi[2], hi[3]);
+        wi.z = pack_bf16(hi[4], hi[5]);
+        wi.w = pack_bf16(hi[6], hi[7]);
+        *reinterpret_cast<uint4*>(arow + j * AI_LBO) = wr;
+        *reinterpret_cast<uint4*>(arow + (8 + j) * AI_LBO) = wi;
+    }
+}
+
 __global__ void __launch_bounds__(T6, 1)
     z_conv_tc6_kernel(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap kmap, Geometry g,
                       __nv_bfloat16* __restrict__ Y16, const float2* __restrict__ tw_g, float out_scale,
@@ -108,8 +168,8 @@ __global__ void __launch_bounds__(T6, 1)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(base + OFF_TSLOT);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lq = warp & 3, half = warp >> 2;  // tensor-memory lane quarter, work half
-    const int row = 32 * lq + lane;             // accumulator row of the multiply (ky column in the tile)
+    const int lq = warp & 3, wp = warp >> 2;  // tensor-memory lane quarter, work part (0..3)
+    const int row = 32 * lq + lane;           // accumulator row of the multiply (ky column in the tile)
     const int py = g.py;
     const int nty = py / MT, ntiles = g.nkx * nty, G = gridDim.x;
     constexpr uint32_t abytes = 3 * (uint32_t)AF_COMP;
@@ -216,66 +276,19 @@ __global__ void __launch_bounds__(T6, 1)
             na++;
         }
         tc::fence_after();
-        // kernel multiply, eight kz at a time (this warp's half of the chunks);
-        // products to the inverse operand
-        for (int j = 4 * half; j < 4 * half + 4; j++) {
-            const int kz0 = 8 * j;
-            // this chunk's kernel pairs first: their shared-memory latency then
-            // overlaps that of the tensor-memory loads below
-            __half2 kq[8][3];
-#pragma unroll
-            for (int e = 0; e < 8; e++) {
-                const int kz = kz0 + e;
-                const int kzp = kz <= HZ6 ? kz : 64 - kz;
-                const __half2* kp = kst + (kzp * 3) * KW6 + ke;
-                kq[e][0] = kp[0];
-                kq[e][1] = kp[KW6];
-                kq[e][2] = kp[2 * KW6];
-            }
-            float mr[3][8], mi[3][8];
-            {
-                const uint32_t a[6] = {trow + kz0, trow + 64 + kz0, trow + 128 + kz0, trow + 192 + kz0,
-                                       trow + 256 + kz0, trow + 320 + kz0};
-                float v6[6][8];
-                tc::ld8x6(a, v6);
-#pragma unroll
-                for (int c = 0; c < 3; c++)
-#pragma unroll
-                    for (int e = 0; e < 8; e++) {
-                        mr[c][e] = v6[2 * c][e];
-                        mi[c][e] = v6[2 * c + 1][e];
-                    }
-            }
-            float hr[3][8], hi[3][8];
-#pragma unroll
-            for (int e = 0; e < 8; e++) {
-                const int kz = kz0 + e;
-                const float sz = kz > HZ6 ? -1.f : 1.f;  // xz and yz are odd in kz
-                const float2 p0 = __half22float2(kq[e][0]), p1 = __half22float2(kq[e][1]), p2 = __half22float2(kq[e][2]);
-                const float xx = p0.x, yy = p0.y, zz = p1.x;
-                const float xy = up ? -p1.y : p1.y, xz = sz * p2.x, yz = (up ? -sz : sz) * p2.y;
-                hr[0][e] = xx * mr[0][e] + xy * mr[1][e] + xz * mr[2][e];
-                hi[0][e] = xx * mi[0][e] + xy * mi[1][e] + xz * mi[2][e];
-                hr[1][e] = xy * mr[0][e] + yy * mr[1][e] + yz * mr[2][e];
-                hi[1][e] = xy * mi[0][e] + yy * mi[1][e] + yz * mi[2][e];
-                hr[2][e] = xz * mr[0][e] + yz * mr[1][e] + zz * mr[2][e];
-                hi[2][e] = xz * mi[0][e] + yz * mi[1][e] + zz * mi[2][e];
-            }
-            // row `row`, k = kz (Re) and 64 + kz (Im): one 16-byte store each
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                unsigned char* arow = AI + c * AI_COMP + (row >> 3) * AI_SBO + (row & 7) * 16;
-                uint4 wr, wi;
-                wr.x = pack_bf16(hr[c][0], hr[c][1]);
-                wr.y = pack_bf16(hr[c][2], hr[c][3]);
-                wr.z = pack_bf16(hr[c][4], hr[c][5]);
-                wr.w = pack_bf16(hr[c][6], hr[c][7]);
-                wi.x = pack_bf16(hi[c][0], hi[c][1]);
-                wi.y = pack_bf16(hi[c][2], hi[c][3]);
-                wi.z = pack_bf16(hi[c][4], hi[c][5]);
-                wi.w = pack_bf16(hi[c][6], hi[c][7]);
-                *reinterpret_cast<uint4*>(arow + j * AI_LBO) = wr;
-                *reinterpret_cast<uint4*>(arow + (8 + j) * AI_LBO) = wi;
+        // kernel multiply: this warp's part of the kz range, two chunks of
+        // eight (parts 2 and 3 lie above kz = 32)
+        {
+            const bool nz_ = wp >= 2;
+#pragma unroll 1
+            for (int j = 2 * wp; j < 2 * wp + 2; j++) {
+                if (up) {
+                    if (nz_) tc6_multiply_chunk<true, true>(j, trow, kst, ke, AI, row);
+                    else tc6_multiply_chunk<true, false>(j, trow, kst, ke, AI, row);
+                } else {
+                    if (nz_) tc6_multiply_chunk<false, true>(j, trow, kst, ke, AI, row);
+                    else tc6_multiply_chunk<false, false>(j, trow, kst, ke, AI, row);
+                }
             }
         }
         fence_proxy_async_smem();
@@ -299,12 +312,14 @@ __global__ void __launch_bounds__(T6, 1)
             }
             ni++;
         }
-        // outputs: the thread of result row m = 16 lq + lane (lane < 16; part = m / 32,
-        // z = m mod 32) holds that row for the tile's 128 ky in columns c 128 + ky; warps
-        // w and w + 4 store the two 64-column halves
+        // outputs: result row m = 16 lq + (lane mod 16) (part = m / 32, z = m mod 32)
+        // sits in lane 32 lq + m mod 16; warp part wp stores the tile's ky
+        // 32 wp .. 32 wp + 31 of it, the two half-warps taking alternate runs of
+        // eight (so that each store instruction writes whole 32-byte sectors)
         {
             const int m = 16 * lq + (lane & 15), part = m >> 5, z = m & 31;
-            const bool keep = lane < 16 && z < g.nz;
+            const bool keep = z < g.nz;
+            const int kyo = 32 * wp + 8 * (lane >> 4);
 #pragma unroll 1
             for (int c = 0; c < 3; c++) {
                 {
@@ -313,24 +328,21 @@ __global__ void __launch_bounds__(T6, 1)
                     if (!ok) failed = true;
                 }
                 tc::fence_after();
-                // line (kx, c, part, z), 64 consecutive ky from ky0 + 64 half
-                __nv_bfloat16* dst =
-                    Y16 + ((((size_t)kx * 3 + c) * 2 + part) * g.nz + z) * (size_t)py + ky0 + 64 * half;
-#pragma unroll
-                for (int hq = 0; hq < 2; hq++) {
-                float v[32];
-                tc::ld32(trow + c * 128 + 64 * half + 32 * hq, v);
+                float v[16];
+                const uint32_t tc0 = trow + c * 128 + 32 * wp;
+                tc::ld16x2_8x2(tc0, tc0 + 16, v);
                 if (keep) {
+                    __nv_bfloat16* dst =
+                        Y16 + ((((size_t)kx * 3 + c) * 2 + part) * g.nz + z) * (size_t)py + ky0 + kyo;
 #pragma unroll
-                    for (int q = 0; q < 4; q++) {
+                    for (int q = 0; q < 2; q++) {
                         uint4 w;
                         w.x = pack_bf16(v[8 * q + 0] * out_scale, v[8 * q + 1] * out_scale);
                         w.y = pack_bf16(v[8 * q + 2] * out_scale, v[8 * q + 3] * out_scale);
                         w.z = pack_bf16(v[8 * q + 4] * out_scale, v[8 * q + 5] * out_scale);
                         w.w = pack_bf16(v[8 * q + 6] * out_scale, v[8 * q + 7] * out_scale);
-                        *reinterpret_cast<uint4*>(dst + 32 * hq + 8 * q) = w;
+                        *reinterpret_cast<uint4*>(dst + 16 * q) = w;
                     }
-                }
                 }
             }
         }
