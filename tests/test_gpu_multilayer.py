@@ -66,6 +66,58 @@ def test_every_inter_plane_sum_kernel_matches_direct_sum(layers, hz, gaps, varia
     assert_close(H, ref, 1e-5)
 
 
+# frames of at least 33 cells in y (py >= 64), the paired-column sum's range
+WIDE = ([(34, 33, 1), (12, 34, 2), (20, 10, 2)], [2e-9, 3e-9, 4e-9], [1e-9, 3e-9])
+_wide_ref = {}
+
+
+def _wide_case():
+    if "ref" not in _wide_ref:
+        st, m, M, _ = stack_case(*WIDE, 4e-9, seed=11)
+        _wide_ref.update(st=st, M=M, ref=ml.direct(st, M))
+    return _wide_ref["st"], _wide_ref["M"], _wide_ref["ref"]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_inter_plane_sum_kernels_on_a_wide_frame(variant, monkeypatch):
+    """Every inter-plane sum variant on a 34 x 34 frame (py = 128: three
+    32-column tiles of folded ky, the last holding only the Nyquist column)
+    against Eq. 4's direct sum over all 2338 cells."""
+    torch = torch_cuda()
+    st, M, ref = _wide_case()
+    monkeypatch.setenv("BORIS_ML_MIX", str(variant))
+    plan = make_plan(st)
+    assert plan.schedule()[2] == variant
+    H = plan.apply(torch.tensor(M, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert_close(H, ref, 1e-5)
+
+
+def test_persistent_sum_with_four_targets_per_warp(monkeypatch):
+    """27 planes (four targets per warp in the persistent sum at two CTAs per
+    SM): twelve cells against Eq. 4's direct sum, and the whole field against
+    the one-CTA-per-tile sum."""
+    torch = torch_cuda()
+    layers, hz, gaps = [(34, 34, 10), (20, 36, 8), (30, 20, 9)], [2e-9, 3e-9, 4e-9], [1e-9, 3e-9]
+    st, m, M, _ = stack_case(layers, hz, gaps, 4e-9, seed=12)
+    Mt = torch.tensor(M, dtype=torch.float32, device="cuda")
+    monkeypatch.setenv("BORIS_ML_MIX", "3")
+    plan = make_plan(st)
+    assert plan.info()[0] == 27 and plan.schedule()[2] == 3
+    H = plan.apply(Mt).cpu().numpy()
+    monkeypatch.setenv("BORIS_ML_MIX", "0")
+    H0 = make_plan(st).apply(Mt).cpu().numpy()
+    assert_close(H, H0, 1e-5)
+    cells = inputs.rng(13).integers(0, st.total(), 12)
+    ref = ml.direct_at(st, M, cells)
+    offs = np.cumsum([0] + st.counts)
+    got = []
+    for gi in cells:
+        l = int(np.searchsorted(offs, gi, side="right") - 1)
+        n = st.counts[l]
+        got.append([H[3 * offs[l] + c * n + gi - offs[l]] for c in range(3)])
+    assert_close(np.array(got), ref, 1e-5)
+
+
 def test_reciprocal_spectra_halve_the_cross_layer_set():
     """Spectra are stored once per (min(a, b), max(a, b), |dz|): two layers of
     z sizes 2 and 3 nm, one plane each, need 3 spectra (a = b = 2, a = b = 3,
