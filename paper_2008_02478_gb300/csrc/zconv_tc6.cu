@@ -55,7 +55,8 @@ namespace boris {
 
 namespace {
 
-constexpr int T6 = 512;       // threads: four warps per tensor-memory lane quarter
+constexpr int NCW6 = 16;                // compute warps: four per tensor-memory lane quarter
+constexpr int T6 = 32 * (NCW6 + 1);     // and one warp that issues the copies and products
 constexpr int MT = 128;       // ky columns per tile
 constexpr int HZ6 = 32;       // z cells held (pz = 64)
 constexpr int KZH6 = HZ6 + 1;  // kz' rows of the kernel octant
@@ -80,7 +81,7 @@ constexpr size_t OFF_AF = OFF_F + F_BYTES;
 constexpr size_t OFF_AI = OFF_AF + 3 * AF_COMP;
 constexpr size_t OFF_K = OFF_AI + 3 * AI_COMP;
 constexpr size_t OFF_BAR = (OFF_K + K_BYTES + 15) / 16 * 16;
-constexpr size_t OFF_TSLOT = OFF_BAR + 6 * 8;
+constexpr size_t OFF_TSLOT = OFF_BAR + 9 * 8;
 constexpr size_t SMEM6 = OFF_TSLOT + 16 + 1024;  // + alignment of the base to 1024 bytes
 static_assert(SMEM6 <= 232448, "one CTA per SM");
 static_assert(OFF_AF % 1024 == 0 && OFF_AI % 1024 == 0 && OFF_K % 128 == 0, "operand and copy alignment");
@@ -93,13 +94,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 
 // The kernel multiply of one chunk of eight kz for accumulator row `row`
 // (kernel entry ke of the staged rows): the forward products of the three
-// components from tensor memory, H_c = sum_d N_cd M_d with the fold signs
+// components from tensor memory (row addresses t0, t1, t2), H_c = sum_d N_cd M_d with the fold signs
 // known at compile time (UP: above the ky fold, xy and yz odd in ky; NEGZ:
 // kz > 32, xz and yz odd in kz, whose kz = 32 entries vanish), BF16 products
 // to the K-major inverse operand (k = kz for Re, 64 + kz for Im).
 template <bool UP, bool NEGZ>
-__device__ __forceinline__ void tc6_multiply_chunk(int j, uint32_t trow, const __half2* __restrict__ kst, int ke,
-                                                   unsigned char* AI, int row)
+__device__ __forceinline__ void tc6_multiply_chunk(int j, uint32_t t0, uint32_t t1, uint32_t t2,
+                                                   const __half2* __restrict__ kst, int ke, unsigned char* AI, int row)
 {
     const int kz0 = 8 * j;
     // this chunk's kernel pairs first: their shared-memory latency then
@@ -116,8 +117,7 @@ __device__ __forceinline__ void tc6_multiply_chunk(int j, uint32_t trow, const _
     }
     float v6[6][8];
     {
-        const uint32_t a[6] = {trow + kz0, trow + 64 + kz0, trow + 128 + kz0, trow + 192 + kz0,
-                               trow + 256 + kz0, trow + 320 + kz0};
+        const uint32_t a[6] = {t0 + kz0, t0 + 64 + kz0, t1 + kz0, t1 + 64 + kz0, t2 + kz0, t2 + 64 + kz0};
         tc::ld8x6(a, v6);
     }
 #pragma unroll
@@ -163,8 +163,10 @@ __global__ void __launch_bounds__(T6, 1)
     const __half2* kst = reinterpret_cast<const __half2*>(base + OFF_K);
     uint64_t* fullA = reinterpret_cast<uint64_t*>(base + OFF_BAR);
     uint64_t* fullK = fullA + 1;
-    uint64_t* mmab = fullA + 2;  // forward products
-    uint64_t* invb = fullA + 3;  // inverse products of component c: invb[c] (one phase per tile each)
+    uint64_t* fwdb = fullA + 2;  // forward products of a tile (tcgen05.commit)
+    uint64_t* mulb = fullA + 3;  // kernel multiply of a tile done (one arrival per compute warp)
+    uint64_t* invb = fullA + 4;  // inverse products of component c: invb[c] (tcgen05.commit)
+    uint64_t* outb = fullA + 7;  // result rows of component c (c < 2) read from tensor memory
     uint32_t* tslot = reinterpret_cast<uint32_t*>(base + OFF_TSLOT);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -204,8 +206,10 @@ __global__ void __launch_bounds__(T6, 1)
     if (tid == 0) {
         mbar_init(fullA, 1);
         mbar_init(fullK, 1);
-        mbar_init(mmab, 1);
+        mbar_init(fwdb, 1);
+        mbar_init(mulb, NCW6);
         for (int c = 0; c < 3; c++) mbar_init(invb + c, 1);
+        for (int c = 0; c < 2; c++) mbar_init(outb + c, NCW6);
         fence_mbar_init();
     }
     fence_proxy_async_smem();
@@ -227,96 +231,134 @@ __global__ void __launch_bounds__(T6, 1)
         mbar_arrive_expect_tx(fullK, kbytes);
         tc::tma_load_3d(base + OFF_K, &kmap, x, 0, kx, fullK);
     };
-    // copies, forward product groups and inverse product groups (tiles) issued by
-    // thread 0 (drained after a timeout)
-    int na = 0, nk = 0, nm = 0, ni = 0;
-    if (tid == 0 && (int)blockIdx.x < ntiles) {
-        load_a(blockIdx.x);
-        load_k(blockIdx.x);
-        na = nk = 1;
-    }
-
-    const uint32_t trow = tbase + ((uint32_t)(32 * lq) << 16);
+    // Tensor memory holds four 128-column regions.  Tile number it (of this CTA)
+    // has its forward products of component c in region (r + c) mod 4, r = 2 it
+    // mod 4, and its inverse products in regions (r + 3, r, r + 1) mod 4: the
+    // region the multiply frees last (r + 2) and the one its inverse leaves free
+    // take the next tile's forward products of components 0 and 1, so those run
+    // while the current tile's results are read and stored.
+    const bool producer = warp == NCW6;
     bool failed = false;
-    uint32_t mp = 0;  // parity of the next product-group completion
-    int it = 0;
-    for (int t = blockIdx.x; t < ntiles; t += G, it++) {
-        const int kx = t / nty, ky0 = (t - kx * nty) * MT;
-        const bool more = t + G < ntiles;
-        const bool up = ky0 >= py / 2;  // above the ky fold: xy and yz change sign
-        const int ke = up ? MT - row : row;
-        {
-            const bool ok = tc::wait(fullA, it & 1, limit_ns);
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-        }
-        if (tid == 0) {
-            tc::fence_after();
-            for (int c = 0; c < 3; c++)
+    int na = 0, nk = 0, nf = 0, ni = 0;  // copies and product groups the producer issued
+    if (producer) {
+        if (lane == 0) {
+            auto fwd = [&](int region, int c) {
 #pragma unroll
                 for (int ks = 0; ks < 4; ks++)
-                    tc::mma_f16(tbase + c * 128, tc::sdesc_sw128(AF + c * AF_COMP + ks * 2 * AF_SBO, AF_LBO, AF_SBO),
+                    tc::mma_f16(tbase + region * 128,
+                                tc::sdesc_sw128(AF + c * AF_COMP + ks * 2 * AF_SBO, AF_LBO, AF_SBO),
                                 tc::sdesc(F + ks * 2 * F_LBO, F_LBO, F_SBO), IDESC_F, ks > 0);
-            tc::commit(mmab);
-            nm++;
-        }
-        {
-            const bool ok = tc::wait(mmab, mp, limit_ns) && tc::wait(fullK, it & 1, limit_ns);
-            mp ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-        }
-        // the data operand is consumed: copy the next tile's data in
-        if (tid == 0 && more) {
-            load_a(t + G);
-            na++;
-        }
-        tc::fence_after();
-        // kernel multiply: this warp's part of the kz range, two chunks of
-        // eight (parts 2 and 3 lie above kz = 32)
-        {
-            const bool nz_ = wp >= 2;
-#pragma unroll 1
-            for (int j = 2 * wp; j < 2 * wp + 2; j++) {
-                if (up) {
-                    if (nz_) tc6_multiply_chunk<true, true>(j, trow, kst, ke, AI, row);
-                    else tc6_multiply_chunk<true, false>(j, trow, kst, ke, AI, row);
+            };
+            if ((int)blockIdx.x < ntiles) {
+                load_a(blockIdx.x);
+                load_k(blockIdx.x);
+                na = nk = 1;
+                if (!tc::wait(fullA, 0, limit_ns)) {
+                    failed = true;
                 } else {
-                    if (nz_) tc6_multiply_chunk<false, true>(j, trow, kst, ke, AI, row);
-                    else tc6_multiply_chunk<false, false>(j, trow, kst, ke, AI, row);
+                    tc::fence_after();
+                    for (int c = 0; c < 3; c++) fwd(c, c);
+                    tc::commit(fwdb);
+                    nf = 1;
                 }
             }
+            int it = 0;
+            for (int t = blockIdx.x; t < ntiles && !failed; t += G, it++) {
+                const int r = (2 * it) & 3;
+                const bool more = t + G < ntiles;
+                // the forward products are done: the data operand is free
+                if (!tc::wait(fwdb, it & 1, limit_ns)) {
+                    failed = true;
+                    break;
+                }
+                if (more) {
+                    load_a(t + G);
+                    na++;
+                }
+                // the multiply is done: products in shared memory, forward regions read,
+                // kernel rows consumed
+                if (!tc::wait(mulb, it & 1, limit_ns)) {
+                    failed = true;
+                    break;
+                }
+                if (more) {
+                    load_k(t + G);
+                    nk++;
+                }
+                tc::fence_after();
+                for (int c = 0; c < 3; c++) {
+                    const int region = c == 0 ? (r + 3) & 3 : c == 1 ? r : (r + 1) & 3;
+#pragma unroll
+                    for (int ks = 0; ks < 8; ks++)
+                        tc::mma_f16(tbase + region * 128, tc::sdesc(F + ks * 2 * FI_LBO, FI_LBO, FI_SBO),
+                                    tc::sdesc(AI + c * AI_COMP + ks * 2 * AI_LBO, AI_LBO, AI_SBO), IDESC_I, ks > 0);
+                    tc::commit(invb + c);
+                }
+                ni++;
+                if (!more) continue;
+                // the next tile's forward products, each into a region as soon as it is free
+                if (!tc::wait(fullA, (it + 1) & 1, limit_ns)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after();
+                fwd((r + 2) & 3, 0);
+                if (!tc::wait(outb, it & 1, limit_ns)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after();
+                fwd((r + 3) & 3, 1);
+                if (!tc::wait(outb + 1, it & 1, limit_ns)) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after();
+                fwd(r, 2);
+                tc::commit(fwdb);
+                nf++;
+            }
         }
-        fence_proxy_async_smem();
-        tc::fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            // the kernel rows are consumed: copy the next tile's in
-            if (more) {
-                load_k(t + G);
-                nk++;
+    } else {
+        const uint32_t trow = tbase + ((uint32_t)(32 * lq) << 16);
+        int it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += G, it++) {
+            const int kx = t / nty, ky0 = (t - kx * nty) * MT;
+            const int r = (2 * it) & 3;
+            const bool up = ky0 >= py / 2;  // above the ky fold: xy and yz change sign
+            const int ke = up ? MT - row : row;
+            {
+                const bool ok = tc::wait(fwdb, it & 1, limit_ns) && tc::wait(fullK, it & 1, limit_ns);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    failed = true;
+                    break;
+                }
             }
             tc::fence_after();
-            // one commit (and barrier) per component: the stores of component c
-            // overlap the products of the later components
-            for (int c = 0; c < 3; c++) {
-#pragma unroll
-                for (int ks = 0; ks < 8; ks++)
-                    tc::mma_f16(tbase + c * 128, tc::sdesc(F + ks * 2 * FI_LBO, FI_LBO, FI_SBO),
-                                tc::sdesc(AI + c * AI_COMP + ks * 2 * AI_LBO, AI_LBO, AI_SBO), IDESC_I, ks > 0);
-                tc::commit(invb + c);
+            // kernel multiply: this warp's part of the kz range, two chunks of
+            // eight (parts 2 and 3 lie above kz = 32)
+            {
+                const uint32_t t0 = trow + 128 * r, t1 = trow + 128 * ((r + 1) & 3), t2 = trow + 128 * ((r + 2) & 3);
+                const bool nz_ = wp >= 2;
+#pragma unroll 1
+                for (int j = 2 * wp; j < 2 * wp + 2; j++) {
+                    if (up) {
+                        if (nz_) tc6_multiply_chunk<true, true>(j, t0, t1, t2, kst, ke, AI, row);
+                        else tc6_multiply_chunk<true, false>(j, t0, t1, t2, kst, ke, AI, row);
+                    } else {
+                        if (nz_) tc6_multiply_chunk<false, true>(j, t0, t1, t2, kst, ke, AI, row);
+                        else tc6_multiply_chunk<false, false>(j, t0, t1, t2, kst, ke, AI, row);
+                    }
+                }
             }
-            ni++;
-        }
-        // outputs: result row m = 16 lq + (lane mod 16) (part = m / 32, z = m mod 32)
-        // sits in lane 32 lq + m mod 16; warp part wp stores the tile's ky
-        // 32 wp .. 32 wp + 31 of it, the two half-warps taking alternate runs of
-        // eight (so that each store instruction writes whole 32-byte sectors)
-        {
+            fence_proxy_async_smem();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(mulb);
+            // outputs: result row m = 16 lq + (lane mod 16) (part = m / 32, z = m mod 32)
+            // sits in lane 32 lq + m mod 16; warp part wp stores the tile's ky
+            // 32 wp .. 32 wp + 31 of it, the two half-warps taking alternate runs of
+            // eight (so that each store instruction writes whole 32-byte sectors)
             const int m = 16 * lq + (lane & 15), part = m >> 5, z = m & 31;
             const bool keep = z < g.nz;
             const int kyo = 32 * wp + 8 * (lane >> 4);
@@ -325,12 +367,22 @@ __global__ void __launch_bounds__(T6, 1)
                 {
                     // the products of component c
                     const bool ok = tc::wait(invb + c, it & 1, limit_ns);
-                    if (!ok) failed = true;
+                    if (__any_sync(0xffffffffu, !ok)) {
+                        failed = true;
+                        break;
+                    }
                 }
                 tc::fence_after();
+                const int region = c == 0 ? (r + 3) & 3 : c == 1 ? r : (r + 1) & 3;
                 float v[16];
-                const uint32_t tc0 = trow + c * 128 + 32 * wp;
+                const uint32_t tc0 = trow + 128 * region + 32 * wp;
                 tc::ld16x2_8x2(tc0, tc0 + 16, v);
+                if (c < 2) {
+                    // this warp's rows of component c are read: the region may be reused
+                    tc::fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(outb + c);
+                }
                 if (keep) {
                     __nv_bfloat16* dst =
                         Y16 + ((((size_t)kx * 3 + c) * 2 + part) * g.nz + z) * (size_t)py + ky0 + kyo;
@@ -345,19 +397,19 @@ __global__ void __launch_bounds__(T6, 1)
                     }
                 }
             }
-        }
-        tc::fence_before();
-        if (__syncthreads_or(failed)) {
-            failed = true;
-            break;
+            if (failed) break;
         }
     }
 
-    if (failed && tid == 0) {
+    // every wait above is bounded, so all warps arrive here; after a timeout the
+    // producer drains what it issued before the tensor memory is freed
+    tc::fence_before();
+    failed = __syncthreads_or(failed);
+    if (failed && producer && lane == 0) {
         atomicCAS(status, 0, STATUS_TIMEOUT6);
         if (na > 0) tc::wait(fullA, (na - 1) & 1, limit_ns);
         if (nk > 0) tc::wait(fullK, (nk - 1) & 1, limit_ns);
-        if (nm > 0) tc::wait(mmab, (nm - 1) & 1, limit_ns);
+        if (nf > 0) tc::wait(fwdb, (nf - 1) & 1, limit_ns);
         for (int c = 0; c < 3 && ni > 0; c++) tc::wait(invb + c, (ni - 1) & 1, limit_ns);
     }
     tc::fence_before();
