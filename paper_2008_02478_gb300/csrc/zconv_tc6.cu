@@ -31,13 +31,19 @@
 //            loads (16 lanes, two column runs) and stored as 16-byte pieces
 // The kernel spectrum arrives as FP16 pairs (xx, yy), (zz, xy), (xz, yz) of
 // the octant scaled by px py pz (the fold of the normalisation is undone on
-// the output).  Everything runs in one persistent CTA of sixteen warps per SM
-// (tensor memory: 3 x 128 accumulator columns); the four warps of a
-// tensor-memory lane quarter split the kz range of the multiply (sixteen kz
-// each, so that the fold signs are fixed per warp and tile) and the ky
-// columns of the output (32 each); tensor-memory loads are issued in groups
-// with one wait each.  The next tile's data and kernel rows are copied in
-// while the current tile is multiplied.
+// the output).  Everything runs in one persistent CTA per SM: sixteen compute
+// warps and one warp whose first thread issues the tensor copies and the
+// products.  The four compute warps of a tensor-memory lane quarter split the
+// kz range of the multiply (sixteen kz each, so that the fold signs are fixed
+// per warp and tile) and the ky columns of the output (32 each);
+// tensor-memory loads are issued in groups with one wait each.  Tensor memory
+// holds four regions of 128 columns; the forward products of a tile take
+// three of them and its inverse products the free one and two that the
+// multiply has consumed, so the next tile's forward products go into each
+// region as soon as the current tile's rows there have been read (mbarrier
+// arrivals of the compute warps), while those rows are being stored.  The
+// next tile's data are copied in once the forward products are done, its
+// kernel rows once the multiply is done.
 //
 // Every mbarrier wait is bounded (device timer); when one gives up the CTA
 // latches BORIS_ERR_TIMEOUT in *status, waits (bounded) for its copies and
