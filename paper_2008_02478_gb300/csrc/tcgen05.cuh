@@ -138,6 +138,30 @@ __device__ __forceinline__ void ld16x2_8x2(uint32_t ta, uint32_t tb, float (&v)[
     for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
 }
 
+// one 16x32bx2 load of sixteen columns: threads 0-15 read lanes base..base+15
+// at columns c .. c + 15, threads 16-31 the same lanes at c + 16 .. c + 31
+__device__ __forceinline__ void ld16x2_16(uint32_t ta, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x32bx2.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16], 16;\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta)
+        : "memory");
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+}
+
+// 32-byte global store (sm_100 and later); p 32-byte aligned
+__device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&w)[8])
+{
+    asm volatile("st.global.v8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                 "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                 : "memory");
+}
+
 // mbarrier wait that lets the hardware suspend the thread (up to 20 us per
 // try); false after limit_ns of device time
 __device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns)

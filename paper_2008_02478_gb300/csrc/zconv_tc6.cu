@@ -363,11 +363,11 @@ __global__ void __launch_bounds__(T6, 1)
             if (lane == 0) mbar_arrive(mulb);
             // outputs: result row m = 16 lq + (lane mod 16) (part = m / 32, z = m mod 32)
             // sits in lane 32 lq + m mod 16; warp part wp stores the tile's ky
-            // 32 wp .. 32 wp + 31 of it, the two half-warps taking alternate runs of
-            // eight (so that each store instruction writes whole 32-byte sectors)
+            // 32 wp .. 32 wp + 31 of it, each half-warp sixteen consecutive ky (one
+            // 32-byte store per thread, 64 contiguous bytes per row and instruction)
             const int m = 16 * lq + (lane & 15), part = m >> 5, z = m & 31;
             const bool keep = z < g.nz;
-            const int kyo = 32 * wp + 8 * (lane >> 4);
+            const int kyo = 32 * wp + 16 * (lane >> 4);
 #pragma unroll 1
             for (int c = 0; c < 3; c++) {
                 {
@@ -381,8 +381,7 @@ __global__ void __launch_bounds__(T6, 1)
                 tc::fence_after();
                 const int region = c == 0 ? (r + 3) & 3 : c == 1 ? r : (r + 1) & 3;
                 float v[16];
-                const uint32_t tc0 = trow + 128 * region + 32 * wp;
-                tc::ld16x2_8x2(tc0, tc0 + 16, v);
+                tc::ld16x2_16(trow + 128 * region + 32 * wp, v);
                 if (c < 2) {
                     // this warp's rows of component c are read: the region may be reused
                     tc::fence_before();
@@ -392,15 +391,10 @@ __global__ void __launch_bounds__(T6, 1)
                 if (keep) {
                     __nv_bfloat16* dst =
                         Y16 + ((((size_t)kx * 3 + c) * 2 + part) * g.nz + z) * (size_t)py + ky0 + kyo;
+                    uint32_t w[8];
 #pragma unroll
-                    for (int q = 0; q < 2; q++) {
-                        uint4 w;
-                        w.x = pack_bf16(v[8 * q + 0] * out_scale, v[8 * q + 1] * out_scale);
-                        w.y = pack_bf16(v[8 * q + 2] * out_scale, v[8 * q + 3] * out_scale);
-                        w.z = pack_bf16(v[8 * q + 4] * out_scale, v[8 * q + 5] * out_scale);
-                        w.w = pack_bf16(v[8 * q + 6] * out_scale, v[8 * q + 7] * out_scale);
-                        *reinterpret_cast<uint4*>(dst + 16 * q) = w;
-                    }
+                    for (int q = 0; q < 8; q++) w[q] = pack_bf16(v[2 * q] * out_scale, v[2 * q + 1] * out_scale);
+                    tc::st_global_v8(dst, w);
                 }
             }
             if (failed) break;
