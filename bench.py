@@ -1055,7 +1055,8 @@ def main():
                          "h_rel_l2_vs_fp64": err, "h_max_rel_vs_fp64": merr,
                          "z_stage_ms_per_launch": kk["z_conv"][0] / max(1, kk["z_conv"][1]),
                          "kernels_ms_per_launch": {k: v[0] / v[1] for k, v in kk.items() if v[1]},
-                         "z_stage": {6: "tcgen05, spectrum between the y and z passes stored in BF16",
+                         "z_stage": {6: "tcgen05, spectrum between the y and z passes stored in " +
+                                        ("FP16 (power-of-two scale from max |M|)" if tc == "fp16" else "BF16"),
                                      5: "tcgen05 (tensor memory), FP32 spectrum", 4: "mma.sync"}.get(pt.schedule()[2], "?")}
             pt.close()
             del mt

@@ -52,9 +52,12 @@ struct YZSchedule {
 };
 
 // Kernel launchers (demag.cu); T = float or double.
+// absmax (optional, length-1024 x transforms only): raised to max |Ms M| over
+// the field (as the bits of a non-negative float) for the FP16 spectrum scale
 template <typename T>
 cudaError_t launch_x_r2c(const Geometry& g, const T* M, const T* ms_map, T ms_scale,
-                         typename Cx<T>::t* X, const typename Cx<T>::t* tw, cudaStream_t st);
+                         typename Cx<T>::t* X, const typename Cx<T>::t* tw, cudaStream_t st,
+                         unsigned* absmax = nullptr);
 template <typename T>
 cudaError_t launch_yz_conv(const Geometry& g, const YZSchedule& sc, typename Cx<T>::t* X,
                            const T* K, const typename Cx<T>::t* tw, cudaStream_t st);
@@ -90,7 +93,7 @@ template <typename T>
 bool y1024_ok(const Geometry& g, int max_smem);
 template <typename T>
 cudaError_t launch_x_r2c_1024(const Geometry& g, const T* M, const T* ms_map, T ms_scale, typename Cx<T>::t* X,
-                              const typename Cx<T>::t* tw, cudaStream_t st);
+                              const typename Cx<T>::t* tw, cudaStream_t st, unsigned* absmax = nullptr);
 template <typename T>
 cudaError_t launch_x_c2r_1024(const Geometry& g, const typename Cx<T>::t* X, T* H, const typename Cx<T>::t* tw,
                               cudaStream_t st);
@@ -98,20 +101,24 @@ template <typename T>
 cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T>::t* Y, const typename Cx<T>::t* tw,
                           cudaStream_t st, bool forward);
 cudaError_t upload_twiddles_fast();
-// y passes of length 1024 on the BF16 spectrum of the mixed-precision split
-// schedule (layout [kx][c][ky/8][part][z][ky%8])
+// y passes of length 1024 on the 16-bit spectrum of the mixed-precision split
+// schedule (layout [kx][c][part][z][ky]); BF16, or with fp16 FP16 scaled by the
+// power of two s with s nx ny nz max|M| < 2^14 (max|M| from absmax)
 cudaError_t launch_y_1024_b16(const Geometry& g, float2* X, void* Y16, const float2* tw, cudaStream_t st,
-                              bool forward);
-// Mixed-precision z stage with the spectrum stored in BF16 (zconv_tc6.cu):
+                              bool forward, bool fp16 = false, const unsigned* absmax = nullptr);
+// max |Ms M| raised into *out (a non-negative float's bits; *out zeroed before)
+cudaError_t launch_absmax(const Geometry& g, const float* M, const float* ms_map, float ms, unsigned* out, int nsm,
+                          cudaStream_t st);
+// Mixed-precision z stage with the spectrum stored in 16 bits (zconv_tc6.cu):
 // pz = 64, py >= 256 in 128-column tiles; reads the FP16 kernel pairs K16
 bool zconv_tc6_supported(const Geometry& g, int max_smem);
 int zconv_tc6_kyp16(const Geometry& g);
 size_t zconv_tc6_y16_bytes(const Geometry& g);
 size_t zconv_tc6_k16_bytes(const Geometry& g);
 cudaError_t zconv_tc6_build_k16(const Geometry& g, const float* K, void* K16, cudaStream_t st);
-cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, void* kmap);
+cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, void* kmap, bool fp16 = false);
 cudaError_t launch_zconv_tc6(const void* ymap, const void* kmap, const Geometry& g, void* Y16, const float2* tw,
-                             int* status, unsigned long long limit_ns, int nsm, cudaStream_t st);
+                             int* status, unsigned long long limit_ns, int nsm, cudaStream_t st, bool fp16 = false);
 // Length-512 passes (meshes of 129..256 cells along the axis), two lines per
 // warp through the length-1024 warp transform (fft512.cu).
 template <typename T>

@@ -30,9 +30,12 @@ struct boris_plan_s {
     bool f64;
     int tc = 0;  // 0: FP32 z stage; 1: FP16 tensor cores; 2: BF16 tensor cores
     bool tc5 = false;  // tensor-core z stage on tcgen05 (else the mma.sync form)
-    // BF16 plans: the padded y-z spectrum stored in BF16 (Y16), the z stage on
-    // tcgen05 with the data as the 128-row operand, FP16 kernel pairs (K16)
+    // BF16 and FP16 plans: the padded y-z spectrum stored in 16 bits (Y16), the z
+    // stage on tcgen05 with the data as the 128-row operand, FP16 kernel pairs
+    // (K16); FP16 plans scale the spectrum by a power of two from max |Ms M|,
+    // which the x pass raises in absmax
     bool tc6 = false;
+    unsigned* d_absmax = nullptr;
     void* Y16 = nullptr;
     void* K16 = nullptr;
     alignas(64) unsigned char ymap16[128] = {};
@@ -226,14 +229,21 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
 {
     using C = typename Cx<T>::t;
     if (sc.kind == 2 && p->tc6) {
-        cudaError_t e = timed(p, 5, [&] { return launch_y_1024_b16(p->g, (float2*)p->X, p->Y16, (const float2*)p->tw, p->stream, true); });
+        const bool h16 = p->tc == 1;
+        cudaError_t e = timed(p, 5, [&] {
+            return launch_y_1024_b16(p->g, (float2*)p->X, p->Y16, (const float2*)p->tw, p->stream, true, h16,
+                                     p->d_absmax);
+        });
         if (e == cudaSuccess)
             e = timed(p, 6, [&] {
                 return launch_zconv_tc6(p->ymap16, p->kmap16, p->g, p->Y16, (const float2*)p->tw, p->d_status,
-                                        p->wait_limit_ns, p->nsm, p->stream);
+                                        p->wait_limit_ns, p->nsm, p->stream, h16);
             });
         if (e == cudaSuccess)
-            e = timed(p, 7, [&] { return launch_y_1024_b16(p->g, (float2*)p->X, p->Y16, (const float2*)p->tw, p->stream, false); });
+            e = timed(p, 7, [&] {
+                return launch_y_1024_b16(p->g, (float2*)p->X, p->Y16, (const float2*)p->tw, p->stream, false, h16,
+                                         p->d_absmax);
+            });
         return e;
     }
     if (sc.kind == 2) {
@@ -295,7 +305,24 @@ template <typename T>
 int demag_to_spectrum_t(boris_plan p, const T* M, const T* ms_map, T ms_scale)
 {
     using C = typename Cx<T>::t;
-    CUDA_TRY(timed(p, 0, [&] { return launch_x_r2c<T>(p->g, M, ms_map, ms_scale, (C*)p->X, (const C*)p->tw, p->stream); }));
+    // FP16 spectrum: the x pass also finds max |Ms M| for the y passes' scale
+    unsigned* absmax = nullptr;
+    if constexpr (sizeof(T) == 4) {
+        if (p->tc6 && p->tc == 1) {
+            absmax = p->d_absmax;
+            CUDA_TRY(cudaMemsetAsync(absmax, 0, sizeof(unsigned), p->stream));
+            if (!x1024_ok<float>(p->g, 227 * 1024)) {
+                CUDA_TRY(timed(p, 4, [&] {
+                    return launch_absmax(p->g, (const float*)M, (const float*)ms_map, (float)ms_scale, absmax, p->nsm,
+                                         p->stream);
+                }));
+                absmax = nullptr;
+            }
+        }
+    }
+    CUDA_TRY(timed(p, 0, [&] {
+        return launch_x_r2c<T>(p->g, M, ms_map, ms_scale, (C*)p->X, (const C*)p->tw, p->stream, absmax);
+    }));
     CUDA_TRY(yz_stage<T>(p, p->yz));
     return BORIS_OK;
 }
@@ -844,11 +871,12 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
         // the mma.sync form (for comparisons)
         const char* ms = std::getenv("BORIS_TC_MMASYNC");
         p->tc5 = zconv_tc5_supported(g, max_smem) && !(ms && std::atoi(ms) == 1);
-        // BF16 plans store the padded spectrum in BF16 where the length-1024 y
-        // passes and the 128-column tiles apply (BORIS_TC_STORE16=0 keeps the
-        // FP32 spectrum with the tcgen05 stage of 16-column tiles)
+        // tensor-core plans store the padded spectrum in their 16-bit format where
+        // the length-1024 x and y passes and the 128-column tiles apply
+        // (BORIS_TC_STORE16=0 keeps the FP32 spectrum with the tcgen05 stage of
+        // 16-column tiles)
         const char* s16 = std::getenv("BORIS_TC_STORE16");
-        p->tc6 = tc == 2 && p->tc5 && zconv_tc6_supported(g, max_smem) && y1024_ok<float>(g, max_smem) &&
+        p->tc6 = p->tc5 && zconv_tc6_supported(g, max_smem) && y1024_ok<float>(g, max_smem) &&
                  !(s16 && std::atoi(s16) == 0);
     }
     if (ncand == 0) return bail(fail(BORIS_ERR_UNSUPPORTED_SIZE, "y-z plane does not fit the cluster shared memory"));
@@ -950,8 +978,9 @@ static int plan_create(int nx, int ny, int nz, double dx, double dy, double dz, 
     if (p->tc6) {
         if ((rc = dev_alloc(p, &p->Y16, zconv_tc6_y16_bytes(g)))) return bail(rc);
         if ((rc = dev_alloc(p, &p->K16, zconv_tc6_k16_bytes(g)))) return bail(rc);
+        if (p->tc == 1 && (rc = dev_alloc(p, (void**)&p->d_absmax, 16))) return bail(rc);
         if ((ce = zconv_tc6_build_k16(g, (const float*)p->K, p->K16, p->stream)) != cudaSuccess ||
-            (ce = zconv_tc6_maps(g, p->Y16, p->K16, p->ymap16, p->kmap16)) != cudaSuccess)
+            (ce = zconv_tc6_maps(g, p->Y16, p->K16, p->ymap16, p->kmap16, p->tc == 1)) != cudaSuccess)
             return bail(fail(BORIS_ERR_CUDA, std::string("16-bit spectrum set-up: ") + cudaGetErrorString(ce)));
     }
     if ((ce = cudaStreamSynchronize(p->stream)) != cudaSuccess)
@@ -1613,7 +1642,7 @@ void boris_plan_destroy(boris_plan p)
 {
     if (!p) return;
     cudaStreamSynchronize(p->stream);
-    void* ptrs[] = {p->Y16, p->K16, p->Kml, p->d_pairs, p->d_pcode, p->d_invhz, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->d_rkf, p->energy,
+    void* ptrs[] = {p->d_absmax, p->Y16, p->K16, p->Kml, p->d_pairs, p->d_pcode, p->d_invhz, p->Mf, p->Hf, p->K, p->K2, p->d_step, p->X, p->Y, p->Hd, p->msa, p->msb, p->acc, p->kbuf, p->mtrial, p->d_rkf, p->energy,
                     p->m_dev_e2e, p->bw};
     for (void* q : ptrs)
         if (q) cudaFree(q);

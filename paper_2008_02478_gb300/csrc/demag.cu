@@ -358,9 +358,10 @@ static cudaError_t launch_r2c_ty(const Geometry& g, const T* M, const T* ms_map,
 
 template <typename T>
 cudaError_t launch_x_r2c(const Geometry& g, const T* M, const T* ms_map, T ms_scale,
-                         typename Cx<T>::t* X, const typename Cx<T>::t* tw, cudaStream_t st)
+                         typename Cx<T>::t* X, const typename Cx<T>::t* tw, cudaStream_t st, unsigned* absmax)
 {
-    if (x1024_ok<T>(g, 227 * 1024)) return launch_x_r2c_1024<T>(g, M, ms_map, ms_scale, X, tw, st);
+    if (x1024_ok<T>(g, 227 * 1024)) return launch_x_r2c_1024<T>(g, M, ms_map, ms_scale, X, tw, st, absmax);
+    if (absmax) return cudaErrorInvalidValue;
     if (x512_ok<T>(g, 227 * 1024)) return launch_x_r2c_512<T>(g, M, ms_map, ms_scale, X, tw, st);
     if (x2048_ok<T>(g, 227 * 1024)) return launch_x_r2c_2048<T>(g, M, ms_map, ms_scale, X, tw, st);
     if (x4096_ok<T>(g, 227 * 1024)) return launch_x_r2c_4096<T>(g, M, ms_map, ms_scale, X, tw, st);
@@ -518,7 +519,7 @@ cudaError_t launch_yz_conv(const Geometry& g, const YZSchedule& sc, typename Cx<
 
 #define BORIS_INST(T)                                                                                         \
     template cudaError_t launch_x_r2c<T>(const Geometry&, const T*, const T*, T, Cx<T>::t*, const Cx<T>::t*, \
-                                         cudaStream_t);                                                       \
+                                         cudaStream_t, unsigned*);                                            \
     template cudaError_t launch_yz_conv<T>(const Geometry&, const YZSchedule&, Cx<T>::t*, const T*,           \
                                            const Cx<T>::t*, cudaStream_t);                                    \
     template cudaError_t launch_x_c2r<T>(const Geometry&, const Cx<T>::t*, T*, const Cx<T>::t*, cudaStream_t, int*, \

@@ -4,6 +4,7 @@
 // (packed) line in registers (warp_fft.cuh); global loads and stores are
 // 32 consecutive elements per instruction.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "boris_internal.cuh"
 #include "bulk_async.cuh"
@@ -19,7 +20,8 @@ template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) x_r2c_1024_kernel(Geometry g, const T* __restrict__ M,
                                                          const T* __restrict__ ms_map, T ms_scale,
                                                          typename Cx<T>::t* __restrict__ X,
-                                                         const typename Cx<T>::t* __restrict__ tw_g)
+                                                         const typename Cx<T>::t* __restrict__ tw_g,
+                                                         unsigned* __restrict__ absmax)
 {
     using C = typename Cx<T>::t;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -58,6 +60,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) x_r2c_1024_kernel
             v[a].x *= ms_scale;
             v[a].y *= ms_scale;
         }
+    }
+    if (absmax) {
+        // the largest |Ms M| this warp loaded (one atomic per warp; the bits of
+        // non-negative floats order like the floats)
+        float mx = 0.f;
+#pragma unroll
+        for (int a = 0; a < 16; a++) mx = fmaxf(mx, fmaxf(fabsf((float)v[a].x), fabsf((float)v[a].y)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(absmax, __float_as_uint(mx));
     }
 #pragma unroll
     for (int a = 16; a < 32; a++) v[a] = C{T(0), T(0)};
@@ -352,9 +364,37 @@ __device__ __forceinline__ size_t y16_index(int kx, int c, int part, int z, int 
     return ((((size_t)kx * 3 + c) * 2 + part) * nz + z) * (size_t)py + ky;
 }
 
+// Power-of-two scale s of an FP16 spectrum: s nx ny nz max|M| < 2^14, so that
+// the spectrum (at most nx ny max|M| after the x and y transforms), its z
+// transform and the kernel products stay inside FP16's range.
+__device__ __forceinline__ float y16_scale_exp(const Geometry& g, const unsigned* absmax, int* e)
+{
+    const float bound = __uint_as_float(*absmax) * ((float)g.nx * (float)g.ny * (float)g.nz);
+    *e = 0;
+    if (!(bound > 0.f) || !isfinite(bound)) return 1.f;
+    frexpf(bound, e);  // bound = f 2^e, 0.5 <= f < 1
+    return ldexpf(1.f, 14 - *e);
+}
+
+template <bool H16>
+__device__ __forceinline__ unsigned short to16(float v)
+{
+    if constexpr (H16) return __half_as_ushort(__float2half_rn(v));
+    else return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <bool H16>
+__device__ __forceinline__ float from16(unsigned short v)
+{
+    if constexpr (H16) return __half2float(__ushort_as_half(v));
+    else return __bfloat162float(__ushort_as_bfloat16(v));
+}
+
+// H16: FP16 values scaled by s (y16_scale_exp), else BF16 unscaled
+template <bool H16>
 __global__ void __launch_bounds__(256, 3) y_fwd_1024_b16_kernel(Geometry g, const float2* __restrict__ X,
-                                                                __nv_bfloat16* __restrict__ Y16,
-                                                                const float2* __restrict__ tw_g)
+                                                                unsigned short* __restrict__ Y16,
+                                                                const float2* __restrict__ tw_g,
+                                                                const unsigned* __restrict__ absmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tws = reinterpret_cast<float2*>(smem_raw);
@@ -374,18 +414,26 @@ __global__ void __launch_bounds__(256, 3) y_fwd_1024_b16_kernel(Geometry g, cons
         v[a] = (a < 16 && y < ny) ? src[y] : float2{0.f, 0.f};
     }
     warp_fft1024_fwd(v, reg + warp * REG1025, tws);
+    float s = 1.f;
+    if constexpr (H16) {
+        int e;
+        s = y16_scale_exp(g, absmax, &e);
+    }
     // v[pos] = Y[ky], ky = lane + 32 brev5(pos)
-    __nv_bfloat16* re = Y16 + y16_index(kx, c, 0, z, lane, nz, 1024);
-    __nv_bfloat16* im = Y16 + y16_index(kx, c, 1, z, lane, nz, 1024);
+    unsigned short* re = Y16 + y16_index(kx, c, 0, z, lane, nz, 1024);
+    unsigned short* im = Y16 + y16_index(kx, c, 1, z, lane, nz, 1024);
 #pragma unroll
     for (int pos = 0; pos < 32; pos++) {
-        re[32 * brev5(pos)] = __float2bfloat16_rn(v[pos].x);
-        im[32 * brev5(pos)] = __float2bfloat16_rn(v[pos].y);
+        re[32 * brev5(pos)] = to16<H16>(H16 ? v[pos].x * s : v[pos].x);
+        im[32 * brev5(pos)] = to16<H16>(H16 ? v[pos].y * s : v[pos].y);
     }
 }
 
-__global__ void __launch_bounds__(256) y_inv_1024_b16_kernel(Geometry g, const __nv_bfloat16* __restrict__ Y16,
-                                                             float2* __restrict__ X, const float2* __restrict__ tw_g)
+// H16: the FP16 result of the z stage carries px py pz s / 128 (see zconv_tc6.cu)
+template <bool H16>
+__global__ void __launch_bounds__(256) y_inv_1024_b16_kernel(Geometry g, const unsigned short* __restrict__ Y16,
+                                                             float2* __restrict__ X, const float2* __restrict__ tw_g,
+                                                             const unsigned* __restrict__ absmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* tws = reinterpret_cast<float2*>(smem_raw);
@@ -397,11 +445,20 @@ __global__ void __launch_bounds__(256) y_inv_1024_b16_kernel(Geometry g, const _
     __syncthreads();
     if (line >= lines) return;
     const int c = line / nz, z = line - c * nz;
-    const __nv_bfloat16* re = Y16 + y16_index(kx, c, 0, z, lane, nz, 1024);
-    const __nv_bfloat16* im = Y16 + y16_index(kx, c, 1, z, lane, nz, 1024);
+    const unsigned short* re = Y16 + y16_index(kx, c, 0, z, lane, nz, 1024);
+    const unsigned short* im = Y16 + y16_index(kx, c, 1, z, lane, nz, 1024);
+    float u = 1.f;
+    if constexpr (H16) {
+        int e;
+        y16_scale_exp(g, absmax, &e);
+        u = ldexpf(128.f / ((float)g.px * (float)g.py * (float)g.pz), e - 14);  // 128 / (px py pz s)
+    }
     float2 v[32];
 #pragma unroll
-    for (int d = 0; d < 32; d++) v[brev5(d)] = float2{__bfloat162float(re[32 * d]), __bfloat162float(im[32 * d])};
+    for (int d = 0; d < 32; d++) {
+        const float a = from16<H16>(re[32 * d]), b = from16<H16>(im[32 * d]);
+        v[brev5(d)] = H16 ? float2{a * u, b * u} : float2{a, b};
+    }
     warp_fft1024_inv<float2, false>(v, reg + warp * REG1025, tws);
     float2* dst = X + ((size_t)kx * lines + line) * ny;
 #pragma unroll
@@ -433,12 +490,12 @@ bool y1024_ok(const Geometry& g, int max_smem)
 
 template <typename T>
 cudaError_t launch_x_r2c_1024(const Geometry& g, const T* M, const T* ms_map, T ms_scale, typename Cx<T>::t* X,
-                              const typename Cx<T>::t* tw, cudaStream_t st)
+                              const typename Cx<T>::t* tw, cudaStream_t st, unsigned* absmax)
 {
     const size_t smem = smem_1024<T>();
     cudaError_t e = cudaFuncSetAttribute(x_r2c_1024_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    x_r2c_1024_kernel<T><<<dim3((g.ny + 15) / 16, g.nz, 3), 256, smem, st>>>(g, M, ms_map, ms_scale, X, tw);
+    x_r2c_1024_kernel<T><<<dim3((g.ny + 15) / 16, g.nz, 3), 256, smem, st>>>(g, M, ms_map, ms_scale, X, tw, absmax);
     return cudaGetLastError();
 }
 template <typename T>
@@ -469,22 +526,56 @@ cudaError_t launch_y_1024(const Geometry& g, typename Cx<T>::t* X, typename Cx<T
     return cudaGetLastError();
 }
 
-cudaError_t launch_y_1024_b16(const Geometry& g, float2* X, void* Y16, const float2* tw, cudaStream_t st,
-                              bool forward)
+// max |Ms M| over the field (SoA [3][nz][ny][nx], Ms per cell from ms_map or
+// the scalar ms) raised into *out, for the FP16 spectrum scale where the x pass
+// is not the length-1024 one (which finds it while loading)
+__global__ void absmax_kernel(const float* __restrict__ M, const float* __restrict__ ms_map, float ms, size_t ncell,
+                              unsigned* __restrict__ out)
+{
+    float mx = 0.f;
+    const size_t n3 = 3 * ncell;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fabsf(M[i] * (ms_map ? ms_map[i % ncell] : ms)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+cudaError_t launch_absmax(const Geometry& g, const float* M, const float* ms_map, float ms, unsigned* out, int nsm,
+                          cudaStream_t st)
+{
+    absmax_kernel<<<4 * nsm, 256, 0, st>>>(M, ms_map, ms, (size_t)g.nx * g.ny * g.nz, out);
+    return cudaGetLastError();
+}
+
+template <bool H16>
+static cudaError_t launch_y16(const Geometry& g, float2* X, void* Y16, const float2* tw, cudaStream_t st,
+                              bool forward, const unsigned* absmax)
 {
     const size_t smem = smem_1024<float>();
     const dim3 grid((3 * g.nz + 7) / 8, g.nkx);
     if (forward) {
-        cudaError_t e = cudaFuncSetAttribute(y_fwd_1024_b16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(y_fwd_1024_b16_kernel<H16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        y_fwd_1024_b16_kernel<<<grid, 256, smem, st>>>(g, X, (__nv_bfloat16*)Y16, tw);
+        y_fwd_1024_b16_kernel<H16><<<grid, 256, smem, st>>>(g, X, (unsigned short*)Y16, tw, absmax);
     } else {
         cudaError_t e =
-            cudaFuncSetAttribute(y_inv_1024_b16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(y_inv_1024_b16_kernel<H16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        y_inv_1024_b16_kernel<<<grid, 256, smem, st>>>(g, (const __nv_bfloat16*)Y16, X, tw);
+        y_inv_1024_b16_kernel<H16><<<grid, 256, smem, st>>>(g, (const unsigned short*)Y16, X, tw, absmax);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_y_1024_b16(const Geometry& g, float2* X, void* Y16, const float2* tw, cudaStream_t st,
+                              bool forward, bool fp16, const unsigned* absmax)
+{
+    if (fp16) {
+        if (!absmax) return cudaErrorInvalidValue;
+        return launch_y16<true>(g, X, Y16, tw, st, forward, absmax);
+    }
+    return launch_y16<false>(g, X, Y16, tw, st, forward, nullptr);
 }
 
 cudaError_t upload_twiddles_fast() { return upload_small_twiddles_here(); }
@@ -493,7 +584,7 @@ cudaError_t upload_twiddles_fast() { return upload_small_twiddles_here(); }
     template bool x1024_ok<T>(const Geometry&, int);                                                             \
     template bool y1024_ok<T>(const Geometry&, int);                                                             \
     template cudaError_t launch_x_r2c_1024<T>(const Geometry&, const T*, const T*, T, Cx<T>::t*, const Cx<T>::t*, \
-                                              cudaStream_t);                                                     \
+                                              cudaStream_t, unsigned*);                                          \
     template cudaError_t launch_x_c2r_1024<T>(const Geometry&, const Cx<T>::t*, T*, const Cx<T>::t*, cudaStream_t); \
     template cudaError_t launch_y_1024<T>(const Geometry&, Cx<T>::t*, Cx<T>::t*, const Cx<T>::t*, cudaStream_t, bool);
 FAST_INST(float)

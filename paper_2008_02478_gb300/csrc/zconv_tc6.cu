@@ -97,6 +97,17 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
 }
+// the operand format: FP16 (H16) or BF16
+template <bool H16>
+__device__ __forceinline__ uint32_t pack16(float a, float b)
+{
+    if constexpr (H16) {
+        __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        return pack_bf16(a, b);
+    }
+}
 
 // The kernel multiply of one chunk of eight kz for accumulator row `row`
 // (kernel entry ke of the staged rows): the forward products of the three
@@ -104,7 +115,7 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b)
 // known at compile time (UP: above the ky fold, xy and yz odd in ky; NEGZ:
 // kz > 32, xz and yz odd in kz, whose kz = 32 entries vanish), BF16 products
 // to the K-major inverse operand (k = kz for Re, 64 + kz for Im).
-template <bool UP, bool NEGZ>
+template <bool UP, bool NEGZ, bool H16>
 __device__ __forceinline__ void tc6_multiply_chunk(int j, uint32_t t0, uint32_t t1, uint32_t t2,
                                                    const __half2* __restrict__ kst, int ke, unsigned char* AI, int row)
 {
@@ -143,22 +154,23 @@ __device__ __forceinline__ void tc6_multiply_chunk(int j, uint32_t t0, uint32_t 
         // row `row`, k = kz (Re) and 64 + kz (Im): one 16-byte store each
         unsigned char* arow = AI + c * AI_COMP + (row >> 3) * AI_SBO + (row & 7) * 16;
         uint4 wr, wi;
-        wr.x = pack_bf16(hr[0], hr[1]);
-        wr.y = pack_bf16(hr[2], hr[3]);
-        wr.z = pack_bf16(hr[4], hr[5]);
-        wr.w = pack_bf16(hr[6], hr[7]);
-        wi.x = pack_bf16(hi[0], hi[1]);
-        wi.y = pack_bf16(hi[2], hi[3]);
-        wi.z = pack_bf16(hi[4], hi[5]);
-        wi.w = pack_bf16(hi[6], hi[7]);
+        wr.x = pack16<H16>(hr[0], hr[1]);
+        wr.y = pack16<H16>(hr[2], hr[3]);
+        wr.z = pack16<H16>(hr[4], hr[5]);
+        wr.w = pack16<H16>(hr[6], hr[7]);
+        wi.x = pack16<H16>(hi[0], hi[1]);
+        wi.y = pack16<H16>(hi[2], hi[3]);
+        wi.z = pack16<H16>(hi[4], hi[5]);
+        wi.w = pack16<H16>(hi[6], hi[7]);
         *reinterpret_cast<uint4*>(arow + j * AI_LBO) = wr;
         *reinterpret_cast<uint4*>(arow + (8 + j) * AI_LBO) = wi;
     }
 }
 
+template <bool H16>
 __global__ void __launch_bounds__(T6, 1)
     z_conv_tc6_kernel(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap kmap, Geometry g,
-                      __nv_bfloat16* __restrict__ Y16, const float2* __restrict__ tw_g, float out_scale,
+                      unsigned short* __restrict__ Y16, const float2* __restrict__ tw_g, float out_scale,
                       int* __restrict__ status, unsigned long long limit_ns)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -182,8 +194,9 @@ __global__ void __launch_bounds__(T6, 1)
     const int nty = py / MT, ntiles = g.nkx * nty, G = gridDim.x;
     constexpr uint32_t abytes = 3 * (uint32_t)AF_COMP;
     constexpr uint32_t kbytes = (uint32_t)K_BYTES;
-    constexpr uint32_t IDESC_F = tc::idesc_f16(1, true, false, 128, 128);  // data MN-major, F K-major
-    constexpr uint32_t IDESC_I = tc::idesc_f16(1, true, false, 64, 128);   // F^T MN-major, products K-major
+    constexpr uint32_t FMT = H16 ? 0 : 1;                                    // FP16 or BF16 operands
+    constexpr uint32_t IDESC_F = tc::idesc_f16(FMT, true, false, 128, 128);  // data MN-major, F K-major
+    constexpr uint32_t IDESC_I = tc::idesc_f16(FMT, true, false, 64, 128);   // F^T MN-major, products K-major
 
     if (warp == 0) tc::alloc(tslot, TMEM6);
     // the forward DFT matrix F, once per CTA; the plan's twiddles are exp(-2 pi i e / lmax)
@@ -206,7 +219,7 @@ __global__ void __launch_bounds__(T6, 1)
                 v[h] = q == p ? cs.x : (q == 0 ? cs.y : -cs.y);
             }
             *reinterpret_cast<uint32_t*>(F + (n >> 3) * F_SBO + (k >> 3) * F_LBO + (n & 7) * 16 + (k & 7) * 2) =
-                pack_bf16(v[0], v[1]);
+                pack16<H16>(v[0], v[1]);
         }
     }
     if (tid == 0) {
@@ -349,11 +362,11 @@ __global__ void __launch_bounds__(T6, 1)
 #pragma unroll 1
                 for (int j = 2 * wp; j < 2 * wp + 2; j++) {
                     if (up) {
-                        if (nz_) tc6_multiply_chunk<true, true>(j, t0, t1, t2, kst, ke, AI, row);
-                        else tc6_multiply_chunk<true, false>(j, t0, t1, t2, kst, ke, AI, row);
+                        if (nz_) tc6_multiply_chunk<true, true, H16>(j, t0, t1, t2, kst, ke, AI, row);
+                        else tc6_multiply_chunk<true, false, H16>(j, t0, t1, t2, kst, ke, AI, row);
                     } else {
-                        if (nz_) tc6_multiply_chunk<false, true>(j, t0, t1, t2, kst, ke, AI, row);
-                        else tc6_multiply_chunk<false, false>(j, t0, t1, t2, kst, ke, AI, row);
+                        if (nz_) tc6_multiply_chunk<false, true, H16>(j, t0, t1, t2, kst, ke, AI, row);
+                        else tc6_multiply_chunk<false, false, H16>(j, t0, t1, t2, kst, ke, AI, row);
                     }
                 }
             }
@@ -389,11 +402,11 @@ __global__ void __launch_bounds__(T6, 1)
                     if (lane == 0) mbar_arrive(outb + c);
                 }
                 if (keep) {
-                    __nv_bfloat16* dst =
+                    unsigned short* dst =
                         Y16 + ((((size_t)kx * 3 + c) * 2 + part) * g.nz + z) * (size_t)py + ky0 + kyo;
                     uint32_t w[8];
 #pragma unroll
-                    for (int q = 0; q < 8; q++) w[q] = pack_bf16(v[2 * q] * out_scale, v[2 * q + 1] * out_scale);
+                    for (int q = 0; q < 8; q++) w[q] = pack16<H16>(v[2 * q] * out_scale, v[2 * q + 1] * out_scale);
                     tc::st_global_v8(dst, w);
                 }
             }
@@ -466,7 +479,7 @@ cudaError_t zconv_tc6_build_k16(const Geometry& g, const float* K, void* K16, cu
 
 // Y16 [kx][c][part][z][ky] as the 5D tensor (ky%8, z, part, ky/8, kx c), boxes of
 // (8, 32, 2, 16, 1); K16 as (ky', kz' pair, kx) of 32-bit pairs, boxes of (136, 99, 1)
-cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, void* kmap)
+cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, void* kmap, bool fp16)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return cudaErrorNotSupported;
@@ -476,7 +489,8 @@ cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, 
                                        (cuuint64_t)2 * g.nz * g.py * 2};
         const cuuint32_t box[5] = {64, (cuuint32_t)HZ6, 2, (cuuint32_t)MT / 64, 1};
         const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-        const CUresult r = enc(reinterpret_cast<CUtensorMap*>(ymap), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, Y16, dims,
+        const CUresult r = enc(reinterpret_cast<CUtensorMap*>(ymap),
+                               fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, Y16, dims,
                                strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
@@ -496,16 +510,29 @@ cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, 
 }
 
 cudaError_t launch_zconv_tc6(const void* ymap_p, const void* kmap_p, const Geometry& g, void* Y16, const float2* tw,
-                             int* status, unsigned long long limit_ns, int nsm, cudaStream_t st)
+                             int* status, unsigned long long limit_ns, int nsm, cudaStream_t st, bool fp16)
 {
     const CUtensorMap& ymap = *reinterpret_cast<const CUtensorMap*>(ymap_p);
     const CUtensorMap& kmap = *reinterpret_cast<const CUtensorMap*>(kmap_p);
-    cudaError_t e = cudaFuncSetAttribute(z_conv_tc6_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM6);
-    if (e != cudaSuccess) return e;
     const int ntiles = g.nkx * (g.py / MT);
     const int grid = std::min(ntiles, nsm);
-    const float out_scale = (float)(1.0 / ((double)g.px * g.py * g.pz));
-    z_conv_tc6_kernel<<<grid, T6, SMEM6, st>>>(ymap, kmap, g, (__nv_bfloat16*)Y16, tw, out_scale, status, limit_ns);
+    // BF16: the output carries the true scale (the kernel pairs' px py pz undone);
+    // FP16: 1/128 keeps the length-64 inverse sums of products below 2^15, and
+    // the y inverse pass divides by px py pz s / 128
+    if (fp16) {
+        cudaError_t e =
+            cudaFuncSetAttribute(z_conv_tc6_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM6);
+        if (e != cudaSuccess) return e;
+        z_conv_tc6_kernel<true><<<grid, T6, SMEM6, st>>>(ymap, kmap, g, (unsigned short*)Y16, tw, 1.f / 128.f, status,
+                                                         limit_ns);
+    } else {
+        cudaError_t e =
+            cudaFuncSetAttribute(z_conv_tc6_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM6);
+        if (e != cudaSuccess) return e;
+        const float out_scale = (float)(1.0 / ((double)g.px * g.py * g.pz));
+        z_conv_tc6_kernel<false><<<grid, T6, SMEM6, st>>>(ymap, kmap, g, (unsigned short*)Y16, tw, out_scale, status,
+                                                          limit_ns);
+    }
     return cudaGetLastError();
 }
 

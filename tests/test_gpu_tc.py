@@ -25,7 +25,8 @@ FORMS = {"tcgen05": 5, "mma.sync": 4}
 
 def tc_plan(monkeypatch, form, *args, **kw):
     """Plan with the tensor-core z stage in the given form; "tcgen05" keeps the
-    FP32 spectrum (BORIS_TC_STORE16=0), "store16" the BF16 one (BF16 plans)."""
+    FP32 spectrum (BORIS_TC_STORE16=0), "store16" the 16-bit one (BF16, or FP16
+    scaled by a power of two from max |M|)."""
     from paper_2008_02478_gb300.binding import Plan
     if form == "mma.sync":
         monkeypatch.setenv("BORIS_TC_MMASYNC", "1")
@@ -138,7 +139,7 @@ def test_large_film_tensor_core_stage_sampled_direct_sum(tc, monkeypatch):
     assert_close(H[:, f["cells"]].T, f["ref"], 1e-2)
 
 
-# meshes for the BF16-storage z stage: length-1024 y passes (257 <= ny <= 512), pz = 64
+# meshes for the 16-bit-storage z stage: length-1024 x and y passes (257 <= nx, ny <= 512), pz = 64
 STORE16 = [
     ((64, 300, 17), (4e-9, 4e-9, 4e-9)),    # ragged nz, partial 128-column tiles of ny
     ((48, 512, 32), (3e-9, 3e-9, 3e-9)),    # full z tile and full y lines
@@ -146,16 +147,18 @@ STORE16 = [
 ]
 
 
+@pytest.mark.parametrize("tc", ["fp16", "bf16"])
 @pytest.mark.parametrize("n,h", STORE16)
-def test_bf16_storage_stage_matches_oracle(n, h, monkeypatch):
-    """BF16 plans store the padded y-z spectrum in BF16 and run the tcgen05
-    z stage with the data as the 128-row operand: H_d against the FP64 oracle
-    (bound 1e-2 on both norms), twice in a row (the persistent CTAs leave no
-    state behind), with no bounded wait giving up."""
+def test_16bit_storage_stage_matches_oracle(n, h, tc, monkeypatch):
+    """Tensor-core plans store the padded y-z spectrum in 16 bits (BF16, or
+    FP16 scaled by a power of two from max |M|) and run the tcgen05 z stage
+    with the data as the 128-row operand: H_d against the FP64 oracle (bound
+    1e-2 on both norms), twice in a row (the persistent CTAs leave no state
+    behind), with no bounded wait giving up."""
     torch = torch_cuda()
     M = 8e5 * inputs.voronoi_columnar(*n, h, 20e-9, seed=5)
     ref = oracle.DemagPlan(*n, *h).apply(M)
-    plan = tc_plan(monkeypatch, "store16", *n, *h, tc="bf16")
+    plan = tc_plan(monkeypatch, "store16", *n, *h, tc=tc)
     assert plan.schedule()[2] == 6
     Md = to_dev(torch, M)
     a = plan.apply(Md).cpu().numpy()
@@ -168,21 +171,24 @@ def test_bf16_storage_stage_matches_oracle(n, h, monkeypatch):
     assert err > 10 * rel_l2(H32, ref)
 
 
-def test_bf16_storage_stage_on_large_film(monkeypatch):
-    """The 512 x 512 x 32 film with the BF16-storage stage against the
+@pytest.mark.parametrize("tc", ["fp16", "bf16"])
+def test_16bit_storage_stage_on_large_film(tc, monkeypatch):
+    """The 512 x 512 x 32 film with the 16-bit-storage stage against the
     oracle's direct sums at sampled cells."""
     torch = torch_cuda()
     f = _large_film_reference()
-    plan = tc_plan(monkeypatch, "store16", *f["n"], *f["cell"], tc="bf16")
+    plan = tc_plan(monkeypatch, "store16", *f["n"], *f["cell"], tc=tc)
     assert plan.schedule()[2] == 6
     H = plan.apply(to_dev(torch, f["M"])).cpu().numpy().reshape(3, -1)
     assert plan.sync_status() == 0
     assert_close(H[:, f["cells"]].T, f["ref"], 1e-2)
 
 
-def test_bf16_storage_rk4_step_matches_oracle(monkeypatch):
-    """One RK4 step of a BF16-storage plan (four evaluations through the new
-    stage) against the FP64 oracle: the change of m within 1e-2."""
+@pytest.mark.parametrize("tc", ["fp16", "bf16"])
+def test_16bit_storage_rk4_step_matches_oracle(tc, monkeypatch):
+    """One RK4 step of a 16-bit-storage plan (four evaluations through the
+    stage, the FP16 scale taken from Ms m) against the FP64 oracle: the change
+    of m within 1e-2."""
     torch = torch_cuda()
     from oracle import llg
     from paper_2008_02478_gb300.binding import LLGParams
@@ -190,7 +196,26 @@ def test_bf16_storage_rk4_step_matches_oracle(monkeypatch):
     m0 = inputs.voronoi_columnar(*n, h, 20e-9, seed=6)
     prm = llg.Params(cell=h, Ms=8e5, A=1.3e-11, alpha=0.02, Hext=(0.0, 0.0, 8e4))
     ref = llg.rk4_step(m0, 1e-13, prm, oracle.DemagPlan(*n, *h).apply)
-    plan = tc_plan(monkeypatch, "store16", *n, *h, tc="bf16")
+    plan = tc_plan(monkeypatch, "store16", *n, *h, tc=tc)
     m = to_dev(torch, m0)
     plan.llg_step(m, LLGParams(Ms=8e5, A=1.3e-11, alpha=0.02, Hext=(0.0, 0.0, 8e4)), 1e-13)
     assert_close(m.cpu().numpy() - m0, ref - m0, 1e-2)
+
+
+@pytest.mark.parametrize("scale", [1e-6, 1.0, 1e7])
+def test_fp16_storage_scale_follows_the_magnetisation(scale, monkeypatch):
+    """The FP16 spectrum's power-of-two scale comes from max |M| of each
+    evaluation: magnetisations 1e-6, 1 and 1e7 times the film's give fields
+    scaled alike, each within the FP16 bound of the oracle (no overflow of
+    the large one, no underflow of the small one), and an FP16 error below
+    the BF16 one."""
+    torch = torch_cuda()
+    n, h = (64, 300, 17), (4e-9, 4e-9, 4e-9)
+    M = 8e5 * scale * inputs.voronoi_columnar(*n, h, 20e-9, seed=8)
+    ref = oracle.DemagPlan(*n, *h).apply(M)
+    H16 = tc_plan(monkeypatch, "store16", *n, *h, tc="fp16").apply(to_dev(torch, M)).cpu().numpy()
+    Hb = tc_plan(monkeypatch, "store16", *n, *h, tc="bf16").apply(to_dev(torch, M)).cpu().numpy()
+    assert np.isfinite(H16).all()
+    e16, _ = assert_close(H16, ref, 1e-3)
+    eb, _ = assert_close(Hb, ref, 1e-2)
+    assert e16 < eb
