@@ -58,9 +58,15 @@ typedef enum {
  * component) column, FP32 accumulation; everything else stays FP32.  Where
  * py >= 64 the products are tcgen05.mma with accumulators in tensor memory
  * (power-of-two column scales); otherwise, or with BORIS_TC_MMASYNC=1 at plan
- * creation, mma.sync with the exact column maxima as scales.  The paper has
- * FP32/FP64 only; expected relative L2 error of H_d ~1e-4 (FP16) to ~1e-3
- * (BF16). */
+ * creation, mma.sync with the exact column maxima as scales.  Where in
+ * addition py = 1024 (257 <= ny <= 512), the
+ * padded y-z spectrum itself is stored in the 16-bit format between the y and
+ * z passes (BF16 as it is; FP16 scaled by the power of two s with
+ * s nx ny nz max|Ms M| < 2^14, max|Ms M| found on the device each evaluation)
+ * and the tcgen05 z stage takes 128 ky columns as the rows of its products
+ * (BORIS_TC_STORE16=0 at plan creation keeps the FP32 spectrum).  The paper
+ * has FP32/FP64 only; expected relative L2 error of H_d ~2e-4 (FP16) to
+ * ~2e-3 (BF16). */
 #define BORIS_FLAG_FP16_TC 0x2u
 #define BORIS_FLAG_BF16_TC 0x4u
 
@@ -406,8 +412,8 @@ int boris_plan_padded(boris_plan p, int out[3]);
  * fitted to, out[2] the z-convolution variant: 1 or 2 for the persistent
  * bulk-copy (TMA) pipeline with one or two tile stages, 3 for the residue-
  * split z convolution, 0 for the shared-memory form; on tensor-core plans 5
- * for the tcgen05 stage, 4 for the mma.sync one and 6 for the BF16 plan whose
- * y passes store the spectrum in BF16 and whose tcgen05 z stage takes the
+ * for the tcgen05 stage, 4 for the mma.sync one and 6 for the plans whose
+ * y passes store the spectrum in 16 bits and whose tcgen05 z stage takes the
  * data as the 128-row operand (BORIS_TC_STORE16=0 at plan creation keeps
  * the FP32 spectrum and variant 5).  Variants 1, 2, 3, 5 and 6 bound their
  * mbarrier waits and latch BORIS_ERR_TIMEOUT in the status word read by
