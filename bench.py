@@ -1048,7 +1048,18 @@ def main():
             pt.profile(True)
             time_steps(torch, pt, mt, prm, max(4, args.steps // 4))
             kk, _ = pt.profile_read()
+            zt = kk["z_conv"][0] / max(1, kk["z_conv"][1])
+            z_roof = None
+            if pt.schedule()[2] == 6:
+                # the 16-bit z stage's own compulsory bytes: Y16 read and written, the FP16 kernel octant
+                px_, py_, pz_ = pt.padded()
+                nkx_ = px_ // 2 + 1
+                zbytes = 2 * nkx_ * 3 * 2 * nz * py_ * 2 + nkx_ * (pz_ // 2 + 1) * 3 * (py_ // 2 + 8) * 4
+                pk, pk_src = measured_peaks()
+                z_roof = {"bytes_per_launch": zbytes, "GBps": zbytes / (zt * 1e-3) / 1e9,
+                          "frac": zbytes / (zt * 1e-3) / 1e9 / pk, "peak": pk, "peak_source": pk_src}
             mixed[tc] = {"demag_evals_per_s": world * 4 * args.steps / td,
+                         "z_stage_roofline": z_roof,
                          "cell_steps_per_s": world * ncell * args.steps / ts,
                          "ms_per_step": 1e3 * ts / args.steps,
                          "speedup_vs_fp32_step": (ncell * args.steps / ts) / (value / world),
