@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256) yz_conv_kernel(Geometry g, int Qc, typena
     if (lgL > 0) fft_dif(data, yl, lgL, 0, tw, lglmax - lgL);
 
     // ---- 3: z stage and kernel multiply, Qc columns at a time ---------------
-    const int kyh = g.kyh, kzh = g.kzh;
+    const int kyh = g.kyh;
     const T* Kx = K + (size_t)kx * kyh * g.krow;
     auto kernel_at = [&](int ky, int kz, T k[6]) {
         const bool fy = ky > py / 2, fz = kz > pz / 2;

@@ -382,13 +382,75 @@ __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z
 
 // The inter-plane sum as one persistent launch over all work items (kx,
 // 32-column tile of folded ky'), tiles of one kx consecutive.  Per item: the
-// Z planes' 32 columns and their mirrors go to shared memory; then for each
-// source plane q every warp stages, by cp.async one source ahead, the 6 x
-// 128-byte spectrum rows of its own targets p = warp + 8 j, whose offsets
-// (in 128-byte units, the kz sign in bit 31) come precomputed in pcode; the
-// 3 x 3 products run as packed FP32x2 multiply-adds on (Re, Im) pairs.
+// Z planes' 32 columns and their mirrors go to shared memory (the mirror's
+// M_y negated, see below); then for each source plane q every warp stages, by
+// cp.async one source ahead, the 6 x 128-byte spectrum rows of its own
+// targets p = warp + 8 j, whose offsets (in 128-byte units, the kz sign in
+// bit 31) come precomputed in pcode; the 3 x 3 products run as packed FP32x2
+// multiply-adds on (Re, Im) pairs.  The mirror column ky -> py - ky flips the
+// ky-odd entries xy and yz; with M_y negated in the mirror the same entries
+// give the mirror's H_x, H_z and -H_y, so both columns share one set of
+// entry pairs.  The source loop is compiled for the warp's exact target count
+// (the counts of the warps differ by at most one), so it has no per-target
+// branches.
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int NT, int PM>
+__device__ __forceinline__ void ml_v2_sum(int Z, int warp, int lane, const float* __restrict__ Kx, int kyp, float* Kw,
+                                          const float2* Ms, const unsigned* pc, float2 (&acc)[PM][2][3])
+{
+    // the NT targets' 6 rows x 8 sixteen-byte pieces of source q into buffer b
+    auto stage = [&](int q, int b) {
+        float* dstb = Kw + (size_t)b * NT * 6 * 32;
+#pragma unroll
+        for (int u = 0; u < (NT * 48 + 31) / 32; u++) {
+            const int k = lane + 32 * u;
+            if ((NT * 48) % 32 == 0 || k < NT * 48) {
+                const int j = k / 48, rr = k - 48 * j, c6 = rr >> 3, part = rr & 7;
+                const unsigned off = pc[(warp + 8 * j) * Z + q] & 0x7fffffffu;
+                cp_async16(dstb + (j * 6 + c6) * 32 + part * 4, Kx + (size_t)off * 32 + (size_t)c6 * kyp + part * 4);
+            }
+        }
+        cp_async_commit();
+    };
+    stage(0, 0);
+    for (int q = 0; q < Z; q++) {
+        if (q + 1 < Z) {
+            stage(q + 1, (q + 1) & 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();  // every lane's copies of source q are visible to the warp
+        const float* kb = Kw + (size_t)(q & 1) * NT * 6 * 32 + lane;
+        // source columns m and i m (i times, for the imaginary xz and yz entries)
+        float2 m[2][3], im[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                m[h][c] = Ms[((q * 3 + c) * 2 + h) * 32 + lane];
+                im[h][c] = make_float2(-m[h][c].y, m[h][c].x);
+            }
+#pragma unroll
+        for (int j = 0; j < NT; j++) {
+            const float* k = kb + j * 6 * 32;
+            // the kz-odd entries change sign for a source above the target
+            const unsigned sg = pc[(warp + 8 * j) * Z + q] & 0x80000000u;
+            const float2 bxx = f2(k[0]), byy = f2(k[32]), bzz = f2(k[64]), bxy = f2(k[96]);
+            const float2 bxz = f2(__uint_as_float(__float_as_uint(k[128]) ^ sg));
+            const float2 byz = f2(__uint_as_float(__float_as_uint(k[160]) ^ sg));
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                acc[j][h][0] = ffma2(bxx, m[h][0], ffma2(bxy, m[h][1], ffma2(bxz, im[h][2], acc[j][h][0])));
+                acc[j][h][1] = ffma2(bxy, m[h][0], ffma2(byy, m[h][1], ffma2(byz, im[h][2], acc[j][h][1])));
+                acc[j][h][2] = ffma2(bxz, im[h][0], ffma2(byz, im[h][1], ffma2(bzz, m[h][2], acc[j][h][2])));
+            }
+        }
+        __syncwarp();  // buffer q & 1 is free for source q + 2
+    }
+}
 
 template <int PMAX>
 __global__ void __launch_bounds__(256, 2) ml_mix_v2_kernel(Geometry g, int Z, float2* __restrict__ Y,
@@ -406,7 +468,6 @@ __global__ void __launch_bounds__(256, 2) ml_mix_v2_kernel(Geometry g, int Z, fl
     unsigned* pc = reinterpret_cast<unsigned*>(Ms + (size_t)Z * 3 * 64);
     float* ih = reinterpret_cast<float*>(pc + (size_t)Z * Z);
     const int py = g.py;
-    const int part = lane & 7, c0 = lane >> 3;
     for (int i = threadIdx.x; i < Z * Z; i += 256) pc[i] = pcode[i];
     for (int i = threadIdx.x; i < Z; i += 256) ih[i] = inv_hz[i];
     __syncthreads();
@@ -416,28 +477,16 @@ __global__ void __launch_bounds__(256, 2) ml_mix_v2_kernel(Geometry g, int Z, fl
         const bool onA = kf <= py / 2;
         const bool onB = kf > 0 && kf < py / 2;
         float2* base = Y + (size_t)kx * 3 * Z * py;
-        const float* Kx = K + (size_t)kx * 6 * kyp + kf0 + part * 4;
-        auto stage = [&](int q, int b) {
-#pragma unroll
-            for (int j = 0; j < PMAX; j++) {
-                const int p = warp + 8 * j;
-                if (p < Z) {
-                    const float* src = Kx + (size_t)(pc[p * Z + q] & 0x7fffffffu) * 32;
-                    float* dst = Kw + ((size_t)(b * nt + j) * 6) * 32 + part * 4;
-                    cp_async16(dst + c0 * 32, src + (size_t)c0 * kyp);
-                    if (c0 < 2) cp_async16(dst + (c0 + 4) * 32, src + (size_t)(c0 + 4) * kyp);
-                }
-            }
-            cp_async_commit();
-        };
-        stage(0, 0);
+        const float* Kx = K + (size_t)kx * 6 * kyp + kf0;
         for (int i = threadIdx.x; i < 3 * Z * 64; i += 256) {
             const int col = i & 31, half = (i >> 5) & 1, line = i >> 6;  // line = c * Z + p
             const int c = line / Z, p = line - c * Z;
             const int f = kf0 + col;
             const bool ok = half ? (f > 0 && f < py / 2) : (f <= py / 2);
             const int ky = half ? py - f : f;
-            Ms[((p * 3 + c) * 2 + half) * 32 + col] = ok ? base[(size_t)line * py + ky] : make_float2(0.f, 0.f);
+            float2 v = ok ? base[(size_t)line * py + ky] : make_float2(0.f, 0.f);
+            if (half && c == 1) v = make_float2(-v.x, -v.y);  // the mirror's M_y, negated
+            Ms[((p * 3 + c) * 2 + half) * 32 + col] = v;
         }
         __syncthreads();  // the columns are in shared memory
         float2 acc[PMAX][2][3];
@@ -447,54 +496,17 @@ __global__ void __launch_bounds__(256, 2) ml_mix_v2_kernel(Geometry g, int Z, fl
             for (int h = 0; h < 2; h++)
 #pragma unroll
                 for (int c = 0; c < 3; c++) acc[j][h][c] = make_float2(0.f, 0.f);
-        for (int q = 0; q < Z; q++) {
-            if (q + 1 < Z) {
-                stage(q + 1, (q + 1) & 1);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
-            }
-            __syncwarp();  // every lane's copies of source q are visible to the warp
-            const float* kb = Kw + (size_t)(q & 1) * nt * 6 * 32 + lane;
-            // source columns m and i m (i times, for the imaginary xz and yz entries)
-            float2 m[2][3], im[2][3];
-#pragma unroll
-            for (int h = 0; h < 2; h++)
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    m[h][c] = Ms[((q * 3 + c) * 2 + h) * 32 + lane];
-                    im[h][c] = make_float2(-m[h][c].y, m[h][c].x);
-                }
-#pragma unroll
-            for (int j = 0; j < PMAX; j++) {
-                const int p = warp + 8 * j;
-                if (p < Z) {
-                    const float sz = (pc[p * Z + q] >> 31) ? -1.f : 1.f;
-                    const float* k = kb + j * 6 * 32;
-                    const float kxx = k[0], kyy = k[32], kzz = k[64], kxy = k[96];
-                    const float kxz = sz * k[128], kyz = sz * k[160];
-#pragma unroll
-                    for (int h = 0; h < 2; h++) {
-                        // the mirror column ky -> py - ky flips the ky-odd entries xy and yz
-                        const float2 bxx = f2(kxx), byy = f2(kyy), bzz = f2(kzz), bxz = f2(kxz);
-                        const float2 bxy = f2(h ? -kxy : kxy), byz = f2(h ? -kyz : kyz);
-                        acc[j][h][0] = ffma2(bxx, m[h][0], ffma2(bxy, m[h][1], ffma2(bxz, im[h][2], acc[j][h][0])));
-                        acc[j][h][1] = ffma2(bxy, m[h][0], ffma2(byy, m[h][1], ffma2(byz, im[h][2], acc[j][h][1])));
-                        acc[j][h][2] = ffma2(bxz, im[h][0], ffma2(byz, im[h][1], ffma2(bzz, m[h][2], acc[j][h][2])));
-                    }
-                }
-            }
-            __syncwarp();  // buffer q & 1 is free for source q + 2
-        }
+        if (nt == PMAX) ml_v2_sum<PMAX, PMAX>(Z, warp, lane, Kx, kyp, Kw, Ms, pc, acc);
+        else if (nt == PMAX - 1) ml_v2_sum<(PMAX > 1 ? PMAX - 1 : 0), PMAX>(Z, warp, lane, Kx, kyp, Kw, Ms, pc, acc);
 #pragma unroll
         for (int j = 0; j < PMAX; j++) {
             const int p = warp + 8 * j;
             if (p < Z) {
-                const float2 ia = f2(ih[p]);  // the spectra hold a N: divide by the target's a
+                const float ia = ih[p];  // the spectra hold a N: divide by the target's a
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    if (onA) base[(size_t)(c * Z + p) * py + kf] = __fmul2_rn(acc[j][0][c], ia);
-                    if (onB) base[(size_t)(c * Z + p) * py + (py - kf)] = __fmul2_rn(acc[j][1][c], ia);
+                    if (onA) base[(size_t)(c * Z + p) * py + kf] = __fmul2_rn(acc[j][0][c], f2(ia));
+                    if (onB) base[(size_t)(c * Z + p) * py + (py - kf)] = __fmul2_rn(acc[j][1][c], f2(c == 1 ? -ia : ia));
                 }
             }
         }
