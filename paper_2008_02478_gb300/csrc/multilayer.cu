@@ -400,17 +400,19 @@ template <int NT, int PM>
 __device__ __forceinline__ void ml_v2_sum(int Z, int warp, int lane, const float* __restrict__ Kx, int kyp, float* Kw,
                                           const float2* Ms, const unsigned* pc, float2 (&acc)[PM][2][3])
 {
-    // the NT targets' 6 rows x 8 sixteen-byte pieces of source q into buffer b
+    // the NT targets' 6 rows x 8 sixteen-byte pieces of source q into buffer b:
+    // lane (c0 = lane / 8, part = lane mod 8) copies piece part of rows c0 and,
+    // for c0 < 2, c0 + 4 of each target
+    const int part = lane & 7, c0 = lane >> 3;
+    const int so0 = c0 * kyp + part * 4, so1 = (c0 + 4) * kyp + part * 4;
+    const int do0 = c0 * 32 + part * 4, do1 = (c0 + 4) * 32 + part * 4;
     auto stage = [&](int q, int b) {
         float* dstb = Kw + (size_t)b * NT * 6 * 32;
 #pragma unroll
-        for (int u = 0; u < (NT * 48 + 31) / 32; u++) {
-            const int k = lane + 32 * u;
-            if ((NT * 48) % 32 == 0 || k < NT * 48) {
-                const int j = k / 48, rr = k - 48 * j, c6 = rr >> 3, part = rr & 7;
-                const unsigned off = pc[(warp + 8 * j) * Z + q] & 0x7fffffffu;
-                cp_async16(dstb + (j * 6 + c6) * 32 + part * 4, Kx + (size_t)off * 32 + (size_t)c6 * kyp + part * 4);
-            }
+        for (int j = 0; j < NT; j++) {
+            const float* src = Kx + (size_t)(pc[(warp + 8 * j) * Z + q] & 0x7fffffffu) * 32;
+            cp_async16(dstb + j * 6 * 32 + do0, src + so0);
+            if (c0 < 2) cp_async16(dstb + j * 6 * 32 + do1, src + so1);
         }
         cp_async_commit();
     };
