@@ -67,7 +67,14 @@ struct ResLayout {
 };
 
 constexpr int lg2c(int v) { return v <= 1 ? 0 : 1 + lg2c(v / 2); }
-constexpr int brevc(int v, int lg) { return lg == 0 ? 0 : ((v & 1) << (lg - 1)) | brevc(v >> 1, lg - 1); }
+// bit reversal of the lg low bits; a plain loop, so that an unrolled caller's
+// constant argument folds to a constant (no call, no run-time branches on it)
+__host__ __device__ __forceinline__ constexpr int brevc(int v, int lg)
+{
+    int r = 0;
+    for (int i = 0; i < lg; i++) r |= ((v >> i) & 1) << (lg - 1 - i);
+    return r;
+}
 
 __device__ __forceinline__ float2 cfma(float2 acc, float2 a, float2 w)  // acc + a w
 {
