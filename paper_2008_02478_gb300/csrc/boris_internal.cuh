@@ -118,7 +118,8 @@ size_t zconv_tc6_k16_bytes(const Geometry& g);
 cudaError_t zconv_tc6_build_k16(const Geometry& g, const float* K, void* K16, cudaStream_t st);
 cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, void* kmap, bool fp16 = false);
 cudaError_t launch_zconv_tc6(const void* ymap, const void* kmap, const Geometry& g, void* Y16, const float2* tw,
-                             int* status, unsigned long long limit_ns, int nsm, cudaStream_t st, bool fp16 = false);
+                             int* status, uint32_t extra_tx, unsigned long long limit_ns, int nsm, cudaStream_t st,
+                             bool fp16 = false);
 // Length-512 passes (meshes of 129..256 cells along the axis), two lines per
 // warp through the length-1024 warp transform (fft512.cu).
 template <typename T>

@@ -237,7 +237,7 @@ cudaError_t yz_stage(boris_plan p, const YZSchedule& sc)
         if (e == cudaSuccess)
             e = timed(p, 6, [&] {
                 return launch_zconv_tc6(p->ymap16, p->kmap16, p->g, p->Y16, (const float2*)p->tw, p->d_status,
-                                        p->wait_limit_ns, p->nsm, p->stream, h16);
+                                        p->wait_extra_tx, p->wait_limit_ns, p->nsm, p->stream, h16);
             });
         if (e == cudaSuccess)
             e = timed(p, 7, [&] {

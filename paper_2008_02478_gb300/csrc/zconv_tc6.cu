@@ -171,7 +171,7 @@ template <bool H16>
 __global__ void __launch_bounds__(T6, 1)
     z_conv_tc6_kernel(const __grid_constant__ CUtensorMap ymap, const __grid_constant__ CUtensorMap kmap, Geometry g,
                       unsigned short* __restrict__ Y16, const float2* __restrict__ tw_g, float out_scale,
-                      int* __restrict__ status, unsigned long long limit_ns)
+                      int* __restrict__ status, uint32_t extra_tx, unsigned long long limit_ns)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -237,9 +237,10 @@ __global__ void __launch_bounds__(T6, 1)
     tc::fence_after();
     const uint32_t tbase = *tslot;
 
-    auto load_a = [&](int t) {
+    // extra: bytes the first copy also waits for (a test hook that makes the wait run out)
+    auto load_a = [&](int t, uint32_t extra) {
         const int kx = t / nty, ky0 = (t - kx * nty) * MT;
-        mbar_arrive_expect_tx(fullA, abytes);
+        mbar_arrive_expect_tx(fullA, abytes + extra);
         for (int c = 0; c < 3; c++) tc::tma_load_5d(AF + c * AF_COMP, &ymap, 0, 0, 0, ky0 / 64, kx * 3 + c, fullA);
     };
     // kernel rows of tile t: ky' = ky below the fold, py - ky above it (a box
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(T6, 1)
                                 tc::sdesc(F + ks * 2 * F_LBO, F_LBO, F_SBO), IDESC_F, ks > 0);
             };
             if ((int)blockIdx.x < ntiles) {
-                load_a(blockIdx.x);
+                load_a(blockIdx.x, extra_tx);
                 load_k(blockIdx.x);
                 na = nk = 1;
                 if (!tc::wait(fullA, 0, limit_ns)) {
@@ -291,7 +292,7 @@ __global__ void __launch_bounds__(T6, 1)
                     break;
                 }
                 if (more) {
-                    load_a(t + G);
+                    load_a(t + G, 0);
                     na++;
                 }
                 // the multiply is done: products in shared memory, forward regions read,
@@ -510,7 +511,8 @@ cudaError_t zconv_tc6_maps(const Geometry& g, void* Y16, void* K16, void* ymap, 
 }
 
 cudaError_t launch_zconv_tc6(const void* ymap_p, const void* kmap_p, const Geometry& g, void* Y16, const float2* tw,
-                             int* status, unsigned long long limit_ns, int nsm, cudaStream_t st, bool fp16)
+                             int* status, uint32_t extra_tx, unsigned long long limit_ns, int nsm, cudaStream_t st,
+                             bool fp16)
 {
     const CUtensorMap& ymap = *reinterpret_cast<const CUtensorMap*>(ymap_p);
     const CUtensorMap& kmap = *reinterpret_cast<const CUtensorMap*>(kmap_p);
@@ -524,14 +526,14 @@ cudaError_t launch_zconv_tc6(const void* ymap_p, const void* kmap_p, const Geome
             cudaFuncSetAttribute(z_conv_tc6_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM6);
         if (e != cudaSuccess) return e;
         z_conv_tc6_kernel<true><<<grid, T6, SMEM6, st>>>(ymap, kmap, g, (unsigned short*)Y16, tw, 1.f / 128.f, status,
-                                                         limit_ns);
+                                                         extra_tx, limit_ns);
     } else {
         cudaError_t e =
             cudaFuncSetAttribute(z_conv_tc6_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM6);
         if (e != cudaSuccess) return e;
         const float out_scale = (float)(1.0 / ((double)g.px * g.py * g.pz));
         z_conv_tc6_kernel<false><<<grid, T6, SMEM6, st>>>(ymap, kmap, g, (unsigned short*)Y16, tw, out_scale, status,
-                                                          limit_ns);
+                                                          extra_tx, limit_ns);
     }
     return cudaGetLastError();
 }

@@ -1,4 +1,5 @@
-"""Bounded device-side waits: the bulk-copy, residue-split and tcgen05 z stages wait on mbarriers
+"""Bounded device-side waits: the bulk-copy, residue-split and tcgen05 z stages (both the
+FP32-spectrum one and the 16-bit-storage one with its producer warp) wait on mbarriers
 with a time limit.  Through a test hook the first wait of every CTA expects
 16 bytes that never arrive; the kernel must give up after its limit, latch
 BORIS_ERR_TIMEOUT in the plan's status word (read by boris_sync_status) and
@@ -59,6 +60,34 @@ def test_tcgen05_stage_wait_that_runs_out(monkeypatch):
     bad.close()
     monkeypatch.delenv("BORIS_TEST_WAIT_TIMEOUT")
     good = Plan(*n, *h, tc="fp16")
+    Hd = good.apply(to_dev(torch, M))
+    good.sync_status()
+    ref = oracle.DemagPlan(*n, *h).apply(M)
+    assert_close(Hd.cpu().numpy(), ref, 1e-2)
+
+
+@pytest.mark.parametrize("tc", ["bf16", "fp16"])
+def test_16bit_storage_stage_wait_that_runs_out(tc, monkeypatch):
+    """The 16-bit-storage z stage: the producer warp's first data copy never
+    completes, so it and the sixteen compute warps (waiting for products that
+    are never issued) give up after the limit; the CTA latches the timeout,
+    lets its kernel-row copy land, frees its tensor memory and returns, and a
+    following plan is correct."""
+    torch = torch_cuda()
+    from paper_2008_02478_gb300.binding import BorisError, Plan
+    n, h = (64, 300, 17), (4e-9, 4e-9, 4e-9)
+    M = 7e5 * inputs.voronoi_columnar(*n, h, 20e-9, seed=23)
+    monkeypatch.setenv("BORIS_TEST_WAIT_TIMEOUT", "1")
+    bad = Plan(*n, *h, tc=tc)
+    assert bad.schedule()[2] == 6
+    bad.apply(to_dev(torch, M))
+    with pytest.raises(BorisError) as ei:
+        bad.sync_status()
+    assert ei.value.code == -5
+    bad.sync_status()
+    bad.close()
+    monkeypatch.delenv("BORIS_TEST_WAIT_TIMEOUT")
+    good = Plan(*n, *h, tc=tc)
     Hd = good.apply(to_dev(torch, M))
     good.sync_status()
     ref = oracle.DemagPlan(*n, *h).apply(M)
