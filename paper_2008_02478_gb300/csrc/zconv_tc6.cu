@@ -1,18 +1,22 @@
 // Mixed-precision z stage with 16-bit storage of the padded y-z spectrum: the
 // zero-padded length-64 z transform of the pipelined convolution (Section 7)
-// and its inverse as dense products on the tcgen05 tensor cores, BF16
-// operands, FP32 accumulation in tensor memory (the paper has FP32 and FP64
-// only; this is the reduced-precision variant of the split schedule).
+// and its inverse as dense products on the tcgen05 tensor cores, BF16 or
+// FP16 operands, FP32 accumulation in tensor memory (the paper has FP32 and
+// FP64 only; this is the reduced-precision variant of the split schedule).
+// BF16 spectra are stored as they are; FP16 spectra carry a power-of-two scale
+// s (chosen by the y forward pass from max |Ms M|), which the multiply and the
+// DFTs preserve, and the output is multiplied by 1/128 instead of 1/(px py pz)
+// (the y inverse pass undoes both).
 //
 // Layout of the 16-bit spectrum Y16 (written by the y forward pass, read by
 // the y inverse): [kx][c][part][z][ky], part 0 = Re, 1 = Im, each (part, z)
 // line of a kx plane py consecutive values.  A 5D tensor-copy view of it -
-// (ky mod 8, z, part, ky / 8, (kx, c)) with the ky / 8 dimension at a stride of
-// 16 bytes, boxes of (8, 32, 2, 16, 1) - lands in shared memory as the
-// no-swizzle MN-major operand of a 128-row product: element (m = ky in the
-// tile, k = 32 part + z) at (m / 8) 1024 + (k / 8) 128 + (k % 8) 16 + (m % 8) 2.
-// z >= nz is filled with zeros by the copy (the zero padding of the z
-// transform).
+// (ky mod 64, z, part, ky / 64, (kx, c)) with the ky / 64 dimension at a stride
+// of 128 bytes, boxes of (64, 32, 2, 2, 1), the 128-byte swizzle - lands in
+// shared memory as the MN-major operand of a 128-row product: element (m = ky
+// in the tile, k = 32 part + z) in the 128-byte row (m / 64) 64 + k at byte
+// 2 (m mod 64), its 16-byte chunk index XOR-ed with k mod 8.  z >= nz is
+// filled with zeros by the copy (the zero padding of the z transform).
 //
 // A tile is 128 ky columns of one kx plane.  Per component c:
 //   forward  D_c (128 x 128) = A_c (128 x 64) . F (64 x 128): the data are the
@@ -28,7 +32,7 @@
 //            row m of the result lands in tensor-memory lane 32 (m / 16) +
 //            m mod 16), the products H_c the K-major B operand (rows = ky
 //            columns); the rows (part, z < nz) are read back by half-warp
-//            loads (16 lanes, two column runs) and stored as 16-byte pieces
+//            loads (16 lanes, two column runs) and stored as 32-byte pieces
 // The kernel spectrum arrives as FP16 pairs (xx, yy), (zz, xy), (xz, yz) of
 // the octant scaled by px py pz (the fold of the normalisation is undone on
 // the output).  Everything runs in one persistent CTA per SM: sixteen compute
