@@ -181,7 +181,9 @@ __global__ void __launch_bounds__(256, 3) x_c2r_1024_tma_kernel(const __grid_con
                                                                  unsigned long long limit_ns)
 {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned to 1024 bytes by an offset from the shared array itself, so that the
+    // compiler keeps every access derived from base in the shared state space
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     float2* S = reinterpret_cast<float2*>(base);               // rows kx < 512, swizzled
     float2* R512 = reinterpret_cast<float2*>(base + 512 * 128);  // row kx = 512
     float2* tws = reinterpret_cast<float2*>(base + 512 * 128 + 128);

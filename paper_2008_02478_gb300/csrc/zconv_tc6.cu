@@ -178,7 +178,9 @@ __global__ void __launch_bounds__(T6, 1)
                       int* __restrict__ status, uint32_t extra_tx, unsigned long long limit_ns)
 {
     extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    // aligned to 1024 bytes by an offset from the shared array itself, so that the
+    // compiler keeps every access derived from base in the shared state space
+    unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     unsigned char* F = base + OFF_F;
     unsigned char* AF = base + OFF_AF;
     unsigned char* AI = base + OFF_AI;
