@@ -219,3 +219,31 @@ def test_fp16_storage_scale_follows_the_magnetisation(scale, monkeypatch):
     e16, _ = assert_close(H16, ref, 1e-3)
     eb, _ = assert_close(Hb, ref, 1e-2)
     assert e16 < eb
+
+
+@pytest.mark.parametrize("n,h", [((64, 300, 17), (4e-9, 4e-9, 4e-9)),     # x length 128: separate maximum
+                                 ((300, 260, 20), (4e-9, 4e-9, 4e-9))])   # x length 1024: maximum in the x pass
+def test_fp16_storage_rk4_step_with_ms_map(n, h, monkeypatch):
+    """An FP16-storage plan stepping a film whose Ms map spans 1e4 to 1e6 A/m:
+    the spectrum's scale comes from max |Ms m| over the map (found by the x
+    pass, or by the separate reduction where the x pass is not the
+    length-1024 one); one RK4 step against the FP64 oracle, the change of m
+    within 1e-2."""
+    torch = torch_cuda()
+    from oracle import llg
+    from paper_2008_02478_gb300.binding import LLGParams
+    # (down to 1e3 A/m the exchange field of the weakest cells turns m by order 1
+    # in one 0.1 ps step, where the step itself, not the demag field, sets the
+    # FP32 / FP64 difference)
+    Ms = inputs.smooth_noise(*n, 3.0, 1e4, 1e6, 31)
+    m0 = inputs.voronoi_columnar(*n, h, 20e-9, seed=32)
+    prm = llg.Params(cell=h, Ms=Ms, A=1.3e-11, alpha=0.02, Hext=(0.0, 0.0, 8e4))
+    ref = llg.rk4_step(m0, 1e-13, prm, oracle.DemagPlan(*n, *h).apply)
+    plan = tc_plan(monkeypatch, "store16", *n, *h, tc="fp16")
+    assert plan.schedule()[2] == 6
+    m = to_dev(torch, m0)
+    gp = LLGParams(A=prm.A, alpha=prm.alpha, Hext=prm.Hext)
+    gp.Ms_map = to_dev(torch, Ms)
+    plan.llg_step(m, gp, 1e-13)
+    assert plan.sync_status() == 0
+    assert_close(m.cpu().numpy() - m0, ref - m0, 1e-2)
