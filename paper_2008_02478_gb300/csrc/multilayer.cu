@@ -406,20 +406,25 @@ __device__ __forceinline__ void ml_v2_sum(int Z, int warp, int lane, const float
     const int part = lane & 7, c0 = lane >> 3;
     const int so0 = c0 * kyp + part * 4, so1 = (c0 + 4) * kyp + part * 4;
     const int do0 = c0 * 32 + part * 4, do1 = (c0 + 4) * 32 + part * 4;
-    auto stage = [&](int q, int b) {
+    // the kz signs of the staged source: bit j = bit 31 of target j's code
+    unsigned sgm = 0, sgm_next = 0;
+    auto stage = [&](int q, int b, unsigned& sgbits) {
         float* dstb = Kw + (size_t)b * NT * 6 * 32;
+        sgbits = 0;
 #pragma unroll
         for (int j = 0; j < NT; j++) {
-            const float* src = Kx + (size_t)(pc[(warp + 8 * j) * Z + q] & 0x7fffffffu) * 32;
+            const unsigned code = pc[(warp + 8 * j) * Z + q];
+            sgbits |= (code >> 31) << j;
+            const float* src = Kx + (size_t)(code & 0x7fffffffu) * 32;
             cp_async16(dstb + j * 6 * 32 + do0, src + so0);
             if (c0 < 2) cp_async16(dstb + j * 6 * 32 + do1, src + so1);
         }
         cp_async_commit();
     };
-    stage(0, 0);
+    stage(0, 0, sgm);
     for (int q = 0; q < Z; q++) {
         if (q + 1 < Z) {
-            stage(q + 1, (q + 1) & 1);
+            stage(q + 1, (q + 1) & 1, sgm_next);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -439,7 +444,7 @@ __device__ __forceinline__ void ml_v2_sum(int Z, int warp, int lane, const float
         for (int j = 0; j < NT; j++) {
             const float* k = kb + j * 6 * 32;
             // the kz-odd entries change sign for a source above the target
-            const unsigned sg = pc[(warp + 8 * j) * Z + q] & 0x80000000u;
+            const unsigned sg = ((sgm >> j) & 1u) << 31;
             const float2 bxx = f2(k[0]), byy = f2(k[32]), bzz = f2(k[64]), bxy = f2(k[96]);
             const float2 bxz = f2(__uint_as_float(__float_as_uint(k[128]) ^ sg));
             const float2 byz = f2(__uint_as_float(__float_as_uint(k[160]) ^ sg));
@@ -451,6 +456,7 @@ __device__ __forceinline__ void ml_v2_sum(int Z, int warp, int lane, const float
             }
         }
         __syncwarp();  // buffer q & 1 is free for source q + 2
+        sgm = sgm_next;
     }
 }
 
