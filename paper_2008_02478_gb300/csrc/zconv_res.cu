@@ -106,6 +106,44 @@ __device__ __forceinline__ void recombine(const float2 (&v)[L], float2* scr, flo
     __syncthreads();
 }
 
+// The 3 x 3 demagnetising multiply of one thread's L accumulator positions
+// (kz = 4 brev(pos) + r): kernel row kz' = kz up to the z Nyquist index HZ,
+// else P - kz with xz and yz negated; FY (the tile lies above the ky fold)
+// negates xy and yz.  Both signs are compile-time constants here, and the
+// products of the real entries with the complex components run as packed
+// FP32x2 multiply-adds.
+template <int L, int LGL, int HZ, int NP, bool FY>
+__device__ __forceinline__ void res_multiply(float2 (&v0)[L], float2 (&v1)[L], float2 (&v2)[L], const float2* Kup,
+                                             const float2* Kdn, int r)
+{
+    constexpr int P = 2 * HZ;
+#pragma unroll
+    for (int pos = 0; pos < L; pos++) {
+        const int j = brevc(pos, LGL);
+        const float2* kp;
+        float sz;
+        if (4 * j < HZ) {
+            kp = Kup + 4 * j * NP * KBW;
+            sz = 1.f;
+        } else if (4 * j > HZ) {
+            kp = Kdn + (P - 4 * j) * NP * KBW;
+            sz = -1.f;
+        } else {
+            kp = Kdn + HZ * NP * KBW;  // kz = HZ + r: the Nyquist row for r = 0
+            sz = r == 0 ? 1.f : -1.f;
+        }
+        const float2 m0 = v0[pos], m1 = v1[pos], m2 = v2[pos];
+        const float2 p0 = kp[0], p1 = kp[KBW], p2 = kp[2 * KBW];
+        const float sy = FY ? -1.f : 1.f;
+        const float2 xx = make_float2(p0.x, p0.x), yy = make_float2(p0.y, p0.y), zz = make_float2(p1.x, p1.x);
+        const float xys = p1.y * sy, xzs = p2.x * sz, yzs = p2.y * (sy * sz);
+        const float2 xy = make_float2(xys, xys), xz = make_float2(xzs, xzs), yz = make_float2(yzs, yzs);
+        v0[pos] = __ffma2_rn(xz, m2, __ffma2_rn(xy, m1, __fmul2_rn(xx, m0)));
+        v1[pos] = __ffma2_rn(yz, m2, __ffma2_rn(yy, m1, __fmul2_rn(xy, m0)));
+        v2[pos] = __ffma2_rn(zz, m2, __ffma2_rn(yz, m1, __fmul2_rn(xz, m0)));
+    }
+}
+
 // FULL: nz == HZ (no cropped rows: no predicates on the loads and stores).
 // CURL: the Oersted multiply H^ = i (J^ x G) instead of the symmetric 3 x 3
 // demagnetising multiply.
@@ -222,27 +260,30 @@ __global__ void __launch_bounds__(RTHREADS, MINB)
         // ky beyond py / 2 reads ky' = py - ky with xy and yz negated.
         {
             const bool fy = ky0 >= py / 2;
-            const float sy = fy ? -1.f : 1.f;
             const float2* Kc = kst + (fy ? 32 - col : col);
             const float2* Kup = Kc + r * NP * KBW;  // rows 4 j + r
             const float2* Kdn = Kc - r * NP * KBW;  // rows P - 4 j - r
+            if (!CURL) {
+                if (fy) res_multiply<L, LGL, HZ, NP, true>(v0, v1, v2, Kup, Kdn, r);
+                else res_multiply<L, LGL, HZ, NP, false>(v0, v1, v2, Kup, Kdn, r);
+            } else {
+                const float sy = fy ? -1.f : 1.f;
 #pragma unroll
-            for (int pos = 0; pos < L; pos++) {
-                const int j = brevc(pos, LGL);
-                const float2* kp;
-                float sz;
-                if (4 * j < HZ) {
-                    kp = Kup + 4 * j * NP * KBW;
-                    sz = 1.f;
-                } else if (4 * j > HZ) {
-                    kp = Kdn + (P - 4 * j) * NP * KBW;
-                    sz = -1.f;
-                } else {
-                    kp = Kdn + HZ * NP * KBW;  // kz = HZ + r: the Nyquist row for r = 0
-                    sz = r == 0 ? 1.f : -1.f;
-                }
-                const float2 m0 = v0[pos], m1 = v1[pos], m2 = v2[pos];
-                if (CURL) {
+                for (int pos = 0; pos < L; pos++) {
+                    const int j = brevc(pos, LGL);
+                    const float2* kp;
+                    float sz;
+                    if (4 * j < HZ) {
+                        kp = Kup + 4 * j * NP * KBW;
+                        sz = 1.f;
+                    } else if (4 * j > HZ) {
+                        kp = Kdn + (P - 4 * j) * NP * KBW;
+                        sz = -1.f;
+                    } else {
+                        kp = Kdn + HZ * NP * KBW;  // kz = HZ + r: the Nyquist row for r = 0
+                        sz = r == 0 ? 1.f : -1.f;
+                    }
+                    const float2 m0 = v0[pos], m1 = v1[pos], m2 = v2[pos];
                     // Gx odd in kx only, Gy odd in ky, Gz odd in kz; H^ = i (J^ x G)
                     const float2 p0 = kp[0], p1 = kp[KBW];
                     const float gx = p0.x, gy = p0.y * sy, gz = p1.x * sz;
@@ -252,13 +293,6 @@ __global__ void __launch_bounds__(RTHREADS, MINB)
                     v0[pos] = float2{-c0.y, c0.x};
                     v1[pos] = float2{-c1.y, c1.x};
                     v2[pos] = float2{-c2.y, c2.x};
-                } else {
-                    const float2 p0 = kp[0], p1 = kp[KBW], p2 = kp[2 * KBW];
-                    const float xx = p0.x, yy = p0.y, zz = p1.x;
-                    const float xy = p1.y * sy, xz = p2.x * sz, yz = p2.y * (sy * sz);
-                    v0[pos] = float2{xx * m0.x + xy * m1.x + xz * m2.x, xx * m0.y + xy * m1.y + xz * m2.y};
-                    v1[pos] = float2{xy * m0.x + yy * m1.x + yz * m2.x, xy * m0.y + yy * m1.y + yz * m2.y};
-                    v2[pos] = float2{xz * m0.x + yz * m1.x + zz * m2.x, xz * m0.y + yz * m1.y + zz * m2.y};
                 }
             }
         }
