@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "boris_internal.cuh"
+#include "bulk_async.cuh"
 #include "multilayer.cuh"
 #include "newell_fg.cuh"
 
@@ -261,14 +262,6 @@ __global__ void __launch_bounds__(256) ml_mix_kernel(Geometry g, int Z, float2* 
 // spectra (the CTA's 32 columns) into its shared-memory buffer by cp.async
 // one source ahead (two buffers), so the loads overlap the previous source's
 // arithmetic and only warp-level synchronisation is needed (Z <= 64).
-__device__ __forceinline__ void cp_async16(void* dst, const void* src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <int PMAX>
 __global__ void __launch_bounds__(256, 2) ml_mix_staged_kernel(Geometry g, int Z, float2* __restrict__ Y,

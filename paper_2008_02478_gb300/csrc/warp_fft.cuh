@@ -43,8 +43,10 @@ __device__ __forceinline__ void load_tw1024_slots(C* tws, const C* __restrict__ 
 }
 
 // Forward.  In: v[a] = x[32 a + lane].  Out: v[pos] = X[lane + 32 brev5(pos)].
+// In two parts: _a ends with the transpose (the tile is free again on return),
+// _b is the second register transform.
 template <typename C>
-__device__ __forceinline__ void warp_fft1024_fwd(C (&v)[32], C* tile, const C* tws)
+__device__ __forceinline__ void warp_fft1024_fwd_a(C (&v)[32], C* tile, const C* tws)
 {
     const int lane = threadIdx.x & 31;
     reg_fft<32, -1>(v);
@@ -58,13 +60,24 @@ __device__ __forceinline__ void warp_fft1024_fwd(C (&v)[32], C* tile, const C* t
 #pragma unroll
     for (int b = 0; b < 32; b++) v[b] = tile[lane * 32 + (b ^ lane)];  // row lane, column b
     __syncwarp();
+}
+template <typename C>
+__device__ __forceinline__ void warp_fft1024_fwd_b(C (&v)[32])
+{
     reg_fft<32, -1>(v);
+}
+template <typename C>
+__device__ __forceinline__ void warp_fft1024_fwd(C (&v)[32], C* tile, const C* tws)
+{
+    warp_fft1024_fwd_a(v, tile, tws);
+    warp_fft1024_fwd_b(v);
 }
 
 // Inverse (unscaled).  In: v[brev5(d)] = Z[lane + 32 d].  Out: v[a] = z[32 a + lane].
-// ROWTAB: tws holds the row table, else the slot table.
+// ROWTAB: tws holds the row table, else the slot table.  Split like the
+// forward transform (_a ends with the transpose).
 template <typename C, bool ROWTAB = true>
-__device__ __forceinline__ void warp_fft1024_inv(C (&v)[32], C* tile, const C* tws)
+__device__ __forceinline__ void warp_fft1024_inv_a(C (&v)[32], C* tile, const C* tws)
 {
     const int lane = threadIdx.x & 31;
     reg_fft<32, 1>(v);  // v[b] = sum_d Z[lane + 32 d] w_32^(-b d)
@@ -77,7 +90,17 @@ __device__ __forceinline__ void warp_fft1024_inv(C (&v)[32], C* tile, const C* t
 #pragma unroll
     for (int c = 0; c < 32; c++) v[brev5(c)] = tile[lane * 32 + (c ^ lane)];  // row b = lane, column c
     __syncwarp();
+}
+template <typename C>
+__device__ __forceinline__ void warp_fft1024_inv_b(C (&v)[32])
+{
     reg_fft<32, 1>(v);
+}
+template <typename C, bool ROWTAB = true>
+__device__ __forceinline__ void warp_fft1024_inv(C (&v)[32], C* tile, const C* tws)
+{
+    warp_fft1024_inv_a<C, ROWTAB>(v, tile, tws);
+    warp_fft1024_inv_b(v);
 }
 
 }  // namespace boris

@@ -26,6 +26,7 @@ CASES = [
     ((256, 64, 1), (1.953125e-9, 1.953125e-9, 3e-9)),  # SP4-shaped film
     ((300, 280, 3), (3e-9, 3e-9, 3e-9)),    # length-1024 x and y transforms, ragged rows
     ((512, 300, 2), (4e-9, 4e-9, 4e-9)),    # full 512-cell rows
+    ((40, 301, 3), (3e-9, 3e-9, 3e-9)),     # odd ny on the length-1024 y passes (one line per warp)
     ((280, 30, 3), (3e-9, 2e-9, 2e-9)),     # length-1024 x pass, ragged 16-row blocks
     ((300, 17, 2), (3e-9, 3e-9, 3e-9)),     # odd ny: the x inverse pass without tensor copies
     ((600, 21, 2), (3e-9, 3e-9, 3e-9)),     # length-2048 x passes, ragged 8-row blocks

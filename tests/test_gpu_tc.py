@@ -144,6 +144,7 @@ STORE16 = [
     ((64, 300, 17), (4e-9, 4e-9, 4e-9)),    # ragged nz, partial 128-column tiles of ny
     ((48, 512, 32), (3e-9, 3e-9, 3e-9)),    # full z tile and full y lines
     ((130, 400, 24), (3e-9, 2e-9, 3e-9)),   # anisotropic cells, odd nx
+    ((40, 301, 20), (3e-9, 3e-9, 3e-9)),    # odd ny: the one-line-per-warp y passes
 ]
 
 
@@ -169,6 +170,26 @@ def test_16bit_storage_stage_matches_oracle(n, h, tc, monkeypatch):
     # it is the reduced-precision path, not an FP32 one
     H32 = __import__("paper_2008_02478_gb300.binding", fromlist=["Plan"]).Plan(*n, *h).apply(Md).cpu().numpy()
     assert err > 10 * rel_l2(H32, ref)
+
+
+@pytest.mark.parametrize("tc", ["bf16", "fp16"])
+def test_persistent_y_passes_match_one_line_per_warp(tc, monkeypatch):
+    """The persistent 16-bit y passes (each warp walks many lines and stages
+    the next line's input by asynchronous copies while it transforms the
+    current one) give bit for bit the results of the one-line-per-warp grid:
+    the same arithmetic in the same order."""
+    torch = torch_cuda()
+    n, h = (72, 400, 20), (3e-9, 3e-9, 3e-9)
+    Md = to_dev(torch, 8e5 * inputs.voronoi_columnar(*n, h, 20e-9, seed=8))
+    out = []
+    for yp in ("0", "1"):
+        monkeypatch.setenv("BORIS_Y_PERSIST", yp)
+        plan = tc_plan(monkeypatch, "store16", *n, *h, tc=tc)
+        assert plan.schedule()[2] == 6
+        out.append(plan.apply(Md).cpu().numpy())
+        assert plan.sync_status() == 0
+        plan.close()
+    assert np.array_equal(out[0], out[1])
 
 
 @pytest.mark.parametrize("tc", ["fp16", "bf16"])
