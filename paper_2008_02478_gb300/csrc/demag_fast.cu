@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) x_r2c_1024_kernel
 #pragma unroll
     for (int a = 16; a < 32; a++) v[a] = C{T(0), T(0)};
     C* mine = reg + warp * REG1025;
-    warp_fft1024_fwd(v, mine, tws);
+    warp_fft1024_fwd<C, true>(v, mine, tws);
 #pragma unroll
     for (int pos = 0; pos < 32; pos++) mine[lane + 32 * brev5(pos)] = v[pos];
     __syncthreads();
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) y_fwd_1024_kernel
         const int y = 32 * a + lane;
         v[a] = (a < 16 && y < ny) ? src[y] : C{T(0), T(0)};
     }
-    warp_fft1024_fwd(v, reg + warp * REG1025, tws);
+    warp_fft1024_fwd<C, true>(v, reg + warp * REG1025, tws);
     C* dst = Y + ((size_t)kx * lines + line) * 1024;
 #pragma unroll
     for (int pos = 0; pos < 32; pos++) dst[lane + 32 * brev5(pos)] = v[pos];
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(256, 3) y_fwd_1024_b16_kernel(Geometry g, cons
         const int y = 32 * a + lane;
         v[a] = (a < 16 && y < ny) ? src[y] : float2{0.f, 0.f};
     }
-    warp_fft1024_fwd(v, reg + warp * REG1025, tws);
+    warp_fft1024_fwd<float2, true>(v, reg + warp * REG1025, tws);
     float s = 1.f;
     if constexpr (H16) {
         int e;
@@ -481,8 +481,9 @@ __global__ void __launch_bounds__(256) y_inv_1024_b16_kernel(Geometry g, const u
 // register transform and the stores of the current line.  Needs even ny
 // (16-byte line starts) and 16-byte aligned arrays.  (The FP32 passes gain
 // nothing from it: they already run at 0.82-0.85 of HBM bandwidth.)
-constexpr int REGP = 1026;  // tile stride of the persistent form: 16-byte aligned tiles, 8 x 1026 = 513 x 16
-constexpr int YP_CTAS = 3;  // resident CTAs per SM (74.4 KB of shared memory, 80 registers)
+constexpr int REGP = 1056;  // per-warp tile of the persistent form: 32 rows of 33 (16-byte aligned tiles)
+constexpr int YP_CTAS = 3;  // resident CTAs per SM (76.3 KB of shared memory, 80 registers)
+constexpr size_t YP_SMEM = ((size_t)TW1024_SLOTS + 8 * (size_t)REGP) * sizeof(float2);
 
 template <bool H16>
 __global__ void __launch_bounds__(256, YP_CTAS) y_fwd_1024_persist_kernel(Geometry g, const float2* __restrict__ X,
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(256, YP_CTAS) y_fwd_1024_persist_kernel(Geomet
             v[a] = (a < 16 && y < ny) ? tile[y] : float2{0.f, 0.f};
         }
         __syncwarp();  // the staged line is in registers: the transpose may overwrite it
-        warp_fft1024_fwd_a(v, tile, tws);
+        warp_fft1024_fwd_a<float2, true, 33>(v, tile, tws);
         if (gl + stride < total) stage(gl + stride);
         warp_fft1024_fwd_b(v);
         // v[pos] = Y[ky], ky = lane + 32 brev5(pos)
@@ -585,7 +586,7 @@ __global__ void __launch_bounds__(256, YP_CTAS) y_inv_1024_persist_kernel(Geomet
             v[brev5(d)] = H16 ? float2{a * u, b * u} : float2{a, b};
         }
         __syncwarp();
-        warp_fft1024_inv_a<float2, false>(v, tile, tws);
+        warp_fft1024_inv_a<float2, false, 33>(v, tile, tws);
         if (gl + stride < total) stage(gl + stride);
         warp_fft1024_inv_b(v);
         float2* dst = X + (size_t)gl * ny;
@@ -650,22 +651,22 @@ template <bool H16>
 static cudaError_t launch_y16_persist(const Geometry& g, float2* X, unsigned short* Y16, const float2* tw,
                                       cudaStream_t st, bool forward, const unsigned* absmax)
 {
-    int dev = 0, nsm = 0;
+    int dev = 0, nsm = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const size_t smem = smem_1024<float>();  // twiddles + 8 tiles of REGP
+    const void* fn = forward ? (const void*)y_fwd_1024_persist_kernel<H16> : (const void*)y_inv_1024_persist_kernel<H16>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)YP_SMEM);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, YP_SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // every CTA resident at once: the grid is the resident count, or fewer when there are fewer lines
     const int total = g.nkx * 3 * g.nz;
-    const int grid = (total + 7) / 8 < YP_CTAS * nsm ? (total + 7) / 8 : YP_CTAS * nsm;
-    if (forward) {
-        e = cudaFuncSetAttribute(y_fwd_1024_persist_kernel<H16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        y_fwd_1024_persist_kernel<H16><<<grid, 256, smem, st>>>(g, X, Y16, tw, absmax, total);
-    } else {
-        e = cudaFuncSetAttribute(y_inv_1024_persist_kernel<H16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        y_inv_1024_persist_kernel<H16><<<grid, 256, smem, st>>>(g, Y16, X, tw, absmax, total);
-    }
+    const int grid = (total + 7) / 8 < per_sm * nsm ? (total + 7) / 8 : per_sm * nsm;
+    if (forward)
+        y_fwd_1024_persist_kernel<H16><<<grid, 256, YP_SMEM, st>>>(g, X, Y16, tw, absmax, total);
+    else
+        y_inv_1024_persist_kernel<H16><<<grid, 256, YP_SMEM, st>>>(g, Y16, X, tw, absmax, total);
     return cudaGetLastError();
 }
 

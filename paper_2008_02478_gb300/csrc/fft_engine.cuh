@@ -223,8 +223,9 @@ __device__ __forceinline__ C twiddle128(C v, int e)
 // In-register transform of length N <= 128 (power of two), fully unrolled.
 // DIR = -1: DIF, natural order in, bit-reversed out, w = exp(-2 pi i/N).
 // DIR = +1: DIT with conjugate twiddles, bit-reversed in, natural out
-// (unscaled inverse).
-template <int N, int DIR, typename C>
+// (unscaled inverse).  ZHI (DIF only): v[N/2 .. N-1] are zero on entry, so
+// the first stage reduces to v[j + N/2] = v[j] w^j (v[j] unchanged).
+template <int N, int DIR, typename C, bool ZHI = false>
 __device__ __forceinline__ void reg_fft(C* v)
 {
     if (DIR < 0) {
@@ -234,6 +235,10 @@ __device__ __forceinline__ void reg_fft(C* v)
             for (int j = 0; j < N; j++) {
                 if ((j & half) == 0) {
                     const int e = (j & (half - 1)) * (64 / half);  // w_{2 half}^{j mod half}
+                    if (ZHI && half == N / 2) {
+                        v[j + half] = twiddle128<-1>(v[j], e);
+                        continue;
+                    }
                     const C a = v[j], b = v[j + half];
                     v[j] = c_add(a, b);
                     v[j + half] = twiddle128<-1>(c_sub(a, b), e);

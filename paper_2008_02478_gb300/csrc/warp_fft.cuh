@@ -44,21 +44,31 @@ __device__ __forceinline__ void load_tw1024_slots(C* tws, const C* __restrict__ 
 
 // Forward.  In: v[a] = x[32 a + lane].  Out: v[pos] = X[lane + 32 brev5(pos)].
 // In two parts: _a ends with the transpose (the tile is free again on return),
-// _b is the second register transform.
-template <typename C>
+// _b is the second register transform.  ZHI: x[n] = 0 for n >= 512 (the
+// zero-padded upper half; v[16..31] are then not read).  TS: the tile layout,
+// 0 = 32 x 32 with the column XOR-swizzled by the row (1024 entries), 33 =
+// rows of 33 entries (1056 entries: constant offsets, no swizzle arithmetic);
+// both keep the row writes and the column reads free of bank conflicts.
+template <int TS>
+__device__ __forceinline__ int tile_at(int row, int col)
+{
+    return TS == 33 ? row * 33 + col : row * 32 + (col ^ row);
+}
+
+template <typename C, bool ZHI = false, int TS = 0>
 __device__ __forceinline__ void warp_fft1024_fwd_a(C (&v)[32], C* tile, const C* tws)
 {
     const int lane = threadIdx.x & 31;
-    reg_fft<32, -1>(v);
+    reg_fft<32, -1, C, ZHI>(v);
 #pragma unroll
     for (int pos = 0; pos < 32; pos++) {
         const int c = brev5(pos);
         const C t = c_mul(v[pos], tws[c * 32 + lane]);
-        tile[c * 32 + (lane ^ c)] = t;  // row c, column lane
+        tile[tile_at<TS>(c, lane)] = t;  // row c, column lane
     }
     __syncwarp();
 #pragma unroll
-    for (int b = 0; b < 32; b++) v[b] = tile[lane * 32 + (b ^ lane)];  // row lane, column b
+    for (int b = 0; b < 32; b++) v[b] = tile[tile_at<TS>(lane, b)];  // row lane, column b
     __syncwarp();
 }
 template <typename C>
@@ -66,17 +76,17 @@ __device__ __forceinline__ void warp_fft1024_fwd_b(C (&v)[32])
 {
     reg_fft<32, -1>(v);
 }
-template <typename C>
+template <typename C, bool ZHI = false>
 __device__ __forceinline__ void warp_fft1024_fwd(C (&v)[32], C* tile, const C* tws)
 {
-    warp_fft1024_fwd_a(v, tile, tws);
+    warp_fft1024_fwd_a<C, ZHI>(v, tile, tws);
     warp_fft1024_fwd_b(v);
 }
 
 // Inverse (unscaled).  In: v[brev5(d)] = Z[lane + 32 d].  Out: v[a] = z[32 a + lane].
 // ROWTAB: tws holds the row table, else the slot table.  Split like the
-// forward transform (_a ends with the transpose).
-template <typename C, bool ROWTAB = true>
+// forward transform (_a ends with the transpose); TS as there.
+template <typename C, bool ROWTAB = true, int TS = 0>
 __device__ __forceinline__ void warp_fft1024_inv_a(C (&v)[32], C* tile, const C* tws)
 {
     const int lane = threadIdx.x & 31;
@@ -84,11 +94,11 @@ __device__ __forceinline__ void warp_fft1024_inv_a(C (&v)[32], C* tile, const C*
 #pragma unroll
     for (int b = 0; b < 32; b++) {
         const C t = c_mulc(v[b], ROWTAB ? tws[b * 32 + lane] : tws[tw1024_slot(lane * b)]);
-        tile[b * 32 + (lane ^ b)] = t;  // row b, column c = lane
+        tile[tile_at<TS>(b, lane)] = t;  // row b, column c = lane
     }
     __syncwarp();
 #pragma unroll
-    for (int c = 0; c < 32; c++) v[brev5(c)] = tile[lane * 32 + (c ^ lane)];  // row b = lane, column c
+    for (int c = 0; c < 32; c++) v[brev5(c)] = tile[tile_at<TS>(lane, c)];  // row b = lane, column c
     __syncwarp();
 }
 template <typename C>
