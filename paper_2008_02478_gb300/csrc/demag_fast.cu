@@ -331,7 +331,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) y_fwd_1024_kernel
 
 // y inverse, py = 1024: Y[kx][line][ky] -> X[kx][line][y], cropped to ny.
 // Its twiddles use the padded-index table layout (measured 0.105 ms against
-// 0.129 ms with the row-per-c layout at 512 x 512 x 32).
+// 0.127-0.129 ms with the row-per-c layout at 512 x 512 x 32; the persistent
+// 16-bit inverse below is the other way round).
 template <typename T>
 __global__ void __launch_bounds__(256) y_inv_1024_kernel(Geometry g, const typename Cx<T>::t* __restrict__ Y,
                                                          typename Cx<T>::t* __restrict__ X,
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(256, YP_CTAS) y_inv_1024_persist_kernel(Geomet
         cp_async_commit();
     };
     if (gl < total) stage(gl);
-    load_tw1024_slots(tws, tw_g, g.lglmax - 10);
+    load_tw1024(tws, tw_g, g.lmax);  // row table: constant offsets, no bank conflicts (0.086 -> 0.074 ms)
     __syncthreads();
     float u = 1.f;
     if constexpr (H16) {
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(256, YP_CTAS) y_inv_1024_persist_kernel(Geomet
             v[brev5(d)] = H16 ? float2{a * u, b * u} : float2{a, b};
         }
         __syncwarp();
-        warp_fft1024_inv_a<float2, false, 33>(v, tile, tws);
+        warp_fft1024_inv_a<float2, true, 33>(v, tile, tws);
         if (gl + stride < total) stage(gl + stride);
         warp_fft1024_inv_b(v);
         float2* dst = X + (size_t)gl * ny;
