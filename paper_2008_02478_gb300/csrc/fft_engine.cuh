@@ -220,42 +220,97 @@ __device__ __forceinline__ C twiddle128(C v, int e)
     return DIR < 0 ? c_mul(v, w) : c_mulc(v, w);
 }
 
-// In-register transform of length N <= 128 (power of two), fully unrolled.
-// DIR = -1: DIF, natural order in, bit-reversed out, w = exp(-2 pi i/N).
+constexpr int reg_fft_lg(int n) { return n <= 1 ? 0 : 1 + reg_fft_lg(n / 2); }
+
+// In-register transform of length N <= 128 (power of two), fully unrolled,
+// radix 4 (one radix-2 stage where log2 N is odd): a radix-4 butterfly does
+// the work of two radix-2 stages with three twiddle multiplies instead of
+// four, the fourth being the free rotation by -i (or +i).  Same output order
+// as the radix-2 form.
+// DIR = -1: DIF, natural order in, bit-reversed out, w = exp(-2 pi i/N); a
+//   block of length s = 4q maps (x0, x1, x2, x3) = v[j + {0, q, 2q, 3q}] to
+//   v[j] = a0 + a2, v[j + q] = (a0 - a2) w_s^(2j), v[j + 2q] = (a1 + a3) w_s^j,
+//   v[j + 3q] = (a1 - a3) w_s^(3j), with a0 = x0 + x2, a1 = x0 - x2,
+//   a2 = x1 + x3, a3 = -i (x1 - x3).  ZHI: v[N/2 .. N-1] are zero on entry
+//   (x2 = x3 = 0 in the first stage).
 // DIR = +1: DIT with conjugate twiddles, bit-reversed in, natural out
-// (unscaled inverse).  ZHI (DIF only): v[N/2 .. N-1] are zero on entry, so
-// the first stage reduces to v[j + N/2] = v[j] w^j (v[j] unchanged).
+//   (unscaled inverse); t0 = x0, t1 = x1 w_s^(-2j), t2 = x2 w_s^(-j),
+//   t3 = x3 w_s^(-3j) give v[j] = t0 + t1 + t2 + t3, v[j + 2q] = t0 + t1 - t2 - t3,
+//   v[j + q] = (t0 - t1) + i (t2 - t3), v[j + 3q] = (t0 - t1) - i (t2 - t3).
 template <int N, int DIR, typename C, bool ZHI = false>
 __device__ __forceinline__ void reg_fft(C* v)
 {
+    constexpr int LG = reg_fft_lg(N);
     if (DIR < 0) {
 #pragma unroll
-        for (int half = N / 2; half >= 1; half >>= 1) {
+        for (int s = N; s >= 4; s /= 4) {
+            const int q = s / 4, u = 128 / s;  // w_s^k = w_128^(k u)
+            const bool zero_hi = ZHI && s == N;
 #pragma unroll
-            for (int j = 0; j < N; j++) {
-                if ((j & half) == 0) {
-                    const int e = (j & (half - 1)) * (64 / half);  // w_{2 half}^{j mod half}
-                    if (ZHI && half == N / 2) {
-                        v[j + half] = twiddle128<-1>(v[j], e);
-                        continue;
+            for (int b = 0; b < N; b += s) {
+#pragma unroll
+                for (int j = 0; j < q; j++) {
+                    C* p = v + b + j;
+                    C a0, a1, a2, t;
+                    if (zero_hi) {
+                        a0 = p[0];
+                        a1 = p[0];
+                        a2 = p[q];
+                        t = p[q];
+                    } else {
+                        a0 = c_add(p[0], p[2 * q]);
+                        a1 = c_sub(p[0], p[2 * q]);
+                        a2 = c_add(p[q], p[3 * q]);
+                        t = c_sub(p[q], p[3 * q]);
                     }
-                    const C a = v[j], b = v[j + half];
-                    v[j] = c_add(a, b);
-                    v[j + half] = twiddle128<-1>(c_sub(a, b), e);
+                    const C a3{t.y, -t.x};  // -i t
+                    p[0] = c_add(a0, a2);
+                    p[q] = twiddle128<-1>(c_sub(a0, a2), (2 * j * u) & 127);
+                    p[2 * q] = twiddle128<-1>(c_add(a1, a3), (j * u) & 127);
+                    p[3 * q] = twiddle128<-1>(c_sub(a1, a3), (3 * j * u) & 127);
+                }
+            }
+        }
+        if (LG & 1) {
+#pragma unroll
+            for (int b = 0; b < N; b += 2) {
+                const C a = v[b];
+                if (ZHI && N == 2) {
+                    v[b + 1] = a;
+                } else {
+                    const C c = v[b + 1];
+                    v[b] = c_add(a, c);
+                    v[b + 1] = c_sub(a, c);
                 }
             }
         }
     } else {
+        if (LG & 1) {
 #pragma unroll
-        for (int half = 1; half <= N / 2; half <<= 1) {
+            for (int b = 0; b < N; b += 2) {
+                const C a = v[b], c = v[b + 1];
+                v[b] = c_add(a, c);
+                v[b + 1] = c_sub(a, c);
+            }
+        }
 #pragma unroll
-            for (int j = 0; j < N; j++) {
-                if ((j & half) == 0) {
-                    const int e = (j & (half - 1)) * (64 / half);
-                    const C a = v[j];
-                    const C b = twiddle128<1>(v[j + half], e);
-                    v[j] = c_add(a, b);
-                    v[j + half] = c_sub(a, b);
+        for (int q = (LG & 1) ? 2 : 1; 4 * q <= N; q *= 4) {
+            const int s = 4 * q, u = 128 / s;
+#pragma unroll
+            for (int b = 0; b < N; b += s) {
+#pragma unroll
+                for (int j = 0; j < q; j++) {
+                    C* p = v + b + j;
+                    const C t0 = p[0];
+                    const C t1 = twiddle128<1>(p[q], (2 * j * u) & 127);
+                    const C t2 = twiddle128<1>(p[2 * q], (j * u) & 127);
+                    const C t3 = twiddle128<1>(p[3 * q], (3 * j * u) & 127);
+                    const C A0 = c_add(t0, t1), A1 = c_sub(t0, t1), B0 = c_add(t2, t3), B1 = c_sub(t2, t3);
+                    const C iB1{-B1.y, B1.x};  // i (t2 - t3)
+                    p[0] = c_add(A0, B0);
+                    p[2 * q] = c_sub(A0, B0);
+                    p[q] = c_add(A1, iB1);
+                    p[3 * q] = c_sub(A1, iB1);
                 }
             }
         }
