@@ -47,7 +47,7 @@ TRAFFIC = {
     "z_conv/plain": (1035.0e6, "b51fe8b7759c3a7a", ["paper_2008_02478_gb300/csrc/demag_split.cu",
                                             "paper_2008_02478_gb300/csrc/fft_engine.cuh",
                                             "paper_2008_02478_gb300/csrc/twiddle128.h"]),
-    "z_conv/res": (993.0e6, "6ccb474e8bf26aa5", ["paper_2008_02478_gb300/csrc/zconv_res.cu",
+    "z_conv/res": (994.3e6, "6e0854fa9ad57272", ["paper_2008_02478_gb300/csrc/zconv_res.cu",
                                           "paper_2008_02478_gb300/csrc/bulk_async.cuh",
                                           "paper_2008_02478_gb300/csrc/fft_engine.cuh",
                                           "paper_2008_02478_gb300/csrc/twiddle128.h"]),
