@@ -301,8 +301,11 @@ cudaError_t launch_x_c2r_1024_tma(const Geometry& g, const float2* X, float* H, 
 }
 
 // y forward, py = 1024: X[kx][line][y] -> Y[kx][line][ky], one line per warp.
+// Two CTAs per SM (93 registers): 0.099 ms at 512 x 512 x 32 against 0.107 ms
+// with three (80 registers) - fewer lines in flight, and more loads in flight
+// per line; the x passes and the 16-bit y passes measured slower with two.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) y_fwd_1024_kernel(Geometry g, const typename Cx<T>::t* __restrict__ X,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) y_fwd_1024_kernel(Geometry g, const typename Cx<T>::t* __restrict__ X,
                                                          typename Cx<T>::t* __restrict__ Y,
                                                          const typename Cx<T>::t* __restrict__ tw_g)
 {
