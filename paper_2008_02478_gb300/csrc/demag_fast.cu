@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(256) y_inv_1024_b16_kernel(Geometry g, const u
 // free (right after the transpose), so that the loads overlap the second
 // register transform and the stores of the current line.  Needs even ny
 // (16-byte line starts) and 16-byte aligned arrays.  (The FP32 passes gain
-// nothing from it: they already run at 0.82-0.85 of HBM bandwidth.)
+// nothing from it: they run at 0.85-0.89 of HBM bandwidth as they are.)
 constexpr int REGP = 1056;  // per-warp tile of the persistent form: 32 rows of 33 (16-byte aligned tiles)
 constexpr int YP_CTAS = 3;  // resident CTAs per SM (76.3 KB of shared memory, 80 registers)
 constexpr size_t YP_SMEM = ((size_t)TW1024_SLOTS + 8 * (size_t)REGP) * sizeof(float2);
